@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Benchmark of the band step (Band_DFT_Col, Sec. 3 Parts 1-6) on the magnetite-shaped cell.
+
+One step = Bloch sums of S and H (Part 1), 128 generalized eigensolves (2 spins x 64 k,
+Parts 2-4), chemical potential, occupations and the density matrix (Parts 5-6), all through
+the C ABI of libnao.so.  Inputs are seeded synthetic stand-ins for the paper's magnetite
+system (n = 568 basis functions, 125 lattice images, 4x4x4 k-grid); they are generated on
+the host, copied to the GPU once, and stay resident (total working set > 8 GB, far above the
+L2 size, so no explicit L2 flush is needed).
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "k-point generalized eigensolves/s (FP64, n=568)"
+UNIT = "solves/s"
+FP64_PEAK_TFLOPS = 4 * 152 * 2.070e9 / 1e12  # 2 FP64 FMA/clk/SM x 152 SMs at 2070 MHz
+
+
+# ------------------------------------------------------------------------------ helpers
+
+def _workload_config(inp, extra=None):
+    cfg = {
+        "workload": "magnetite-shaped cell: n=568 (24 heavy x 13 + 32 light x 8 orbitals), 125 images, "
+                    "4x4x4 k, 2 spins = 128 generalized eigensolves + mu + rho per step",
+        "n": inp.n, "nk": inp.nk, "nspin": inp.nspin, "nR": inp.nR, "problems_per_step": inp.nprob,
+        "n_electrons": inp.n_electrons, "kT_Ha": inp.kT, "precision": "fp64",
+        "l2": "inputs larger than L2 (H(R)+S(R) 968 MB; working set > 8 GB), no flush needed",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def _oracle_worker(args):
+    """One (spin, k) problem of the workload through the oracle (Parts 1-4), timed."""
+    path_h, path_s, path_r, path_k, p, nk = args
+    import numpy as np
+    import oracle
+    HR = np.load(path_h, mmap_mode="r")
+    SR = np.load(path_s, mmap_mode="r")
+    R = np.load(path_r)
+    kp = np.load(path_k)
+    sg, q = divmod(p, nk)
+    t0 = time.perf_counter()
+    Hk = oracle.bloch_sum(HR[sg], R, kp[q:q + 1])[0]
+    Sk = oracle.bloch_sum(SR, R, kp[q:q + 1])[0]
+    eps, C, m, _ = oracle.generalized_eigensolve(Hk, Sk)
+    return time.perf_counter() - t0, int(m)
+
+
+class OracleSampler:
+    """Spawned process pool (created before any GPU call) running the oracle one problem per
+    core with single-threaded BLAS."""
+
+    def __init__(self, inp, cores):
+        self.tmp = tempfile.mkdtemp(prefix="nao_bench_")
+        import numpy as np
+        self.paths = []
+        for name, arr in (("HR", inp.HR), ("SR", inp.SR), ("R", inp.R), ("k", inp.kpts)):
+            pth = os.path.join(self.tmp, name + ".npy")
+            np.save(pth, arr)
+            self.paths.append(pth)
+        self.nk = inp.nk
+        self.nprob = inp.nprob
+        self.cores = cores
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"
+        self.pool = mp.get_context("spawn").Pool(cores)
+        self.next = 0
+
+    def run(self):
+        probs = [(self.next + i) % self.nprob for i in range(self.cores)]
+        self.next += self.cores
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_worker, [(*self.paths, p, self.nk) for p in probs])
+        wall = time.perf_counter() - t0
+        return len(probs), wall, max(r[0] for r in res)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        import shutil
+        shutil.rmtree(self.tmp, ignore_errors=True)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _stage_flops(stage, inp, m_mean, nocc_mean):
+    """Algorithmic FLOPs of one step for a traced stage (FP64, real-flop count)."""
+    n, ns, npb, nR, nk = inp.n, inp.nk, inp.nprob, inp.nR, inp.nk
+    m = m_mean
+    if stage == "hetrd":       # Hermitian tridiagonalization: 16/3 n^3 per matrix
+        return ns * 16.0 / 3.0 * n ** 3 + npb * 16.0 / 3.0 * m ** 3
+    if stage == "backtransform":  # Q Z with Q from n-1 complex reflectors: 8 n^2 per column
+        return ns * 8.0 * n * n * m + npb * 8.0 * m ** 3
+    if stage == "ortho_ns":    # Z (3I - Z^T Z)/2: two real n^3 GEMMs
+        return ns * 4.0 * n ** 3 + npb * 4.0 * m ** 3
+    if stage == "zgemm_HX":
+        return npb * 8.0 * n * n * m
+    if stage == "zgemm_XHY":   # lower triangle of X^H (H X)
+        return npb * 4.0 * n * m * m
+    if stage == "zgemm_XV":
+        return npb * 8.0 * n * m * m
+    if stage == "zgemm_P":     # Hermitian C f C^H over occupied bands
+        return npb * 4.0 * n * n * nocc_mean
+    if stage == "bloch_sum":   # (1 + nspin) matrices, lower triangle, complex phase x real
+        return (1 + inp.nspin) * nk * nR * 4.0 * n * (n + 1) / 2
+    if stage == "rho_phase":
+        return inp.nspin * nk * nR * 4.0 * n * n
+    return None
+
+
+def _load_traffic(stage):
+    """DRAM bytes per launch of a stage's kernel from a committed ncu summary, if the kernel
+    source has not changed since it was captured."""
+    import hashlib
+    pth = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(pth):
+        return None
+    try:
+        data = json.load(open(pth))
+        ent = data.get(stage)
+        if not ent:
+            return None
+        src = os.path.join(ROOT, "paper_1402_4247_gb300", "csrc", ent["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return ent["bytes_per_launch"] if h == ent["source_sha256_16"] else None
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------------------ arms
+
+def run_reference(args, rank, world):
+    """CPU oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    from paper_1402_4247_gb300 import synth
+    inp = synth.magnetite_cell()
+    cores = min(os.cpu_count() or 1, args.cpu_cores)
+    sampler = OracleSampler(inp, cores)
+    for _ in range(args.warmup):
+        sampler.run()
+    tot, wall = 0, 0.0
+    for _ in range(args.steps):
+        c, w, _ = sampler.run()
+        tot += c
+        wall += w
+    sampler.close()
+    value = tot / wall
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _workload_config(inp, {"sample": f"{cores} problems (one per core) per step, Parts 1-4"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{cores} of 128 (spin, k) problems per step through Parts 1-4 "
+                                   f"(Bloch sum for one k + generalized eigensolve), one per process, "
+                                   f"single-threaded BLAS"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    from paper_1402_4247_gb300 import synth
+
+    inp = synth.magnetite_cell()
+    sampler = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = min(os.cpu_count() or 1, args.cpu_cores)
+        sampler = OracleSampler(inp, cores)  # spawned before the first GPU call
+
+    import torch
+    from paper_1402_4247_gb300.nao import Context
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    ctx = Context(local_rank)
+    n, nk, nspin, nprob, nR = inp.n, inp.nk, inp.nspin, inp.nprob, inp.nR
+
+    # pinned host inputs (for the end-to-end arm) and resident device copies
+    h_in = {"HR": torch.from_numpy(inp.HR).pin_memory(), "SR": torch.from_numpy(inp.SR)[None].pin_memory(),
+            "R": torch.from_numpy(inp.R).pin_memory(), "k": torch.from_numpy(inp.kpts).pin_memory(),
+            "w": torch.from_numpy(inp.wk).pin_memory()}
+    d_in = {k_: v.to(dev) for k_, v in h_in.items()}
+    Hk = torch.empty((nspin, nk, n, n), dtype=torch.complex128, device=dev)
+    Sk = torch.empty((1, nk, n, n), dtype=torch.complex128, device=dev)
+    eps = torch.empty((nprob, n), dtype=torch.float64, device=dev)
+    C = torch.empty((nprob, n, n), dtype=torch.complex128, device=dev)
+    m = torch.empty(nprob, dtype=torch.int32, device=dev)
+    st = torch.empty(nprob, dtype=torch.int32, device=dev)
+    mu = torch.empty(1, dtype=torch.float64, device=dev)
+    eb = torch.empty(1, dtype=torch.float64, device=dev)
+    f = torch.empty((nprob, n), dtype=torch.float64, device=dev)
+    rho = torch.empty((nspin, nR, n, n), dtype=torch.float64, device=dev)
+    rst = torch.empty(1, dtype=torch.int32, device=dev)
+    smap = (torch.arange(nprob, dtype=torch.int32) % nk).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(src):
+        ctx.nao_bloch_sum(src["SR"], src["R"], src["k"], out=Sk)
+        ctx.nao_bloch_sum(src["HR"], src["R"], src["k"], out=Hk)
+        ctx.nao_gen_eig(Hk.view(nprob, n, n), Sk[0], s_of_prob=smap, out=(eps, C, m, st))
+        ctx.nao_density_matrix(src["w"], src["k"], eps, C, m, inp.n_electrons, inp.kT, src["R"], nspin,
+                               out=(mu, eb, f, rho, rst))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(d_in)
+    torch.cuda.synchronize()
+    assert int(st.abs().sum()) == 0 and int(rst[0]) == 0, "band step reported a failure status"
+
+    clocks = ClockSampler(local_rank)
+    barrier()
+    ctx.nao_profile_enable(True)
+    l0 = ctx.nao_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(d_in)
+    e1.record(stream)
+    barrier()
+    ms_total = e0.elapsed_time(e1)
+    launches = ctx.nao_launch_count() - l0
+    prof = ctx.nao_profile_read()
+    ctx.nao_profile_enable(False)
+    clk = clocks.stop()
+
+    # end to end through the public API: pinned host inputs -> device, step, results -> host
+    out_h = {"eps": torch.empty_like(eps, device="cpu").pin_memory(), "m": torch.empty_like(m, device="cpu").pin_memory(),
+             "mu": torch.empty_like(mu, device="cpu").pin_memory(), "eb": torch.empty_like(eb, device="cpu").pin_memory(),
+             "rho": torch.empty_like(rho, device="cpu").pin_memory()}
+    h2d = sum(v.numel() * v.element_size() for v in h_in.values())
+    d2h = sum(v.numel() * v.element_size() for v in out_h.values())
+    d_e2e = {k_: torch.empty_like(v) for k_, v in d_in.items()}
+    k_e2e = max(1, min(args.steps, 3))
+    barrier()
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x0.record(stream)
+    for _ in range(k_e2e):
+        for k_, v in h_in.items():
+            d_e2e[k_].copy_(v, non_blocking=True)
+        step(d_e2e)
+        out_h["eps"].copy_(eps, non_blocking=True)
+        out_h["m"].copy_(m, non_blocking=True)
+        out_h["mu"].copy_(mu, non_blocking=True)
+        out_h["eb"].copy_(eb, non_blocking=True)
+        out_h["rho"].copy_(rho, non_blocking=True)
+        stream.synchronize()
+        _ = float(out_h["mu"][0])
+    x1.record(stream)
+    barrier()
+    e2e_ms = x0.elapsed_time(x1) / k_e2e
+
+    t_max = ms_total
+    e2e_max = e2e_ms
+    if dist is not None:
+        tt = torch.tensor([ms_total, e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max, e2e_max = float(tt[0]), float(tt[1])
+
+    cpu = None
+    if sampler is not None:
+        cnt, wall, _ = sampler.run()
+        sampler.close()
+        cpu = {"value": cnt / wall, "unit": UNIT, "cores": sampler.cores, "kind": "oracle",
+               "sample": f"{cnt} of 128 (spin, k) problems through Parts 1-4 (Bloch sum for one k + "
+                         f"generalized eigensolve), one per process, single-threaded BLAS, {wall:.1f} s wall"}
+
+    if rank == 0:
+        m_mean = float(m.double().mean())
+        nocc_mean = float((f > 1e-16).sum(1).double().mean())
+        stages = {}
+        for name, (tms, calls, nl) in prof.items():
+            fl = _stage_flops(name, inp, m_mean, nocc_mean)
+            stages[name] = {"ms_per_step": tms / args.steps, "launches_per_step": nl / args.steps,
+                            "share": tms / max(sum(v[0] for v in prof.values()), 1e-9)}
+            if fl is not None:
+                stages[name]["gflop_per_step"] = fl / 1e9
+        dom = max(prof.items(), key=lambda kv: kv[1][0])
+        dname, (dms, dcalls, dl) = dom
+        fl = _stage_flops(dname, inp, m_mean, nocc_mean)
+        per_launch_ms = dms / max(dl, 1)
+        achieved = (fl * args.steps / max(dl, 1)) / (per_launch_ms * 1e-3) / 1e12 if fl else None
+        roof = {"kernel": dname, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": _load_traffic(dname),
+                "peak_source": "FP64 FMA pipe: 2 FMA/clk/SM x 152 SMs x 2070 MHz (derived; 1.20 TFLOP/s measured "
+                               "by a DFMA microbenchmark); HBM 6780 GB/s is not the bound"}
+        value = nprob * world * args.steps / (t_max * 1e-3)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _workload_config(inp, {"parallelism": "replicas" if world > 1 else "single GPU"}),
+            "roofline": roof, "stages": stages,
+            "e2e": {"value": nprob * world / (e2e_max * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
+            "status_ok": bool(int(st.abs().sum()) == 0 and int(rst[0]) == 0),
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-cores", type=int, default=16)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

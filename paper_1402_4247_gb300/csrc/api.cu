@@ -1,0 +1,374 @@
+// C ABI of the band-step library: argument checks, workspace layout and the stream-ordered
+// launch sequence of Band_DFT_Col (Sec. 3, Parts 1-6).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "nao_internal.cuh"
+
+static std::string g_init_error;
+
+int nao_fail(nao_ctx* ctx, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->last_error = buf;
+  else g_init_error = buf;
+  return code;
+}
+
+int nao_ws_reserve(nao_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return NAO_OK;
+  // Growing the arena frees the old one: wait for work that may still use it.
+  NAO_CUDA_TRY(ctx, cudaDeviceSynchronize());
+  if (ctx->ws) {
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+  }
+  size_t want = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&ctx->ws, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ws = nullptr;
+    return nao_fail(ctx, NAO_E_NOMEM, "workspace allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
+  }
+  ctx->ws_bytes = want;
+  return NAO_OK;
+}
+
+static cudaEvent_t take_event(nao_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+static void drain_pending(nao_ctx* c) {
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    cudaEventSynchronize(p.b);
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) c->stages[p.stage].ms += ms;
+    c->event_pool.push_back(p.a);
+    c->event_pool.push_back(p.b);
+  }
+  c->pending.clear();
+}
+
+NaoStage::NaoStage(nao_ctx* c, const char* name, cudaStream_t s, int nlaunch) : ctx(c), st(s) {
+  c->launches += nlaunch;
+  if (!c->profiling) return;
+  for (size_t i = 0; i < c->stages.size(); ++i)
+    if (strcmp(c->stages[i].name, name) == 0) idx = (int)i;
+  if (idx < 0) {
+    c->stages.push_back(NaoStageStat{name, 0.0, 0, 0});
+    idx = (int)c->stages.size() - 1;
+  }
+  c->stages[idx].calls += 1;
+  c->stages[idx].launches += nlaunch;
+  if (c->pending.size() > 8192) drain_pending(c);
+  a = take_event(c);
+  cudaEventRecord(a, s);
+}
+
+NaoStage::~NaoStage() {
+  if (idx < 0 || !a) return;
+  cudaEvent_t b = take_event(ctx);
+  cudaEventRecord(b, st);
+  ctx->pending.push_back(NaoPending{idx, a, b});
+}
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+inline cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+// Run one launcher inside a traced stage.
+#define NAO_STAGE(name, nl, call)              \
+  do {                                         \
+    NaoStage stage_(ctx, name, st, nl);        \
+    NAO_CUDA_TRY(ctx, call);                   \
+  } while (0)
+
+// tiny gather: m of each problem from its S, the number of C columns, and the status
+__global__ void gather_m_kernel(int nprob, const int32_t* map, const int32_t* mS, const int32_t* statS, int nb,
+                                int32_t* mP, int32_t* nbP, int32_t* statP) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nprob) return;
+  const int s = map ? map[p] : p;
+  const int m = mS[s];
+  mP[p] = m;
+  nbP[p] = m < nb ? m : nb;
+  statP[p] = statS[s];
+}
+
+__global__ void finish_status_kernel(int nprob, const int32_t* mP, const int32_t* statP, const int32_t* statH,
+                                     int32_t* m_kept, int32_t* status) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nprob) return;
+  m_kept[p] = mP[p];
+  int32_t s = statP[p];
+  if (s == 0) s = statH[p];
+  status[p] = s;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nao_init(nao_ctx** out, int device) {
+  if (!out) return nao_fail(nullptr, NAO_E_INVALID, "nao_init: out is NULL");
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || count == 0)
+    return nao_fail(nullptr, NAO_E_CUDA, "nao_init: no CUDA device (%s)", cudaGetErrorString(e));
+  if (device < 0 || device >= count) return nao_fail(nullptr, NAO_E_INVALID, "nao_init: bad device %d", device);
+  nao_ctx* c = new nao_ctx();
+  c->device = device;
+  DeviceGuard g(device);
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, device);
+  if (e != cudaSuccess) {
+    delete c;
+    return nao_fail(nullptr, NAO_E_CUDA, "nao_init: %s", cudaGetErrorString(e));
+  }
+  c->num_sms = prop.multiProcessorCount;
+  *out = c;
+  return NAO_OK;
+}
+
+void nao_destroy(nao_ctx* ctx) {
+  if (!ctx) return;
+  {
+    DeviceGuard g(ctx->device);
+    drain_pending(ctx);
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->ws) cudaFree(ctx->ws);
+  }
+  delete ctx;
+}
+
+int nao_profile_enable(nao_ctx* ctx, int on) {
+  if (!ctx) return nao_fail(nullptr, NAO_E_INVALID, "nao_profile_enable: ctx is NULL");
+  DeviceGuard g(ctx->device);
+  drain_pending(ctx);
+  ctx->stages.clear();
+  ctx->profiling = on != 0;
+  return NAO_OK;
+}
+
+int nao_profile_read(nao_ctx* ctx, int max, const char** names, double* ms, int64_t* calls, int64_t* launches) {
+  if (!ctx) return nao_fail(nullptr, NAO_E_INVALID, "nao_profile_read: ctx is NULL");
+  DeviceGuard g(ctx->device);
+  drain_pending(ctx);
+  const int n = (int)ctx->stages.size();
+  for (int i = 0; i < n && i < max; ++i) {
+    if (names) names[i] = ctx->stages[i].name;
+    if (ms) ms[i] = ctx->stages[i].ms;
+    if (calls) calls[i] = ctx->stages[i].calls;
+    if (launches) launches[i] = ctx->stages[i].launches;
+  }
+  return n;
+}
+
+int64_t nao_launch_count(const nao_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+const char* nao_last_error(const nao_ctx* ctx) { return ctx ? ctx->last_error.c_str() : g_init_error.c_str(); }
+
+size_t nao_workspace_bytes(const nao_ctx* ctx) { return ctx ? ctx->ws_bytes : 0; }
+
+int nao_bloch_sum(nao_ctx* ctx, int n, int nR, const int32_t* R, int nmat, const double* MR, int nk,
+                  const double* kpts, nao_c128* Mk, void* stream) {
+  if (!ctx) return nao_fail(nullptr, NAO_E_INVALID, "nao_bloch_sum: ctx is NULL");
+  if (n < 1 || nR < 1 || nmat < 1 || nk < 1) return nao_fail(ctx, NAO_E_INVALID, "nao_bloch_sum: sizes must be >= 1");
+  if (!R || !MR || !kpts || !Mk) return nao_fail(ctx, NAO_E_INVALID, "nao_bloch_sum: NULL array");
+  if ((size_t)8 * nR * 2 > 200 * 1024) return nao_fail(ctx, NAO_E_INVALID, "nao_bloch_sum: nR too large");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = as_stream(stream);
+  NAO_STAGE("bloch_sum", 1, launch_bloch_sum(n, nR, R, nmat, MR, nk, kpts, (z64*)Mk, st));
+  return NAO_OK;
+}
+
+int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c128* S, const int32_t* s_of_prob,
+                int nS, double s_cut, int precision, int nb, double* eps, nao_c128* C, int32_t* m_kept,
+                int32_t* status, void* stream) {
+  if (!ctx) return nao_fail(nullptr, NAO_E_INVALID, "nao_gen_eig: ctx is NULL");
+  if (n < 1 || nprob < 1) return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig: n and nprob must be >= 1");
+  if (n > 4096) return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig: n = %d above the supported 4096", n);
+  if (!H || !S || !eps || !m_kept || !status) return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig: NULL array");
+  if (precision != NAO_FP64) return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig: precision %d not available", precision);
+  if (nb < 1 || nb > n) return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig: nb must be in [1, n]");
+  if (s_of_prob && nS < 1) return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig: nS must be >= 1 with a map");
+  if (!(s_cut >= 0.0)) return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig: s_cut must be >= 0");
+  const int nSe = s_of_prob ? nS : nprob;
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = as_stream(stream);
+  const size_t nn = (size_t)n * n;
+  const int nmax = nSe > nprob ? nSe : nprob;
+
+  WsPlan P;
+  const size_t oAS = P.take<z64>(nn * nSe), oTauS = P.take<z64>((size_t)n * nSe);
+  const size_t odS = P.take<double>((size_t)n * nSe), oeS = P.take<double>((size_t)n * nSe),
+               owS = P.take<double>((size_t)n * nSe);
+  const size_t oZ = P.take<double>(nn * nmax), oZ2 = P.take<double>(nn * nmax), oG = P.take<double>(nn * nmax);
+  const size_t oScr = P.take<double>(stein_scratch_doubles(n, nmax));
+  const size_t omS = P.take<int32_t>(nSe), ostS = P.take<int32_t>(nSe);
+  const size_t oX = P.take<z64>(nn * nSe);
+  const size_t oHf = P.take<z64>(nn * nprob), oY = P.take<z64>(nn * nprob), oHp = P.take<z64>(nn * nprob),
+               oV = P.take<z64>(nn * nprob);
+  const size_t oTauH = P.take<z64>((size_t)n * nprob), odH = P.take<double>((size_t)n * nprob),
+               oeH = P.take<double>((size_t)n * nprob), owH = P.take<double>((size_t)n * nprob);
+  const size_t omP = P.take<int32_t>(nprob), onbP = P.take<int32_t>(nprob), ostP = P.take<int32_t>(nprob),
+               ostH = P.take<int32_t>(nprob);
+  int rc = nao_ws_reserve(ctx, P.off);
+  if (rc) return rc;
+  char* ws = (char*)ctx->ws;
+  z64* AS = (z64*)(ws + oAS);
+  z64* tauS = (z64*)(ws + oTauS);
+  double *dS = (double*)(ws + odS), *eS = (double*)(ws + oeS), *wS = (double*)(ws + owS);
+  double *Z = (double*)(ws + oZ), *Z2 = (double*)(ws + oZ2), *G = (double*)(ws + oG), *scr = (double*)(ws + oScr);
+  int32_t *mS = (int32_t*)(ws + omS), *stS = (int32_t*)(ws + ostS);
+  z64* X = (z64*)(ws + oX);
+  z64 *Hf = (z64*)(ws + oHf), *Y = (z64*)(ws + oY), *Hp = (z64*)(ws + oHp), *V = (z64*)(ws + oV);
+  z64* tauH = (z64*)(ws + oTauH);
+  double *dH = (double*)(ws + odH), *eH = (double*)(ws + oeH), *wH = (double*)(ws + owH);
+  int32_t *mP = (int32_t*)(ws + omP), *nbP = (int32_t*)(ws + onbP), *stP = (int32_t*)(ws + ostP),
+          *stH = (int32_t*)(ws + ostH);
+  const long long snn = (long long)nn;
+  const z64 one = zmk(1.0, 0.0), zero = zmk(0.0, 0.0);
+
+  // ---- Part 2: Eigen_HH(S) -> s, U;  X = U_m s_m^{-1/2}
+  NAO_STAGE("herm_fill", 1, launch_herm_fill(n, nSe, (const z64*)S, snn, nullptr, AS, n, snn, st));
+  NAO_STAGE("hetrd", 1, launch_hetrd(n, nSe, nullptr, AS, n, snn, dS, eS, tauS, n, st));
+  NAO_STAGE("stein", 1, launch_stein(n, nSe, nullptr, dS, eS, n, wS, Z, n, snn, scr, stS, st));
+  NAO_STAGE("misc", 1, launch_count_kept(n, nSe, wS, n, s_cut, mS, stS, st));
+  {  // one Newton-Schulz step: Z2 = Z (3I - Z^T Z)/2
+    GemmDims d{n, n, n, nullptr, nullptr, nullptr};
+    NaoStage stage_(ctx, "ortho_ns", st, 3);
+    NAO_CUDA_TRY(ctx, launch_dgemm(nSe, d, 1.0, GemmOperand{Z, snn, n, 1, 0, nullptr},
+                                   GemmOperand{Z, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, st));
+    NAO_CUDA_TRY(ctx, launch_copy_real(n, nSe, nullptr, Z, n, snn, Z2, n, snn, st));
+    NAO_CUDA_TRY(ctx, launch_dgemm(nSe, d, -0.5, GemmOperand{Z, snn, 1, n, 0, nullptr},
+                                   GemmOperand{G, snn, 1, n, 0, nullptr}, 1.5, Z2, snn, 1, n, st));
+  }
+  NAO_STAGE("backtransform", 1, launch_backtransform(n, nSe, nullptr, mS, AS, n, snn, tauS, n, Z2, n, snn, wS, 1, X, n, snn, st));
+  {
+    NaoStage stage_(ctx, "misc", st, 1);
+    gather_m_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(nprob, s_of_prob, mS, stS, nb, mP, nbP, stP);
+    NAO_CUDA_TRY(ctx, cudaGetLastError());
+  }
+
+  // ---- Part 3: H' = X^H H X
+  NAO_STAGE("herm_fill", 1, launch_herm_fill(n, nprob, (const z64*)H, snn, nullptr, Hf, n, snn, st));
+  {
+    GemmDims d{n, n, n, nullptr, mP, nullptr};  // Y = Hf X : n x m
+    NAO_STAGE("zgemm_HX", 1, launch_zgemm(nprob, d, one, GemmOperand{Hf, snn, 1, n, 0, nullptr},
+                                   GemmOperand{X, snn, 1, n, 0, s_of_prob}, zero, Y, snn, 1, n, st));
+    GemmDims d2{n, n, n, mP, mP, nullptr};  // Hp = X^H Y : m x m
+    NAO_STAGE("zgemm_XHY", 1, launch_zgemm(nprob, d2, one, GemmOperand{X, snn, n, 1, 1, s_of_prob},
+                                   GemmOperand{Y, snn, 1, n, 0, nullptr}, zero, Hp, snn, 1, n, st));
+  }
+  NAO_STAGE("misc", 1, launch_hermitize(n, nprob, mP, Hp, n, snn, st));
+
+  // ---- Part 4: Eigen_HH(H') -> eps, V;  C = X V
+  NAO_STAGE("hetrd", 1, launch_hetrd(n, nprob, mP, Hp, n, snn, dH, eH, tauH, n, st));
+  NAO_STAGE("stein", 1, launch_stein(n, nprob, mP, dH, eH, n, wH, Z, n, snn, scr, stH, st));
+  {
+    GemmDims d{n, n, n, mP, mP, mP};
+    NaoStage stage_(ctx, "ortho_ns", st, 3);
+    NAO_CUDA_TRY(ctx, launch_dgemm(nprob, d, 1.0, GemmOperand{Z, snn, n, 1, 0, nullptr},
+                                   GemmOperand{Z, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, st));
+    NAO_CUDA_TRY(ctx, launch_copy_real(n, nprob, mP, Z, n, snn, Z2, n, snn, st));
+    NAO_CUDA_TRY(ctx, launch_dgemm(nprob, d, -0.5, GemmOperand{Z, snn, 1, n, 0, nullptr},
+                                   GemmOperand{G, snn, 1, n, 0, nullptr}, 1.5, Z2, snn, 1, n, st));
+  }
+  NAO_STAGE("backtransform", 1, launch_backtransform(n, nprob, mP, nullptr, Hp, n, snn, tauH, n, Z2, n, snn, wH, 0, V, n, snn, st));
+  if (C) {
+    GemmDims d{n, nb, n, nullptr, nbP, mP};  // C = X V(:, :nb) : n x nb, row-major [n][nb]
+    NAO_STAGE("zgemm_XV", 1, launch_zgemm(nprob, d, one, GemmOperand{X, snn, 1, n, 0, s_of_prob},
+                                   GemmOperand{V, snn, 1, n, 0, nullptr}, zero, (z64*)C, (long long)n * nb, nb, 1,
+                                   st));
+    NAO_STAGE("misc", 1, launch_zero_cols(n, nprob, nb, mP, (z64*)C, st));
+  }
+  NAO_STAGE("misc", 1, launch_write_eps(n, nprob, mP, wH, n, eps, st));
+  {
+    NaoStage stage_(ctx, "misc", st, 1);
+    finish_status_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(nprob, mP, stP, stH, m_kept, status);
+    NAO_CUDA_TRY(ctx, cudaGetLastError());
+  }
+  return NAO_OK;
+}
+
+int nao_density_matrix(nao_ctx* ctx, int n, int nspin, int nk, const double* wk, const double* kpts,
+                       const double* eps, const nao_c128* C, int nb, const int32_t* m_kept, double n_electrons,
+                       double kT, int nR, const int32_t* R, double* mu_out, double* eband_out, double* f_out,
+                       double* rhoR, int32_t* status, void* stream) {
+  if (!ctx) return nao_fail(nullptr, NAO_E_INVALID, "nao_density_matrix: ctx is NULL");
+  if (n < 1 || nk < 1 || nR < 1 || nb < 1 || nb > n || (nspin != 1 && nspin != 2))
+    return nao_fail(ctx, NAO_E_INVALID, "nao_density_matrix: bad sizes");
+  if (!wk || !kpts || !eps || !C || !m_kept || !R || !mu_out || !eband_out || !rhoR)
+    return nao_fail(ctx, NAO_E_INVALID, "nao_density_matrix: NULL array");
+  if (!(kT > 0.0)) return nao_fail(ctx, NAO_E_INVALID, "nao_density_matrix: kT must be > 0");
+  if ((size_t)16 * nk * 8 > 200 * 1024) return nao_fail(ctx, NAO_E_INVALID, "nao_density_matrix: nk too large");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = as_stream(stream);
+  const int nprob = nspin * nk;
+  const size_t nn = (size_t)n * n;
+  const double gdeg = (nspin == 1) ? 2.0 : 1.0;
+  WsPlan P;
+  const size_t of = P.take<double>((size_t)nprob * n), onocc = P.take<int32_t>(nprob),
+               oscr = P.take<double>(fermi_scratch_doubles(ctx->num_sms)), ost = P.take<int32_t>(1),
+               oCs = P.take<z64>((size_t)nprob * n * nb), oP = P.take<z64>(nn * nprob);
+  int rc = nao_ws_reserve(ctx, P.off);
+  if (rc) return rc;
+  char* ws = (char*)ctx->ws;
+  double* f = f_out ? f_out : (double*)(ws + of);
+  int32_t* nocc = (int32_t*)(ws + onocc);
+  double* scr = (double*)(ws + oscr);
+  int32_t* st_local = (int32_t*)(ws + ost);
+  z64* Cs = (z64*)(ws + oCs);
+  z64* Pk = (z64*)(ws + oP);
+  NAO_STAGE("fermi", 1, launch_fermi(ctx->num_sms, n, nprob, nk, gdeg, wk, eps, m_kept, nb, n_electrons, kT, f, nocc,
+                                 mu_out, eband_out, status ? status : st_local, scr, st));
+  NAO_STAGE("misc", 1, launch_scale_cols_sqrt(n, nprob, nb, (const z64*)C, f, Cs, st));
+  {
+    // P(k) = Cs Cs^H over the occupied bands (row-major [n][n])
+    GemmDims d{n, n, nb, nullptr, nullptr, nocc};
+    NAO_STAGE("zgemm_P", 1, launch_zgemm(nprob, d, zmk(1.0, 0.0), GemmOperand{Cs, (long long)n * nb, nb, 1, 0, nullptr},
+                                   GemmOperand{Cs, (long long)n * nb, 1, nb, 1, nullptr}, zmk(0.0, 0.0), Pk,
+                                   (long long)nn, n, 1, st));
+  }
+  NAO_STAGE("rho_phase", 1, launch_rho_phase_sum(n, nspin, nk, nR, R, kpts, wk, gdeg, Pk, rhoR, st));
+  return NAO_OK;
+}
+
+}  // extern "C"

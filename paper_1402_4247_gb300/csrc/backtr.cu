@@ -1,0 +1,182 @@
+// Eigen_HH steps 3-4 (Sec. 3: "rearrangement of eigenvectors" and "normalization"): the
+// eigenvectors of A are U = Q Z with Q = H_0 H_1 ... H_{m-2} from the tridiagonalization,
+// applied to each tridiagonal eigenvector z from the last reflector to the first, then
+// scaled to unit 2-norm.  For the overlap matrix the same pass applies Part 2's canonical
+// orthogonalization X = U_m diag(s_m^{-1/2}) (only the kept, largest, eigenpairs).
+//
+// One warp per output column; the column lives in shared memory with a fixed row-to-lane
+// ownership (row r belongs to lane r mod 32) so the warp needs no barriers.
+#include "nao_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void backtr_kernel(int n, const int32_t* __restrict__ size, const int32_t* __restrict__ ncols,
+                              const z64* __restrict__ Abase, int lda, long long strideA,
+                              const z64* __restrict__ taubase, long long strideV, const double* __restrict__ Zbase,
+                              int ldz, long long strideZ, const double* __restrict__ wbase, int use_rsqrt,
+                              z64* __restrict__ Ubase, int ldu, long long strideU) {
+  extern __shared__ z64 colbuf[];
+  const int p = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int m = size ? size[p] : n;
+  const int nc = ncols ? ncols[p] : m;
+  const int c = blockIdx.y * wpb + wid;
+  if (c >= nc || m <= 0) return;
+  const int j = (m - nc) + c;  // source eigenpair
+  z64* u = colbuf + (size_t)wid * n;
+  const z64* A = Abase + (size_t)p * strideA;
+  const z64* tau = taubase + (size_t)p * strideV;
+  const double* z = Zbase + (size_t)p * strideZ + (size_t)j * ldz;
+  for (int r = lane; r < m; r += 32) u[r] = zmk(z[r], 0.0);
+  for (int i = m - 2; i >= 0; --i) {
+    const z64 t = tau[i];
+    if (t.x == 0.0 && t.y == 0.0) continue;
+    const z64* v = A + (size_t)i * lda;  // v(i+1) = 1, v(r) = A(r, i) for r >= i+2
+    const int r0 = (i + 1) + ((lane - (i + 1)) & 31);
+    double sre = 0.0, sim = 0.0;
+    for (int r = r0; r < m; r += 32) {
+      const z64 vr = (r == i + 1) ? zmk(1.0, 0.0) : v[r];
+      const z64 ur = u[r];
+      // conj(vr) * ur
+      sre = fma(vr.x, ur.x, fma(vr.y, ur.y, sre));
+      sim = fma(vr.x, ur.y, fma(-vr.y, ur.x, sim));
+    }
+    sre = wsum(sre);
+    sim = wsum(sim);
+    const z64 f = zmul(t, zmk(sre, sim));  // u -= v * (tau * v^H u)
+    for (int r = r0; r < m; r += 32) {
+      const z64 vr = (r == i + 1) ? zmk(1.0, 0.0) : v[r];
+      u[r] = zsub(u[r], zmul(vr, f));
+    }
+  }
+  double nrm = 0.0;
+  for (int r = lane; r < m; r += 32) nrm += zabs2(u[r]);
+  nrm = wsum(nrm);
+  double sc = 1.0 / sqrt(nrm);
+  if (use_rsqrt) sc /= sqrt(wbase[(size_t)p * strideV + j]);
+  z64* out = Ubase + (size_t)p * strideU + (size_t)c * ldu;
+  for (int r = lane; r < m; r += 32) out[r] = zscale(u[r], sc);
+}
+
+__global__ void count_kept_kernel(int n, int nprob, const double* __restrict__ w, long long strideV, double s_cut,
+                                  int32_t* __restrict__ m, int32_t* __restrict__ status) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nprob) return;
+  const double* wp = w + (size_t)p * strideV;
+  int k = 0;
+  for (int j = 0; j < n; ++j) k += (wp[j] >= s_cut);
+  m[p] = k;
+  if (k == 0 && status[p] == 0) status[p] = NAO_E_ALLCUT;
+}
+
+__global__ void hermitize_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Abase, int ld,
+                                 long long strideA) {
+  const int p = blockIdx.z;
+  const int m = size ? size[p] : n;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;  // row
+  const int c = blockIdx.y;                             // column
+  if (r >= m || c >= m || r > c) return;
+  z64* A = Abase + (size_t)p * strideA;
+  if (r == c) {
+    A[(size_t)c * ld + r].y = 0.0;
+  } else {
+    A[(size_t)c * ld + r] = zconj(A[(size_t)r * ld + c]);  // upper (r < c) from lower (c, r)
+  }
+}
+
+__global__ void copy_real_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ src, int lds,
+                                 long long sstride, double* __restrict__ dst, int ldd, long long dstride) {
+  const int p = blockIdx.z;
+  const int m = size ? size[p] : n;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (r >= m || c >= m) return;
+  dst[(size_t)p * dstride + (size_t)c * ldd + r] = src[(size_t)p * sstride + (size_t)c * lds + r];
+}
+
+__global__ void write_eps_kernel(int n, int nprob, const int32_t* __restrict__ m, const double* __restrict__ w,
+                                 long long strideV, double* __restrict__ eps) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * nprob) return;
+  const int p = (int)(idx / n), j = (int)(idx % n);
+  eps[idx] = (j < m[p]) ? w[(size_t)p * strideV + j] : __longlong_as_double(0x7ff0000000000000ll);
+}
+
+__global__ void zero_cols_kernel(int n, int nprob, int nb, const int32_t* __restrict__ m, z64* __restrict__ C) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * nb * nprob) return;
+  const int p = (int)(idx / ((size_t)n * nb));
+  const int j = (int)(idx % nb);
+  if (j >= m[p]) C[idx] = zmk(0.0, 0.0);
+}
+
+__global__ void scale_cols_sqrt_kernel(int n, int nprob, int nb, const z64* __restrict__ C, const double* __restrict__ f,
+                                       z64* __restrict__ Cs) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * nb * nprob) return;
+  const int p = (int)(idx / ((size_t)n * nb));
+  const int j = (int)(idx % nb);
+  const double fj = f[(size_t)p * n + j];
+  Cs[idx] = zscale(C[idx], fj > 0.0 ? sqrt(fj) : 0.0);
+}
+
+}  // namespace
+
+cudaError_t launch_backtransform(int n, int nprob, const int32_t* size, const int32_t* ncols, const z64* A, int lda,
+                                 long long strideA, const z64* tau, long long strideV, const double* Z, int ldz,
+                                 long long strideZ, const double* w, int use_rsqrt_scale, z64* U, int ldu,
+                                 long long strideU, cudaStream_t st) {
+  int wpb = 8;
+  while (wpb > 1 && (size_t)wpb * n * sizeof(z64) > 200 * 1024) --wpb;
+  size_t smem = (size_t)wpb * n * sizeof(z64);
+  cudaError_t err = cudaFuncSetAttribute(backtr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  dim3 grid(nprob, (n + wpb - 1) / wpb);
+  backtr_kernel<<<grid, 32 * wpb, smem, st>>>(n, size, ncols, A, lda, strideA, tau, strideV, Z, ldz, strideZ, w,
+                                               use_rsqrt_scale, U, ldu, strideU);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_kept(int n, int nprob, const double* w, long long strideV, double s_cut, int32_t* m,
+                              int32_t* status, cudaStream_t st) {
+  count_kept_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(n, nprob, w, strideV, s_cut, m, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hermitize(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA, cudaStream_t st) {
+  dim3 grid((n + 127) / 128, n, nprob);
+  hermitize_kernel<<<grid, 128, 0, st>>>(n, size, A, ld, strideA);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_real(int n, int nprob, const int32_t* size, const double* src, int lds, long long sstride,
+                             double* dst, int ldd, long long dstride, cudaStream_t st) {
+  dim3 grid((n + 127) / 128, n, nprob);
+  copy_real_kernel<<<grid, 128, 0, st>>>(n, size, src, lds, sstride, dst, ldd, dstride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_write_eps(int n, int nprob, const int32_t* m, const double* w, long long strideV, double* eps,
+                             cudaStream_t st) {
+  const size_t tot = (size_t)n * nprob;
+  write_eps_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, nprob, m, w, strideV, eps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_cols(int n, int nprob, int nb, const int32_t* m, z64* C, cudaStream_t st) {
+  const size_t tot = (size_t)n * nb * nprob;
+  zero_cols_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, nprob, nb, m, C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_cols_sqrt(int n, int nprob, int nb, const z64* C, const double* f, z64* Cs, cudaStream_t st) {
+  const size_t tot = (size_t)n * nb * nprob;
+  scale_cols_sqrt_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, nprob, nb, C, f, Cs);
+  return cudaGetLastError();
+}

@@ -1,0 +1,161 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/nao.h"
+
+typedef double2 z64;  // complex128 as (x = re, y = im)
+
+// ---------------------------------------------------------------- complex helpers
+__host__ __device__ __forceinline__ z64 zmk(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ z64 zadd(z64 a, z64 b) { return zmk(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ z64 zsub(z64 a, z64 b) { return zmk(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ z64 zmul(z64 a, z64 b) {
+  return zmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ z64 zconj(z64 a) { return zmk(a.x, -a.y); }
+__host__ __device__ __forceinline__ z64 zscale(z64 a, double s) { return zmk(a.x * s, a.y * s); }
+// acc + a*b
+__host__ __device__ __forceinline__ z64 zfma(z64 a, z64 b, z64 acc) {
+  return zmk(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+// acc + conj(a)*b
+__host__ __device__ __forceinline__ z64 zcfma(z64 a, z64 b, z64 acc) {
+  return zmk(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+__host__ __device__ __forceinline__ double zabs2(z64 a) { return a.x * a.x + a.y * a.y; }
+
+// ---------------------------------------------------------------- context
+struct NaoStageStat {
+  const char* name;
+  double ms;
+  long long calls, launches;
+};
+struct NaoPending {
+  int stage;
+  cudaEvent_t a, b;
+};
+struct nao_ctx {
+  int device = 0;
+  int num_sms = 0;
+  void* ws = nullptr;       // device workspace arena
+  size_t ws_bytes = 0;
+  std::string last_error;
+  long long launches = 0;   // kernels launched by this context
+  bool profiling = false;
+  std::vector<NaoStageStat> stages;
+  std::vector<NaoPending> pending;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+// Stage bracketing for tracing (no-ops unless profiling is on).
+struct NaoStage {
+  nao_ctx* ctx;
+  cudaStream_t st;
+  int idx = -1;
+  cudaEvent_t a = nullptr;
+  NaoStage(nao_ctx* c, const char* name, cudaStream_t s, int nlaunch);
+  ~NaoStage();
+};
+
+// Bump allocator over the context's workspace (256-byte aligned slices).
+struct WsPlan {
+  size_t off = 0;
+  template <class T>
+  size_t take(size_t count) {
+    size_t o = (off + 255) & ~size_t(255);
+    off = o + count * sizeof(T);
+    return o;
+  }
+};
+
+int nao_ws_reserve(nao_ctx* ctx, size_t bytes);  // grow workspace (synchronises the device)
+int nao_fail(nao_ctx* ctx, int code, const char* fmt, ...);
+
+#define NAO_CUDA_TRY(ctx, call)                                                             \
+  do {                                                                                      \
+    cudaError_t _e = (call);                                                                \
+    if (_e != cudaSuccess)                                                                  \
+      return nao_fail((ctx), NAO_E_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(_e), \
+                      __FILE__, __LINE__);                                                  \
+  } while (0)
+
+// ---------------------------------------------------------------- launchers (host side)
+// Each returns cudaSuccess or the launch error; all are stream-ordered.
+
+// Part 1: Mk[a][q] = sum_r e^{2 pi i k_q.R_r} MR[a][r], lower triangle + mirror.
+cudaError_t launch_bloch_sum(int n, int nR, const int32_t* R, int nmat, const double* MR, int nk,
+                             const double* kpts, z64* Mk, cudaStream_t st);
+
+// Build the full Hermitian matrix (column-major, ld) from a row-major lower triangle.
+// src(p) = src + p*src_stride (row-major n x n), dst(p) = dst + p*dst_stride.
+// If map != null, the source of problem p is map[p].
+cudaError_t launch_herm_fill(int n, int nprob, const z64* src, long long src_stride, const int32_t* map,
+                             z64* dst, int ld, long long dst_stride, cudaStream_t st);
+
+// Eigen_HH step 1: Householder tridiagonalization, one block per problem, in place on the
+// full Hermitian column-major matrix A (ld).  size[p] (or n when size == null) is the order.
+cudaError_t launch_hetrd(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA,
+                         double* d, double* e, z64* tau, long long strideV, cudaStream_t st);
+
+// Eigen_HH step 2: eigenvalues w (ascending) and orthonormal eigenvectors Z (column-major,
+// ld) of tridiag(e, d, e) by bisection + inverse iteration.  scratch: see stein_scratch_doubles.
+size_t stein_scratch_doubles(int n, int nprob);
+cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d, const double* e,
+                         long long strideV, double* w, double* Z, int ld, long long strideZ,
+                         double* scratch, int32_t* status, cudaStream_t st);
+
+// Eigen_HH steps 3-4: U(:, c) = Q Z(:, j0+c) normalised, times colscale (optional)
+// for c in [0, ncols[p]); j0 = size[p] - ncols[p] (keeps the top ncols eigenpairs).
+cudaError_t launch_backtransform(int n, int nprob, const int32_t* size, const int32_t* ncols,
+                                 const z64* A, int lda, long long strideA, const z64* tau,
+                                 long long strideV, const double* Z, int ldz, long long strideZ,
+                                 const double* w, int use_rsqrt_scale, z64* U, int ldu, long long strideU,
+                                 cudaStream_t st);
+
+// Generic batched GEMM:  C(p) = alpha * opA(A(p)) * opB(B(p)) + beta * C(p)
+// Element (i, j) of an operand X at X.ptr + p*X.bs + i*X.rs + j*X.cs; conj flags per operand.
+// Dimensions: M, N, K fixed, or per problem from dim arrays when non-null.
+struct GemmOperand {
+  const void* ptr;
+  long long bs, rs, cs;
+  int conj;
+  const int32_t* map;  // nullable: problem p reads batch entry map[p]
+};
+struct GemmDims {
+  int M, N, K;                          // maxima (grid sizing) / fixed values
+  const int32_t *Mp, *Np, *Kp;          // per-problem overrides (nullable)
+};
+cudaError_t launch_zgemm(int nprob, GemmDims dims, z64 alpha, GemmOperand A, GemmOperand B, z64 beta,
+                         z64* C, long long Cbs, long long Crs, long long Ccs, cudaStream_t st);
+cudaError_t launch_dgemm(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta,
+                         double* C, long long Cbs, long long Crs, long long Ccs, cudaStream_t st);
+
+// Small helpers of the gen-eig chain.
+cudaError_t launch_count_kept(int n, int nprob, const double* w, long long strideV, double s_cut,
+                              int32_t* m, int32_t* status, cudaStream_t st);
+cudaError_t launch_hermitize(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA,
+                             cudaStream_t st);
+cudaError_t launch_copy_real(int n, int nprob, const int32_t* size, const double* src, int lds, long long sstride,
+                             double* dst, int ldd, long long dstride, cudaStream_t st);
+cudaError_t launch_write_eps(int n, int nprob, const int32_t* m, const double* w, long long strideV,
+                             double* eps, cudaStream_t st);
+cudaError_t launch_zero_cols(int n, int nprob, int nb, const int32_t* m, z64* C, cudaStream_t st);
+
+// Part 5: mu by bisection on the electron count, f, E_band, and per problem the number of
+// occupied bands (f > NAO_F_MIN), in one cooperative grid-wide kernel.
+constexpr double NAO_F_MIN = 1e-16;
+cudaError_t launch_fermi(int num_sms, int n, int nprob, int nk, double g, const double* wk, const double* eps,
+                         const int32_t* m, int nb, double n_electrons, double kT, double* f, int32_t* nocc,
+                         double* mu, double* eband, int32_t* status, double* scratch, cudaStream_t st);
+size_t fermi_scratch_doubles(int num_sms);
+
+// Part 6 helpers: Cs = C diag(sqrt f) and the inverse phase sum to rho(R).
+cudaError_t launch_scale_cols_sqrt(int n, int nprob, int nb, const z64* C, const double* f, z64* Cs,
+                                   cudaStream_t st);
+cudaError_t launch_rho_phase_sum(int n, int nspin, int nk, int nR, const int32_t* R, const double* kpts,
+                                 const double* wk, double g, const z64* P, double* rho, cudaStream_t st);

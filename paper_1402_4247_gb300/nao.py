@@ -1,0 +1,193 @@
+"""Python binding of the C ABI in include/nao.h (argument marshalling only).
+
+Every function has the C entry point's name and forwards device pointers (from torch
+tensors) and the current CUDA stream to ``libnao.so``; all computation happens in the
+library's CUDA kernels.  There is no CPU fallback: if the library cannot be loaded the
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+NAO_OK = 0
+NAO_E_INVALID = -1
+NAO_E_NOMEM = -2
+NAO_E_NOCONV = -3
+NAO_E_TIMEOUT = -4
+NAO_E_CUDA = -5
+NAO_E_ALLCUT = -6
+NAO_E_BUSY = -7
+NAO_E_RANGE = -8
+NAO_FP64 = 0
+NAO_MIXED_TF32 = 1
+NAO_MIXED_BF16X3 = 2
+
+#: every symbol include/nao.h declares
+EXPORTS = ("nao_init", "nao_destroy", "nao_last_error", "nao_workspace_bytes", "nao_bloch_sum",
+           "nao_gen_eig", "nao_density_matrix", "nao_profile_enable", "nao_profile_read", "nao_launch_count")
+
+_lib = None
+
+
+class NaoError(RuntimeError):
+    pass
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libnao.so (building it first if it is missing or older than its sources)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if path == _build.LIB and _build.is_stale():
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, i32, f64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    lib.nao_init.argtypes = [ctypes.POINTER(vp), i32]
+    lib.nao_init.restype = i32
+    lib.nao_destroy.argtypes = [vp]
+    lib.nao_destroy.restype = None
+    lib.nao_last_error.argtypes = [vp]
+    lib.nao_last_error.restype = ctypes.c_char_p
+    lib.nao_workspace_bytes.argtypes = [vp]
+    lib.nao_workspace_bytes.restype = sz
+    lib.nao_bloch_sum.argtypes = [vp, i32, i32, vp, i32, vp, i32, vp, vp, vp]
+    lib.nao_bloch_sum.restype = i32
+    lib.nao_gen_eig.argtypes = [vp, i32, i32, vp, vp, vp, i32, f64, i32, i32, vp, vp, vp, vp, vp]
+    lib.nao_gen_eig.restype = i32
+    lib.nao_density_matrix.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, i32, vp, f64, f64, i32, vp, vp, vp,
+                                       vp, vp, vp, vp]
+    lib.nao_density_matrix.restype = i32
+    lib.nao_profile_enable.argtypes = [vp, i32]
+    lib.nao_profile_enable.restype = i32
+    lib.nao_profile_read.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(f64),
+                                     ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.nao_profile_read.restype = i32
+    lib.nao_launch_count.argtypes = [vp]
+    lib.nao_launch_count.restype = ctypes.c_int64
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """Owns an ``nao_ctx`` (device workspace) on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load_library()
+        self.handle = ctypes.c_void_p()
+        rc = self.lib.nao_init(ctypes.byref(self.handle), int(device))
+        if rc != NAO_OK:
+            raise NaoError(f"nao_init failed ({rc}): {self.lib.nao_last_error(None).decode()}")
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            self.lib.nao_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, name):
+        if rc != NAO_OK:
+            raise NaoError(f"{name} failed ({rc}): {self.lib.nao_last_error(self.handle).decode()}")
+
+    def workspace_bytes(self) -> int:
+        return int(self.lib.nao_workspace_bytes(self.handle))
+
+    def nao_profile_enable(self, on: bool = True):
+        self._check(self.lib.nao_profile_enable(self.handle, 1 if on else 0), "nao_profile_enable")
+
+    def nao_profile_read(self) -> dict:
+        """{stage: (total_ms, calls, launches)} from the CUDA events recorded so far."""
+        cap = 64
+        names = (ctypes.c_char_p * cap)()
+        ms = (ctypes.c_double * cap)()
+        calls = (ctypes.c_int64 * cap)()
+        launches = (ctypes.c_int64 * cap)()
+        k = self.lib.nao_profile_read(self.handle, cap, names, ms, calls, launches)
+        if k < 0:
+            self._check(k, "nao_profile_read")
+        return {names[i].decode(): (ms[i], int(calls[i]), int(launches[i])) for i in range(min(k, cap))}
+
+    def nao_launch_count(self) -> int:
+        return int(self.lib.nao_launch_count(self.handle))
+
+    # ------------------------------------------------------------------ Part 1
+    def nao_bloch_sum(self, MR, R, kpts, out=None, stream=None):
+        """MR float64 [nmat][nR][n][n], R int32 [nR][3], kpts float64 [nk][3] -> complex128 [nmat][nk][n][n]."""
+        nmat, nR, n, _ = MR.shape
+        nk = kpts.shape[0]
+        if out is None:
+            out = torch.empty((nmat, nk, n, n), dtype=torch.complex128, device=MR.device)
+        rc = self.lib.nao_bloch_sum(self.handle, n, nR, _ptr(R), nmat, _ptr(MR), nk, _ptr(kpts), _ptr(out),
+                                    _stream(stream))
+        self._check(rc, "nao_bloch_sum")
+        return out
+
+    # ------------------------------------------------------------------ Parts 2-4
+    def nao_gen_eig(self, H, S, s_of_prob=None, s_cut=1e-10, nb=None, precision=NAO_FP64, want_vectors=True,
+                    out=None, stream=None):
+        """H complex128 [nprob][n][n], S complex128 [nS][n][n] -> (eps, C, m_kept, status)."""
+        nprob, n, _ = H.shape
+        nS = S.shape[0]
+        nb = n if nb is None else int(nb)
+        dev = H.device
+        if out is None:
+            eps = torch.empty((nprob, n), dtype=torch.float64, device=dev)
+            C = torch.empty((nprob, n, nb), dtype=torch.complex128, device=dev) if want_vectors else None
+            m = torch.empty(nprob, dtype=torch.int32, device=dev)
+            st = torch.empty(nprob, dtype=torch.int32, device=dev)
+        else:
+            eps, C, m, st = out
+        if s_of_prob is None and nS != nprob:
+            raise ValueError("S must have one matrix per problem unless s_of_prob is given")
+        rc = self.lib.nao_gen_eig(self.handle, n, nprob, _ptr(H), _ptr(S), _ptr(s_of_prob), nS, float(s_cut),
+                                  int(precision), nb, _ptr(eps), _ptr(C), _ptr(m), _ptr(st), _stream(stream))
+        self._check(rc, "nao_gen_eig")
+        return eps, C, m, st
+
+    # ------------------------------------------------------------------ Parts 5-6
+    def nao_density_matrix(self, wk, kpts, eps, C, m_kept, n_electrons, kT, R, nspin, want_f=True, out=None,
+                           stream=None):
+        """-> (mu [1], eband [1], f [nprob][n] or None, rho [nspin][nR][n][n], status [1])."""
+        nprob, n, nb = C.shape
+        nk = wk.shape[0]
+        nR = R.shape[0]
+        dev = C.device
+        if out is None:
+            mu = torch.empty(1, dtype=torch.float64, device=dev)
+            eb = torch.empty(1, dtype=torch.float64, device=dev)
+            f = torch.empty((nprob, n), dtype=torch.float64, device=dev) if want_f else None
+            rho = torch.empty((nspin, nR, n, n), dtype=torch.float64, device=dev)
+            st = torch.empty(1, dtype=torch.int32, device=dev)
+        else:
+            mu, eb, f, rho, st = out
+        rc = self.lib.nao_density_matrix(self.handle, n, nspin, nk, _ptr(wk), _ptr(kpts), _ptr(eps), _ptr(C), nb,
+                                         _ptr(m_kept), float(n_electrons), float(kT), nR, _ptr(R), _ptr(mu),
+                                         _ptr(eb), _ptr(f), _ptr(rho), _ptr(st), _stream(stream))
+        self._check(rc, "nao_density_matrix")
+        return mu, eb, f, rho, st

@@ -1,0 +1,154 @@
+"""CUDA path vs the CPU oracle, element by element on the same seeded inputs (GPU only)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1402_4247_gb300 import synth
+from tests.gpu_helpers import (TOL_RHO, check_problem, gpu_band_step)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_4247_gb300.nao import Context
+    c = Context(0)
+    yield c
+    c.close()
+
+
+DEV = "cuda:0"
+
+
+def _oracle(inp, problems=None):
+    return oracle.band_step(inp.HR, inp.SR, inp.R, inp.kpts, inp.wk, inp.n_electrons, inp.kT, problems=problems)
+
+
+def _compare_all(inp, g, ref, nb=None):
+    for p in range(inp.nprob):
+        sg, k = divmod(p, inp.nk)
+        check_problem(ref["Hk"][sg, k], ref["Sk"][k], g["eps"][p], g["C"][p], int(g["m"][p]), ref["eps"][p],
+                      ref["C"][p], ref["m"][p], label=f"{inp.name} p={p}")
+        assert int(g["status"][p]) == 0
+
+
+def test_bloch_sum_matches_oracle(ctx):
+    inp = synth.small_cell(21, 2, 3, kgrid=(3, 2, 1), nspin=2)
+    g = gpu_band_step(ctx, inp, torch, DEV, density=False)
+    Hk = oracle.bloch_sum(inp.HR, inp.R, inp.kpts).reshape(-1, inp.n, inp.n)
+    Sk = oracle.bloch_sum(inp.SR, inp.R, inp.kpts)
+    sc = np.abs(inp.HR).max() * inp.nR
+    assert np.abs(g["Hk"] - Hk).max() <= 1e-14 * sc
+    assert np.abs(g["Sk"] - Sk).max() <= 1e-14 * np.abs(inp.SR).max() * inp.nR
+    for A in list(g["Hk"]) + list(g["Sk"]):
+        assert np.array_equal(A, A.conj().T)
+
+
+def test_bloch_sum_hand_values(ctx):
+    R = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0]], dtype=np.int32)
+    M = np.array([[[1, 2], [2, 3]], [[0, 5], [7, 0]], [[0, 7], [5, 0]], [[4, 0], [0, 0]], [[4, 0], [0, 0]]],
+                 dtype=np.float64)
+    k = np.array([[0.25, 0, 0], [0, 0.5, 0], [0.125, 0.25, 0]])
+    out = ctx.nao_bloch_sum(torch.from_numpy(M)[None].to(DEV), torch.from_numpy(R).to(DEV),
+                            torch.from_numpy(k).to(DEV)).cpu().numpy()[0]
+    r2 = np.sqrt(2.0)
+    want = [np.array([[9, 2 - 2j], [2 + 2j, 3]]), np.array([[-7, 14], [14, 3]]),
+            np.array([[1, 2 + 6 * r2 - r2 * 1j], [2 + 6 * r2 + r2 * 1j, 3]])]
+    for q in range(3):
+        assert np.abs(out[q] - want[q]).max() < 1e-13
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: synth.tiny_cell(),
+    lambda: synth.small_cell(31, 1, 2, kgrid=(2, 1, 1), nspin=2),       # n = 29
+    lambda: synth.small_cell(32, 3, 5, kgrid=(2, 2, 1), nspin=1),       # n = 79
+    lambda: synth.small_cell(33, 5, 8, kgrid=(1, 2, 1), nspin=2),       # n = 129: several tiles + ragged tail
+], ids=["tiny64", "n29", "n79", "n129"])
+def test_band_step_matches_oracle(ctx, maker):
+    inp = maker()
+    g = gpu_band_step(ctx, inp, torch, DEV)
+    ref = _oracle(inp)
+    _compare_all(inp, g, ref)
+    # Part 5: mu is only fixed up to the flatness of N(mu); check the count at the GPU's mu,
+    # then occupations, band energy and rho elementwise
+    assert int(g["rstatus"][0]) == 0
+    g_deg = 2.0 if inp.nspin == 1 else 1.0
+    cnt = g_deg * sum(inp.wk[p % inp.nk] * (1.0 / (1.0 + np.exp((ref["eps"][p] - g["mu"][0]) / inp.kT))).sum()
+                      for p in range(inp.nprob))
+    assert abs(cnt - inp.n_electrons) <= 1e-9 * max(1.0, inp.n_electrons)
+    for p in range(inp.nprob):
+        m = ref["m"][p]
+        assert np.abs(g["f"][p][:m] - ref["f"][p]).max() <= 1e-9
+    assert abs(g["eband"][0] - ref["eband"]) <= 1e-9 * max(1.0, abs(ref["eband"]))
+    drho = np.abs(g["rho"] - ref["rho"]).max()
+    assert drho <= TOL_RHO, f"rho differs by {drho:.3e}"
+
+
+def test_nb_subset_and_zero_padding(ctx):
+    inp = synth.small_cell(34, 2, 2, kgrid=(2, 1, 1), nspin=1)  # n = 42
+    g = gpu_band_step(ctx, inp, torch, DEV, nb=17, density=False)
+    ref = _oracle(inp, problems=list(range(inp.nprob)))
+    for p in range(inp.nprob):
+        check_problem(ref["Hk"][0, p], ref["Sk"][p], g["eps"][p], g["C"][p], int(g["m"][p]), ref["eps"][p],
+                      ref["C"][p], ref["m"][p], label=f"nb17 p={p}")
+
+
+@pytest.mark.parametrize("N,alpha,beta,s,k", [(64, 0.0, -1.0, 0.45, 0.0), (97, 0.05, -0.7, 0.2, 0.21),
+                                              (33, 0.1, -0.25, 0.3, 0.37)])
+def test_chain_closed_form_on_gpu(ctx, N, alpha, beta, s, k):
+    inp = synth.chain_1orb(N, alpha, beta, s, np.array([[k, 0.0, 0.0]]))
+    g = gpu_band_step(ctx, inp, torch, DEV, density=False)
+    t = 2 * np.pi * (k + np.arange(N)) / N
+    exact = np.sort((alpha + 2 * beta * np.cos(t)) / (1 + 2 * s * np.cos(t)))
+    assert int(g["m"][0]) == N
+    assert np.abs(g["eps"][0] - exact).max() <= 1e-10 * np.abs(exact).max()
+
+
+def test_exactly_singular_overlap_is_cut(ctx):
+    N = 8
+    inp = synth.chain_1orb(N, 0.2, -0.6, 0.5, np.array([[0.0, 0.0, 0.0]]))
+    g = gpu_band_step(ctx, inp, torch, DEV, density=False)
+    assert int(g["m"][0]) == N - 1
+    t = 2 * np.pi * np.arange(N) / N
+    keep = np.abs(np.cos(t) + 1) > 1e-9
+    exact = np.sort((0.2 - 1.2 * np.cos(t[keep])) / (1 + np.cos(t[keep])))
+    assert np.abs(g["eps"][0][:N - 1] - exact).max() <= 1e-10 * np.abs(exact).max()
+    assert np.isinf(g["eps"][0][N - 1])
+    assert np.all(g["C"][0][:, N - 1] == 0)
+
+
+def _gen_eig_direct(ctx, H, S, nb=None):
+    Ht = torch.from_numpy(np.ascontiguousarray(H[None])).to(DEV)
+    St = torch.from_numpy(np.ascontiguousarray(S[None])).to(DEV)
+    eps, C, m, st = ctx.nao_gen_eig(Ht, St, nb=nb)
+    torch.cuda.synchronize()
+    return eps.cpu().numpy()[0], C.cpu().numpy()[0], int(m[0]), int(st[0])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 33, 65, 130])
+def test_random_pencils(ctx, n):
+    rng = np.random.Generator(np.random.PCG64(500 + n))
+    H, S = synth.random_hermitian_pair(rng, n, cond=100.0)
+    e, C, m, st = _gen_eig_direct(ctx, H, S)
+    eo, Co, mo, _ = oracle.generalized_eigensolve(H, S)
+    assert st == 0
+    check_problem(H, S, e, C, m, eo, Co, mo, label=f"random n={n}")
+
+
+def test_identity_overlap_and_diagonal(ctx):
+    rng = np.random.Generator(np.random.PCG64(9))
+    H, _ = synth.random_hermitian_pair(rng, 40)
+    e, C, m, st = _gen_eig_direct(ctx, H, np.eye(40, dtype=complex))
+    eo, Co, mo, _ = oracle.generalized_eigensolve(H, np.eye(40, dtype=complex))
+    check_problem(H, np.eye(40), e, C, m, eo, Co, mo, label="S=I")
+    h = np.array([3.0, -1.0, 0.5, 2.0, -4.0, 0.5])
+    s = np.array([1.0, 0.5, 2.0, 0.25, 1.5, 1.0])
+    e, C, m, st = _gen_eig_direct(ctx, np.diag(h).astype(complex), np.diag(s).astype(complex))
+    assert m == 6 and st == 0
+    assert np.abs(e - np.sort(h / s)).max() < 1e-14
+    # degenerate eigenvalue 0.5 (twice): compare the projector
+    eo, Co, mo, _ = oracle.generalized_eigensolve(np.diag(h).astype(complex), np.diag(s).astype(complex))
+    check_problem(np.diag(h).astype(complex), np.diag(s).astype(complex), e, C, m, eo, Co, mo, label="diag")
