@@ -5,7 +5,8 @@ import numpy as np
 # Tolerances (floating point): eigenvalues |d eps| <= 1e-10 * ||H'|| with ||H'|| = max |eps|
 # (the norm of X^H H X, the matrix whose eigenvalues are computed); residual
 # ||H C - S C eps||_F / (n ||H||_2) <= 1e-12; ||C^H S C - I||_max <= 1e-11; rho elementwise
-# <= 1e-10; spectral projectors of eigenvalue clusters <= 1e-9 max(1, ||P||).
+# <= 1e-10 max(1, max|rho|) (rho reaches ~1e3 here: |c_i| ~ s_min^{-1/2}); spectral projectors
+# of eigenvalue clusters <= 1e-9 max(1, ||P||).
 TOL_EPS = 1e-10
 TOL_RES = 1e-12
 TOL_ORTH = 1e-11

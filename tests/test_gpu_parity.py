@@ -76,15 +76,16 @@ def test_band_step_matches_oracle(ctx, maker):
     # then occupations, band energy and rho elementwise
     assert int(g["rstatus"][0]) == 0
     g_deg = 2.0 if inp.nspin == 1 else 1.0
-    cnt = g_deg * sum(inp.wk[p % inp.nk] * (1.0 / (1.0 + np.exp((ref["eps"][p] - g["mu"][0]) / inp.kT))).sum()
-                      for p in range(inp.nprob))
+    with np.errstate(over="ignore"):
+        cnt = g_deg * sum(inp.wk[p % inp.nk] * (1.0 / (1.0 + np.exp((ref["eps"][p] - g["mu"][0]) / inp.kT))).sum()
+                          for p in range(inp.nprob))
     assert abs(cnt - inp.n_electrons) <= 1e-9 * max(1.0, inp.n_electrons)
     for p in range(inp.nprob):
         m = ref["m"][p]
         assert np.abs(g["f"][p][:m] - ref["f"][p]).max() <= 1e-9
     assert abs(g["eband"][0] - ref["eband"]) <= 1e-9 * max(1.0, abs(ref["eband"]))
     drho = np.abs(g["rho"] - ref["rho"]).max()
-    assert drho <= TOL_RHO, f"rho differs by {drho:.3e}"
+    assert drho <= TOL_RHO * max(1.0, np.abs(ref["rho"]).max()), f"rho differs by {drho:.3e}"
 
 
 def test_nb_subset_and_zero_padding(ctx):
