@@ -166,9 +166,10 @@ def _stage_flops(stage, inp, m_mean, nocc_mean):
     return None
 
 
-def _load_traffic(stage):
-    """DRAM bytes per launch of a stage's kernel from a committed ncu summary, if the kernel
-    source has not changed since it was captured."""
+def _load_traffic(stage, units_per_launch):
+    """DRAM bytes per launch of a stage's kernel: the per-unit figure of a committed ncu
+    capture (a smaller case) times the units one launch processes, provided the kernel
+    source has not changed since the capture."""
     import hashlib
     pth = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(pth):
@@ -180,7 +181,7 @@ def _load_traffic(stage):
             return None
         src = os.path.join(ROOT, "paper_1402_4247_gb300", "csrc", ent["source"])
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        return ent["bytes_per_launch"] if h == ent["source_sha256_16"] else None
+        return ent["bytes_per_unit"] * units_per_launch if h == ent["source_sha256_16"] else None
     except Exception:
         return None
 
@@ -350,7 +351,7 @@ def run_ours(args, rank, world, local_rank):
         per_launch_ms = dms / max(dl, 1)
         achieved = (fl * args.steps / max(dl, 1)) / (per_launch_ms * 1e-3) / 1e12 if fl else None
         roof = {"kernel": dname, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": _load_traffic(dname),
+                "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": _load_traffic(dname, (inp.nk + inp.nprob) / 2.0 if dname == "hetrd" else 0.0),
                 "peak_source": "FP64 FMA pipe: 2 FMA/clk/SM x 152 SMs x 2070 MHz (derived; 1.20 TFLOP/s measured "
                                "by a DFMA microbenchmark); HBM 6780 GB/s is not the bound"}
         value = nprob * world * args.steps / (t_max * 1e-3)
