@@ -125,6 +125,29 @@ int nao_profile_read(nao_ctx* ctx, int max, const char** names, double* ms, int6
 /* Kernels this context has launched since nao_init (always counted).                    */
 int64_t nao_launch_count(const nao_ctx* ctx);
 
+/* Part 5 without allocation (no counterpart in the paper) ----------------------------- *
+ * Same result as the mu / f / E_band part of nao_density_matrix, for callers that must not
+ * let the library allocate device memory: codes that give the library a fixed memory pool
+ * and forbid allocations behind their back, and loops that cannot afford the device
+ * synchronisation a cudaMalloc/cudaFree may cause.  It takes no context and never calls
+ * cudaMalloc, cudaFree or an allocating library routine: its scratch (grid partial sums
+ * and per-problem occupied-band counts, 296 KiB) is a static array in the library image,
+ * resident on every GPU that loads the library until the process exits.
+ *   Limits: nspin * nk <= 65536 problems (else NAO_E_INVALID); runs on the current
+ *   device, on `stream`; f_out float64 [nspin*nk][n] is required.
+ *   Set-up: the first call on a device looks up the scratch array's device address
+ *   (cudaGetSymbolAddress, once per device, with that device current); make that first
+ *   call before any stream capture.
+ *   Sharing: every call uses the same scratch and leaves its contents behind (the kernel
+ *   resets what must start at zero).  Calls that overlap on the GPU (other streams, other
+ *   host threads) race on it and must be serialised by the caller.
+ *   Arguments and outputs as in nao_density_matrix; errors: NAO_E_INVALID, NAO_E_CUDA
+ *   (text via nao_last_error(NULL)).                                                      */
+int nao_fermi_level_noalloc(int n, int nspin, int nk, const double* wk, const double* eps,
+                            const int32_t* m_kept, int nb, double n_electrons, double kT,
+                            double* f_out, double* mu_out, double* eband_out, int32_t* status,
+                            void* stream);
+
 #ifdef __cplusplus
 }
 #endif

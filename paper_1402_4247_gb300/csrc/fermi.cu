@@ -165,3 +165,76 @@ cudaError_t launch_fermi(int num_sms, int n, int nprob, int nk, double g, const 
   void* args[] = {&n, &nprob, &nk, &g, &wk, &eps, &m, &nb, &n_electrons, &kT, &f, &nocc, &mu, &eband, &status, &scratch};
   return cudaLaunchCooperativeKernel((const void*)fermi_kernel, dim3(grid), dim3(FT), args, 0, st);
 }
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of Part 5 (no counterpart in the paper).
+//
+// The entry point above takes its scratch (grid partial sums, per-problem occupied-band
+// counts) from the context's workspace, which the library grows with cudaMalloc.  Some
+// callers cannot allow that: host codes that hand the library a fixed device-memory pool
+// and forbid allocations behind their back (DFT drivers in Fortran/MPI with their own
+// allocators), and serving loops that must never synchronise the device in the middle
+// of a step (cudaMalloc/cudaFree can synchronise).  For them nao_fermi_level_noalloc
+// runs the same kernel on a scratch array that is part of the library image itself.
+// ---------------------------------------------------------------------------------------
+
+#include <mutex>
+
+namespace {
+constexpr int NOALLOC_MAX_BLOCKS = 1024;           // grid blocks whose partial sums fit
+constexpr int NOALLOC_MAX_PROBLEMS = 65536;        // (spin, k) problems whose band counts fit
+constexpr size_t NOALLOC_PART_DOUBLES = 4 * (size_t)NOALLOC_MAX_BLOCKS + 64;
+constexpr size_t NOALLOC_DOUBLES = NOALLOC_PART_DOUBLES + NOALLOC_MAX_PROBLEMS / 2;  // + int32 counts
+}  // namespace
+
+// 296 KiB of device memory, held by every GPU that loads the library until the process exits.
+static __device__ __align__(256) double nao_fermi_scratch[NOALLOC_DOUBLES];
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of nao_fermi_scratch on the current device, looked up once per device.
+// (In host code the symbol names a host-side shadow, not device memory.)
+cudaError_t noalloc_scratch(int dev, double** out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, nao_fermi_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = (double*)g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" int nao_fermi_level_noalloc(int n, int nspin, int nk, const double* wk, const double* eps,
+                                       const int32_t* m_kept, int nb, double n_electrons, double kT, double* f_out,
+                                       double* mu_out, double* eband_out, int32_t* status, void* stream) {
+  if (n < 1 || nk < 1 || (nspin != 1 && nspin != 2) || nb < 1 || nb > n)
+    return nao_fail(nullptr, NAO_E_INVALID, "nao_fermi_level_noalloc: bad sizes");
+  if ((long long)nspin * nk > NOALLOC_MAX_PROBLEMS)
+    return nao_fail(nullptr, NAO_E_INVALID,
+                    "nao_fermi_level_noalloc: %d problems exceed the fixed scratch limit of %d",
+                    nspin * nk, NOALLOC_MAX_PROBLEMS);
+  if (!wk || !eps || !m_kept || !f_out || !mu_out || !eband_out || !status)
+    return nao_fail(nullptr, NAO_E_INVALID, "nao_fermi_level_noalloc: NULL array");
+  if (!(kT > 0.0)) return nao_fail(nullptr, NAO_E_INVALID, "nao_fermi_level_noalloc: kT must be > 0");
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  double* scratch = nullptr;
+  if (e == cudaSuccess) e = noalloc_scratch(dev, &scratch);
+  if (e != cudaSuccess)
+    return nao_fail(nullptr, NAO_E_CUDA, "nao_fermi_level_noalloc: %s", cudaGetErrorString(e));
+  const int grid = sms < NOALLOC_MAX_BLOCKS ? sms : NOALLOC_MAX_BLOCKS;
+  int32_t* nocc = (int32_t*)(scratch + NOALLOC_PART_DOUBLES);
+  e = launch_fermi(grid, n, nspin * nk, nk, nspin == 1 ? 2.0 : 1.0, wk, eps, m_kept, nb, n_electrons, kT, f_out,
+                   nocc, mu_out, eband_out, status, scratch, (cudaStream_t)stream);
+  if (e != cudaSuccess)
+    return nao_fail(nullptr, NAO_E_CUDA, "nao_fermi_level_noalloc: launch failed: %s", cudaGetErrorString(e));
+  return NAO_OK;
+}

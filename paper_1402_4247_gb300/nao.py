@@ -29,7 +29,8 @@ NAO_MIXED_BF16X3 = 2
 
 #: every symbol include/nao.h declares
 EXPORTS = ("nao_init", "nao_destroy", "nao_last_error", "nao_workspace_bytes", "nao_bloch_sum",
-           "nao_gen_eig", "nao_density_matrix", "nao_profile_enable", "nao_profile_read", "nao_launch_count")
+           "nao_gen_eig", "nao_density_matrix", "nao_profile_enable", "nao_profile_read", "nao_launch_count",
+           "nao_fermi_level_noalloc")
 
 _lib = None
 
@@ -70,6 +71,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.nao_profile_read.restype = i32
     lib.nao_launch_count.argtypes = [vp]
     lib.nao_launch_count.restype = ctypes.c_int64
+    lib.nao_fermi_level_noalloc.argtypes = [i32, i32, i32, vp, vp, vp, i32, f64, f64, vp, vp, vp, vp, vp]
+    lib.nao_fermi_level_noalloc.restype = i32
     _lib = lib
     return lib
 
@@ -191,3 +194,18 @@ class Context:
                                          _ptr(eb), _ptr(f), _ptr(rho), _ptr(st), _stream(stream))
         self._check(rc, "nao_density_matrix")
         return mu, eb, f, rho, st
+
+
+def nao_fermi_level_noalloc(wk, eps, m_kept, nb, n_electrons, kT, nspin, f_out, mu_out, eband_out, status,
+                            stream=None):
+    """Part 5 (mu, f, E_band) through the allocation-free entry point: the library allocates
+    nothing; all outputs are caller tensors on the current device."""
+    lib = load_library()
+    nprob, n = eps.shape
+    nk = wk.shape[0]
+    rc = lib.nao_fermi_level_noalloc(n, int(nspin), nk, _ptr(wk), _ptr(eps), _ptr(m_kept), int(nb),
+                                     float(n_electrons), float(kT), _ptr(f_out), _ptr(mu_out), _ptr(eband_out),
+                                     _ptr(status), _stream(stream))
+    if rc != NAO_OK:
+        raise NaoError(f"nao_fermi_level_noalloc failed ({rc}): {lib.nao_last_error(None).decode()}")
+    return mu_out, eband_out, f_out, status
