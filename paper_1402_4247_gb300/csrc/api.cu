@@ -268,17 +268,16 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
 
   // ---- Part 2: Eigen_HH(S) -> s, U;  X = U_m s_m^{-1/2}
   NAO_STAGE("herm_fill", 1, launch_herm_fill(n, nSe, (const z64*)S, snn, nullptr, AS, n, snn, st));
-  NAO_STAGE("hetrd", 1, launch_hetrd(n, nSe, nullptr, AS, n, snn, dS, eS, tauS, n, st));
+  NAO_STAGE("hetrd", 1, launch_hetrd(n, nSe, nullptr, AS, n, snn, dS, eS, tauS, n,
+                                     hetrd_cluster_size(nSe, ctx->num_sms), st));
   NAO_STAGE("stein", 1, launch_stein(n, nSe, nullptr, dS, eS, n, wS, Z, n, snn, scr, stS, st));
   NAO_STAGE("misc", 1, launch_count_kept(n, nSe, wS, n, s_cut, mS, stS, st));
-  {  // one Newton-Schulz step: Z2 = Z (3I - Z^T Z)/2
-    GemmDims d{n, n, n, nullptr, nullptr, nullptr};
-    NaoStage stage_(ctx, "ortho_ns", st, 3);
+  {  // one Newton-Schulz step: Z2 = Z (3I - Z^T Z)/2 = Z - Z (Z^T Z - I)/2
+    GemmDims d{n, n, n, nullptr, nullptr, nullptr, 1};
+    NaoStage stage_(ctx, "ortho_ns", st, 2);
     NAO_CUDA_TRY(ctx, launch_dgemm(nSe, d, 1.0, GemmOperand{Z, snn, n, 1, 0, nullptr},
                                    GemmOperand{Z, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, st));
-    NAO_CUDA_TRY(ctx, launch_copy_real(n, nSe, nullptr, Z, n, snn, Z2, n, snn, st));
-    NAO_CUDA_TRY(ctx, launch_dgemm(nSe, d, -0.5, GemmOperand{Z, snn, 1, n, 0, nullptr},
-                                   GemmOperand{G, snn, 1, n, 0, nullptr}, 1.5, Z2, snn, 1, n, st));
+    NAO_CUDA_TRY(ctx, launch_ns_correct(n, nSe, nullptr, Z, G, n, snn, Z2, st));
   }
   NAO_STAGE("backtransform", 1, launch_backtransform(n, nSe, nullptr, mS, AS, n, snn, tauS, n, Z2, n, snn, wS, 1, X, n, snn, st));
   {
@@ -293,23 +292,22 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
     GemmDims d{n, n, n, nullptr, mP, nullptr};  // Y = Hf X : n x m
     NAO_STAGE("zgemm_HX", 1, launch_zgemm(nprob, d, one, GemmOperand{Hf, snn, 1, n, 0, nullptr},
                                    GemmOperand{X, snn, 1, n, 0, s_of_prob}, zero, Y, snn, 1, n, st));
-    GemmDims d2{n, n, n, mP, mP, nullptr};  // Hp = X^H Y : m x m
+    GemmDims d2{n, n, n, mP, mP, nullptr, 1};  // Hp = X^H Y : m x m, lower triangle
     NAO_STAGE("zgemm_XHY", 1, launch_zgemm(nprob, d2, one, GemmOperand{X, snn, n, 1, 1, s_of_prob},
                                    GemmOperand{Y, snn, 1, n, 0, nullptr}, zero, Hp, snn, 1, n, st));
   }
   NAO_STAGE("misc", 1, launch_hermitize(n, nprob, mP, Hp, n, snn, st));
 
   // ---- Part 4: Eigen_HH(H') -> eps, V;  C = X V
-  NAO_STAGE("hetrd", 1, launch_hetrd(n, nprob, mP, Hp, n, snn, dH, eH, tauH, n, st));
+  NAO_STAGE("hetrd", 1, launch_hetrd(n, nprob, mP, Hp, n, snn, dH, eH, tauH, n,
+                                     hetrd_cluster_size(nprob, ctx->num_sms), st));
   NAO_STAGE("stein", 1, launch_stein(n, nprob, mP, dH, eH, n, wH, Z, n, snn, scr, stH, st));
   {
-    GemmDims d{n, n, n, mP, mP, mP};
-    NaoStage stage_(ctx, "ortho_ns", st, 3);
+    GemmDims d{n, n, n, mP, mP, mP, 1};
+    NaoStage stage_(ctx, "ortho_ns", st, 2);
     NAO_CUDA_TRY(ctx, launch_dgemm(nprob, d, 1.0, GemmOperand{Z, snn, n, 1, 0, nullptr},
                                    GemmOperand{Z, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, st));
-    NAO_CUDA_TRY(ctx, launch_copy_real(n, nprob, mP, Z, n, snn, Z2, n, snn, st));
-    NAO_CUDA_TRY(ctx, launch_dgemm(nprob, d, -0.5, GemmOperand{Z, snn, 1, n, 0, nullptr},
-                                   GemmOperand{G, snn, 1, n, 0, nullptr}, 1.5, Z2, snn, 1, n, st));
+    NAO_CUDA_TRY(ctx, launch_ns_correct(n, nprob, mP, Z, G, n, snn, Z2, st));
   }
   NAO_STAGE("backtransform", 1, launch_backtransform(n, nprob, mP, nullptr, Hp, n, snn, tauH, n, Z2, n, snn, wH, 0, V, n, snn, st));
   if (C) {

@@ -4,8 +4,9 @@
 // scaled to unit 2-norm.  For the overlap matrix the same pass applies Part 2's canonical
 // orthogonalization X = U_m diag(s_m^{-1/2}) (only the kept, largest, eigenpairs).
 //
-// One warp per output column; the column lives in shared memory with a fixed row-to-lane
-// ownership (row r belongs to lane r mod 32) so the warp needs no barriers.
+// One warp per output column (templated for several); the columns live in shared memory
+// with a fixed row-to-lane ownership (row r belongs to lane r mod 32) so the warp needs no
+// barriers.
 #include "nao_internal.cuh"
 
 namespace {
@@ -16,6 +17,9 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
+// CPW columns per warp share every reflector load (4; fewer only when 4 columns of the
+// largest n would not fit in shared memory).
+template <int CPW>
 __global__ void backtr_kernel(int n, const int32_t* __restrict__ size, const int32_t* __restrict__ ncols,
                               const z64* __restrict__ Abase, int lda, long long strideA,
                               const z64* __restrict__ taubase, long long strideV, const double* __restrict__ Zbase,
@@ -26,42 +30,55 @@ __global__ void backtr_kernel(int n, const int32_t* __restrict__ size, const int
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int m = size ? size[p] : n;
   const int nc = ncols ? ncols[p] : m;
-  const int c = blockIdx.y * wpb + wid;
-  if (c >= nc || m <= 0) return;
-  const int j = (m - nc) + c;  // source eigenpair
-  z64* u = colbuf + (size_t)wid * n;
+  const int c0 = (blockIdx.y * wpb + wid) * CPW;
+  if (c0 >= nc || m <= 0) return;
+  const int ncw = min(CPW, nc - c0);
+  z64* u = colbuf + (size_t)wid * CPW * n;  // u[q * n + r]
   const z64* A = Abase + (size_t)p * strideA;
   const z64* tau = taubase + (size_t)p * strideV;
-  const double* z = Zbase + (size_t)p * strideZ + (size_t)j * ldz;
-  for (int r = lane; r < m; r += 32) u[r] = zmk(z[r], 0.0);
+  const int j0 = (m - nc) + c0;  // first source eigenpair
+  const double* Zp = Zbase + (size_t)p * strideZ;
+#pragma unroll
+  for (int q = 0; q < CPW; ++q) {
+    const double* z = Zp + (size_t)(j0 + (q < ncw ? q : 0)) * ldz;
+    for (int r = lane; r < m; r += 32) u[q * n + r] = zmk(q < ncw ? z[r] : 0.0, 0.0);
+  }
   for (int i = m - 2; i >= 0; --i) {
     const z64 t = tau[i];
     if (t.x == 0.0 && t.y == 0.0) continue;
     const z64* v = A + (size_t)i * lda;  // v(i+1) = 1, v(r) = A(r, i) for r >= i+2
     const int r0 = (i + 1) + ((lane - (i + 1)) & 31);
-    double sre = 0.0, sim = 0.0;
+    double sre[CPW], sim[CPW];
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) sre[q] = sim[q] = 0.0;
     for (int r = r0; r < m; r += 32) {
       const z64 vr = (r == i + 1) ? zmk(1.0, 0.0) : v[r];
-      const z64 ur = u[r];
-      // conj(vr) * ur
-      sre = fma(vr.x, ur.x, fma(vr.y, ur.y, sre));
-      sim = fma(vr.x, ur.y, fma(-vr.y, ur.x, sim));
+#pragma unroll
+      for (int q = 0; q < CPW; ++q) {
+        const z64 ur = u[q * n + r];
+        sre[q] = fma(vr.x, ur.x, fma(vr.y, ur.y, sre[q]));  // conj(vr) * ur
+        sim[q] = fma(vr.x, ur.y, fma(-vr.y, ur.x, sim[q]));
+      }
     }
-    sre = wsum(sre);
-    sim = wsum(sim);
-    const z64 f = zmul(t, zmk(sre, sim));  // u -= v * (tau * v^H u)
+    z64 f[CPW];
+#pragma unroll
+    for (int q = 0; q < CPW; ++q) f[q] = zmul(t, zmk(wsum(sre[q]), wsum(sim[q])));  // tau * v^H u
     for (int r = r0; r < m; r += 32) {
       const z64 vr = (r == i + 1) ? zmk(1.0, 0.0) : v[r];
-      u[r] = zsub(u[r], zmul(vr, f));
+#pragma unroll
+      for (int q = 0; q < CPW; ++q) u[q * n + r] = zsub(u[q * n + r], zmul(vr, f[q]));
     }
   }
-  double nrm = 0.0;
-  for (int r = lane; r < m; r += 32) nrm += zabs2(u[r]);
-  nrm = wsum(nrm);
-  double sc = 1.0 / sqrt(nrm);
-  if (use_rsqrt) sc /= sqrt(wbase[(size_t)p * strideV + j]);
-  z64* out = Ubase + (size_t)p * strideU + (size_t)c * ldu;
-  for (int r = lane; r < m; r += 32) out[r] = zscale(u[r], sc);
+  for (int q = 0; q < ncw; ++q) {
+    const int j = j0 + q;
+    double nrm = 0.0;
+    for (int r = lane; r < m; r += 32) nrm += zabs2(u[q * n + r]);
+    nrm = wsum(nrm);
+    double sc = 1.0 / sqrt(nrm);
+    if (use_rsqrt) sc /= sqrt(wbase[(size_t)p * strideV + j]);
+    z64* out = Ubase + (size_t)p * strideU + (size_t)(c0 + q) * ldu;
+    for (int r = lane; r < m; r += 32) out[r] = zscale(u[q * n + r], sc);
+  }
 }
 
 __global__ void count_kept_kernel(int n, int nprob, const double* __restrict__ w, long long strideV, double s_cut,
@@ -132,14 +149,29 @@ cudaError_t launch_backtransform(int n, int nprob, const int32_t* size, const in
                                  long long strideA, const z64* tau, long long strideV, const double* Z, int ldz,
                                  long long strideZ, const double* w, int use_rsqrt_scale, z64* U, int ldu,
                                  long long strideU, cudaStream_t st) {
+  const size_t limit = 200 * 1024;
+  // One column per warp: a wider warp footprint costs more occupancy (fewer warps per SM to
+  // hide the per-reflector reduction latency) than it saves in reflector loads.
+  const int cpw = 1;
   int wpb = 8;
-  while (wpb > 1 && (size_t)wpb * n * sizeof(z64) > 200 * 1024) --wpb;
-  size_t smem = (size_t)wpb * n * sizeof(z64);
-  cudaError_t err = cudaFuncSetAttribute(backtr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  dim3 grid(nprob, (n + wpb - 1) / wpb);
-  backtr_kernel<<<grid, 32 * wpb, smem, st>>>(n, size, ncols, A, lda, strideA, tau, strideV, Z, ldz, strideZ, w,
-                                               use_rsqrt_scale, U, ldu, strideU);
+  while (wpb > 1 && (size_t)wpb * cpw * n * sizeof(z64) > limit) --wpb;
+  size_t smem = (size_t)wpb * cpw * n * sizeof(z64);
+  const int cols_per_block = wpb * cpw;
+  dim3 grid(nprob, (n + cols_per_block - 1) / cols_per_block);
+  cudaError_t err;
+#define NAO_BT_LAUNCH(K)                                                                                      \
+  err = cudaFuncSetAttribute(backtr_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
+  if (err != cudaSuccess) return err;                                                                       \
+  backtr_kernel<K><<<grid, 32 * wpb, smem, st>>>(n, size, ncols, A, lda, strideA, tau, strideV, Z, ldz, strideZ, \
+                                                 w, use_rsqrt_scale, U, ldu, strideU);
+  if (cpw == 4) {
+    NAO_BT_LAUNCH(4)
+  } else if (cpw == 2) {
+    NAO_BT_LAUNCH(2)
+  } else {
+    NAO_BT_LAUNCH(1)
+  }
+#undef NAO_BT_LAUNCH
   return cudaGetLastError();
 }
 

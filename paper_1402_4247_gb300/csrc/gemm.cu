@@ -43,6 +43,7 @@ gemm_kernel(GemmDims dims, T alpha, GemmOperand A, GemmOperand B, T beta, T* __r
   const int K = dims.Kp ? dims.Kp[p] : dims.K;
   const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
   if (i0 >= M || j0 >= Nn) return;
+  if (dims.lower && j0 > i0 + BM - 1) return;  // tile entirely above the diagonal
   const T* Ap = (const T*)A.ptr + (size_t)(A.map ? A.map[p] : p) * A.bs;
   const T* Bp = (const T*)B.ptr + (size_t)(B.map ? B.map[p] : p) * B.bs;
   T* Cp = C + (size_t)p * Cbs;
@@ -125,7 +126,80 @@ cudaError_t launch_gemm_t(int nprob, GemmDims dims, T alpha, GemmOperand A, Gemm
   return cudaGetLastError();
 }
 
+// Z2 = Z - 0.5 Z (G - I), G symmetric from its lower triangle; FP32 product.
+constexpr int NB = 64, NK = 16;
+__global__ void __launch_bounds__(256)
+ns_correct_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ Zb, const double* __restrict__ Gb,
+                  int ld, long long stride, double* __restrict__ Z2b) {
+  __shared__ float Zs[NK][NB + 1];
+  __shared__ float Es[NK][NB + 1];
+  const int p = blockIdx.z;
+  const int m = size ? size[p] : n;
+  const int i0 = blockIdx.y * NB, j0 = blockIdx.x * NB;
+  if (i0 >= m || j0 >= m) return;
+  const double* Z = Zb + (size_t)p * stride;
+  const double* G = Gb + (size_t)p * stride;
+  double* Z2 = Z2b + (size_t)p * stride;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  for (int k0 = 0; k0 < m; k0 += NK) {
+#pragma unroll
+    for (int s = 0; s < (NB * NK) / 256; ++s) {
+      const int e = tid + 256 * s;
+      const int row = e % NB, kk = e / NB;  // Z(i0+row, k0+kk): column-major, rows fast
+      const int gi = i0 + row, gk = k0 + kk;
+      Zs[kk][row] = (gi < m && gk < m) ? (float)Z[(size_t)gk * ld + gi] : 0.f;
+      const int col = e % NB, kk2 = e / NB;  // E(k0+kk2, j0+col)
+      const int gj = j0 + col, gk2 = k0 + kk2;
+      float ev = 0.f;
+      if (gj < m && gk2 < m) {
+        double g = (gk2 >= gj) ? G[(size_t)gj * ld + gk2] : G[(size_t)gk2 * ld + gj];
+        if (gk2 == gj) g -= 1.0;
+        ev = (float)g;
+      }
+      Es[kk2][col] = ev;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < NK; ++kk) {
+      float av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = Zs[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Es[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int gi = i0 + ty + 16 * a;
+    if (gi >= m) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int gj = j0 + tx + 16 * b;
+      if (gj >= m) continue;
+      const size_t o = (size_t)gj * ld + gi;
+      Z2[o] = Z[o] - 0.5 * (double)acc[a][b];
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_ns_correct(int n, int nprob, const int32_t* size, const double* Z, const double* G, int ld,
+                              long long stride, double* Z2, cudaStream_t st) {
+  dim3 grid((n + NB - 1) / NB, (n + NB - 1) / NB, nprob);
+  ns_correct_kernel<<<grid, 256, 0, st>>>(n, size, Z, G, ld, stride, Z2);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_zgemm(int nprob, GemmDims dims, z64 alpha, GemmOperand A, GemmOperand B, z64 beta, z64* C,
                          long long Cbs, long long Crs, long long Ccs, cudaStream_t st) {

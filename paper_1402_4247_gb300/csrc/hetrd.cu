@@ -1,5 +1,5 @@
 // Eigen_HH step 1 (Sec. 3, Procedures 1-6): Householder reduction of a Hermitian matrix to
-// real symmetric tridiagonal form, one thread block per problem.
+// real symmetric tridiagonal form.
 //
 // Column i: x = A(i+1:m, i) (Procedure 1); a reflector H_i = I - tau v v^H with v(0) = 1 and
 // a REAL beta, H_i^H x = beta e_1, is formed from |x| (Procedure 2) and kept in place for the
@@ -7,15 +7,31 @@
 // (Procedure 5); A22 <- A22 - v w^H - w v^H (Procedure 6).  Choosing beta real removes the
 // separate phase pass: Q^H A Q = T with Q = H_0 H_1 ... H_{m-2}.
 //
-// Storage: full Hermitian matrix, column-major (element (r, c) at A[r + c*ld]); both
-// triangles are kept current so that the Hermitian matrix-vector product streams whole
-// columns.  Output: d[0..m), e[0..m-1) (e[m-1] = 0), tau[0..m) (tau[m-1] = 0), and v_i in
-// A(i+2:m, i).
+// GB300 layout of the work.  On this chip the FP64 pipe (1/64 of FP32) bounds the kernel,
+// so the design minimises FP64 operations and spreads one matrix over several SMs:
+//  * only the lower triangle is stored and updated (column-major, element (r, c) at
+//    A[r + c*ld], r >= c): the Hermitian product reads row r's part left of the diagonal
+//    and column r's part below it, so the rank-2 update costs 8 (m-i)^2 flops, not 16;
+//  * a thread-block cluster of C blocks (C = 1..8) shares one matrix: rows are dealt out in
+//    pairs (r, mt-1-r) so every pair costs the same in both the product and the update;
+//  * each block computes p for its rows, the pieces meet through distributed shared memory,
+//    and every block then forms the full w itself (identical, fixed-order arithmetic);
+//  * each pair's work (its full Hermitian row: row part + column part, and its share of the
+//    rank-2 update) is split over K threads so that ~1000 threads per block keep the FP64
+//    pipe fed; the K partial sums meet in shared memory in a fixed order;
+//  * two cluster barriers per column (release/acquire at cluster scope, so rows written by
+//    another block in the previous column are visible to ordinary loads afterwards).
+// Output: d[0..m), e[0..m-1) (e[m-1] = 0), tau[0..m) (tau[m-1] = 0), v_i in A(i+2:m, i).
+#include <cooperative_groups.h>
+
 #include "nao_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
 constexpr int HT_THREADS = 1024;
+constexpr int HT_MAXK = 8;  // threads per row pair
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -41,29 +57,38 @@ __device__ __forceinline__ double2 block_sum2(double a, double b, double* red) {
   return make_double2(a, b);
 }
 
+
+// first pair index of block k when npairs pairs are dealt to C blocks
+__device__ __forceinline__ int pair_start(int k, int npairs, int C) { return (int)(((long long)k * npairs) / C); }
+
 __global__ void __launch_bounds__(HT_THREADS)
 hetrd_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Abase, int ld, long long strideA,
              double* __restrict__ dbase, double* __restrict__ ebase, z64* __restrict__ taubase, long long strideV) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
   extern __shared__ z64 sm[];
-  z64* v = sm;          // [n]
-  z64* w = sm + n;      // [n]
-  z64* part = sm + 2 * n;  // [HT_THREADS]
+  z64* v = sm;           // [n] reflector of the current column (trailing coordinates)
+  z64* w = sm + n;       // [n] p, then w
+  z64* pown = sm + 2 * n;  // [n] p for this block's rows, read by the other blocks
+  z64* part = sm + 3 * n;  // [2 * HT_THREADS] partial sums of the K threads of each pair
   __shared__ double red[64];
   __shared__ z64 s_tau, s_scale;
+  __shared__ double s_beta;
 
-  const int p = blockIdx.x;
+  const int p = blockIdx.x / C;
   const int m = size ? size[p] : n;
   z64* A = Abase + (size_t)p * strideA;
   double* d = dbase + (size_t)p * strideV;
   double* e = ebase + (size_t)p * strideV;
   z64* tau = taubase + (size_t)p * strideV;
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (m <= 0) return;
+  if (m <= 0) return;  // uniform over the cluster
 
   for (int i = 0; i < m - 1; ++i) {
-    const int mt = m - i - 1;          // order of the trailing block A22 = A(i+1:m, i+1:m)
-    z64* col = A + (size_t)i * ld;     // column i
-    // Procedure 1-2: |x(1:)|^2 of x = A(i+1:m, i)
+    const int mt = m - i - 1;  // order of the trailing block A22 = A(i+1:m, i+1:m)
+    const z64* col = A + (size_t)i * ld;
+    // Procedures 1-2 (every block, redundantly): |x(1:)|^2 of x = A(i+1:m, i)
     double s = 0.0;
     for (int r = i + 2 + tid; r < m; r += nt) s += zabs2(col[r]);
     s = block_sum2(s, 0.0, red).x;
@@ -85,80 +110,120 @@ hetrd_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Abase, i
       }
       s_tau = t;
       s_scale = scale;
-      d[i] = A[(size_t)i * ld + i].x;
-      e[i] = beta;
-      tau[i] = t;
-      col[i + 1] = zmk(beta, 0.0);
+      s_beta = beta;
+      if (rank == 0) {
+        d[i] = A[(size_t)i * ld + i].x;
+        e[i] = beta;
+        tau[i] = t;
+      }
     }
     __syncthreads();
     const z64 t = s_tau;
     const z64 scale = s_scale;
-    // Procedure 3: v (implicit leading 1) kept in A(i+2:m, i) and in shared memory
-    for (int r = i + 1 + tid; r < m; r += nt) {
-      z64 val;
-      if (r == i + 1) {
-        val = zmk(1.0, 0.0);
-      } else {
-        val = zmul(col[r], scale);
-        col[r] = val;
-      }
-      v[r - i - 1] = val;
-    }
+    // Procedure 3: v in shared memory (trailing coordinates, v[0] = 1)
+    for (int r = tid; r < mt; r += nt) v[r] = (r == 0) ? zmk(1.0, 0.0) : zmul(col[i + 1 + r], scale);
     __syncthreads();
-    if (t.x == 0.0 && t.y == 0.0) continue;  // H_i = I (uniform branch: s_tau is shared)
+    const bool active = !(t.x == 0.0 && t.y == 0.0);  // H_i = I otherwise (uniform)
 
-    // Procedure 4: p = tau * A22 v.  Threads own rows (coalesced column reads); when the
-    // block is narrower than the thread count, CS column groups split the columns.
+    // Procedure 4: p = A22 v for this block's row pairs (lower triangle only).  Thread
+    // (k, g) covers the k-th slice of the column range of both rows of pair g.
     z64* A22 = A + (size_t)(i + 1) * ld + (i + 1);
-    const int rows = mt < nt ? mt : nt;
-    const int CS = mt < nt ? nt / mt : 1;
-    const int g = tid / rows, r0 = tid - g * rows;
-    if (g < CS) {
-      for (int r = r0; r < mt; r += rows) {
-        z64 acc = zmk(0.0, 0.0);
-        const z64* Ar = A22 + r;
-        for (int c = g; c < mt; c += CS) acc = zfma(Ar[(size_t)c * ld], v[c], acc);
-        if (CS == 1) w[r] = acc;
-        else part[g * mt + r] = acc;
-      }
-    }
-    __syncthreads();
-    if (CS > 1) {
-      for (int r = tid; r < mt; r += nt) {
-        z64 acc = zmk(0.0, 0.0);
-        for (int gg = 0; gg < CS; ++gg) acc = zadd(acc, part[gg * mt + r]);
-        w[r] = acc;
+    const int npairs = (mt + 1) >> 1;
+    const int g0 = pair_start(rank, npairs, C), g1 = pair_start(rank + 1, npairs, C);
+    const int P = g1 - g0;
+    int K = P > 0 ? nt / P : 1;
+    K = K < 1 ? 1 : (K > HT_MAXK ? HT_MAXK : K);
+    if (active) {
+      for (int tt = tid; tt < K * P; tt += nt) {
+        const int k = tt / P, gl = tt - k * P, g = g0 + gl;
+        const int c0 = (int)(((long long)k * mt) / K), c1 = (int)(((long long)(k + 1) * mt) / K);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = h ? mt - 1 - g : g;
+          z64 acc = zmk(0.0, 0.0);
+          if (!(h && r == g)) {
+            // row part: A(r, c) for c <= r (coalesced over consecutive r)
+            const int ce = min(c1, r + 1);
+            for (int c = c0; c < ce; ++c) acc = zfma(A22[(size_t)c * ld + r], v[c], acc);
+            // column part: conj(A(c, r)) for c > r (column r, contiguous per thread)
+            const z64* colr = A22 + (size_t)r * ld;
+            for (int c = max(c0, r + 1); c < c1; ++c) acc = zcfma(colr[c], v[c], acc);
+          }
+          part[(size_t)k * 2 * P + 2 * gl + h] = acc;
+        }
       }
       __syncthreads();
+      for (int tt = tid; tt < 2 * P; tt += nt) {
+        const int gl = tt >> 1, h = tt & 1, g = g0 + gl;
+        const int r = h ? mt - 1 - g : g;
+        if (h && r == g) continue;
+        z64 acc = zmk(0.0, 0.0);
+        for (int k = 0; k < K; ++k) acc = zadd(acc, part[(size_t)k * 2 * P + tt]);
+        pown[r] = acc;
+      }
     }
-    // p = tau * (A22 v); dot = p^H v
-    double dre = 0.0, dim = 0.0;
-    for (int r = tid; r < mt; r += nt) {
-      const z64 pr = zmul(t, w[r]);
-      w[r] = pr;
-      const z64 c = zcfma(pr, v[r], zmk(0.0, 0.0));
-      dre += c.x;
-      dim += c.y;
+    cluster.sync();  // every block's p pieces are written; every block is done reading column i
+    if (rank == 0) {  // Procedure 3: store v below the subdiagonal of column i
+      z64* colw = A + (size_t)i * ld;
+      for (int r = tid; r < mt; r += nt) colw[i + 1 + r] = (r == 0) ? zmk(s_beta, 0.0) : v[r];
     }
-    const double2 dot = block_sum2(dre, dim, red);
-    // Procedure 5: w = p - (tau/2) (p^H v) v
-    const z64 alpha2 = zscale(zmul(t, zmk(dot.x, dot.y)), -0.5);
-    for (int r = tid; r < mt; r += nt) w[r] = zfma(alpha2, v[r], w[r]);
-    __syncthreads();
-    // Procedure 6: A22 -= v w^H + w v^H (both triangles)
-    const long long tot = (long long)mt * mt;
-    for (long long idx = tid; idx < tot; idx += nt) {
-      const int c = (int)(idx / mt), r = (int)(idx - (long long)c * mt);
-      z64 a = A22[(size_t)c * ld + r];
-      const z64 vr = v[r], wr = w[r], vc = v[c], wc = w[c];
-      // a -= vr * conj(wc) + wr * conj(vc)
-      a.x -= vr.x * wc.x + vr.y * wc.y + wr.x * vc.x + wr.y * vc.y;
-      a.y -= vr.y * wc.x - vr.x * wc.y + wr.y * vc.x - wr.x * vc.y;
-      A22[(size_t)c * ld + r] = a;
+    if (active) {
+      // gather p from its owners; p := tau * p; dot = p^H v
+      double dre = 0.0, dim = 0.0;
+      for (int g = tid; g < npairs; g += nt) {
+        int k = 0;
+        while (k + 1 < C && pair_start(k + 1, npairs, C) <= g) ++k;
+        const z64* src = cluster.map_shared_rank(pown, k);
+        const int ra = g, rb = mt - 1 - g;
+        z64 pa = zmul(t, src[ra]);
+        w[ra] = pa;
+        z64 c1 = zcfma(pa, v[ra], zmk(0.0, 0.0));
+        dre += c1.x;
+        dim += c1.y;
+        if (rb != ra) {
+          z64 pb = zmul(t, src[rb]);
+          w[rb] = pb;
+          z64 c2 = zcfma(pb, v[rb], zmk(0.0, 0.0));
+          dre += c2.x;
+          dim += c2.y;
+        }
+      }
+      const double2 dot = block_sum2(dre, dim, red);
+      // Procedure 5: w = p - (tau/2) (p^H v) v
+      const z64 alpha2 = zscale(zmul(t, zmk(dot.x, dot.y)), -0.5);
+      for (int r = tid; r < mt; r += nt) w[r] = zfma(alpha2, v[r], w[r]);
+      __syncthreads();
+      // Procedure 6: A22 -= v w^H + w v^H on the lower triangle, enumerated column by column
+      // (column c holds rows c..mt-1); the cluster's blocks take equal contiguous shares and
+      // consecutive threads consecutive rows, so every access is coalesced.
+      const long long ntri = (long long)mt * (mt + 1) / 2;
+      const long long q0 = (ntri * rank) / C, q1 = (ntri * (rank + 1)) / C;
+      long long q = q0 + tid;
+      if (q < q1) {
+        // locate element q: column c with start(c) = c*mt - c(c-1)/2 <= q < start(c+1)
+        int c = (int)((2.0 * mt + 1.0 - sqrt((2.0 * mt + 1.0) * (2.0 * mt + 1.0) - 8.0 * (double)q)) * 0.5);
+        if (c < 0) c = 0;
+        while (c > 0 && (long long)c * mt - (long long)c * (c - 1) / 2 > q) --c;
+        while ((long long)(c + 1) * mt - (long long)(c + 1) * c / 2 <= q) ++c;
+        int r = c + (int)(q - ((long long)c * mt - (long long)c * (c - 1) / 2));
+        for (; q < q1; q += nt) {
+          z64* ap = A22 + (size_t)c * ld + r;
+          z64 a = *ap;
+          const z64 vr = v[r], wr = w[r], vc = v[c], wc = w[c];
+          a.x -= vr.x * wc.x + vr.y * wc.y + wr.x * vc.x + wr.y * vc.y;
+          a.y -= vr.y * wc.x - vr.x * wc.y + wr.y * vc.x - wr.x * vc.y;
+          *ap = a;
+          r += nt;  // advance by nt elements along the column-major enumeration
+          while (r >= mt && c < mt) {
+            r -= mt - c - 1;  // leave column c (rows c..mt-1), enter column c+1 at row c+1
+            ++c;
+          }
+        }
+      }
     }
-    __syncthreads();
+    cluster.sync();  // the update is complete (and the remote p pieces are no longer read)
   }
-  if (tid == 0) {
+  if (tid == 0 && rank == 0) {
     d[m - 1] = A[(size_t)(m - 1) * ld + (m - 1)].x;
     e[m - 1] = 0.0;
     tau[m - 1] = zmk(0.0, 0.0);
@@ -167,11 +232,28 @@ hetrd_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Abase, i
 
 }  // namespace
 
+int hetrd_cluster_size(int nprob, int num_sms) {
+  int c = 1;
+  while (c < 8 && (long long)nprob * c * 2 <= num_sms) c *= 2;
+  return c;
+}
+
 cudaError_t launch_hetrd(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA, double* d,
-                         double* e, z64* tau, long long strideV, cudaStream_t st) {
-  size_t smem = sizeof(z64) * (2 * (size_t)n + HT_THREADS);
+                         double* e, z64* tau, long long strideV, int cluster, cudaStream_t st) {
+  size_t smem = sizeof(z64) * (3 * (size_t)n + 2 * HT_THREADS);
   cudaError_t err = cudaFuncSetAttribute(hetrd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  hetrd_kernel<<<nprob, HT_THREADS, smem, st>>>(n, size, A, ld, strideA, d, e, tau, strideV);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nprob * cluster));
+  cfg.blockDim = dim3(HT_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, hetrd_kernel, n, size, A, ld, strideA, d, e, tau, strideV);
 }

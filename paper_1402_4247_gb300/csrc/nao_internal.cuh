@@ -99,8 +99,11 @@ cudaError_t launch_herm_fill(int n, int nprob, const z64* src, long long src_str
 
 // Eigen_HH step 1: Householder tridiagonalization, one block per problem, in place on the
 // full Hermitian column-major matrix A (ld).  size[p] (or n when size == null) is the order.
+// Only the lower triangle of A is read and updated.  `cluster` blocks (1..8, a thread-block
+// cluster) share each matrix; hetrd_cluster_size picks it from the problem count.
+int hetrd_cluster_size(int nprob, int num_sms);
 cudaError_t launch_hetrd(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA,
-                         double* d, double* e, z64* tau, long long strideV, cudaStream_t st);
+                         double* d, double* e, z64* tau, long long strideV, int cluster, cudaStream_t st);
 
 // Eigen_HH step 2: eigenvalues w (ascending) and orthonormal eigenvectors Z (column-major,
 // ld) of tridiag(e, d, e) by bisection + inverse iteration.  scratch: see stein_scratch_doubles.
@@ -129,11 +132,19 @@ struct GemmOperand {
 struct GemmDims {
   int M, N, K;                          // maxima (grid sizing) / fixed values
   const int32_t *Mp, *Np, *Kp;          // per-problem overrides (nullable)
+  int lower = 0;                        // 1: only output tiles that meet the lower triangle
 };
 cudaError_t launch_zgemm(int nprob, GemmDims dims, z64 alpha, GemmOperand A, GemmOperand B, z64 beta,
                          z64* C, long long Cbs, long long Crs, long long Ccs, cudaStream_t st);
 cudaError_t launch_dgemm(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta,
                          double* C, long long Cbs, long long Crs, long long Ccs, cudaStream_t st);
+
+// Newton-Schulz re-orthogonalisation, second half: Z2 = Z - Z E / 2 with E = G - I and G
+// = Z^T Z given by its lower triangle (column-major, ld).  E is ~1e-9, so the product runs
+// in FP32 on the FP32 pipe; its rounding (~1e-7 relative of a 1e-9 term) stays below FP64
+// rounding of Z.
+cudaError_t launch_ns_correct(int n, int nprob, const int32_t* size, const double* Z, const double* G, int ld,
+                              long long stride, double* Z2, cudaStream_t st);
 
 // Small helpers of the gen-eig chain.
 cudaError_t launch_count_kept(int n, int nprob, const double* w, long long strideV, double s_cut,
