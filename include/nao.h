@@ -45,6 +45,14 @@ enum {
 
 enum { NAO_FP64 = 0, NAO_MIXED_TF32 = 1, NAO_MIXED_BF16X3 = 2 };
 
+/* How the FP64 matrix products of the band step are computed (both FP64-accurate). */
+enum {
+  NAO_GEMM_FP64 = 0,  /* FP64 FMA on the CUDA cores                                        */
+  NAO_GEMM_TC = 1     /* BF16 tensor cores on exact 6-bit digit planes of the FP64 operands
+                         (60-bit splitting, FP32-exact partial sums; FP64-level accuracy);
+                         used where the contraction length allows (2K <= 2048), else FP64 */
+};
+
 /* Library / context ------------------------------------------------------------------ */
 
 /* Create a context bound to CUDA device `device`.  *out receives the handle.             */
@@ -56,6 +64,20 @@ void nao_destroy(nao_ctx* ctx);
 const char* nao_last_error(const nao_ctx* ctx);
 /* Bytes of device workspace currently held by the context.                              */
 size_t nao_workspace_bytes(const nao_ctx* ctx);
+
+/* Select the product method of this context's band-step calls (default NAO_GEMM_TC).    */
+int nao_set_gemm_method(nao_ctx* ctx, int method);
+
+/* Batched complex GEMM (the products of Parts 3, 4 and 6):
+ *   C[p] = alpha op(A[p]) op(B[p]) + beta C[p],  p = 0..nprob-1, real alpha and beta.
+ * Row-major storage: A[p] at A + p*strideA with leading dimension lda (elements); op(X) is
+ * X (trans = 0), X^T (1) or X^H (2).  op(A) is M x K, op(B) is K x N, C[p] is M x N with
+ * leading dimension ldc.  method: NAO_GEMM_FP64 or NAO_GEMM_TC (NAO_E_INVALID if 2K > 2048
+ * for NAO_GEMM_TC).  Device arrays; stream-ordered.                                       */
+int nao_zgemm(nao_ctx* ctx, int method, int nprob, int M, int N, int K, double alpha,
+              const nao_c128* A, int lda, long long strideA, int transA,
+              const nao_c128* B, int ldb, long long strideB, int transB, double beta,
+              nao_c128* C, int ldc, long long strideC, void* stream);
 
 /* Part 1: k dependence (Sec. 3, Part 1) ---------------------------------------------- *
  * Mk[a][q][i][j] = sum_r exp(+2 pi i kpts[q].R[r]) MR[a][r][i][j]   for i >= j, and

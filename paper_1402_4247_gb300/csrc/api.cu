@@ -122,13 +122,27 @@ __global__ void gather_m_kernel(int nprob, const int32_t* map, const int32_t* mS
 }
 
 __global__ void finish_status_kernel(int nprob, const int32_t* mP, const int32_t* statP, const int32_t* statH,
-                                     int32_t* m_kept, int32_t* status) {
+                                     const int* flags, int32_t* m_kept, int32_t* status) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nprob) return;
   m_kept[p] = mP[p];
   int32_t s = statP[p];
   if (s == 0) s = statH[p];
+  if (s == 0 && flags[0]) s = NAO_E_TIMEOUT;
   status[p] = s;
+}
+
+// One batched complex product of the band step, on the tensor cores (digit planes) when the
+// context asks for it and the contraction length allows, else on the FP64 CUDA cores.
+cudaError_t run_zgemm(nao_ctx* ctx, const char* stage, int nprob, GemmDims d, double alpha, GemmOperand A,
+                      GemmOperand B, double beta, z64* C, long long Cbs, long long Crs, long long Ccs, void* ozws,
+                      cudaStream_t st) {
+  if (ctx->gemm_method == NAO_GEMM_TC && ozws && zgemm_oz_supported(d)) {
+    NaoStage stage_(ctx, stage, st, 3);
+    return launch_zgemm_oz(nprob, d, alpha, A, B, beta, C, Cbs, Crs, Ccs, ozws, ctx->dev_flags, st);
+  }
+  NaoStage stage_(ctx, stage, st, 1);
+  return launch_zgemm(nprob, d, zmk(alpha, 0.0), A, B, zmk(beta, 0.0), C, Cbs, Crs, Ccs, st);
 }
 
 bool is_device_ptr(const void* p) {
@@ -162,6 +176,12 @@ int nao_init(nao_ctx** out, int device) {
     return nao_fail(nullptr, NAO_E_CUDA, "nao_init: %s", cudaGetErrorString(e));
   }
   c->num_sms = prop.multiProcessorCount;
+  e = cudaMalloc(&c->dev_flags, 64 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->dev_flags, 0, 64 * sizeof(int));
+  if (e != cudaSuccess) {
+    delete c;
+    return nao_fail(nullptr, NAO_E_CUDA, "nao_init: %s", cudaGetErrorString(e));
+  }
   *out = c;
   return NAO_OK;
 }
@@ -173,6 +193,7 @@ void nao_destroy(nao_ctx* ctx) {
     drain_pending(ctx);
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->dev_flags) cudaFree(ctx->dev_flags);
   }
   delete ctx;
 }
@@ -201,6 +222,41 @@ int nao_profile_read(nao_ctx* ctx, int max, const char** names, double* ms, int6
 }
 
 int64_t nao_launch_count(const nao_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int nao_set_gemm_method(nao_ctx* ctx, int method) {
+  if (!ctx) return nao_fail(nullptr, NAO_E_INVALID, "nao_set_gemm_method: ctx is NULL");
+  if (method != NAO_GEMM_FP64 && method != NAO_GEMM_TC)
+    return nao_fail(ctx, NAO_E_INVALID, "nao_set_gemm_method: unknown method %d", method);
+  ctx->gemm_method = method;
+  return NAO_OK;
+}
+
+int nao_zgemm(nao_ctx* ctx, int method, int nprob, int M, int N, int K, double alpha, const nao_c128* A, int lda,
+              long long strideA, int transA, const nao_c128* B, int ldb, long long strideB, int transB, double beta,
+              nao_c128* C, int ldc, long long strideC, void* stream) {
+  if (!ctx) return nao_fail(nullptr, NAO_E_INVALID, "nao_zgemm: ctx is NULL");
+  if (nprob < 1 || M < 1 || N < 1 || K < 1 || !A || !B || !C) return nao_fail(ctx, NAO_E_INVALID, "nao_zgemm: bad sizes");
+  if (transA < 0 || transA > 2 || transB < 0 || transB > 2) return nao_fail(ctx, NAO_E_INVALID, "nao_zgemm: bad trans");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = as_stream(stream);
+  GemmOperand a{A, strideA, transA ? 1 : lda, transA ? lda : 1, transA == 2, nullptr};
+  GemmOperand b{B, strideB, transB ? 1 : ldb, transB ? ldb : 1, transB == 2, nullptr};
+  GemmDims d{M, N, K, nullptr, nullptr, nullptr, 0};
+  if (method == NAO_GEMM_TC) {
+    if (!zgemm_oz_supported(d)) return nao_fail(ctx, NAO_E_INVALID, "nao_zgemm: K = %d too long for NAO_GEMM_TC", K);
+    WsPlan P;
+    const size_t o = P.take<char>(zgemm_oz_workspace(nprob, d));
+    int rc = nao_ws_reserve(ctx, P.off);
+    if (rc) return rc;
+    NAO_STAGE("zgemm_tc", 3, launch_zgemm_oz(nprob, d, alpha, a, b, beta, (z64*)C, strideC, ldc, 1,
+                                            (char*)ctx->ws + o, ctx->dev_flags, st));
+  } else if (method == NAO_GEMM_FP64) {
+    NAO_STAGE("zgemm_fp64", 1, launch_zgemm(nprob, d, zmk(alpha, 0.0), a, b, zmk(beta, 0.0), (z64*)C, strideC, ldc, 1, st));
+  } else {
+    return nao_fail(ctx, NAO_E_INVALID, "nao_zgemm: unknown method %d", method);
+  }
+  return NAO_OK;
+}
 
 const char* nao_last_error(const nao_ctx* ctx) { return ctx ? ctx->last_error.c_str() : g_init_error.c_str(); }
 
@@ -249,6 +305,9 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
                oeH = P.take<double>((size_t)n * nprob), owH = P.take<double>((size_t)n * nprob);
   const size_t omP = P.take<int32_t>(nprob), onbP = P.take<int32_t>(nprob), ostP = P.take<int32_t>(nprob),
                ostH = P.take<int32_t>(nprob);
+  const GemmDims dmax{n, n, n, nullptr, nullptr, nullptr, 0};
+  const bool use_tc = ctx->gemm_method == NAO_GEMM_TC && zgemm_oz_supported(dmax);
+  const size_t oOz = P.take<char>(use_tc ? zgemm_oz_workspace(nprob, dmax) : 1);
   int rc = nao_ws_reserve(ctx, P.off);
   if (rc) return rc;
   char* ws = (char*)ctx->ws;
@@ -263,8 +322,8 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   double *dH = (double*)(ws + odH), *eH = (double*)(ws + oeH), *wH = (double*)(ws + owH);
   int32_t *mP = (int32_t*)(ws + omP), *nbP = (int32_t*)(ws + onbP), *stP = (int32_t*)(ws + ostP),
           *stH = (int32_t*)(ws + ostH);
+  void* ozws = use_tc ? (void*)(ws + oOz) : nullptr;
   const long long snn = (long long)nn;
-  const z64 one = zmk(1.0, 0.0), zero = zmk(0.0, 0.0);
 
   // ---- Part 2: Eigen_HH(S) -> s, U;  X = U_m s_m^{-1/2}
   NAO_STAGE("herm_fill", 1, launch_herm_fill(n, nSe, (const z64*)S, snn, nullptr, AS, n, snn, st));
@@ -290,11 +349,11 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   NAO_STAGE("herm_fill", 1, launch_herm_fill(n, nprob, (const z64*)H, snn, nullptr, Hf, n, snn, st));
   {
     GemmDims d{n, n, n, nullptr, mP, nullptr};  // Y = Hf X : n x m
-    NAO_STAGE("zgemm_HX", 1, launch_zgemm(nprob, d, one, GemmOperand{Hf, snn, 1, n, 0, nullptr},
-                                   GemmOperand{X, snn, 1, n, 0, s_of_prob}, zero, Y, snn, 1, n, st));
+    NAO_CUDA_TRY(ctx, run_zgemm(ctx, "zgemm_HX", nprob, d, 1.0, GemmOperand{Hf, snn, 1, n, 0, nullptr},
+                                GemmOperand{X, snn, 1, n, 0, s_of_prob}, 0.0, Y, snn, 1, n, ozws, st));
     GemmDims d2{n, n, n, mP, mP, nullptr, 1};  // Hp = X^H Y : m x m, lower triangle
-    NAO_STAGE("zgemm_XHY", 1, launch_zgemm(nprob, d2, one, GemmOperand{X, snn, n, 1, 1, s_of_prob},
-                                   GemmOperand{Y, snn, 1, n, 0, nullptr}, zero, Hp, snn, 1, n, st));
+    NAO_CUDA_TRY(ctx, run_zgemm(ctx, "zgemm_XHY", nprob, d2, 1.0, GemmOperand{X, snn, n, 1, 1, s_of_prob},
+                                GemmOperand{Y, snn, 1, n, 0, nullptr}, 0.0, Hp, snn, 1, n, ozws, st));
   }
   NAO_STAGE("misc", 1, launch_hermitize(n, nprob, mP, Hp, n, snn, st));
 
@@ -312,15 +371,15 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   NAO_STAGE("backtransform", 1, launch_backtransform(n, nprob, mP, nullptr, Hp, n, snn, tauH, n, Z2, n, snn, wH, 0, V, n, snn, st));
   if (C) {
     GemmDims d{n, nb, n, nullptr, nbP, mP};  // C = X V(:, :nb) : n x nb, row-major [n][nb]
-    NAO_STAGE("zgemm_XV", 1, launch_zgemm(nprob, d, one, GemmOperand{X, snn, 1, n, 0, s_of_prob},
-                                   GemmOperand{V, snn, 1, n, 0, nullptr}, zero, (z64*)C, (long long)n * nb, nb, 1,
-                                   st));
+    NAO_CUDA_TRY(ctx, run_zgemm(ctx, "zgemm_XV", nprob, d, 1.0, GemmOperand{X, snn, 1, n, 0, s_of_prob},
+                                GemmOperand{V, snn, 1, n, 0, nullptr}, 0.0, (z64*)C, (long long)n * nb, nb, 1, ozws,
+                                st));
     NAO_STAGE("misc", 1, launch_zero_cols(n, nprob, nb, mP, (z64*)C, st));
   }
   NAO_STAGE("misc", 1, launch_write_eps(n, nprob, mP, wH, n, eps, st));
   {
     NaoStage stage_(ctx, "misc", st, 1);
-    finish_status_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(nprob, mP, stP, stH, m_kept, status);
+    finish_status_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(nprob, mP, stP, stH, ctx->dev_flags, m_kept, status);
     NAO_CUDA_TRY(ctx, cudaGetLastError());
   }
   return NAO_OK;
@@ -346,6 +405,9 @@ int nao_density_matrix(nao_ctx* ctx, int n, int nspin, int nk, const double* wk,
   const size_t of = P.take<double>((size_t)nprob * n), onocc = P.take<int32_t>(nprob),
                oscr = P.take<double>(fermi_scratch_doubles(ctx->num_sms)), ost = P.take<int32_t>(1),
                oCs = P.take<z64>((size_t)nprob * n * nb), oP = P.take<z64>(nn * nprob);
+  const GemmDims dP{n, n, nb, nullptr, nullptr, nullptr, 0};
+  const bool use_tc = ctx->gemm_method == NAO_GEMM_TC && zgemm_oz_supported(dP);
+  const size_t oOz = P.take<char>(use_tc ? zgemm_oz_workspace(nprob, dP) : 1);
   int rc = nao_ws_reserve(ctx, P.off);
   if (rc) return rc;
   char* ws = (char*)ctx->ws;
@@ -361,9 +423,9 @@ int nao_density_matrix(nao_ctx* ctx, int n, int nspin, int nk, const double* wk,
   {
     // P(k) = Cs Cs^H over the occupied bands (row-major [n][n])
     GemmDims d{n, n, nb, nullptr, nullptr, nocc};
-    NAO_STAGE("zgemm_P", 1, launch_zgemm(nprob, d, zmk(1.0, 0.0), GemmOperand{Cs, (long long)n * nb, nb, 1, 0, nullptr},
-                                   GemmOperand{Cs, (long long)n * nb, 1, nb, 1, nullptr}, zmk(0.0, 0.0), Pk,
-                                   (long long)nn, n, 1, st));
+    NAO_CUDA_TRY(ctx, run_zgemm(ctx, "zgemm_P", nprob, d, 1.0, GemmOperand{Cs, (long long)n * nb, nb, 1, 0, nullptr},
+                                GemmOperand{Cs, (long long)n * nb, 1, nb, 1, nullptr}, 0.0, Pk, (long long)nn, n, 1,
+                                use_tc ? (void*)(ws + oOz) : nullptr, st));
   }
   NAO_STAGE("rho_phase", 1, launch_rho_phase_sum(n, nspin, nk, nR, R, kpts, wk, gdeg, Pk, rhoR, st));
   return NAO_OK;

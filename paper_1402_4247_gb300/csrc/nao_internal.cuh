@@ -50,6 +50,8 @@ struct nao_ctx {
   std::vector<NaoStageStat> stages;
   std::vector<NaoPending> pending;
   std::vector<cudaEvent_t> event_pool;
+  int gemm_method = NAO_GEMM_TC;
+  int* dev_flags = nullptr;  // [0]: a bounded wait in a tensor-core kernel expired
 };
 
 // Stage bracketing for tracing (no-ops unless profiling is on).
@@ -145,6 +147,14 @@ cudaError_t launch_dgemm(int nprob, GemmDims dims, double alpha, GemmOperand A, 
 // rounding of Z.
 cudaError_t launch_ns_correct(int n, int nprob, const int32_t* size, const double* Z, const double* G, int ld,
                               long long stride, double* Z2, cudaStream_t st);
+
+// FP64-accurate complex GEMM on the BF16 tensor cores (digit-plane splitting): C = alpha
+// op(A) op(B) + beta C with real alpha, beta.  Requires 2K <= 2048.  ws: zgemm_oz_workspace
+// bytes; err: device int set to 1 if a bounded wait expired.
+bool zgemm_oz_supported(GemmDims dims);
+size_t zgemm_oz_workspace(int nprob, GemmDims dims);
+cudaError_t launch_zgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta, z64* C,
+                            long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st);
 
 // Small helpers of the gen-eig chain.
 cudaError_t launch_count_kept(int n, int nprob, const double* w, long long strideV, double s_cut,

@@ -1,0 +1,399 @@
+// FP64-accurate complex GEMM on the BF16 tensor cores (tcgen05), for the GEMM-shaped steps
+// of the band step (Sec. 3: Parts 3-4 use ZGEMM; the back-transformation and Part 6 are
+// products too).  On this GPU FP64 runs at 1.2 TFLOP/s and BF16 tcgen05 at ~2.4 PFLOP/s, so
+// an exact splitting of the FP64 operands into small-integer digit planes (the error-free
+// splitting of Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 59, 2012) is ~20x faster than
+// FP64 arithmetic while keeping FP64-level accuracy.
+//
+// Scheme (all my own design choices):
+//  * complex -> real: C'' = A' B'' with A' = [Re op(A) | Im op(A)] (M x 2K) and the columns
+//    of B'' interleaved, column 2j = (Re b_j ; -Im b_j), 2j+1 = (Im b_j ; Re b_j), so
+//    C''(:, 2j) = Re c_j and C''(:, 2j+1) = Im c_j;
+//  * every row of A' (column of B'') is scaled by a power of two 2^e so that |x| < 2^e, then
+//    q = round(x 2^{60-e}) (int64, exact integer arithmetic on the FP64 bits) is written in
+//    ten signed base-64 digits d_1..d_10 (|d_1| <= 64, |d_s| <= 32): 60 bits, so that even
+//    entries far below their row's maximum keep FP64-level accuracy in the product;
+//  * digit planes are stored as BF16 (exact): A_s = d_s 2^{-6(s-1)}, B_t = d_t 2^{-6(t-6)};
+//  * the 55 products A_s B_t with s + t <= 11 run on tcgen05 (M = 128, N = 64, K = 16,
+//    FP32 accumulation in TMEM).  Products of one "group" g = s + t share a power-of-two
+//    scale, so for g <= 7 their FP32 sums are exact integers while below 2^24 (guaranteed
+//    for 2K <= 2048); these six groups get one TMEM accumulator each.  Groups 8..11 share a
+//    seventh: it is 64x below group 7, so the FP32 rounding it collects over the whole K loop
+//    stays below FP64 rounding of the result (merging group 7 as well costs ~10x accuracy);
+//  * epilogue: the exact groups are combined in int64, the sum of everything converted to
+//    FP64 once and scaled by 2^{e_i + f_j - 42}; alpha (real) and beta (real) applied.
+// Pipeline: the whole block copies the digit tiles of one K step (16) into one of two
+// shared-memory stages while the MMAs of the previous step run; one thread issues the MMAs
+// and commits them to the stage's mbarrier.  Every wait is bounded (clock64); on timeout the
+// block records an error, skips its epilogue and still frees its tensor memory.
+#include <cuda_bf16.h>
+
+#include "nao_internal.cuh"
+
+namespace {
+
+constexpr int OZ_S = 10;             // digit planes per operand (60 bits)
+constexpr int OZ_BM = 128;           // tile rows (C'' rows)
+constexpr int OZ_BN = 64;            // tile columns (C'' columns = 32 complex columns)
+constexpr int OZ_BK = 16;            // K' per MMA step
+constexpr int OZ_TILE_A = OZ_BM * OZ_BK * 2;  // bytes of one A plane tile (4096)
+constexpr int OZ_TILE_B = OZ_BN * OZ_BK * 2;  // bytes of one B plane tile (2048)
+constexpr int OZ_STAGE = OZ_S * (OZ_TILE_A + OZ_TILE_B);
+constexpr int OZ_THREADS = 256;
+constexpr int OZ_NACC = 7;
+constexpr int OZ_TMEM_COLS = 512;
+constexpr long long OZ_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+constexpr int OZ_MAX_K2 = 2048;      // 2K bound for exact FP32 group sums
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// no-swizzle K-major descriptor: core matrices of 8 rows x 16 bytes; LBO = K-direction core
+// stride (128 B), SBO = 8-row-group stride (256 B); version 1 (bit 46).
+__device__ __forceinline__ uint64_t oz_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+
+// kind::f16 instruction descriptor: F32 accumulate, BF16 A and B, K-major both, M = 128, N = 64.
+constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+                              ((uint32_t)(OZ_BM >> 4) << 24);
+
+// byte offset of element (row, k) inside a plane tile (rows x 16 K, bf16)
+__device__ __forceinline__ int oz_tile_off(int row, int k) {
+  return (row >> 3) * 256 + ((k >> 3) & 1) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// biased exponent field of x (0 for zero / subnormal)
+__device__ __forceinline__ int exp_field(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7ff); }
+
+// q = round(x * 2^{6 OZ_S - e}) for |x| < 2^e, by integer arithmetic on the bits of x
+__device__ __forceinline__ long long oz_fixed(double x, int e) {
+  const long long bits = __double_as_longlong(x);
+  const int b = (int)((bits >> 52) & 0x7ff);
+  if (b == 0) return 0;  // zero (subnormals are far below any row scale used here)
+  long long m = (bits & 0xFFFFFFFFFFFFFll) | 0x10000000000000ll;  // 53-bit integer mantissa
+  const int sh = b - 1075 + 6 * OZ_S - e;                           // x 2^{6S-e} = m 2^{sh}
+  long long q;
+  if (sh >= 0) q = m << sh;
+  else if (sh <= -62) q = 0;
+  else q = (m + (1ll << (-sh - 1))) >> (-sh);
+  return bits < 0 ? -q : q;
+}
+
+// OZ_S signed base-64 digits of q (|q| < 2^{6 OZ_S}): q = sum_s d_s 2^{6(OZ_S-s)}
+__device__ __forceinline__ void oz_digits(long long q, int* d) {
+#pragma unroll
+  for (int s = 0; s < OZ_S - 1; ++s) {
+    const int sh = 6 * (OZ_S - 1 - s);
+    const long long ds = (q + (1ll << (sh - 1))) >> sh;
+    d[s] = (int)ds;
+    q -= ds * (1ll << sh);
+  }
+  d[OZ_S - 1] = (int)q;
+}
+
+// ---------------------------------------------------------------------------- split kernels
+// A' rows: one warp per row i of op(A) (M rows, 2K columns).  Plane layout:
+//   Ap[prob][s][rb][ks][4096 B], rb = i / 128, ks = k' / 16.
+__global__ void oz_split_a(int nprob, GemmDims dims, GemmOperand A, int Mp, int K2p, __nv_bfloat16* __restrict__ planes,
+                           int* __restrict__ rexp) {
+  const int p = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= Mp) return;
+  const int M = dims.Mp ? dims.Mp[p] : dims.M;
+  const int K = dims.Kp ? dims.Kp[p] : dims.K;
+  const z64* Ab = (const z64*)A.ptr + (size_t)(A.map ? A.map[p] : p) * A.bs;
+  const bool live = i < M;
+  // row exponent
+  int bmax = 0;
+  if (live)
+    for (int k = lane; k < K; k += 32) {
+      const z64 a = Ab[(long long)i * A.rs + (long long)k * A.cs];
+      bmax = max(bmax, max(exp_field(a.x), exp_field(a.y)));
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+  const int e = bmax == 0 ? -1100 : bmax - 1022;  // |x| < 2^e
+  if (lane == 0) rexp[(size_t)p * Mp + i] = e;
+  const int nks = K2p / OZ_BK, rb = i / OZ_BM, r = i % OZ_BM;
+  const size_t plane_elems = (size_t)(Mp / OZ_BM) * nks * (OZ_TILE_A / 2);
+  unsigned char* base = (unsigned char*)(planes + (size_t)p * OZ_S * plane_elems);
+  for (int kk = lane; kk < K2p; kk += 32) {
+    double x = 0.0;
+    if (live && kk < 2 * K) {
+      const int k = kk < K ? kk : kk - K;
+      z64 a = Ab[(long long)i * A.rs + (long long)k * A.cs];
+      if (A.conj) a.y = -a.y;
+      x = kk < K ? a.x : a.y;
+    }
+    int d[OZ_S];
+    oz_digits(oz_fixed(x, e), d);
+    const size_t off = ((size_t)rb * nks + kk / OZ_BK) * OZ_TILE_A + oz_tile_off(r, kk % OZ_BK);
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+      const float v = ldexpf((float)d[s], -6 * s);
+      *(__nv_bfloat16*)(base + (size_t)s * plane_elems * 2 + off) = __float2bfloat16_rn(v);
+    }
+  }
+}
+
+// B'' rows (= C'' columns): one warp per complex column j of op(B) (K x N), producing rows
+// 2j and 2j+1 of the K-major B'' tile.  Bp[prob][t][cb][ks][2048 B], cb = (2j) / 64.
+__global__ void oz_split_b(int nprob, GemmDims dims, GemmOperand B, int N2p, int K2p, __nv_bfloat16* __restrict__ planes,
+                           int* __restrict__ cexp) {
+  const int p = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (2 * j >= N2p) return;
+  const int N = dims.Np ? dims.Np[p] : dims.N;
+  const int K = dims.Kp ? dims.Kp[p] : dims.K;
+  const z64* Bb = (const z64*)B.ptr + (size_t)(B.map ? B.map[p] : p) * B.bs;
+  const bool live = j < N;
+  int bmax = 0;
+  if (live)
+    for (int k = lane; k < K; k += 32) {
+      const z64 b = Bb[(long long)k * B.rs + (long long)j * B.cs];
+      bmax = max(bmax, max(exp_field(b.x), exp_field(b.y)));
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+  const int f = bmax == 0 ? -1100 : bmax - 1022;
+  if (lane == 0) cexp[(size_t)p * (N2p / 2) + j] = f;
+  const int nks = K2p / OZ_BK;
+  const size_t plane_elems = (size_t)(N2p / OZ_BN) * nks * (OZ_TILE_B / 2);
+  unsigned char* base = (unsigned char*)(planes + (size_t)p * OZ_S * plane_elems);
+  for (int kk = lane; kk < K2p; kk += 32) {
+    double x0 = 0.0, x1 = 0.0;  // rows 2j and 2j+1 of B''^T at k'
+    if (live && kk < 2 * K) {
+      const int k = kk < K ? kk : kk - K;
+      z64 b = Bb[(long long)k * B.rs + (long long)j * B.cs];
+      if (B.conj) b.y = -b.y;
+      if (kk < K) {
+        x0 = b.x;   // Re b
+        x1 = b.y;   // Im b
+      } else {
+        x0 = -b.y;  // -Im b
+        x1 = b.x;   // Re b
+      }
+    }
+    int d0[OZ_S], d1[OZ_S];
+    oz_digits(oz_fixed(x0, f), d0);
+    oz_digits(oz_fixed(x1, f), d1);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int row = 2 * j + h, cb = row / OZ_BN, rr = row % OZ_BN;
+      const size_t off = ((size_t)cb * nks + kk / OZ_BK) * OZ_TILE_B + oz_tile_off(rr, kk % OZ_BK);
+#pragma unroll
+      for (int s = 0; s < OZ_S; ++s) {
+        const float v = ldexpf((float)(h ? d1[s] : d0[s]), 30 - 6 * s);
+        *(__nv_bfloat16*)(base + (size_t)s * plane_elems * 2 + off) = __float2bfloat16_rn(v);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------- tensor kernel
+__device__ __forceinline__ void oz_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+               :: "r"(dtmem), "l"(adesc), "l"(bdesc), "r"(OZ_IDESC), "r"(acc));
+}
+
+__device__ __forceinline__ bool oz_wait(uint64_t* mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(smem_u32(mbar)), "r"(parity));
+    if (ok) return true;
+    if (clock64() - t0 > OZ_WAIT_CYCLES) return false;
+  }
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_bfloat16* __restrict__ Ap,
+               const __nv_bfloat16* __restrict__ Bp, const int* __restrict__ rexp, const int* __restrict__ cexp, int Mp,
+               int N2p, int K2p, z64* __restrict__ C, long long Cbs, long long Crs, long long Ccs, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char oz_smem[];
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t tbase;
+  __shared__ int s_fail;
+  const int p = blockIdx.z;
+  const int rb = blockIdx.y, cb = blockIdx.x;
+  const int M = dims.Mp ? dims.Mp[p] : dims.M;
+  const int N = dims.Np ? dims.Np[p] : dims.N;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // uniform early exits (before any barrier or allocation)
+  if (rb * OZ_BM >= M || cb * (OZ_BN / 2) >= N) return;
+  if (dims.lower && cb * (OZ_BN / 2) > rb * OZ_BM + OZ_BM - 1) return;
+  unsigned char* stage0 = (unsigned char*)(((uintptr_t)oz_smem + 1023) & ~(uintptr_t)1023);
+  const int nks = K2p / OZ_BK;
+  const size_t aplane = (size_t)(Mp / OZ_BM) * nks * (OZ_TILE_A / 2);
+  const size_t bplane = (size_t)(N2p / OZ_BN) * nks * (OZ_TILE_B / 2);
+  const unsigned char* Abase = (const unsigned char*)(Ap + (size_t)p * OZ_S * aplane) + (size_t)rb * nks * OZ_TILE_A;
+  const unsigned char* Bbase = (const unsigned char*)(Bp + (size_t)p * OZ_S * bplane) + (size_t)cb * nks * OZ_TILE_B;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tbase)), "r"(OZ_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    s_fail = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tbase;
+
+  uint32_t init_mask = 0;  // accumulators written at least once (issuing thread only)
+  for (int ks = 0; ks < nks; ++ks) {
+    const int b = ks & 1;
+    if (ks >= 2) {  // the MMAs of step ks-2 read this stage
+      if (!oz_wait(&mbar[b], ((ks - 2) >> 1) & 1)) {
+        if (tid == 0) s_fail = 1;
+      }
+    }
+    __syncthreads();
+    if (s_fail) break;
+    unsigned char* st = stage0 + b * OZ_STAGE;
+    // copy: 9 A tiles (4096 B) then 9 B tiles (2560 B), 16 B per thread per pass
+    for (int o = tid * 16; o < OZ_S * OZ_TILE_A; o += OZ_THREADS * 16) {
+      const int s = o / OZ_TILE_A, w = o % OZ_TILE_A;
+      *(uint4*)(st + o) = __ldg((const uint4*)(Abase + (size_t)s * aplane * 2 + (size_t)ks * OZ_TILE_A + w));
+    }
+    for (int o = tid * 16; o < OZ_S * OZ_TILE_B; o += OZ_THREADS * 16) {
+      const int s = o / OZ_TILE_B, w = o % OZ_TILE_B;
+      *(uint4*)(st + OZ_S * OZ_TILE_A + o) =
+          __ldg((const uint4*)(Bbase + (size_t)s * bplane * 2 + (size_t)ks * OZ_TILE_B + w));
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t sa = smem_u32(st), sb = smem_u32(st + OZ_S * OZ_TILE_A);
+#pragma unroll
+      for (int s = 0; s < OZ_S; ++s) {
+#pragma unroll
+        for (int t = 0; t < OZ_S; ++t) {
+          const int g = (s + 1) + (t + 1);
+          if (g > OZ_S + 1) continue;
+          const int acc = g <= 7 ? g - 2 : OZ_NACC - 1;
+          const uint32_t on = (init_mask >> acc) & 1u;
+          oz_mma(tmem + acc * OZ_BN, oz_desc(sa + s * OZ_TILE_A), oz_desc(sb + t * OZ_TILE_B), on);
+          init_mask |= 1u << acc;
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(smem_u32(&mbar[b])));
+    }
+  }
+  // wait for the last committed step (it covers every earlier MMA of this thread)
+  if (!s_fail && nks > 0) {
+    const int last = nks - 1;
+    if (!oz_wait(&mbar[last & 1], (last >> 1) & 1) && tid == 0) s_fail = 1;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (s_fail) {
+    if (tid == 0) atomicExch(err, 1);
+  } else {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows); warps 0-3 take
+    // complex columns 0..15 of the tile, warps 4-7 columns 16..31.
+    const int row = 32 * (warp & 3) + lane;
+    const int gi = rb * OZ_BM + row;
+    const int half = warp >> 2;
+    const int erow = (gi < M) ? rexp[(size_t)p * Mp + gi] : 0;
+    z64* Cp = C + (size_t)p * Cbs;
+    for (int cc = 0; cc < OZ_BN / 4; cc += 4) {  // 4 complex = 8 C'' columns per round
+      const int col0 = half * (OZ_BN / 2) + 2 * cc;
+      uint32_t v[OZ_NACC][8];
+#pragma unroll
+      for (int a = 0; a < OZ_NACC; ++a) {
+        const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + a * OZ_BN + col0;
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]), "=r"(v[a][5]),
+                       "=r"(v[a][6]), "=r"(v[a][7])
+                     : "r"(taddr));
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (gi >= M) continue;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int gj = cb * (OZ_BN / 2) + half * (OZ_BN / 4) + cc + q;  // complex column
+        if (gj >= N) continue;
+        double part[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = 2 * q + h;
+          // exact groups g = 2..7 (accumulator g-2): G_g = n_g 2^{6(7-g)} with integer n_g
+          long long hi = 0;
+#pragma unroll
+          for (int a = 0; a < OZ_NACC - 1; ++a) {
+            const float gv = __uint_as_float(v[a][c]);
+            const long long ng = (long long)__float2int_rn(ldexpf(gv, -6 * (5 - a)));
+            hi += ng * (1ll << (6 * (5 - a)));
+          }
+          part[h] = (double)hi + (double)__uint_as_float(v[OZ_NACC - 1][c]);
+        }
+        const int fcol = cexp[(size_t)p * (N2p / 2) + gj];
+        int E = erow + fcol - 42;
+        E = E < -1022 ? -1022 : (E > 1023 ? 1023 : E);
+        const double sc = __longlong_as_double((long long)(E + 1023) << 52) * alpha;
+        z64* cp = Cp + (long long)gi * Crs + (long long)gj * Ccs;
+        z64 r = zmk(part[0] * sc, part[1] * sc);
+        if (beta != 0.0) {
+          const z64 old = *cp;
+          r.x = fma(beta, old.x, r.x);
+          r.y = fma(beta, old.y, r.y);
+        }
+        *cp = r;
+      }
+    }
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(OZ_TMEM_COLS));
+}
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+bool zgemm_oz_supported(GemmDims dims) { return 2 * (long long)dims.K <= OZ_MAX_K2 && dims.M > 0 && dims.N > 0; }
+
+size_t zgemm_oz_workspace(int nprob, GemmDims dims) {
+  const int Mp = round_up(dims.M, OZ_BM), N2p = round_up(2 * dims.N, OZ_BN), K2p = round_up(2 * dims.K, OZ_BK);
+  const size_t a = (size_t)nprob * OZ_S * Mp * K2p * 2, b = (size_t)nprob * OZ_S * N2p * K2p * 2;
+  return a + b + (size_t)nprob * (Mp + N2p) * sizeof(int) + 4096;
+}
+
+cudaError_t launch_zgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta, z64* C,
+                            long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st) {
+  if (nprob <= 0 || dims.M <= 0 || dims.N <= 0) return cudaSuccess;
+  const int Mp = round_up(dims.M, OZ_BM), N2p = round_up(2 * dims.N, OZ_BN), K2p = round_up(2 * dims.K, OZ_BK);
+  unsigned char* w = (unsigned char*)ws;
+  __nv_bfloat16* Apl = (__nv_bfloat16*)w;
+  w += (size_t)nprob * OZ_S * Mp * K2p * 2;
+  __nv_bfloat16* Bpl = (__nv_bfloat16*)w;
+  w += (size_t)nprob * OZ_S * N2p * K2p * 2;
+  int* rexp = (int*)w;
+  int* cexp = rexp + (size_t)nprob * Mp;
+  oz_split_a<<<dim3((Mp + 7) / 8, nprob), 256, 0, st>>>(nprob, dims, A, Mp, K2p, Apl, rexp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  oz_split_b<<<dim3((N2p / 2 + 7) / 8, nprob), 256, 0, st>>>(nprob, dims, B, N2p, K2p, Bpl, cexp);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = 2 * (size_t)OZ_STAGE + 1024;
+  e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(N2p / OZ_BN, Mp / OZ_BM, nprob);
+  oz_gemm_kernel<<<grid, OZ_THREADS, smem, st>>>(nprob, dims, alpha, beta, Apl, Bpl, rexp, cexp, Mp, N2p, K2p, C, Cbs,
+                                                  Crs, Ccs, err);
+  return cudaGetLastError();
+}

@@ -30,7 +30,9 @@ NAO_MIXED_BF16X3 = 2
 #: every symbol include/nao.h declares
 EXPORTS = ("nao_init", "nao_destroy", "nao_last_error", "nao_workspace_bytes", "nao_bloch_sum",
            "nao_gen_eig", "nao_density_matrix", "nao_profile_enable", "nao_profile_read", "nao_launch_count",
-           "nao_fermi_level_noalloc")
+           "nao_fermi_level_noalloc", "nao_set_gemm_method", "nao_zgemm")
+NAO_GEMM_FP64 = 0
+NAO_GEMM_TC = 1
 
 _lib = None
 
@@ -71,6 +73,12 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.nao_profile_read.restype = i32
     lib.nao_launch_count.argtypes = [vp]
     lib.nao_launch_count.restype = ctypes.c_int64
+    lib.nao_set_gemm_method.argtypes = [vp, i32]
+    lib.nao_set_gemm_method.restype = i32
+    i64 = ctypes.c_longlong
+    lib.nao_zgemm.argtypes = [vp, i32, i32, i32, i32, i32, f64, vp, i32, i64, i32, vp, i32, i64, i32, f64, vp, i32,
+                              i64, vp]
+    lib.nao_zgemm.restype = i32
     lib.nao_fermi_level_noalloc.argtypes = [i32, i32, i32, vp, vp, vp, i32, f64, f64, vp, vp, vp, vp, vp]
     lib.nao_fermi_level_noalloc.restype = i32
     _lib = lib
@@ -120,6 +128,24 @@ class Context:
 
     def workspace_bytes(self) -> int:
         return int(self.lib.nao_workspace_bytes(self.handle))
+
+    def nao_set_gemm_method(self, method: int):
+        self._check(self.lib.nao_set_gemm_method(self.handle, int(method)), "nao_set_gemm_method")
+
+    def nao_zgemm(self, A, B, C=None, alpha=1.0, beta=0.0, transA=0, transB=0, method=NAO_GEMM_TC, stream=None):
+        """Batched C[p] = alpha op(A[p]) op(B[p]) + beta C[p] (complex128, row-major, 3-d tensors)."""
+        nprob = A.shape[0]
+        M = A.shape[2] if transA else A.shape[1]
+        K = A.shape[1] if transA else A.shape[2]
+        N = B.shape[1] if transB else B.shape[2]
+        if C is None:
+            C = torch.zeros((nprob, M, N), dtype=torch.complex128, device=A.device)
+        rc = self.lib.nao_zgemm(self.handle, int(method), nprob, M, N, K, float(alpha), _ptr(A), A.shape[2],
+                                A.shape[1] * A.shape[2], int(transA), _ptr(B), B.shape[2], B.shape[1] * B.shape[2],
+                                int(transB), float(beta), _ptr(C), C.shape[2], C.shape[1] * C.shape[2],
+                                _stream(stream))
+        self._check(rc, "nao_zgemm")
+        return C
 
     def nao_profile_enable(self, on: bool = True):
         self._check(self.lib.nao_profile_enable(self.handle, 1 if on else 0), "nao_profile_enable")

@@ -10,12 +10,14 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=[1, 0], ids=["tc", "fp64"])
+def ctx(request):
+    """A context per product method: tensor-core digit planes (default) and FP64 cores."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1402_4247_gb300.nao import Context
     c = Context(0)
+    c.nao_set_gemm_method(request.param)
     yield c
     c.close()
 
