@@ -145,6 +145,55 @@ cudaError_t run_zgemm(nao_ctx* ctx, const char* stage, int nprob, GemmDims d, do
   return launch_zgemm(nprob, d, zmk(alpha, 0.0), A, B, zmk(beta, 0.0), C, Cbs, Crs, Ccs, st);
 }
 
+// Eigen_HH steps 3-4 in blocked form: U(:, c) = Q Z(:, m - nc + c) for c < nc (nc = ncols[p]),
+// normalised (times 1/sqrt(w) when use_rsqrt), with Q = prod_j (I - V_j T_j V_j^H) applied from
+// the last block of NAO_WY_NB reflectors to the first; every block costs three products
+// (W = V^H U, W = T W, U -= V W) plus its Gram matrix V^H V for T.
+cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, const int32_t* ncols, const z64* A,
+                                  const z64* tau, const double* Z, const double* w, int use_rsqrt, z64* U, z64* Vf,
+                                  z64* tauc, z64* G, z64* T, z64* W, z64* W2, void* ozws, cudaStream_t st) {
+  const int nb = NAO_WY_NB;
+  const int ncolv = (n + nb - 1) / nb * nb;
+  const long long snn = (long long)n * n, svf = (long long)n * ncolv, snb2 = (long long)nb * nb,
+                  snbn = (long long)nb * n;
+  cudaError_t e;
+  {
+    NaoStage stage_(ctx, "backtransform", st, 2);
+    e = launch_extract_v(n, nprob, size, A, n, snn, tau, n, ncolv, Vf, n, svf, tauc, st);
+    if (e == cudaSuccess) e = launch_init_u(n, nprob, size, ncols, Z, n, snn, U, n, snn, st);
+    if (e != cudaSuccess) return e;
+  }
+  const int nblk = (n - 1 + nb - 1) / nb;
+  for (int j = nblk - 1; j >= 0; --j) {
+    const int R0 = j * nb + 1, rows = n - R0;
+    if (rows <= 0) continue;
+    const z64* Vj = Vf + R0 + (size_t)j * nb * n;  // V_j(r, c) at Vj[r + c n]
+    GemmDims dg{nb, nb, rows, nullptr, nullptr, nullptr, 0};
+    e = run_zgemm(ctx, "backtransform", nprob, dg, 1.0, GemmOperand{Vj, svf, n, 1, 1, nullptr},
+                  GemmOperand{Vj, svf, 1, n, 0, nullptr}, 0.0, G, snb2, nb, 1, ozws, st);
+    if (e != cudaSuccess) return e;
+    {
+      NaoStage stage_(ctx, "backtransform", st, 1);
+      e = launch_build_t(nb, nprob, G, tauc, ncolv, j * nb, T, st);
+      if (e != cudaSuccess) return e;
+    }
+    GemmDims dw{nb, n, rows, nullptr, ncols, nullptr, 0};
+    e = run_zgemm(ctx, "backtransform", nprob, dw, 1.0, GemmOperand{Vj, svf, n, 1, 1, nullptr},
+                  GemmOperand{U + R0, snn, 1, n, 0, nullptr}, 0.0, W, snbn, n, 1, ozws, st);
+    if (e != cudaSuccess) return e;
+    GemmDims dt{nb, n, nb, nullptr, ncols, nullptr, 0};
+    e = run_zgemm(ctx, "backtransform", nprob, dt, 1.0, GemmOperand{T, snb2, nb, 1, 0, nullptr},
+                  GemmOperand{W, snbn, n, 1, 0, nullptr}, 0.0, W2, snbn, n, 1, ozws, st);
+    if (e != cudaSuccess) return e;
+    GemmDims du{rows, n, nb, nullptr, ncols, nullptr, 0};
+    e = run_zgemm(ctx, "backtransform", nprob, du, -1.0, GemmOperand{Vj, svf, 1, n, 0, nullptr},
+                  GemmOperand{W2, snbn, n, 1, 0, nullptr}, 1.0, U + R0, snn, 1, n, ozws, st);
+    if (e != cudaSuccess) return e;
+  }
+  NaoStage stage_(ctx, "backtransform", st, 1);
+  return launch_normalize_cols(n, nprob, size, ncols, w, n, use_rsqrt, U, n, snn, st);
+}
+
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -305,9 +354,16 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
                oeH = P.take<double>((size_t)n * nprob), owH = P.take<double>((size_t)n * nprob);
   const size_t omP = P.take<int32_t>(nprob), onbP = P.take<int32_t>(nprob), ostP = P.take<int32_t>(nprob),
                ostH = P.take<int32_t>(nprob);
-  const GemmDims dmax{n, n, n, nullptr, nullptr, nullptr, 0};
-  const bool use_tc = ctx->gemm_method == NAO_GEMM_TC && zgemm_oz_supported(dmax);
-  const size_t oOz = P.take<char>(use_tc ? zgemm_oz_workspace(nprob, dmax) : 1);
+  // largest product of the step: n x n x n, or the blocked back-transform's nb-wide ones
+  const int nd = n > NAO_WY_NB ? n : NAO_WY_NB;
+  const GemmDims dmax{nd, nd, nd, nullptr, nullptr, nullptr, 0};
+  const bool use_tc = ctx->gemm_method == NAO_GEMM_TC && zgemm_oz_supported(GemmDims{n, n, n, nullptr, nullptr, nullptr, 0});
+  const size_t oOz = P.take<char>(use_tc ? zgemm_oz_workspace(nmax, dmax) : 1);
+  const int ncolv = (n + NAO_WY_NB - 1) / NAO_WY_NB * NAO_WY_NB;
+  const size_t oVf = P.take<z64>((size_t)n * ncolv * nmax), oTc = P.take<z64>((size_t)ncolv * nmax),
+               oG2 = P.take<z64>((size_t)NAO_WY_NB * NAO_WY_NB * nmax),
+               oT2 = P.take<z64>((size_t)NAO_WY_NB * NAO_WY_NB * nmax),
+               oW = P.take<z64>((size_t)NAO_WY_NB * n * nmax), oW2 = P.take<z64>((size_t)NAO_WY_NB * n * nmax);
   int rc = nao_ws_reserve(ctx, P.off);
   if (rc) return rc;
   char* ws = (char*)ctx->ws;
@@ -323,6 +379,8 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   int32_t *mP = (int32_t*)(ws + omP), *nbP = (int32_t*)(ws + onbP), *stP = (int32_t*)(ws + ostP),
           *stH = (int32_t*)(ws + ostH);
   void* ozws = use_tc ? (void*)(ws + oOz) : nullptr;
+  z64 *Vf = (z64*)(ws + oVf), *tauc = (z64*)(ws + oTc), *Gw = (z64*)(ws + oG2), *Tw = (z64*)(ws + oT2),
+      *Ww = (z64*)(ws + oW), *W2w = (z64*)(ws + oW2);
   const long long snn = (long long)nn;
 
   // ---- Part 2: Eigen_HH(S) -> s, U;  X = U_m s_m^{-1/2}
@@ -338,7 +396,8 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
                                    GemmOperand{Z, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, st));
     NAO_CUDA_TRY(ctx, launch_ns_correct(n, nSe, nullptr, Z, G, n, snn, Z2, st));
   }
-  NAO_STAGE("backtransform", 1, launch_backtransform(n, nSe, nullptr, mS, AS, n, snn, tauS, n, Z2, n, snn, wS, 1, X, n, snn, st));
+  NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nSe, nullptr, mS, AS, tauS, Z2, wS, 1, X, Vf, tauc, Gw, Tw, Ww, W2w,
+                                          ozws, st));
   {
     NaoStage stage_(ctx, "misc", st, 1);
     gather_m_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(nprob, s_of_prob, mS, stS, nb, mP, nbP, stP);
@@ -368,7 +427,8 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
                                    GemmOperand{Z, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, st));
     NAO_CUDA_TRY(ctx, launch_ns_correct(n, nprob, mP, Z, G, n, snn, Z2, st));
   }
-  NAO_STAGE("backtransform", 1, launch_backtransform(n, nprob, mP, nullptr, Hp, n, snn, tauH, n, Z2, n, snn, wH, 0, V, n, snn, st));
+  NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nprob, mP, mP, Hp, tauH, Z2, wH, 0, V, Vf, tauc, Gw, Tw, Ww, W2w, ozws,
+                                          st));
   if (C) {
     GemmDims d{n, nb, n, nullptr, nbP, mP};  // C = X V(:, :nb) : n x nb, row-major [n][nb]
     NAO_CUDA_TRY(ctx, run_zgemm(ctx, "zgemm_XV", nprob, d, 1.0, GemmOperand{X, snn, 1, n, 0, s_of_prob},

@@ -212,3 +212,117 @@ cudaError_t launch_scale_cols_sqrt(int n, int nprob, int nb, const z64* C, const
   scale_cols_sqrt_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, nprob, nb, C, f, Cs);
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------------------
+// Blocked form of steps 3-4 (compact WY): Q = Q_0 Q_1 ... with Q_j = H_{j nb} ... H_{j nb+nb-1}
+// = I - V_j T_j V_j^H, applied as three matrix products per block (run on the tensor
+// cores by the caller).  The kernels below prepare the operands.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+// Vfull(:, i) = explicit reflector i (1 at row i+1, A(r, i) below, 0 elsewhere) for
+// i < m-1, zero columns otherwise (ncolv >= n columns); tauc[i] = tau[i] or 0.
+__global__ void extract_v_kernel(int n, const int32_t* __restrict__ size, const z64* __restrict__ Abase, int lda,
+                                 long long strideA, const z64* __restrict__ taubase, long long strideV, int ncolv,
+                                 z64* __restrict__ Vbase, int ldv, long long strideVf, z64* __restrict__ taucbase) {
+  const int p = blockIdx.z;
+  const int m = size ? size[p] : n;
+  const int i = blockIdx.y;  // column
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n || i >= ncolv) return;
+  const z64* A = Abase + (size_t)p * strideA;
+  z64 val = zmk(0.0, 0.0);
+  if (i < m - 1) {
+    if (r == i + 1) val = zmk(1.0, 0.0);
+    else if (r > i + 1 && r < m) val = A[(size_t)i * lda + r];
+  }
+  Vbase[(size_t)p * strideVf + (size_t)i * ldv + r] = val;
+  if (r == 0) taucbase[(size_t)p * ncolv + i] = (i < m - 1) ? taubase[(size_t)p * strideV + i] : zmk(0.0, 0.0);
+}
+
+// U(:, c) = Z(:, m - nc + c) as complex for c < nc, rows < m; zero elsewhere (n x n).
+__global__ void init_u_kernel(int n, const int32_t* __restrict__ size, const int32_t* __restrict__ ncols,
+                              const double* __restrict__ Zbase, int ldz, long long strideZ, z64* __restrict__ Ubase,
+                              int ldu, long long strideU) {
+  const int p = blockIdx.z;
+  const int m = size ? size[p] : n;
+  const int nc = ncols ? ncols[p] : m;
+  const int c = blockIdx.y;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double v = 0.0;
+  if (c < nc && r < m) v = Zbase[(size_t)p * strideZ + (size_t)(m - nc + c) * ldz + r];
+  Ubase[(size_t)p * strideU + (size_t)c * ldu + r] = zmk(v, 0.0);
+}
+
+// T (nb x nb, row-major, upper triangular) of block j0..j0+nb-1 from G = V^H V (row-major):
+// T_ii = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) G(0:i, i).  One block of nb threads per problem.
+__global__ void build_t_kernel(int nb, const z64* __restrict__ Gbase, const z64* __restrict__ taucbase, int ncolv, int j0,
+                               z64* __restrict__ Tbase) {
+  extern __shared__ z64 tcol[];
+  const int p = blockIdx.x;
+  const int r = threadIdx.x;
+  const z64* G = Gbase + (size_t)p * nb * nb;
+  const z64* tau = taucbase + (size_t)p * ncolv + j0;
+  z64* T = Tbase + (size_t)p * nb * nb;
+  for (int i = 0; i < nb; ++i) {
+    const z64 ti = tau[i];
+    z64 acc = zmk(0.0, 0.0);
+    if (r < i)
+      for (int c = r; c < i; ++c) acc = zfma(T[(size_t)r * nb + c], G[(size_t)c * nb + i], acc);
+    tcol[r] = zmul(zmk(-ti.x, -ti.y), acc);
+    __syncthreads();
+    T[(size_t)r * nb + i] = (r < i) ? tcol[r] : (r == i ? ti : zmk(0.0, 0.0));
+    __syncthreads();
+  }
+}
+
+// column c < nc: U(:, c) /= ||U(:, c)||, times 1/sqrt(w[m - nc + c]) when use_rsqrt
+__global__ void normalize_cols_kernel(int n, const int32_t* __restrict__ size, const int32_t* __restrict__ ncols,
+                                      const double* __restrict__ wbase, long long strideV, int use_rsqrt,
+                                      z64* __restrict__ Ubase, int ldu, long long strideU) {
+  const int p = blockIdx.y;
+  const int m = size ? size[p] : n;
+  const int nc = ncols ? ncols[p] : m;
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= nc) return;
+  z64* u = Ubase + (size_t)p * strideU + (size_t)c * ldu;
+  double s = 0.0;
+  for (int r = lane; r < m; r += 32) s += zabs2(u[r]);
+  s = wsum(s);
+  double sc = 1.0 / sqrt(s);
+  if (use_rsqrt) sc /= sqrt(wbase[(size_t)p * strideV + (m - nc + c)]);
+  for (int r = lane; r < m; r += 32) u[r] = zscale(u[r], sc);
+}
+
+}  // namespace
+
+cudaError_t launch_extract_v(int n, int nprob, const int32_t* size, const z64* A, int lda, long long strideA,
+                             const z64* tau, long long strideV, int ncolv, z64* V, int ldv, long long strideVf,
+                             z64* tauc, cudaStream_t st) {
+  dim3 grid((n + 127) / 128, ncolv, nprob);
+  extract_v_kernel<<<grid, 128, 0, st>>>(n, size, A, lda, strideA, tau, strideV, ncolv, V, ldv, strideVf, tauc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_u(int n, int nprob, const int32_t* size, const int32_t* ncols, const double* Z, int ldz,
+                          long long strideZ, z64* U, int ldu, long long strideU, cudaStream_t st) {
+  dim3 grid((n + 127) / 128, n, nprob);
+  init_u_kernel<<<grid, 128, 0, st>>>(n, size, ncols, Z, ldz, strideZ, U, ldu, strideU);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_t(int nb, int nprob, const z64* G, const z64* tauc, int ncolv, int j0, z64* T,
+                           cudaStream_t st) {
+  build_t_kernel<<<nprob, nb, nb * sizeof(z64), st>>>(nb, G, tauc, ncolv, j0, T);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normalize_cols(int n, int nprob, const int32_t* size, const int32_t* ncols, const double* w,
+                                  long long strideV, int use_rsqrt, z64* U, int ldu, long long strideU,
+                                  cudaStream_t st) {
+  dim3 grid((n + 7) / 8, nprob);
+  normalize_cols_kernel<<<grid, 256, 0, st>>>(n, size, ncols, w, strideV, use_rsqrt, U, ldu, strideU);
+  return cudaGetLastError();
+}

@@ -122,6 +122,19 @@ cudaError_t launch_backtransform(int n, int nprob, const int32_t* size, const in
                                  const double* w, int use_rsqrt_scale, z64* U, int ldu, long long strideU,
                                  cudaStream_t st);
 
+// Blocked (compact WY) back-transformation helpers, see backtr.cu.
+constexpr int NAO_WY_NB = 128;
+cudaError_t launch_extract_v(int n, int nprob, const int32_t* size, const z64* A, int lda, long long strideA,
+                             const z64* tau, long long strideV, int ncolv, z64* V, int ldv, long long strideVf,
+                             z64* tauc, cudaStream_t st);
+cudaError_t launch_init_u(int n, int nprob, const int32_t* size, const int32_t* ncols, const double* Z, int ldz,
+                          long long strideZ, z64* U, int ldu, long long strideU, cudaStream_t st);
+cudaError_t launch_build_t(int nb, int nprob, const z64* G, const z64* tauc, int ncolv, int j0, z64* T,
+                           cudaStream_t st);
+cudaError_t launch_normalize_cols(int n, int nprob, const int32_t* size, const int32_t* ncols, const double* w,
+                                  long long strideV, int use_rsqrt, z64* U, int ldu, long long strideU,
+                                  cudaStream_t st);
+
 // Generic batched GEMM:  C(p) = alpha * opA(A(p)) * opB(B(p)) + beta * C(p)
 // Element (i, j) of an operand X at X.ptr + p*X.bs + i*X.rs + j*X.cs; conj flags per operand.
 // Dimensions: M, N, K fixed, or per problem from dim arrays when non-null.
@@ -149,7 +162,7 @@ cudaError_t launch_ns_correct(int n, int nprob, const int32_t* size, const doubl
                               long long stride, double* Z2, cudaStream_t st);
 
 // FP64-accurate complex GEMM on the BF16 tensor cores (digit-plane splitting): C = alpha
-// op(A) op(B) + beta C with real alpha, beta.  Requires 2K <= 2048.  ws: zgemm_oz_workspace
+// op(A) op(B) + beta C with real alpha, beta.  Requires 2K <= 1792.  ws: zgemm_oz_workspace
 // bytes; err: device int set to 1 if a bounded wait expired.
 bool zgemm_oz_supported(GemmDims dims);
 size_t zgemm_oz_workspace(int nprob, GemmDims dims);

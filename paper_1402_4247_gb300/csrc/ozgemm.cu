@@ -16,12 +16,13 @@
 //  * digit planes are stored as BF16 (exact): A_s = d_s 2^{-6(s-1)}, B_t = d_t 2^{-6(t-6)};
 //  * the 55 products A_s B_t with s + t <= 11 run on tcgen05 (M = 128, N = 64, K = 16,
 //    FP32 accumulation in TMEM).  Products of one "group" g = s + t share a power-of-two
-//    scale, so for g <= 7 their FP32 sums are exact integers while below 2^24 (guaranteed
-//    for 2K <= 2048); these six groups get one TMEM accumulator each.  Groups 8..11 share a
-//    seventh: it is 64x below group 7, so the FP32 rounding it collects over the whole K loop
-//    stays below FP64 rounding of the result (merging group 7 as well costs ~10x accuracy);
-//  * epilogue: the exact groups are combined in int64, the sum of everything converted to
-//    FP64 once and scaled by 2^{e_i + f_j - 42}; alpha (real) and beta (real) applied.
+//    scale, so for g <= 8 their FP32 sums are exact integers while below 2^24 (guaranteed
+//    for 2K <= 1792); these seven groups get one TMEM accumulator each.  Groups 9..11 share an
+//    eighth (8 x 64 columns = all 512 of TMEM): it is 2^-12 below group 7, so the FP32
+//    rounding it collects over thousands of MMAs stays below FP64 rounding of the result
+//    (sharing one accumulator from group 7 or 8 on was measured 2-10x less accurate);
+//  * epilogue: the exact groups are combined in int64 (units of group 8), the sum of
+//    everything converted to FP64 once and scaled by 2^{e_i + f_j - 42}; real alpha, beta.
 // Pipeline: the whole block copies the digit tiles of one K step (16) into one of two
 // shared-memory stages while the MMAs of the previous step run; one thread issues the MMAs
 // and commits them to the stage's mbarrier.  Every wait is bounded (clock64); on timeout the
@@ -40,10 +41,10 @@ constexpr int OZ_TILE_A = OZ_BM * OZ_BK * 2;  // bytes of one A plane tile (4096
 constexpr int OZ_TILE_B = OZ_BN * OZ_BK * 2;  // bytes of one B plane tile (2048)
 constexpr int OZ_STAGE = OZ_S * (OZ_TILE_A + OZ_TILE_B);
 constexpr int OZ_THREADS = 256;
-constexpr int OZ_NACC = 7;
+constexpr int OZ_NACC = 8;
 constexpr int OZ_TMEM_COLS = 512;
 constexpr long long OZ_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
-constexpr int OZ_MAX_K2 = 2048;      // 2K bound for exact FP32 group sums
+constexpr int OZ_MAX_K2 = 1792;      // 2K bound for exact FP32 group sums (group 8: 9 2^10 per k)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -281,7 +282,7 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
         for (int t = 0; t < OZ_S; ++t) {
           const int g = (s + 1) + (t + 1);
           if (g > OZ_S + 1) continue;
-          const int acc = g <= 7 ? g - 2 : OZ_NACC - 1;
+          const int acc = g <= 8 ? g - 2 : OZ_NACC - 1;
           const uint32_t on = (init_mask >> acc) & 1u;
           oz_mma(tmem + acc * OZ_BN, oz_desc(sa + s * OZ_TILE_A), oz_desc(sb + t * OZ_TILE_B), on);
           init_mask |= 1u << acc;
@@ -329,15 +330,16 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int c = 2 * q + h;
-          // exact groups g = 2..7 (accumulator g-2): G_g = n_g 2^{6(7-g)} with integer n_g
+          // exact groups g = 2..8 (accumulator g-2): G_g = n_g 2^{6(7-g)} with integer n_g;
+          // hi = sum_g n_g 2^{6(8-g)} counts in units of group 8 (2^-6)
           long long hi = 0;
 #pragma unroll
           for (int a = 0; a < OZ_NACC - 1; ++a) {
             const float gv = __uint_as_float(v[a][c]);
             const long long ng = (long long)__float2int_rn(ldexpf(gv, -6 * (5 - a)));
-            hi += ng * (1ll << (6 * (5 - a)));
+            hi += ng * (1ll << (6 * (6 - a)));
           }
-          part[h] = (double)hi + (double)__uint_as_float(v[OZ_NACC - 1][c]);
+          part[h] = (double)hi * 0x1p-6 + (double)__uint_as_float(v[OZ_NACC - 1][c]);
         }
         const int fcol = cexp[(size_t)p * (N2p / 2) + gj];
         int E = erow + fcol - 42;
