@@ -229,7 +229,10 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
   if (rb * OZ_BM >= M || cb * (OZ_BN / 2) >= N) return;
   if (dims.lower && cb * (OZ_BN / 2) > rb * OZ_BM + OZ_BM - 1) return;
   unsigned char* stage0 = (unsigned char*)(((uintptr_t)oz_smem + 1023) & ~(uintptr_t)1023);
-  const int nks = K2p / OZ_BK;
+  const int nks = K2p / OZ_BK;  // plane layout (all problems)
+  // this problem's digit planes are zero beyond column 2 K_p: stop the K loop there
+  const int Kprob = dims.Kp ? dims.Kp[p] : dims.K;
+  const int nks_p = max(1, min(nks, (2 * Kprob + OZ_BK - 1) / OZ_BK));
   const size_t aplane = (size_t)(Mp / OZ_BM) * nks * (OZ_TILE_A / 2);
   const size_t bplane = (size_t)(N2p / OZ_BN) * nks * (OZ_TILE_B / 2);
   const unsigned char* Abase = (const unsigned char*)(Ap + (size_t)p * OZ_S * aplane) + (size_t)rb * nks * OZ_TILE_A;
@@ -251,7 +254,7 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
   const uint32_t tmem = tbase;
 
   uint32_t init_mask = 0;  // accumulators written at least once (issuing thread only)
-  for (int ks = 0; ks < nks; ++ks) {
+  for (int ks = 0; ks < nks_p; ++ks) {
     const int b = ks & 1;
     if (ks >= 2) {  // the MMAs of step ks-2 read this stage
       if (!oz_wait(&mbar[b], ((ks - 2) >> 1) & 1)) {
@@ -293,8 +296,8 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
     }
   }
   // wait for the last committed step (it covers every earlier MMA of this thread)
-  if (!s_fail && nks > 0) {
-    const int last = nks - 1;
+  if (!s_fail) {
+    const int last = nks_p - 1;
     if (!oz_wait(&mbar[last & 1], (last >> 1) & 1) && tid == 0) s_fail = 1;
   }
   __syncthreads();
