@@ -256,10 +256,11 @@ __global__ void init_u_kernel(int n, const int32_t* __restrict__ size, const int
 }
 
 // T (nb x nb, row-major, upper triangular) of block j0..j0+nb-1 from G = V^H V (row-major):
-// T_ii = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) G(0:i, i).  One block of nb threads per problem.
+// T_ii = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) G(0:i, i).  One block of nb threads per
+// problem; T is built in shared memory, packed by columns (column c holds rows 0..c).
 __global__ void build_t_kernel(int nb, const z64* __restrict__ Gbase, const z64* __restrict__ taucbase, int ncolv, int j0,
                                z64* __restrict__ Tbase) {
-  extern __shared__ z64 tcol[];
+  extern __shared__ z64 tp[];  // nb (nb + 1) / 2
   const int p = blockIdx.x;
   const int r = threadIdx.x;
   const z64* G = Gbase + (size_t)p * nb * nb;
@@ -269,12 +270,12 @@ __global__ void build_t_kernel(int nb, const z64* __restrict__ Gbase, const z64*
     const z64 ti = tau[i];
     z64 acc = zmk(0.0, 0.0);
     if (r < i)
-      for (int c = r; c < i; ++c) acc = zfma(T[(size_t)r * nb + c], G[(size_t)c * nb + i], acc);
-    tcol[r] = zmul(zmk(-ti.x, -ti.y), acc);
-    __syncthreads();
-    T[(size_t)r * nb + i] = (r < i) ? tcol[r] : (r == i ? ti : zmk(0.0, 0.0));
+      for (int c = r; c < i; ++c) acc = zfma(tp[c * (c + 1) / 2 + r], G[(size_t)c * nb + i], acc);
+    if (r < i) tp[i * (i + 1) / 2 + r] = zmul(zmk(-ti.x, -ti.y), acc);
+    else if (r == i) tp[i * (i + 1) / 2 + r] = ti;
     __syncthreads();
   }
+  for (int c = 0; c < nb; ++c) T[(size_t)r * nb + c] = (c >= r) ? tp[c * (c + 1) / 2 + r] : zmk(0.0, 0.0);
 }
 
 // column c < nc: U(:, c) /= ||U(:, c)||, times 1/sqrt(w[m - nc + c]) when use_rsqrt
@@ -315,7 +316,10 @@ cudaError_t launch_init_u(int n, int nprob, const int32_t* size, const int32_t* 
 
 cudaError_t launch_build_t(int nb, int nprob, const z64* G, const z64* tauc, int ncolv, int j0, z64* T,
                            cudaStream_t st) {
-  build_t_kernel<<<nprob, nb, nb * sizeof(z64), st>>>(nb, G, tauc, ncolv, j0, T);
+  const size_t smem = (size_t)nb * (nb + 1) / 2 * sizeof(z64);
+  cudaError_t e = cudaFuncSetAttribute(build_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  build_t_kernel<<<nprob, nb, smem, st>>>(nb, G, tauc, ncolv, j0, T);
   return cudaGetLastError();
 }
 

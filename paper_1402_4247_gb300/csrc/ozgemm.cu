@@ -23,10 +23,11 @@
 //    (sharing one accumulator from group 7 or 8 on was measured 2-10x less accurate);
 //  * epilogue: the exact groups are combined in int64 (units of group 8), the sum of
 //    everything converted to FP64 once and scaled by 2^{e_i + f_j - 42}; real alpha, beta.
-// Pipeline: the whole block copies the digit tiles of one K step (16) into one of two
-// shared-memory stages while the MMAs of the previous step run; one thread issues the MMAs
-// and commits them to the stage's mbarrier.  Every wait is bounded (clock64); on timeout the
-// block records an error, skips its epilogue and still frees its tensor memory.
+// Pipeline: the digit tiles of each K step (16) arrive in one of three shared-memory stages
+// by bulk asynchronous copies (TMA) issued by one producer thread; one thread issues the
+// MMAs and commits them to the stage's barrier.  Every wait is bounded (clock64); on
+// timeout the block records an error, lets its copies land, skips its epilogue and still
+// frees its tensor memory.
 #include <cuda_bf16.h>
 
 #include "nao_internal.cuh"
@@ -39,7 +40,8 @@ constexpr int OZ_BN = 64;            // tile columns (C'' columns = 32 complex c
 constexpr int OZ_BK = 16;            // K' per MMA step
 constexpr int OZ_TILE_A = OZ_BM * OZ_BK * 2;  // bytes of one A plane tile (4096)
 constexpr int OZ_TILE_B = OZ_BN * OZ_BK * 2;  // bytes of one B plane tile (2048)
-constexpr int OZ_STAGE = OZ_S * (OZ_TILE_A + OZ_TILE_B);
+constexpr int OZ_STAGE = OZ_S * (OZ_TILE_A + OZ_TILE_B);  // bytes per pipeline stage
+constexpr int OZ_STAGES = 3;
 constexpr int OZ_THREADS = 256;
 constexpr int OZ_NACC = 8;
 constexpr int OZ_TMEM_COLS = 512;
@@ -212,14 +214,31 @@ __device__ __forceinline__ bool oz_wait(uint64_t* mbar, uint32_t parity) {
   }
 }
 
+__device__ __forceinline__ void oz_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void oz_bulk_copy(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(smem_u32(dst_smem)), "l"(src_gmem), "r"(bytes), "r"(smem_u32(mbar)) : "memory");
+}
+
+// Warp-specialised pipeline over OZ_STAGES shared-memory stages:
+//   warp 0 / lane 0 (producer): waits until a stage is free (its "empty" barrier, arrived
+//     by the MMA commit), then loads it with 20 bulk copies (cp.async.bulk, the 1-D TMA)
+//     that complete on the stage's "full" barrier;
+//   warp 1 / lane 0 (MMA issuer): waits for a full stage, issues the 55 MMAs, commits them
+//     to the stage's empty barrier, and after the last stage to the "done" barrier;
+//   all 8 warps: wait for "done", then run the epilogue from TMEM.
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_bfloat16* __restrict__ Ap,
                const __nv_bfloat16* __restrict__ Bp, const int* __restrict__ rexp, const int* __restrict__ cexp, int Mp,
                int N2p, int K2p, z64* __restrict__ C, long long Cbs, long long Crs, long long Ccs, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char oz_smem[];
-  __shared__ uint64_t mbar[2];
+  __shared__ uint64_t full_bar[OZ_STAGES], empty_bar[OZ_STAGES], done_bar;
   __shared__ uint32_t tbase;
-  __shared__ int s_fail;
+  __shared__ volatile int s_fail;
+  __shared__ int s_issued;
   const int p = blockIdx.z;
   const int rb = blockIdx.y, cb = blockIdx.x;
   const int M = dims.Mp ? dims.Mp[p] : dims.M;
@@ -245,40 +264,54 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
   }
   if (tid == 0) {
     s_fail = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])));
+    s_issued = 0;
+    for (int st = 0; st < OZ_STAGES; ++st) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full_bar[st])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty_bar[st])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&done_bar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tbase;
 
-  uint32_t init_mask = 0;  // accumulators written at least once (issuing thread only)
-  for (int ks = 0; ks < nks_p; ++ks) {
-    const int b = ks & 1;
-    if (ks >= 2) {  // the MMAs of step ks-2 read this stage
-      if (!oz_wait(&mbar[b], ((ks - 2) >> 1) & 1)) {
-        if (tid == 0) s_fail = 1;
+  if (warp == 0 && lane == 0) {
+    // ---------------- producer
+    int ks = 0;
+    for (; ks < nks_p; ++ks) {
+      const int st = ks % OZ_STAGES;
+      if (ks >= OZ_STAGES && !oz_wait(&empty_bar[st], ((ks / OZ_STAGES) - 1) & 1)) {
+        s_fail = 1;
+        break;
       }
+      if (s_fail) break;
+      unsigned char* sdst = stage0 + st * OZ_STAGE;
+      oz_expect_tx(&full_bar[st], OZ_STAGE);
+#pragma unroll
+      for (int s = 0; s < OZ_S; ++s)
+        oz_bulk_copy(sdst + s * OZ_TILE_A, Abase + (size_t)s * aplane * 2 + (size_t)ks * OZ_TILE_A, OZ_TILE_A,
+                     &full_bar[st]);
+#pragma unroll
+      for (int t = 0; t < OZ_S; ++t)
+        oz_bulk_copy(sdst + OZ_S * OZ_TILE_A + t * OZ_TILE_B, Bbase + (size_t)t * bplane * 2 + (size_t)ks * OZ_TILE_B,
+                     OZ_TILE_B, &full_bar[st]);
     }
-    __syncthreads();
-    if (s_fail) break;
-    unsigned char* st = stage0 + b * OZ_STAGE;
-    // copy: 9 A tiles (4096 B) then 9 B tiles (2560 B), 16 B per thread per pass
-    for (int o = tid * 16; o < OZ_S * OZ_TILE_A; o += OZ_THREADS * 16) {
-      const int s = o / OZ_TILE_A, w = o % OZ_TILE_A;
-      *(uint4*)(st + o) = __ldg((const uint4*)(Abase + (size_t)s * aplane * 2 + (size_t)ks * OZ_TILE_A + w));
-    }
-    for (int o = tid * 16; o < OZ_S * OZ_TILE_B; o += OZ_THREADS * 16) {
-      const int s = o / OZ_TILE_B, w = o % OZ_TILE_B;
-      *(uint4*)(st + OZ_S * OZ_TILE_A + o) =
-          __ldg((const uint4*)(Bbase + (size_t)s * bplane * 2 + (size_t)ks * OZ_TILE_B + w));
-    }
-    asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
-    if (tid == 0) {
+    s_issued = ks;
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    uint32_t init_mask = 0;  // accumulators written at least once
+    int ks = 0;
+    for (; ks < nks_p; ++ks) {
+      const int st = ks % OZ_STAGES;
+      if (!oz_wait(&full_bar[st], (ks / OZ_STAGES) & 1)) {
+        s_fail = 1;
+        break;
+      }
+      if (s_fail) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t sa = smem_u32(st), sb = smem_u32(st + OZ_S * OZ_TILE_A);
+      unsigned char* ssrc = stage0 + st * OZ_STAGE;
+      const uint32_t sa = smem_u32(ssrc), sb = smem_u32(ssrc + OZ_S * OZ_TILE_A);
 #pragma unroll
       for (int s = 0; s < OZ_S; ++s) {
 #pragma unroll
@@ -292,18 +325,25 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   :: "r"(smem_u32(&mbar[b])));
+                   :: "r"(smem_u32(&empty_bar[st])));
     }
+    // "done" arrives when every MMA issued above has completed (also after a failure)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(smem_u32(&done_bar)));
   }
-  // wait for the last committed step (it covers every earlier MMA of this thread)
-  if (!s_fail) {
-    const int last = nks_p - 1;
-    if (!oz_wait(&mbar[last & 1], (last >> 1) & 1) && tid == 0) s_fail = 1;
-  }
+  // everyone: wait for the MMAs (bounded), then the epilogue
+  const bool done_ok = oz_wait(&done_bar, 0);
+  if (!done_ok && tid == 0) s_fail = 1;
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (s_fail) {
-    if (tid == 0) atomicExch(err, 1);
+    if (tid == 0) {
+      atomicExch(err, 1);
+      // let every bulk copy that was issued land before the block (and its shared memory) goes
+      const int issued = s_issued;
+      for (int ks = (issued > OZ_STAGES ? issued - OZ_STAGES : 0); ks < issued; ++ks)
+        oz_wait(&full_bar[ks % OZ_STAGES], (ks / OZ_STAGES) & 1);
+    }
   } else {
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows); warps 0-3 take
     // complex columns 0..15 of the tile, warps 4-7 columns 16..31.
@@ -394,7 +434,7 @@ cudaError_t launch_zgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand 
   oz_split_b<<<dim3((N2p / 2 + 7) / 8, nprob), 256, 0, st>>>(nprob, dims, B, N2p, K2p, Bpl, cexp);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = 2 * (size_t)OZ_STAGE + 1024;
+  const size_t smem = OZ_STAGES * (size_t)OZ_STAGE + 1024;
   e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(N2p / OZ_BN, Mp / OZ_BM, nprob);

@@ -9,12 +9,15 @@
 //   p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (a zero minor takes the sign of its
 //   predecessor), rescaled by powers of two: the division-free form of the LDL^T pivot
 //   count, three operations per step.
-//     1. bisection in FP32 (64x the FP64 rate on this GPU) to ~1e-7 |T|;
+//     1. bisection in FP32 (64x the FP64 rate on this GPU) to ~1e-7 |T|, counting negative
+//        pivots of the LDL^T form with a fast reciprocal;
 //     2. the FP32 bracket, widened by 64 eps_32 |T| (an FP32 count is exact for a matrix
 //        within a few eps_32 |T| of T), is verified with two FP64 counts; if it holds exactly
 //        this one eigenvalue, safeguarded Newton on p_n (derivative from the same
-//        recurrence) converges in a few steps, every iterate also tightening the bracket by
-//        its count; otherwise (tight clusters, failed verification) FP64 bisection.
+//        recurrence) converges in a few steps to the rounding noise of p_n, and a bracket of
+//        a few noise widths around it, verified by two FP64 counts, replaces the FP32 one;
+//     3. FP64 bisection closes the bracket to eps |T| (tight clusters and failed
+//        verifications take this path from the wider bracket).
 // * Eigenvectors (kernel 2, same block split): inverse iteration with a partially pivoted LU
 //   of T - lambda I (tiny pivots perturbed to eps |T|), a scaled right-hand side, the growth
 //   test |x|_inf >= sqrt(0.1/blocksize) plus two extra solves, and modified Gram-Schmidt
@@ -110,30 +113,18 @@ __device__ TriInfo load_tridiag(int m, const double* __restrict__ din, const dou
   return t;
 }
 
-// FP32 Sturm count of T[b0:b1) below x (matrix rounded to FP32)
+// FP32 Sturm count of T[b0:b1) below x (matrix rounded to FP32), pivot form
+// q_i = (d_i - x) - e_{i-1}^2 / q_{i-1} with a fast approximate reciprocal: this count only
+// isolates eigenvalues; the bracket it gives is widened and re-verified in FP64.
 __device__ int sturm_count32(const float* __restrict__ d, const float* __restrict__ e2, int b0, int b1, float x) {
-  float pm1 = 1.0f, p = d[b0] - x;
-  int bits = __float_as_int(p);
-  int sn = (bits < 0) && ((bits << 1) != 0);
-  int cnt = sn;
+  const float pivmin = 1e-30f;
+  float q = d[b0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  int cnt = q < 0.f;
   for (int i = b0 + 1; i < b1; ++i) {
-    const float pn = fmaf(d[i] - x, p, -e2[i - 1] * pm1);
-    pm1 = p;
-    p = pn;
-    bits = __float_as_int(p);
-    const int zero = (bits << 1) == 0;
-    const int ns = zero ? sn : (int)(bits < 0);
-    cnt += (ns != sn);
-    sn = ns;
-    const int ex = (bits >> 23) & 0xff, ex1 = (__float_as_int(pm1) >> 23) & 0xff;
-    const int emax = ex > ex1 ? ex : ex1;
-    if (emax > 127 + 50) {
-      p *= 0x1p-50f;
-      pm1 *= 0x1p-50f;
-    } else if (emax < 127 - 50) {
-      p *= 0x1p50f;
-      pm1 *= 0x1p50f;
-    }
+    q = (d[i] - x) - __fdividef(e2[i - 1], q);
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += q < 0.f;
   }
   return cnt;
 }
@@ -249,31 +240,45 @@ stebz_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__
       hi = T.gu;
     }
     const bool isolated = (clo == idx && chi == idx + 1);
-    double x = 0.5 * (lo + hi);
-    for (int it = 0; it < 128; ++it) {
-      const double tol = fmax(2.0 * eps * fmax(fabs(lo), fabs(hi)), eps * T.tnorm);
-      if (hi - lo <= tol) break;
-      double pn = 0.0, dpn = 0.0;
-      const int c = sturm64(d, e2, b0, b1, x, isolated, &pn, &dpn);
-      if (c > idx) hi = x;
-      else lo = x;
-      double xn = 0.5 * (lo + hi);
-      if (isolated && dpn != 0.0) {
-        const double step = pn / dpn;
-        const double cand = x - step;
-        if (cand > lo && cand < hi) {
-          xn = cand;
-          if (fabs(step) <= tol) {  // converged Newton iterate
-            x = cand;
-            break;
-          }
+    if (isolated) {
+      // safeguarded Newton on p_n; its step bottoms out at the rounding noise of p_n, so
+      // it only narrows the bracket, which bisection then closes to eps |T|
+      double x = 0.5 * (lo + hi), last = hi - lo;
+      bool conv = false;
+      for (int it = 0; it < 8; ++it) {
+        double pn = 0.0, dpn = 0.0;
+        const int c = sturm64(d, e2, b0, b1, x, true, &pn, &dpn);
+        if (c > idx) hi = x;
+        else lo = x;
+        if (dpn == 0.0) break;
+        const double step = pn / dpn, cand = x - step;
+        if (!(cand > lo && cand < hi)) break;
+        x = cand;
+        last = fabs(step);
+        if (last <= 64.0 * eps * T.tnorm) {
+          conv = true;
+          break;
         }
       }
-      if (xn <= lo || xn >= hi) break;  // bracket at rounding level
-      x = xn;
+      if (conv) {
+        const double del = 16.0 * last + 4.0 * eps * T.tnorm;
+        const double l2 = fmax(x - del, lo), h2 = fmin(x + del, hi);
+        const int cl = sturm64(d, e2, b0, b1, l2, false, nullptr, nullptr);
+        const int ch = sturm64(d, e2, b0, b1, h2, false, nullptr, nullptr);
+        if (cl <= idx && idx < ch) {
+          lo = l2;
+          hi = h2;
+        }
+      }
     }
-    lam = (hi - lo <= fmax(2.0 * eps * fmax(fabs(lo), fabs(hi)), eps * T.tnorm)) ? 0.5 * (lo + hi) : x;
-    lam = fmin(fmax(lam, lo), hi);
+    for (int it = 0; it < 128; ++it) {  // FP64 bisection to eps |T|
+      const double mid = 0.5 * (lo + hi);
+      const double tol = fmax(2.0 * eps * fmax(fabs(lo), fabs(hi)), eps * T.tnorm);
+      if (hi - lo <= tol || mid <= lo || mid >= hi) break;
+      if (sturm64(d, e2, b0, b1, mid, false, nullptr, nullptr) > idx) hi = mid;
+      else lo = mid;
+    }
+    lam = 0.5 * (lo + hi);
   }
   wslot[(size_t)p * n + j] = lam;
 }
