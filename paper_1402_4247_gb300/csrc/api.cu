@@ -194,6 +194,33 @@ cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t*
   return launch_normalize_cols(n, nprob, size, ncols, w, n, use_rsqrt, U, n, snn, st);
 }
 
+// Eigen_HH step 1, blocked: panels of NAO_HT_NB columns reduced by the cluster kernel, each
+// followed by the deferred update A(r0:, r0:) -= V W^H + W V^H of the rest (lower triangle,
+// one rank-2 NB product).  VW: [nprob][n][3 NB] workspace.
+cudaError_t hetrd_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, z64* A, double* d, double* e, z64* tau,
+                          z64* VW, void* ozws, cudaStream_t st) {
+  const int NB = NAO_HT_NB;
+  const int cl = hetrd_cluster_size(nprob, ctx->num_sms);
+  const long long snn = (long long)n * n, svw = (long long)n * 3 * NB;
+  for (int i0 = 0; i0 < n; i0 += NB) {
+    cudaError_t err;
+    {
+      NaoStage stage_(ctx, "hetrd", st, 1);
+      err = launch_hetrd_panel(n, nprob, size, A, n, snn, d, e, tau, n, VW, svw, i0, cl, st);
+    }
+    if (err != cudaSuccess) return err;
+    const int r0 = i0 + NB;
+    if (r0 >= n) break;
+    const int rows = n - r0;
+    GemmDims dd{rows, rows, 2 * NB, nullptr, nullptr, nullptr, 1};
+    err = run_zgemm(ctx, "hetrd", nprob, dd, -1.0, GemmOperand{VW + (size_t)r0 * 3 * NB, svw, 3 * NB, 1, 0, nullptr},
+                    GemmOperand{VW + (size_t)r0 * 3 * NB + NB, svw, 1, 3 * NB, 1, nullptr}, 1.0,
+                    A + r0 + (size_t)r0 * n, snn, 1, n, ozws, st);
+    if (err != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -363,7 +390,8 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   const size_t oVf = P.take<z64>((size_t)n * ncolv * nmax), oTc = P.take<z64>((size_t)ncolv * nmax),
                oG2 = P.take<z64>((size_t)NAO_WY_NB * NAO_WY_NB * nmax),
                oT2 = P.take<z64>((size_t)NAO_WY_NB * NAO_WY_NB * nmax),
-               oW = P.take<z64>((size_t)NAO_WY_NB * n * nmax), oW2 = P.take<z64>((size_t)NAO_WY_NB * n * nmax);
+               oW = P.take<z64>((size_t)NAO_WY_NB * n * nmax), oW2 = P.take<z64>((size_t)NAO_WY_NB * n * nmax),
+               oVW = P.take<z64>((size_t)3 * NAO_HT_NB * n * nmax);
   int rc = nao_ws_reserve(ctx, P.off);
   if (rc) return rc;
   char* ws = (char*)ctx->ws;
@@ -380,13 +408,12 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
           *stH = (int32_t*)(ws + ostH);
   void* ozws = use_tc ? (void*)(ws + oOz) : nullptr;
   z64 *Vf = (z64*)(ws + oVf), *tauc = (z64*)(ws + oTc), *Gw = (z64*)(ws + oG2), *Tw = (z64*)(ws + oT2),
-      *Ww = (z64*)(ws + oW), *W2w = (z64*)(ws + oW2);
+      *Ww = (z64*)(ws + oW), *W2w = (z64*)(ws + oW2), *VWp = (z64*)(ws + oVW);
   const long long snn = (long long)nn;
 
   // ---- Part 2: Eigen_HH(S) -> s, U;  X = U_m s_m^{-1/2}
   NAO_STAGE("herm_fill", 1, launch_herm_fill(n, nSe, (const z64*)S, snn, nullptr, AS, n, snn, st));
-  NAO_STAGE("hetrd", 1, launch_hetrd(n, nSe, nullptr, AS, n, snn, dS, eS, tauS, n,
-                                     hetrd_cluster_size(nSe, ctx->num_sms), st));
+  NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nSe, nullptr, AS, dS, eS, tauS, VWp, ozws, st));
   NAO_STAGE("stein", 1, launch_stein(n, nSe, nullptr, dS, eS, n, wS, Z, n, snn, scr, stS, st));
   NAO_STAGE("misc", 1, launch_count_kept(n, nSe, wS, n, s_cut, mS, stS, st));
   {  // one Newton-Schulz step: Z2 = Z (3I - Z^T Z)/2 = Z - Z (Z^T Z - I)/2
@@ -417,8 +444,7 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   NAO_STAGE("misc", 1, launch_hermitize(n, nprob, mP, Hp, n, snn, st));
 
   // ---- Part 4: Eigen_HH(H') -> eps, V;  C = X V
-  NAO_STAGE("hetrd", 1, launch_hetrd(n, nprob, mP, Hp, n, snn, dH, eH, tauH, n,
-                                     hetrd_cluster_size(nprob, ctx->num_sms), st));
+  NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nprob, mP, Hp, dH, eH, tauH, VWp, ozws, st));
   NAO_STAGE("stein", 1, launch_stein(n, nprob, mP, dH, eH, n, wH, Z, n, snn, scr, stH, st));
   {
     GemmDims d{n, n, n, mP, mP, mP, 1};

@@ -1,5 +1,7 @@
 // Eigen_HH step 1 (Sec. 3, Procedures 1-6): Householder reduction of a Hermitian matrix to
-// real symmetric tridiagonal form.
+// real symmetric tridiagonal form, blocked by panels of NAO_HT_NB columns (the rank-2
+// update of Procedure 6 is deferred within a panel and applied once per panel as a
+// rank-2 NB product on the tensor cores by the caller).
 //
 // Column i: x = A(i+1:m, i) (Procedure 1); a reflector H_i = I - tau v v^H with v(0) = 1 and
 // a REAL beta, H_i^H x = beta e_1, is formed from |x| (Procedure 2) and kept in place for the
@@ -61,17 +63,28 @@ __device__ __forceinline__ double2 block_sum2(double a, double b, double* red) {
 // first pair index of block k when npairs pairs are dealt to C blocks
 __device__ __forceinline__ int pair_start(int k, int npairs, int C) { return (int)(((long long)k * npairs) / C); }
 
+// One panel of NAO_HT_NB columns i0.. of the blocked reduction.  The rank-2 updates of the
+// panel's columns are deferred: column i first receives the updates of the earlier panel
+// columns (a), its reflector is formed (b), and the Hermitian product with the trailing
+// matrix as it stood at the panel start is corrected by the panel's V and W columns:
+//   p = A22 v - V (W^H v) - W (V^H v)   (c, d),   w = tau p - (tau/2)(p^H tau p ...) v (e).
+// The caller applies A22 -= V W^H + W V^H to the rest of the matrix after the panel
+// (a rank-2 NB update, run as one tensor-core product).  VW holds, per row, [V | W | V].
 __global__ void __launch_bounds__(HT_THREADS)
-hetrd_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Abase, int ld, long long strideA,
-             double* __restrict__ dbase, double* __restrict__ ebase, z64* __restrict__ taubase, long long strideV) {
+hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Abase, int ld, long long strideA,
+                   double* __restrict__ dbase, double* __restrict__ ebase, z64* __restrict__ taubase, long long strideV,
+                   z64* __restrict__ VWbase, long long strideVW, int i0) {
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
+  constexpr int NB = NAO_HT_NB;
+  constexpr int LDVW = 3 * NB;
   extern __shared__ z64 sm[];
-  z64* v = sm;           // [n] reflector of the current column (trailing coordinates)
-  z64* w = sm + n;       // [n] p, then w
-  z64* pown = sm + 2 * n;  // [n] p for this block's rows, read by the other blocks
-  z64* part = sm + 3 * n;  // [2 * HT_THREADS] partial sums of the K threads of each pair
+  z64* v = sm;               // [n] reflector (trailing coordinates)
+  z64* w = sm + n;           // [n] p, then w
+  z64* pown = sm + 2 * n;    // [n] corrected p for this block's rows (read by the others)
+  z64* part = sm + 3 * n;    // [2 * HT_THREADS] partial sums of the K threads of each pair
+  __shared__ z64 ypart[2 * NB], yfull[2 * NB];
   __shared__ double red[64];
   __shared__ z64 s_tau, s_scale;
   __shared__ double s_beta;
@@ -82,13 +95,38 @@ hetrd_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Abase, i
   double* d = dbase + (size_t)p * strideV;
   double* e = ebase + (size_t)p * strideV;
   z64* tau = taubase + (size_t)p * strideV;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (m <= 0) return;  // uniform over the cluster
+  z64* VW = VWbase + (size_t)p * strideVW;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int iend = min(i0 + NB, m);  // uniform over the cluster (one problem per cluster)
 
-  for (int i = 0; i < m - 1; ++i) {
-    const int mt = m - i - 1;  // order of the trailing block A22 = A(i+1:m, i+1:m)
+  for (int i = i0; i < iend; ++i) {
+    const int j = i - i0;
+    // (a) column i (rows i..m-1) receives the updates of panel columns 0..j-1
+    if (j > 0) {
+      for (int r = i + rank * nt + tid; r < m; r += C * nt) {
+        z64 acc = A[(size_t)i * ld + r];
+        const z64* Vr = VW + (size_t)r * LDVW;
+        const z64* Vi = VW + (size_t)i * LDVW;
+        for (int jj = 0; jj < j; ++jj) {
+          acc = zsub(acc, zmul(Vr[jj], zconj(Vi[NB + jj])));  // V(r,jj) conj(W(i,jj))
+          acc = zsub(acc, zmul(Vr[NB + jj], zconj(Vi[jj])));  // W(r,jj) conj(V(i,jj))
+        }
+        if (r == i) acc.y = 0.0;
+        A[(size_t)i * ld + r] = acc;
+      }
+    }
+    cluster.sync();  // S1: column i is final everywhere
+    if (i == m - 1) {  // last diagonal element, no reflector
+      if (rank == 0 && tid == 0) {
+        d[m - 1] = A[(size_t)(m - 1) * ld + (m - 1)].x;
+        e[m - 1] = 0.0;
+        tau[m - 1] = zmk(0.0, 0.0);
+      }
+      break;
+    }
+    const int mt = m - i - 1;
     const z64* col = A + (size_t)i * ld;
-    // Procedures 1-2 (every block, redundantly): |x(1:)|^2 of x = A(i+1:m, i)
+    // (b) Procedures 1-2 (every block, redundantly): the reflector of x = A(i+1:m, i)
     double s = 0.0;
     for (int r = i + 2 + tid; r < m; r += nt) s += zabs2(col[r]);
     s = block_sum2(s, 0.0, red).x;
@@ -120,14 +158,13 @@ hetrd_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Abase, i
     __syncthreads();
     const z64 t = s_tau;
     const z64 scale = s_scale;
-    // Procedure 3: v in shared memory (trailing coordinates, v[0] = 1)
     for (int r = tid; r < mt; r += nt) v[r] = (r == 0) ? zmk(1.0, 0.0) : zmul(col[i + 1 + r], scale);
     __syncthreads();
     const bool active = !(t.x == 0.0 && t.y == 0.0);  // H_i = I otherwise (uniform)
 
-    // Procedure 4: p = A22 v for this block's row pairs (lower triangle only).  Thread
-    // (k, g) covers the k-th slice of the column range of both rows of pair g.
-    z64* A22 = A + (size_t)(i + 1) * ld + (i + 1);
+    // (c) Procedure 4 on the panel-start trailing matrix: p_raw = A22 v for this block's
+    // row pairs, and the partial corrections y1 = W^H v, y2 = V^H v over the same rows
+    const z64* A22 = A + (size_t)(i + 1) * ld + (i + 1);
     const int npairs = (mt + 1) >> 1;
     const int g0 = pair_start(rank, npairs, C), g1 = pair_start(rank + 1, npairs, C);
     const int P = g1 - g0;
@@ -142,15 +179,34 @@ hetrd_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Abase, i
           const int r = h ? mt - 1 - g : g;
           z64 acc = zmk(0.0, 0.0);
           if (!(h && r == g)) {
-            // row part: A(r, c) for c <= r (coalesced over consecutive r)
             const int ce = min(c1, r + 1);
             for (int c = c0; c < ce; ++c) acc = zfma(A22[(size_t)c * ld + r], v[c], acc);
-            // column part: conj(A(c, r)) for c > r (column r, contiguous per thread)
             const z64* colr = A22 + (size_t)r * ld;
             for (int c = max(c0, r + 1); c < c1; ++c) acc = zcfma(colr[c], v[c], acc);
           }
           part[(size_t)k * 2 * P + 2 * gl + h] = acc;
         }
+      }
+      // partial y over this block's rows: warp-strided over the 2j entries
+      for (int jj = wid; jj < 2 * j; jj += nw) {
+        const int cidx = jj < j ? NB + jj : jj - j;  // W column jj, or V column jj - j
+        double sre = 0.0, sim = 0.0;
+        for (int g = g0 + lane; g < g1; g += 32) {
+          const int ra = g, rb = mt - 1 - g;
+          const z64 a = VW[(size_t)(i + 1 + ra) * LDVW + cidx];
+          const z64 ca = zcfma(a, v[ra], zmk(0.0, 0.0));
+          sre += ca.x;
+          sim += ca.y;
+          if (rb != ra) {
+            const z64 b = VW[(size_t)(i + 1 + rb) * LDVW + cidx];
+            const z64 cb = zcfma(b, v[rb], zmk(0.0, 0.0));
+            sre += cb.x;
+            sim += cb.y;
+          }
+        }
+        sre = warp_sum(sre);
+        sim = warp_sum(sim);
+        if (lane == 0) ypart[jj] = zmk(sre, sim);
       }
       __syncthreads();
       for (int tt = tid; tt < 2 * P; tt += nt) {
@@ -162,71 +218,69 @@ hetrd_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Abase, i
         pown[r] = acc;
       }
     }
-    cluster.sync();  // every block's p pieces are written; every block is done reading column i
-    if (rank == 0) {  // Procedure 3: store v below the subdiagonal of column i
+    cluster.sync();  // S2: partial results ready; every block is done reading column i
+    if (rank == 0) {  // Procedure 3: keep v below the subdiagonal of column i, and in V
       z64* colw = A + (size_t)i * ld;
-      for (int r = tid; r < mt; r += nt) colw[i + 1 + r] = (r == 0) ? zmk(s_beta, 0.0) : v[r];
+      for (int r = tid; r < mt; r += nt) {
+        colw[i + 1 + r] = (r == 0) ? zmk(s_beta, 0.0) : v[r];
+        z64* row = VW + (size_t)(i + 1 + r) * LDVW;
+        row[j] = active ? v[r] : zmk(0.0, 0.0);
+        row[2 * NB + j] = row[j];
+      }
     }
     if (active) {
-      // gather p from its owners; p := tau * p; dot = p^H v
+      // (d) y = sum over the cluster's blocks (fixed order), then the corrections of this
+      // block's rows: p_raw -= V y2 + W y1  (y1 = W^H v multiplies V, y2 = V^H v multiplies W)
+      for (int jj = tid; jj < 2 * j; jj += nt) {
+        z64 acc = zmk(0.0, 0.0);
+        for (int k = 0; k < C; ++k) acc = zadd(acc, cluster.map_shared_rank(ypart, k)[jj]);
+        yfull[jj] = acc;
+      }
+      __syncthreads();
+      if (j > 0)
+        for (int tt = tid; tt < 2 * P; tt += nt) {
+          const int gl = tt >> 1, h = tt & 1, g = g0 + gl;
+          const int r = h ? mt - 1 - g : g;
+          if (h && r == g) continue;
+          const z64* row = VW + (size_t)(i + 1 + r) * LDVW;
+          z64 acc = pown[r];
+          for (int jj = 0; jj < j; ++jj) {
+            acc = zsub(acc, zmul(row[jj], yfull[jj]));           // V(r,jj) (W^H v)_jj
+            acc = zsub(acc, zmul(row[NB + jj], yfull[j + jj]));  // W(r,jj) (V^H v)_jj
+          }
+          pown[r] = acc;
+        }
+    }
+    cluster.sync();  // S3: corrected pieces of p ready
+    if (active) {
+      // (e) Procedure 5: w = tau p - (tau/2) ((tau p)^H v) v on the full vector
       double dre = 0.0, dim = 0.0;
       for (int g = tid; g < npairs; g += nt) {
         int k = 0;
         while (k + 1 < C && pair_start(k + 1, npairs, C) <= g) ++k;
         const z64* src = cluster.map_shared_rank(pown, k);
         const int ra = g, rb = mt - 1 - g;
-        z64 pa = zmul(t, src[ra]);
+        const z64 pa = zmul(t, src[ra]);
         w[ra] = pa;
-        z64 c1 = zcfma(pa, v[ra], zmk(0.0, 0.0));
+        const z64 c1 = zcfma(pa, v[ra], zmk(0.0, 0.0));
         dre += c1.x;
         dim += c1.y;
         if (rb != ra) {
-          z64 pb = zmul(t, src[rb]);
+          const z64 pb = zmul(t, src[rb]);
           w[rb] = pb;
-          z64 c2 = zcfma(pb, v[rb], zmk(0.0, 0.0));
+          const z64 c2 = zcfma(pb, v[rb], zmk(0.0, 0.0));
           dre += c2.x;
           dim += c2.y;
         }
       }
       const double2 dot = block_sum2(dre, dim, red);
-      // Procedure 5: w = p - (tau/2) (p^H v) v
       const z64 alpha2 = zscale(zmul(t, zmk(dot.x, dot.y)), -0.5);
       for (int r = tid; r < mt; r += nt) w[r] = zfma(alpha2, v[r], w[r]);
       __syncthreads();
-      // Procedure 6: A22 -= v w^H + w v^H on the lower triangle, enumerated column by column
-      // (column c holds rows c..mt-1); the cluster's blocks take equal contiguous shares and
-      // consecutive threads consecutive rows, so every access is coalesced.
-      const long long ntri = (long long)mt * (mt + 1) / 2;
-      const long long q0 = (ntri * rank) / C, q1 = (ntri * (rank + 1)) / C;
-      long long q = q0 + tid;
-      if (q < q1) {
-        // locate element q: column c with start(c) = c*mt - c(c-1)/2 <= q < start(c+1)
-        int c = (int)((2.0 * mt + 1.0 - sqrt((2.0 * mt + 1.0) * (2.0 * mt + 1.0) - 8.0 * (double)q)) * 0.5);
-        if (c < 0) c = 0;
-        while (c > 0 && (long long)c * mt - (long long)c * (c - 1) / 2 > q) --c;
-        while ((long long)(c + 1) * mt - (long long)(c + 1) * c / 2 <= q) ++c;
-        int r = c + (int)(q - ((long long)c * mt - (long long)c * (c - 1) / 2));
-        for (; q < q1; q += nt) {
-          z64* ap = A22 + (size_t)c * ld + r;
-          z64 a = *ap;
-          const z64 vr = v[r], wr = w[r], vc = v[c], wc = w[c];
-          a.x -= vr.x * wc.x + vr.y * wc.y + wr.x * vc.x + wr.y * vc.y;
-          a.y -= vr.y * wc.x - vr.x * wc.y + wr.y * vc.x - wr.x * vc.y;
-          *ap = a;
-          r += nt;  // advance by nt elements along the column-major enumeration
-          while (r >= mt && c < mt) {
-            r -= mt - c - 1;  // leave column c (rows c..mt-1), enter column c+1 at row c+1
-            ++c;
-          }
-        }
-      }
     }
-    cluster.sync();  // the update is complete (and the remote p pieces are no longer read)
-  }
-  if (tid == 0 && rank == 0) {
-    d[m - 1] = A[(size_t)(m - 1) * ld + (m - 1)].x;
-    e[m - 1] = 0.0;
-    tau[m - 1] = zmk(0.0, 0.0);
+    if (rank == 0)
+      for (int r = tid; r < mt; r += nt) VW[(size_t)(i + 1 + r) * LDVW + NB + j] = active ? w[r] : zmk(0.0, 0.0);
+    cluster.sync();  // S4: V and W column j visible to the whole cluster
   }
 }
 
@@ -238,10 +292,11 @@ int hetrd_cluster_size(int nprob, int num_sms) {
   return c;
 }
 
-cudaError_t launch_hetrd(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA, double* d,
-                         double* e, z64* tau, long long strideV, int cluster, cudaStream_t st) {
+cudaError_t launch_hetrd_panel(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA, double* d,
+                               double* e, z64* tau, long long strideV, z64* VW, long long strideVW, int i0, int cluster,
+                               cudaStream_t st) {
   size_t smem = sizeof(z64) * (3 * (size_t)n + 2 * HT_THREADS);
-  cudaError_t err = cudaFuncSetAttribute(hetrd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = cudaFuncSetAttribute(hetrd_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nprob * cluster));
@@ -255,5 +310,5 @@ cudaError_t launch_hetrd(int n, int nprob, const int32_t* size, z64* A, int ld, 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, hetrd_kernel, n, size, A, ld, strideA, d, e, tau, strideV);
+  return cudaLaunchKernelEx(&cfg, hetrd_panel_kernel, n, size, A, ld, strideA, d, e, tau, strideV, VW, strideVW, i0);
 }

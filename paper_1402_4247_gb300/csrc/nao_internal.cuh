@@ -103,9 +103,14 @@ cudaError_t launch_herm_fill(int n, int nprob, const z64* src, long long src_str
 // full Hermitian column-major matrix A (ld).  size[p] (or n when size == null) is the order.
 // Only the lower triangle of A is read and updated.  `cluster` blocks (1..8, a thread-block
 // cluster) share each matrix; hetrd_cluster_size picks it from the problem count.
+// One launch reduces the panel of columns i0 .. i0+NAO_HT_NB-1; VW ([nprob][n][3 NB],
+// per row [V | W | V]) receives the panel's reflectors and update vectors, and the caller
+// applies A(i0+NB:, i0+NB:) -= V W^H + W V^H before the next panel.
+constexpr int NAO_HT_NB = 32;
 int hetrd_cluster_size(int nprob, int num_sms);
-cudaError_t launch_hetrd(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA,
-                         double* d, double* e, z64* tau, long long strideV, int cluster, cudaStream_t st);
+cudaError_t launch_hetrd_panel(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA, double* d,
+                               double* e, z64* tau, long long strideV, z64* VW, long long strideVW, int i0, int cluster,
+                               cudaStream_t st);
 
 // Eigen_HH step 2: eigenvalues w (ascending) and orthonormal eigenvectors Z (column-major,
 // ld) of tridiag(e, d, e) by bisection + inverse iteration.  scratch: see stein_scratch_doubles.
