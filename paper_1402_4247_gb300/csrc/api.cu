@@ -145,6 +145,18 @@ cudaError_t run_zgemm(nao_ctx* ctx, const char* stage, int nprob, GemmDims d, do
   return launch_zgemm(nprob, d, zmk(alpha, 0.0), A, B, zmk(beta, 0.0), C, Cbs, Crs, Ccs, st);
 }
 
+// Real counterpart of run_zgemm (the Newton-Schulz Gram matrix).
+cudaError_t run_dgemm(nao_ctx* ctx, const char* stage, int nprob, GemmDims d, double alpha, GemmOperand A,
+                      GemmOperand B, double beta, double* C, long long Cbs, long long Crs, long long Ccs, void* ozws,
+                      cudaStream_t st) {
+  if (ctx->gemm_method == NAO_GEMM_TC && ozws && dgemm_oz_supported(d)) {
+    NaoStage stage_(ctx, stage, st, 3);
+    return launch_dgemm_oz(nprob, d, alpha, A, B, beta, C, Cbs, Crs, Ccs, ozws, ctx->dev_flags, st);
+  }
+  NaoStage stage_(ctx, stage, st, 1);
+  return launch_dgemm(nprob, d, alpha, A, B, beta, C, Cbs, Crs, Ccs, st);
+}
+
 // Eigen_HH steps 3-4 in blocked form: U(:, c) = Q Z(:, m - nc + c) for c < nc (nc = ncols[p]),
 // normalised (times 1/sqrt(w) when use_rsqrt), with Q = prod_j (I - V_j T_j V_j^H) applied from
 // the last block of NAO_WY_NB reflectors to the first; every block costs three products
@@ -418,9 +430,9 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   NAO_STAGE("misc", 1, launch_count_kept(n, nSe, wS, n, s_cut, mS, stS, st));
   {  // one Newton-Schulz step: Z2 = Z (3I - Z^T Z)/2 = Z - Z (Z^T Z - I)/2
     GemmDims d{n, n, n, nullptr, nullptr, nullptr, 1};
-    NaoStage stage_(ctx, "ortho_ns", st, 2);
-    NAO_CUDA_TRY(ctx, launch_dgemm(nSe, d, 1.0, GemmOperand{Z, snn, n, 1, 0, nullptr},
-                                   GemmOperand{Z, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, st));
+    NAO_CUDA_TRY(ctx, run_dgemm(ctx, "ortho_ns", nSe, d, 1.0, GemmOperand{Z, snn, n, 1, 0, nullptr},
+                                GemmOperand{Z, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, ozws, st));
+    NaoStage stage_(ctx, "ortho_ns", st, 1);
     NAO_CUDA_TRY(ctx, launch_ns_correct(n, nSe, nullptr, Z, G, n, snn, Z2, st));
   }
   NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nSe, nullptr, mS, AS, tauS, Z2, wS, 1, X, Vf, tauc, Gw, Tw, Ww, W2w,
@@ -448,9 +460,9 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   NAO_STAGE("stein", 1, launch_stein(n, nprob, mP, dH, eH, n, wH, Z, n, snn, scr, stH, st));
   {
     GemmDims d{n, n, n, mP, mP, mP, 1};
-    NaoStage stage_(ctx, "ortho_ns", st, 2);
-    NAO_CUDA_TRY(ctx, launch_dgemm(nprob, d, 1.0, GemmOperand{Z, snn, n, 1, 0, nullptr},
-                                   GemmOperand{Z, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, st));
+    NAO_CUDA_TRY(ctx, run_dgemm(ctx, "ortho_ns", nprob, d, 1.0, GemmOperand{Z, snn, n, 1, 0, nullptr},
+                                GemmOperand{Z, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, ozws, st));
+    NaoStage stage_(ctx, "ortho_ns", st, 1);
     NAO_CUDA_TRY(ctx, launch_ns_correct(n, nprob, mP, Z, G, n, snn, Z2, st));
   }
   NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nprob, mP, mP, Hp, tauH, Z2, wH, 0, V, Vf, tauc, Gw, Tw, Ww, W2w, ozws,

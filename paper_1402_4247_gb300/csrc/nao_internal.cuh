@@ -174,6 +174,12 @@ size_t zgemm_oz_workspace(int nprob, GemmDims dims);
 cudaError_t launch_zgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta, z64* C,
                             long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st);
 
+// The same method for real float64 operands (C = alpha op(A) op(B) + beta C, K <= 1792);
+// fits in the workspace of a complex product of the same M, N, K.
+bool dgemm_oz_supported(GemmDims dims);
+cudaError_t launch_dgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta, double* C,
+                            long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st);
+
 // Small helpers of the gen-eig chain.
 cudaError_t launch_count_kept(int n, int nprob, const double* w, long long strideV, double s_cut,
                               int32_t* m, int32_t* status, cudaStream_t st);

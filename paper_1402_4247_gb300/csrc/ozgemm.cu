@@ -196,6 +196,69 @@ __global__ void oz_split_b(int nprob, GemmDims dims, GemmOperand B, int N2p, int
   }
 }
 
+// Real operands (float64): A' = op(A) itself (M x K), B'' rows = the N columns of op(B).
+__global__ void oz_split_a_real(int nprob, GemmDims dims, GemmOperand A, int Mp, int K2p,
+                                __nv_bfloat16* __restrict__ planes, int* __restrict__ rexp) {
+  const int p = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= Mp) return;
+  const int M = dims.Mp ? dims.Mp[p] : dims.M;
+  const int K = dims.Kp ? dims.Kp[p] : dims.K;
+  const double* Ab = (const double*)A.ptr + (size_t)(A.map ? A.map[p] : p) * A.bs;
+  const bool live = i < M;
+  int bmax = 0;
+  if (live)
+    for (int k = lane; k < K; k += 32) bmax = max(bmax, exp_field(Ab[(long long)i * A.rs + (long long)k * A.cs]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+  const int e = bmax == 0 ? -1100 : bmax - 1022;
+  if (lane == 0) rexp[(size_t)p * Mp + i] = e;
+  const int nks = K2p / OZ_BK, rb = i / OZ_BM, r = i % OZ_BM;
+  const size_t plane_elems = (size_t)(Mp / OZ_BM) * nks * (OZ_TILE_A / 2);
+  unsigned char* base = (unsigned char*)(planes + (size_t)p * OZ_S * plane_elems);
+  for (int kk = lane; kk < K2p; kk += 32) {
+    const double x = (live && kk < K) ? Ab[(long long)i * A.rs + (long long)kk * A.cs] : 0.0;
+    int d[OZ_S];
+    oz_digits(oz_fixed(x, e), d);
+    const size_t off = ((size_t)rb * nks + kk / OZ_BK) * OZ_TILE_A + oz_tile_off(r, kk % OZ_BK);
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s)
+      *(__nv_bfloat16*)(base + (size_t)s * plane_elems * 2 + off) = __float2bfloat16_rn(ldexpf((float)d[s], -6 * s));
+  }
+}
+
+__global__ void oz_split_b_real(int nprob, GemmDims dims, GemmOperand B, int N2p, int K2p,
+                                __nv_bfloat16* __restrict__ planes, int* __restrict__ cexp) {
+  const int p = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= N2p) return;
+  const int N = dims.Np ? dims.Np[p] : dims.N;
+  const int K = dims.Kp ? dims.Kp[p] : dims.K;
+  const double* Bb = (const double*)B.ptr + (size_t)(B.map ? B.map[p] : p) * B.bs;
+  const bool live = j < N;
+  int bmax = 0;
+  if (live)
+    for (int k = lane; k < K; k += 32) bmax = max(bmax, exp_field(Bb[(long long)k * B.rs + (long long)j * B.cs]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+  const int f = bmax == 0 ? -1100 : bmax - 1022;
+  if (lane == 0) cexp[(size_t)p * N2p + j] = f;
+  const int nks = K2p / OZ_BK, cb = j / OZ_BN, rr = j % OZ_BN;
+  const size_t plane_elems = (size_t)(N2p / OZ_BN) * nks * (OZ_TILE_B / 2);
+  unsigned char* base = (unsigned char*)(planes + (size_t)p * OZ_S * plane_elems);
+  for (int kk = lane; kk < K2p; kk += 32) {
+    const double x = (live && kk < K) ? Bb[(long long)kk * B.rs + (long long)j * B.cs] : 0.0;
+    int d[OZ_S];
+    oz_digits(oz_fixed(x, f), d);
+    const size_t off = ((size_t)cb * nks + kk / OZ_BK) * OZ_TILE_B + oz_tile_off(rr, kk % OZ_BK);
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s)
+      *(__nv_bfloat16*)(base + (size_t)s * plane_elems * 2 + off) = __float2bfloat16_rn(ldexpf((float)d[s], 30 - 6 * s));
+  }
+}
+
 // ---------------------------------------------------------------------------- tensor kernel
 __device__ __forceinline__ void oz_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
   asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -230,10 +293,11 @@ __device__ __forceinline__ void oz_bulk_copy(void* dst_smem, const void* src_gme
 //   warp 1 / lane 0 (MMA issuer): waits for a full stage, issues the 55 MMAs, commits them
 //     to the stage's empty barrier, and after the last stage to the "done" barrier;
 //   all 8 warps: wait for "done", then run the epilogue from TMEM.
+template <bool REAL>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_bfloat16* __restrict__ Ap,
                const __nv_bfloat16* __restrict__ Bp, const int* __restrict__ rexp, const int* __restrict__ cexp, int Mp,
-               int N2p, int K2p, z64* __restrict__ C, long long Cbs, long long Crs, long long Ccs, int* __restrict__ err) {
+               int N2p, int K2p, void* __restrict__ Cv, long long Cbs, long long Crs, long long Ccs, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char oz_smem[];
   __shared__ uint64_t full_bar[OZ_STAGES], empty_bar[OZ_STAGES], done_bar;
   __shared__ uint32_t tbase;
@@ -245,13 +309,14 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
   const int N = dims.Np ? dims.Np[p] : dims.N;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // uniform early exits (before any barrier or allocation)
-  if (rb * OZ_BM >= M || cb * (OZ_BN / 2) >= N) return;
-  if (dims.lower && cb * (OZ_BN / 2) > rb * OZ_BM + OZ_BM - 1) return;
+  const int CPT = REAL ? OZ_BN : OZ_BN / 2;  // output columns per tile
+  if (rb * OZ_BM >= M || cb * CPT >= N) return;
+  if (dims.lower && cb * CPT > rb * OZ_BM + OZ_BM - 1) return;
   unsigned char* stage0 = (unsigned char*)(((uintptr_t)oz_smem + 1023) & ~(uintptr_t)1023);
   const int nks = K2p / OZ_BK;  // plane layout (all problems)
-  // this problem's digit planes are zero beyond column 2 K_p: stop the K loop there
+  // this problem's digit planes are zero beyond column 2 K_p (K_p when real): stop the K loop there
   const int Kprob = dims.Kp ? dims.Kp[p] : dims.K;
-  const int nks_p = max(1, min(nks, (2 * Kprob + OZ_BK - 1) / OZ_BK));
+  const int nks_p = max(1, min(nks, ((REAL ? 1 : 2) * Kprob + OZ_BK - 1) / OZ_BK));
   const size_t aplane = (size_t)(Mp / OZ_BM) * nks * (OZ_TILE_A / 2);
   const size_t bplane = (size_t)(N2p / OZ_BN) * nks * (OZ_TILE_B / 2);
   const unsigned char* Abase = (const unsigned char*)(Ap + (size_t)p * OZ_S * aplane) + (size_t)rb * nks * OZ_TILE_A;
@@ -351,8 +416,7 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
     const int gi = rb * OZ_BM + row;
     const int half = warp >> 2;
     const int erow = (gi < M) ? rexp[(size_t)p * Mp + gi] : 0;
-    z64* Cp = C + (size_t)p * Cbs;
-    for (int cc = 0; cc < OZ_BN / 4; cc += 4) {  // 4 complex = 8 C'' columns per round
+    for (int cc = 0; cc < OZ_BN / 4; cc += 4) {  // 8 C'' columns per round
       const int col0 = half * (OZ_BN / 2) + 2 * cc;
       uint32_t v[OZ_NACC][8];
 #pragma unroll
@@ -365,37 +429,52 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
       }
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       if (gi >= M) continue;
+      double part[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int gj = cb * (OZ_BN / 2) + half * (OZ_BN / 4) + cc + q;  // complex column
-        if (gj >= N) continue;
-        double part[2];
+      for (int c = 0; c < 8; ++c) {
+        // exact groups g = 2..8 (accumulator g-2): G_g = n_g 2^{6(7-g)} with integer n_g;
+        // hi = sum_g n_g 2^{6(8-g)} counts in units of group 8 (2^-6)
+        long long hi = 0;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int c = 2 * q + h;
-          // exact groups g = 2..8 (accumulator g-2): G_g = n_g 2^{6(7-g)} with integer n_g;
-          // hi = sum_g n_g 2^{6(8-g)} counts in units of group 8 (2^-6)
-          long long hi = 0;
+        for (int a = 0; a < OZ_NACC - 1; ++a) {
+          const float gv = __uint_as_float(v[a][c]);
+          const long long ng = (long long)__float2int_rn(ldexpf(gv, -6 * (5 - a)));
+          hi += ng * (1ll << (6 * (6 - a)));
+        }
+        part[c] = (double)hi * 0x1p-6 + (double)__uint_as_float(v[OZ_NACC - 1][c]);
+      }
+      if (REAL) {
+        double* Cp = (double*)Cv + (size_t)p * Cbs;
 #pragma unroll
-          for (int a = 0; a < OZ_NACC - 1; ++a) {
-            const float gv = __uint_as_float(v[a][c]);
-            const long long ng = (long long)__float2int_rn(ldexpf(gv, -6 * (5 - a)));
-            hi += ng * (1ll << (6 * (6 - a)));
+        for (int c = 0; c < 8; ++c) {
+          const int gj = cb * OZ_BN + col0 + c;
+          if (gj >= N) continue;
+          int E = erow + cexp[(size_t)p * N2p + gj] - 42;
+          E = E < -1022 ? -1022 : (E > 1023 ? 1023 : E);
+          const double sc = __longlong_as_double((long long)(E + 1023) << 52) * alpha;
+          double* cp = Cp + (long long)gi * Crs + (long long)gj * Ccs;
+          double r = part[c] * sc;
+          if (beta != 0.0) r = fma(beta, *cp, r);
+          *cp = r;
+        }
+      } else {
+        z64* Cp = (z64*)Cv + (size_t)p * Cbs;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int gj = cb * (OZ_BN / 2) + half * (OZ_BN / 4) + cc + q;  // complex column
+          if (gj >= N) continue;
+          int E = erow + cexp[(size_t)p * (N2p / 2) + gj] - 42;
+          E = E < -1022 ? -1022 : (E > 1023 ? 1023 : E);
+          const double sc = __longlong_as_double((long long)(E + 1023) << 52) * alpha;
+          z64* cp = Cp + (long long)gi * Crs + (long long)gj * Ccs;
+          z64 r = zmk(part[2 * q] * sc, part[2 * q + 1] * sc);
+          if (beta != 0.0) {
+            const z64 old = *cp;
+            r.x = fma(beta, old.x, r.x);
+            r.y = fma(beta, old.y, r.y);
           }
-          part[h] = (double)hi * 0x1p-6 + (double)__uint_as_float(v[OZ_NACC - 1][c]);
+          *cp = r;
         }
-        const int fcol = cexp[(size_t)p * (N2p / 2) + gj];
-        int E = erow + fcol - 42;
-        E = E < -1022 ? -1022 : (E > 1023 ? 1023 : E);
-        const double sc = __longlong_as_double((long long)(E + 1023) << 52) * alpha;
-        z64* cp = Cp + (long long)gi * Crs + (long long)gj * Ccs;
-        z64 r = zmk(part[0] * sc, part[1] * sc);
-        if (beta != 0.0) {
-          const z64 old = *cp;
-          r.x = fma(beta, old.x, r.x);
-          r.y = fma(beta, old.y, r.y);
-        }
-        *cp = r;
       }
     }
   }
@@ -435,10 +514,38 @@ cudaError_t launch_zgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand 
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = OZ_STAGES * (size_t)OZ_STAGE + 1024;
-  e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(oz_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(N2p / OZ_BN, Mp / OZ_BM, nprob);
-  oz_gemm_kernel<<<grid, OZ_THREADS, smem, st>>>(nprob, dims, alpha, beta, Apl, Bpl, rexp, cexp, Mp, N2p, K2p, C, Cbs,
-                                                  Crs, Ccs, err);
+  oz_gemm_kernel<false><<<grid, OZ_THREADS, smem, st>>>(nprob, dims, alpha, beta, Apl, Bpl, rexp, cexp, Mp, N2p, K2p,
+                                                         (void*)C, Cbs, Crs, Ccs, err);
+  return cudaGetLastError();
+}
+
+bool dgemm_oz_supported(GemmDims dims) { return (long long)dims.K <= OZ_MAX_K2 && dims.M > 0 && dims.N > 0; }
+
+cudaError_t launch_dgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta, double* C,
+                            long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st) {
+  if (nprob <= 0 || dims.M <= 0 || dims.N <= 0) return cudaSuccess;
+  const int Mp = round_up(dims.M, OZ_BM), N2p = round_up(dims.N, OZ_BN), K2p = round_up(dims.K, OZ_BK);
+  unsigned char* w = (unsigned char*)ws;
+  __nv_bfloat16* Apl = (__nv_bfloat16*)w;
+  w += (size_t)nprob * OZ_S * Mp * K2p * 2;
+  __nv_bfloat16* Bpl = (__nv_bfloat16*)w;
+  w += (size_t)nprob * OZ_S * N2p * K2p * 2;
+  int* rexp = (int*)w;
+  int* cexp = rexp + (size_t)nprob * Mp;
+  oz_split_a_real<<<dim3((Mp + 7) / 8, nprob), 256, 0, st>>>(nprob, dims, A, Mp, K2p, Apl, rexp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  oz_split_b_real<<<dim3((N2p + 7) / 8, nprob), 256, 0, st>>>(nprob, dims, B, N2p, K2p, Bpl, cexp);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = OZ_STAGES * (size_t)OZ_STAGE + 1024;
+  e = cudaFuncSetAttribute(oz_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(N2p / OZ_BN, Mp / OZ_BM, nprob);
+  oz_gemm_kernel<true><<<grid, OZ_THREADS, smem, st>>>(nprob, dims, alpha, beta, Apl, Bpl, rexp, cexp, Mp, N2p, K2p,
+                                                        (void*)C, Cbs, Crs, Ccs, err);
   return cudaGetLastError();
 }

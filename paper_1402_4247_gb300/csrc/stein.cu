@@ -243,9 +243,9 @@ stebz_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__
     if (isolated) {
       // safeguarded Newton on p_n; its step bottoms out at the rounding noise of p_n, so
       // it only narrows the bracket, which bisection then closes to eps |T|
-      double x = 0.5 * (lo + hi), last = hi - lo;
+      double x = 0.5 * (lo + hi), last = hi - lo, prev = hi - lo;
       bool conv = false;
-      for (int it = 0; it < 8; ++it) {
+      for (int it = 0; it < 10; ++it) {
         double pn = 0.0, dpn = 0.0;
         const int c = sturm64(d, e2, b0, b1, x, true, &pn, &dpn);
         if (c > idx) hi = x;
@@ -255,19 +255,25 @@ stebz_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__
         if (!(cand > lo && cand < hi)) break;
         x = cand;
         last = fabs(step);
-        if (last <= 64.0 * eps * T.tnorm) {
+        // converged to ~1e-11 |T|, or stalled at the rounding noise of p_n (no longer
+        // shrinking quadratically)
+        if (last <= 1e-11 * T.tnorm || last >= 0.25 * prev) {
           conv = true;
           break;
         }
+        prev = last;
       }
       if (conv) {
-        const double del = 16.0 * last + 4.0 * eps * T.tnorm;
-        const double l2 = fmax(x - del, lo), h2 = fmin(x + del, hi);
-        const int cl = sturm64(d, e2, b0, b1, l2, false, nullptr, nullptr);
-        const int ch = sturm64(d, e2, b0, b1, h2, false, nullptr, nullptr);
-        if (cl <= idx && idx < ch) {
-          lo = l2;
-          hi = h2;
+        double del = 16.0 * last + 8.0 * eps * T.tnorm;
+        for (int tries = 0; tries < 3; ++tries, del *= 16.0) {
+          const double l2 = fmax(x - del, lo), h2 = fmin(x + del, hi);
+          const int cl = sturm64(d, e2, b0, b1, l2, false, nullptr, nullptr);
+          const int ch = sturm64(d, e2, b0, b1, h2, false, nullptr, nullptr);
+          if (cl <= idx && idx < ch) {
+            lo = l2;
+            hi = h2;
+            break;
+          }
         }
       }
     }
