@@ -212,7 +212,7 @@ cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t*
 cudaError_t hetrd_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, z64* A, double* d, double* e, z64* tau,
                           z64* VW, void* ozws, cudaStream_t st) {
   const int NB = NAO_HT_NB;
-  const int cl = hetrd_cluster_size(nprob, ctx->num_sms);
+  const int cl = hetrd_cluster_size(n, nprob, ctx->num_sms);
   const long long snn = (long long)n * n, svw = (long long)n * 3 * NB;
   for (int i0 = 0; i0 < n; i0 += NB) {
     cudaError_t err;
@@ -225,7 +225,7 @@ cudaError_t hetrd_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, z
     if (r0 >= n) break;
     const int rows = n - r0;
     GemmDims dd{rows, rows, 2 * NB, nullptr, nullptr, nullptr, 1};
-    err = run_zgemm(ctx, "hetrd", nprob, dd, -1.0, GemmOperand{VW + (size_t)r0 * 3 * NB, svw, 3 * NB, 1, 0, nullptr},
+    err = run_zgemm(ctx, "hetrd_update", nprob, dd, -1.0, GemmOperand{VW + (size_t)r0 * 3 * NB, svw, 3 * NB, 1, 0, nullptr},
                     GemmOperand{VW + (size_t)r0 * 3 * NB + NB, svw, 1, 3 * NB, 1, nullptr}, 1.0,
                     A + r0 + (size_t)r0 * n, snn, 1, n, ozws, st);
     if (err != cudaSuccess) return err;

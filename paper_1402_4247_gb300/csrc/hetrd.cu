@@ -286,10 +286,37 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
 
 }  // namespace
 
-int hetrd_cluster_size(int nprob, int num_sms) {
-  int c = 1;
-  while (c < 8 && (long long)nprob * c * 2 <= num_sms) c *= 2;
-  return c;
+// Largest cluster size C (1..8, at most one block per 128 rows) for which the nprob clusters
+// of C blocks are all resident at once, as the occupancy calculator reports for this kernel.
+int hetrd_cluster_size(int n, int nprob, int num_sms) {
+  const size_t smem = sizeof(z64) * (3 * (size_t)n + 2 * HT_THREADS);
+  if (cudaFuncSetAttribute(hetrd_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(hetrd_panel_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  const int cmax = max(1, min(8, n / 128));
+  for (int c = cmax; c > 1; --c) {
+    if ((long long)nprob * c > num_sms) continue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nprob * c));
+    cfg.blockDim = dim3(HT_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, hetrd_panel_kernel, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (clusters >= nprob) return c;
+  }
+  return 1;
 }
 
 cudaError_t launch_hetrd_panel(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA, double* d,

@@ -107,7 +107,7 @@ cudaError_t launch_herm_fill(int n, int nprob, const z64* src, long long src_str
 // per row [V | W | V]) receives the panel's reflectors and update vectors, and the caller
 // applies A(i0+NB:, i0+NB:) -= V W^H + W V^H before the next panel.
 constexpr int NAO_HT_NB = 32;
-int hetrd_cluster_size(int nprob, int num_sms);
+int hetrd_cluster_size(int n, int nprob, int num_sms);
 cudaError_t launch_hetrd_panel(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA, double* d,
                                double* e, z64* tau, long long strideV, z64* VW, long long strideVW, int i0, int cluster,
                                cudaStream_t st);
