@@ -96,166 +96,107 @@ __device__ __forceinline__ void oz_digits(long long q, int* d) {
 }
 
 // ---------------------------------------------------------------------------- split kernels
-// A' rows: one warp per row i of op(A) (M rows, 2K columns).  Plane layout:
-//   Ap[prob][s][rb][ks][4096 B], rb = i / 128, ks = k' / 16.
-__global__ void oz_split_a(int nprob, GemmDims dims, GemmOperand A, int Mp, int K2p, __nv_bfloat16* __restrict__ planes,
-                           int* __restrict__ rexp) {
+// One kernel for both operands, complex or real.  The rows it splits are
+//   A (IS_B = false): the M rows of A' = op(A), A' = [Re op(A) | Im op(A)] when complex;
+//   B (IS_B = true):  the rows of B''^T, i.e. the columns of B'' (2N interleaved columns when
+//                     complex: row 2j = (Re b_j ; -Im b_j), row 2j+1 = (Im b_j ; Re b_j)).
+// Plane layout (K-major tiles of TR = 128 (A) or 64 (B) rows x 16 K, bf16):
+//   planes[prob][s][row / TR][k' / 16][oz_tile_off(row % TR, k' % 16)].
+// A block of 256 threads owns 16 consecutive rows and walks all of K'.  Lane l of a warp
+// holds row (l & 7) + 8 (l >> 4) and the 8-element half (l >> 3) & 1 of a 16-wide K step, so
+// each of its 16-byte plane chunks is contiguous and a warp stores 512 contiguous bytes per
+// plane.  Pass 1 takes the row's largest exponent (the power-of-two row scale), pass 2 writes
+// the digits.  Complex rows 2j and 2j+1 of B see the same set of values, hence one scale.
+template <bool IS_B, bool REAL>
+__global__ void __launch_bounds__(256) oz_split(int nprob, GemmDims dims, GemmOperand X, int Rp, int K2p,
+                                                 __nv_bfloat16* __restrict__ planes, int* __restrict__ xexp) {
+  constexpr int TR = IS_B ? OZ_BN : OZ_BM;            // rows per plane tile
+  constexpr int TB = TR * OZ_BK * 2;                  // bytes per plane tile
+  constexpr int SCALE0 = IS_B ? 30 : 0;               // plane s holds d_s 2^{SCALE0 - 6 s}
   const int p = blockIdx.y;
-  const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (i >= Mp) return;
-  const int M = dims.Mp ? dims.Mp[p] : dims.M;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lr = (lane & 7) + 8 * (lane >> 4);
+  const int kh = (lane >> 3) & 1;
+  const int row = blockIdx.x * 16 + lr;
+  const int R = IS_B ? (dims.Np ? dims.Np[p] : dims.N) : (dims.Mp ? dims.Mp[p] : dims.M);
   const int K = dims.Kp ? dims.Kp[p] : dims.K;
-  const z64* Ab = (const z64*)A.ptr + (size_t)(A.map ? A.map[p] : p) * A.bs;
-  const bool live = i < M;
-  // row exponent
+  const int rows_live = (IS_B && !REAL) ? 2 * R : R;
+  const bool live = row < rows_live;
+  const int x = (IS_B && !REAL) ? row >> 1 : row;  // row (A) or column (B) of op(X)
+  const int h = (IS_B && !REAL) ? row & 1 : 0;
+  const unsigned char* xb = (const unsigned char*)X.ptr +
+                            (size_t)(X.map ? X.map[p] : p) * X.bs * (REAL ? sizeof(double) : sizeof(z64));
+  // element k of the row (0 <= k < K): op(X)(x, k) for A, op(X)(k, x) for B
+  auto at = [&](int k) -> long long {
+    return IS_B ? (long long)k * X.rs + (long long)x * X.cs : (long long)x * X.rs + (long long)k * X.cs;
+  };
+  // pass 1: largest exponent field over the row's values
   int bmax = 0;
   if (live)
-    for (int k = lane; k < K; k += 32) {
-      const z64 a = Ab[(long long)i * A.rs + (long long)k * A.cs];
-      bmax = max(bmax, max(exp_field(a.x), exp_field(a.y)));
-    }
+    for (int k = warp * 16 + kh * 8; k < K; k += 8 * 16) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
-  const int e = bmax == 0 ? -1100 : bmax - 1022;  // |x| < 2^e
-  if (lane == 0) rexp[(size_t)p * Mp + i] = e;
-  const int nks = K2p / OZ_BK, rb = i / OZ_BM, r = i % OZ_BM;
-  const size_t plane_elems = (size_t)(Mp / OZ_BM) * nks * (OZ_TILE_A / 2);
-  unsigned char* base = (unsigned char*)(planes + (size_t)p * OZ_S * plane_elems);
-  for (int kk = lane; kk < K2p; kk += 32) {
-    double x = 0.0;
-    if (live && kk < 2 * K) {
-      const int k = kk < K ? kk : kk - K;
-      z64 a = Ab[(long long)i * A.rs + (long long)k * A.cs];
-      if (A.conj) a.y = -a.y;
-      x = kk < K ? a.x : a.y;
-    }
-    int d[OZ_S];
-    oz_digits(oz_fixed(x, e), d);
-    const size_t off = ((size_t)rb * nks + kk / OZ_BK) * OZ_TILE_A + oz_tile_off(r, kk % OZ_BK);
-#pragma unroll
-    for (int s = 0; s < OZ_S; ++s) {
-      const float v = ldexpf((float)d[s], -6 * s);
-      *(__nv_bfloat16*)(base + (size_t)s * plane_elems * 2 + off) = __float2bfloat16_rn(v);
-    }
-  }
-}
-
-// B'' rows (= C'' columns): one warp per complex column j of op(B) (K x N), producing rows
-// 2j and 2j+1 of the K-major B'' tile.  Bp[prob][t][cb][ks][2048 B], cb = (2j) / 64.
-__global__ void oz_split_b(int nprob, GemmDims dims, GemmOperand B, int N2p, int K2p, __nv_bfloat16* __restrict__ planes,
-                           int* __restrict__ cexp) {
-  const int p = blockIdx.y;
-  const int lane = threadIdx.x & 31;
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (2 * j >= N2p) return;
-  const int N = dims.Np ? dims.Np[p] : dims.N;
-  const int K = dims.Kp ? dims.Kp[p] : dims.K;
-  const z64* Bb = (const z64*)B.ptr + (size_t)(B.map ? B.map[p] : p) * B.bs;
-  const bool live = j < N;
-  int bmax = 0;
-  if (live)
-    for (int k = lane; k < K; k += 32) {
-      const z64 b = Bb[(long long)k * B.rs + (long long)j * B.cs];
-      bmax = max(bmax, max(exp_field(b.x), exp_field(b.y)));
-    }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
-  const int f = bmax == 0 ? -1100 : bmax - 1022;
-  if (lane == 0) cexp[(size_t)p * (N2p / 2) + j] = f;
-  const int nks = K2p / OZ_BK;
-  const size_t plane_elems = (size_t)(N2p / OZ_BN) * nks * (OZ_TILE_B / 2);
-  unsigned char* base = (unsigned char*)(planes + (size_t)p * OZ_S * plane_elems);
-  for (int kk = lane; kk < K2p; kk += 32) {
-    double x0 = 0.0, x1 = 0.0;  // rows 2j and 2j+1 of B''^T at k'
-    if (live && kk < 2 * K) {
-      const int k = kk < K ? kk : kk - K;
-      z64 b = Bb[(long long)k * B.rs + (long long)j * B.cs];
-      if (B.conj) b.y = -b.y;
-      if (kk < K) {
-        x0 = b.x;   // Re b
-        x1 = b.y;   // Im b
-      } else {
-        x0 = -b.y;  // -Im b
-        x1 = b.x;   // Re b
+      for (int e = 0; e < 8; ++e) {
+        if (k + e >= K) break;
+        if (REAL) {
+          bmax = max(bmax, exp_field(((const double*)xb)[at(k + e)]));
+        } else {
+          const z64 v = ((const z64*)xb)[at(k + e)];
+          bmax = max(bmax, max(exp_field(v.x), exp_field(v.y)));
+        }
       }
     }
-    int d0[OZ_S], d1[OZ_S];
-    oz_digits(oz_fixed(x0, f), d0);
-    oz_digits(oz_fixed(x1, f), d1);
+  bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, 8));
+  __shared__ int s_e[8][16];
+  if (kh == 0) s_e[warp][lr] = bmax;
+  __syncthreads();
+  int bm = 0;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int row = 2 * j + h, cb = row / OZ_BN, rr = row % OZ_BN;
-      const size_t off = ((size_t)cb * nks + kk / OZ_BK) * OZ_TILE_B + oz_tile_off(rr, kk % OZ_BK);
+  for (int w = 0; w < 8; ++w) bm = max(bm, s_e[w][lr]);
+  const int ex = bm == 0 ? -1100 : bm - 1022;  // |value| < 2^ex
+  if (warp == 0 && kh == 0 && row < Rp) {
+    if (IS_B && !REAL) {
+      if (h == 0) xexp[(size_t)p * (Rp / 2) + x] = ex;
+    } else {
+      xexp[(size_t)p * Rp + row] = ex;
+    }
+  }
+  // pass 2: digits of 8 consecutive K' entries per thread, one 16-byte store per plane
+  const int KK = REAL ? K : 2 * K;
+  const int nks = K2p / OZ_BK;
+  const size_t plane_bytes = (size_t)(Rp / TR) * nks * TB;
+  unsigned char* base = (unsigned char*)planes + (size_t)p * OZ_S * plane_bytes +
+                        (size_t)(row / TR) * nks * TB + oz_tile_off(row % TR, kh * 8);
+  for (int c = warp; c < nks; c += 8) {
+    uint32_t pk[OZ_S][4];
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) pk[s][0] = pk[s][1] = pk[s][2] = pk[s][3] = 0u;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int kk = c * OZ_BK + kh * 8 + e;
+      double v = 0.0;
+      if (live && kk < KK) {
+        if (REAL) {
+          v = ((const double*)xb)[at(kk)];
+        } else {
+          const bool hi = kk >= K;
+          z64 z = ((const z64*)xb)[at(hi ? kk - K : kk)];
+          if (X.conj) z.y = -z.y;
+          if (!IS_B) v = hi ? z.y : z.x;              // [Re | Im]
+          else if (h == 0) v = hi ? -z.y : z.x;       // (Re b ; -Im b)
+          else v = hi ? z.x : z.y;                    // (Im b ; Re b)
+        }
+      }
+      int d[OZ_S];
+      oz_digits(oz_fixed(v, ex), d);
 #pragma unroll
       for (int s = 0; s < OZ_S; ++s) {
-        const float v = ldexpf((float)(h ? d1[s] : d0[s]), 30 - 6 * s);
-        *(__nv_bfloat16*)(base + (size_t)s * plane_elems * 2 + off) = __float2bfloat16_rn(v);
+        const __nv_bfloat16 b = __float2bfloat16_rn(ldexpf((float)d[s], SCALE0 - 6 * s));
+        pk[s][e >> 1] |= (uint32_t)__bfloat16_as_ushort(b) << (16 * (e & 1));
       }
     }
-  }
-}
-
-// Real operands (float64): A' = op(A) itself (M x K), B'' rows = the N columns of op(B).
-__global__ void oz_split_a_real(int nprob, GemmDims dims, GemmOperand A, int Mp, int K2p,
-                                __nv_bfloat16* __restrict__ planes, int* __restrict__ rexp) {
-  const int p = blockIdx.y;
-  const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (i >= Mp) return;
-  const int M = dims.Mp ? dims.Mp[p] : dims.M;
-  const int K = dims.Kp ? dims.Kp[p] : dims.K;
-  const double* Ab = (const double*)A.ptr + (size_t)(A.map ? A.map[p] : p) * A.bs;
-  const bool live = i < M;
-  int bmax = 0;
-  if (live)
-    for (int k = lane; k < K; k += 32) bmax = max(bmax, exp_field(Ab[(long long)i * A.rs + (long long)k * A.cs]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
-  const int e = bmax == 0 ? -1100 : bmax - 1022;
-  if (lane == 0) rexp[(size_t)p * Mp + i] = e;
-  const int nks = K2p / OZ_BK, rb = i / OZ_BM, r = i % OZ_BM;
-  const size_t plane_elems = (size_t)(Mp / OZ_BM) * nks * (OZ_TILE_A / 2);
-  unsigned char* base = (unsigned char*)(planes + (size_t)p * OZ_S * plane_elems);
-  for (int kk = lane; kk < K2p; kk += 32) {
-    const double x = (live && kk < K) ? Ab[(long long)i * A.rs + (long long)kk * A.cs] : 0.0;
-    int d[OZ_S];
-    oz_digits(oz_fixed(x, e), d);
-    const size_t off = ((size_t)rb * nks + kk / OZ_BK) * OZ_TILE_A + oz_tile_off(r, kk % OZ_BK);
 #pragma unroll
     for (int s = 0; s < OZ_S; ++s)
-      *(__nv_bfloat16*)(base + (size_t)s * plane_elems * 2 + off) = __float2bfloat16_rn(ldexpf((float)d[s], -6 * s));
-  }
-}
-
-__global__ void oz_split_b_real(int nprob, GemmDims dims, GemmOperand B, int N2p, int K2p,
-                                __nv_bfloat16* __restrict__ planes, int* __restrict__ cexp) {
-  const int p = blockIdx.y;
-  const int lane = threadIdx.x & 31;
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (j >= N2p) return;
-  const int N = dims.Np ? dims.Np[p] : dims.N;
-  const int K = dims.Kp ? dims.Kp[p] : dims.K;
-  const double* Bb = (const double*)B.ptr + (size_t)(B.map ? B.map[p] : p) * B.bs;
-  const bool live = j < N;
-  int bmax = 0;
-  if (live)
-    for (int k = lane; k < K; k += 32) bmax = max(bmax, exp_field(Bb[(long long)k * B.rs + (long long)j * B.cs]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
-  const int f = bmax == 0 ? -1100 : bmax - 1022;
-  if (lane == 0) cexp[(size_t)p * N2p + j] = f;
-  const int nks = K2p / OZ_BK, cb = j / OZ_BN, rr = j % OZ_BN;
-  const size_t plane_elems = (size_t)(N2p / OZ_BN) * nks * (OZ_TILE_B / 2);
-  unsigned char* base = (unsigned char*)(planes + (size_t)p * OZ_S * plane_elems);
-  for (int kk = lane; kk < K2p; kk += 32) {
-    const double x = (live && kk < K) ? Bb[(long long)kk * B.rs + (long long)j * B.cs] : 0.0;
-    int d[OZ_S];
-    oz_digits(oz_fixed(x, f), d);
-    const size_t off = ((size_t)cb * nks + kk / OZ_BK) * OZ_TILE_B + oz_tile_off(rr, kk % OZ_BK);
-#pragma unroll
-    for (int s = 0; s < OZ_S; ++s)
-      *(__nv_bfloat16*)(base + (size_t)s * plane_elems * 2 + off) = __float2bfloat16_rn(ldexpf((float)d[s], 30 - 6 * s));
+      *(uint4*)(base + (size_t)s * plane_bytes + (size_t)c * TB) = make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
   }
 }
 
@@ -507,10 +448,10 @@ cudaError_t launch_zgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand 
   w += (size_t)nprob * OZ_S * N2p * K2p * 2;
   int* rexp = (int*)w;
   int* cexp = rexp + (size_t)nprob * Mp;
-  oz_split_a<<<dim3((Mp + 7) / 8, nprob), 256, 0, st>>>(nprob, dims, A, Mp, K2p, Apl, rexp);
+  oz_split<false, false><<<dim3(Mp / 16, nprob), 256, 0, st>>>(nprob, dims, A, Mp, K2p, Apl, rexp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  oz_split_b<<<dim3((N2p / 2 + 7) / 8, nprob), 256, 0, st>>>(nprob, dims, B, N2p, K2p, Bpl, cexp);
+  oz_split<true, false><<<dim3(N2p / 16, nprob), 256, 0, st>>>(nprob, dims, B, N2p, K2p, Bpl, cexp);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = OZ_STAGES * (size_t)OZ_STAGE + 1024;
@@ -535,10 +476,10 @@ cudaError_t launch_dgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand 
   w += (size_t)nprob * OZ_S * N2p * K2p * 2;
   int* rexp = (int*)w;
   int* cexp = rexp + (size_t)nprob * Mp;
-  oz_split_a_real<<<dim3((Mp + 7) / 8, nprob), 256, 0, st>>>(nprob, dims, A, Mp, K2p, Apl, rexp);
+  oz_split<false, true><<<dim3(Mp / 16, nprob), 256, 0, st>>>(nprob, dims, A, Mp, K2p, Apl, rexp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  oz_split_b_real<<<dim3((N2p + 7) / 8, nprob), 256, 0, st>>>(nprob, dims, B, N2p, K2p, Bpl, cexp);
+  oz_split<true, true><<<dim3(N2p / 16, nprob), 256, 0, st>>>(nprob, dims, B, N2p, K2p, Bpl, cexp);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = OZ_STAGES * (size_t)OZ_STAGE + 1024;
