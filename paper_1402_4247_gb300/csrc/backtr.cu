@@ -1,12 +1,9 @@
-// Eigen_HH steps 3-4 (Sec. 3: "rearrangement of eigenvectors" and "normalization"): the
-// eigenvectors of A are U = Q Z with Q = H_0 H_1 ... H_{m-2} from the tridiagonalization,
-// applied to each tridiagonal eigenvector z from the last reflector to the first, then
-// scaled to unit 2-norm.  For the overlap matrix the same pass applies Part 2's canonical
-// orthogonalization X = U_m diag(s_m^{-1/2}) (only the kept, largest, eigenpairs).
-//
-// One warp per output column (templated for several); the columns live in shared memory
-// with a fixed row-to-lane ownership (row r belongs to lane r mod 32) so the warp needs no
-// barriers.
+// Eigen_HH steps 3-4 (Sec. 3: "rearrangement of eigenvectors" and "normalization") and the
+// small element-wise steps around them.  The eigenvectors of A are U = Q Z with
+// Q = H_0 H_1 ... H_{m-2} from the tridiagonalization; Q is applied in compact WY blocks
+// (Q_j = I - V_j T_j V_j^H, three tensor-core products per block issued by the caller), then
+// the columns are scaled to unit 2-norm.  For the overlap matrix the normalization also
+// applies Part 2's canonical orthogonalization X = U_m diag(s_m^{-1/2}).
 #include "nao_internal.cuh"
 
 namespace {
@@ -15,70 +12,6 @@ __device__ __forceinline__ double wsum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
-}
-
-// CPW columns per warp share every reflector load (4; fewer only when 4 columns of the
-// largest n would not fit in shared memory).
-template <int CPW>
-__global__ void backtr_kernel(int n, const int32_t* __restrict__ size, const int32_t* __restrict__ ncols,
-                              const z64* __restrict__ Abase, int lda, long long strideA,
-                              const z64* __restrict__ taubase, long long strideV, const double* __restrict__ Zbase,
-                              int ldz, long long strideZ, const double* __restrict__ wbase, int use_rsqrt,
-                              z64* __restrict__ Ubase, int ldu, long long strideU) {
-  extern __shared__ z64 colbuf[];
-  const int p = blockIdx.x;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  const int m = size ? size[p] : n;
-  const int nc = ncols ? ncols[p] : m;
-  const int c0 = (blockIdx.y * wpb + wid) * CPW;
-  if (c0 >= nc || m <= 0) return;
-  const int ncw = min(CPW, nc - c0);
-  z64* u = colbuf + (size_t)wid * CPW * n;  // u[q * n + r]
-  const z64* A = Abase + (size_t)p * strideA;
-  const z64* tau = taubase + (size_t)p * strideV;
-  const int j0 = (m - nc) + c0;  // first source eigenpair
-  const double* Zp = Zbase + (size_t)p * strideZ;
-#pragma unroll
-  for (int q = 0; q < CPW; ++q) {
-    const double* z = Zp + (size_t)(j0 + (q < ncw ? q : 0)) * ldz;
-    for (int r = lane; r < m; r += 32) u[q * n + r] = zmk(q < ncw ? z[r] : 0.0, 0.0);
-  }
-  for (int i = m - 2; i >= 0; --i) {
-    const z64 t = tau[i];
-    if (t.x == 0.0 && t.y == 0.0) continue;
-    const z64* v = A + (size_t)i * lda;  // v(i+1) = 1, v(r) = A(r, i) for r >= i+2
-    const int r0 = (i + 1) + ((lane - (i + 1)) & 31);
-    double sre[CPW], sim[CPW];
-#pragma unroll
-    for (int q = 0; q < CPW; ++q) sre[q] = sim[q] = 0.0;
-    for (int r = r0; r < m; r += 32) {
-      const z64 vr = (r == i + 1) ? zmk(1.0, 0.0) : v[r];
-#pragma unroll
-      for (int q = 0; q < CPW; ++q) {
-        const z64 ur = u[q * n + r];
-        sre[q] = fma(vr.x, ur.x, fma(vr.y, ur.y, sre[q]));  // conj(vr) * ur
-        sim[q] = fma(vr.x, ur.y, fma(-vr.y, ur.x, sim[q]));
-      }
-    }
-    z64 f[CPW];
-#pragma unroll
-    for (int q = 0; q < CPW; ++q) f[q] = zmul(t, zmk(wsum(sre[q]), wsum(sim[q])));  // tau * v^H u
-    for (int r = r0; r < m; r += 32) {
-      const z64 vr = (r == i + 1) ? zmk(1.0, 0.0) : v[r];
-#pragma unroll
-      for (int q = 0; q < CPW; ++q) u[q * n + r] = zsub(u[q * n + r], zmul(vr, f[q]));
-    }
-  }
-  for (int q = 0; q < ncw; ++q) {
-    const int j = j0 + q;
-    double nrm = 0.0;
-    for (int r = lane; r < m; r += 32) nrm += zabs2(u[q * n + r]);
-    nrm = wsum(nrm);
-    double sc = 1.0 / sqrt(nrm);
-    if (use_rsqrt) sc /= sqrt(wbase[(size_t)p * strideV + j]);
-    z64* out = Ubase + (size_t)p * strideU + (size_t)(c0 + q) * ldu;
-    for (int r = lane; r < m; r += 32) out[r] = zscale(u[q * n + r], sc);
-  }
 }
 
 __global__ void count_kept_kernel(int n, int nprob, const double* __restrict__ w, long long strideV, double s_cut,
@@ -105,16 +38,6 @@ __global__ void hermitize_kernel(int n, const int32_t* __restrict__ size, z64* _
   } else {
     A[(size_t)c * ld + r] = zconj(A[(size_t)r * ld + c]);  // upper (r < c) from lower (c, r)
   }
-}
-
-__global__ void copy_real_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ src, int lds,
-                                 long long sstride, double* __restrict__ dst, int ldd, long long dstride) {
-  const int p = blockIdx.z;
-  const int m = size ? size[p] : n;
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  const int c = blockIdx.y;
-  if (r >= m || c >= m) return;
-  dst[(size_t)p * dstride + (size_t)c * ldd + r] = src[(size_t)p * sstride + (size_t)c * lds + r];
 }
 
 __global__ void write_eps_kernel(int n, int nprob, const int32_t* __restrict__ m, const double* __restrict__ w,
@@ -145,36 +68,6 @@ __global__ void scale_cols_sqrt_kernel(int n, int nprob, int nb, const z64* __re
 
 }  // namespace
 
-cudaError_t launch_backtransform(int n, int nprob, const int32_t* size, const int32_t* ncols, const z64* A, int lda,
-                                 long long strideA, const z64* tau, long long strideV, const double* Z, int ldz,
-                                 long long strideZ, const double* w, int use_rsqrt_scale, z64* U, int ldu,
-                                 long long strideU, cudaStream_t st) {
-  const size_t limit = 200 * 1024;
-  // One column per warp: a wider warp footprint costs more occupancy (fewer warps per SM to
-  // hide the per-reflector reduction latency) than it saves in reflector loads.
-  const int cpw = 1;
-  int wpb = 8;
-  while (wpb > 1 && (size_t)wpb * cpw * n * sizeof(z64) > limit) --wpb;
-  size_t smem = (size_t)wpb * cpw * n * sizeof(z64);
-  const int cols_per_block = wpb * cpw;
-  dim3 grid(nprob, (n + cols_per_block - 1) / cols_per_block);
-  cudaError_t err;
-#define NAO_BT_LAUNCH(K)                                                                                      \
-  err = cudaFuncSetAttribute(backtr_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
-  if (err != cudaSuccess) return err;                                                                       \
-  backtr_kernel<K><<<grid, 32 * wpb, smem, st>>>(n, size, ncols, A, lda, strideA, tau, strideV, Z, ldz, strideZ, \
-                                                 w, use_rsqrt_scale, U, ldu, strideU);
-  if (cpw == 4) {
-    NAO_BT_LAUNCH(4)
-  } else if (cpw == 2) {
-    NAO_BT_LAUNCH(2)
-  } else {
-    NAO_BT_LAUNCH(1)
-  }
-#undef NAO_BT_LAUNCH
-  return cudaGetLastError();
-}
-
 cudaError_t launch_count_kept(int n, int nprob, const double* w, long long strideV, double s_cut, int32_t* m,
                               int32_t* status, cudaStream_t st) {
   count_kept_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(n, nprob, w, strideV, s_cut, m, status);
@@ -184,13 +77,6 @@ cudaError_t launch_count_kept(int n, int nprob, const double* w, long long strid
 cudaError_t launch_hermitize(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA, cudaStream_t st) {
   dim3 grid((n + 127) / 128, n, nprob);
   hermitize_kernel<<<grid, 128, 0, st>>>(n, size, A, ld, strideA);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_copy_real(int n, int nprob, const int32_t* size, const double* src, int lds, long long sstride,
-                             double* dst, int ldd, long long dstride, cudaStream_t st) {
-  dim3 grid((n + 127) / 128, n, nprob);
-  copy_real_kernel<<<grid, 128, 0, st>>>(n, size, src, lds, sstride, dst, ldd, dstride);
   return cudaGetLastError();
 }
 

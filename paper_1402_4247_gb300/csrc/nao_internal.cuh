@@ -119,14 +119,6 @@ cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d,
                          long long strideV, double* w, double* Z, int ld, long long strideZ,
                          double* scratch, int32_t* status, cudaStream_t st);
 
-// Eigen_HH steps 3-4: U(:, c) = Q Z(:, j0+c) normalised, times colscale (optional)
-// for c in [0, ncols[p]); j0 = size[p] - ncols[p] (keeps the top ncols eigenpairs).
-cudaError_t launch_backtransform(int n, int nprob, const int32_t* size, const int32_t* ncols,
-                                 const z64* A, int lda, long long strideA, const z64* tau,
-                                 long long strideV, const double* Z, int ldz, long long strideZ,
-                                 const double* w, int use_rsqrt_scale, z64* U, int ldu, long long strideU,
-                                 cudaStream_t st);
-
 // Blocked (compact WY) back-transformation helpers, see backtr.cu.
 constexpr int NAO_WY_NB = 128;
 cudaError_t launch_extract_v(int n, int nprob, const int32_t* size, const z64* A, int lda, long long strideA,
@@ -185,8 +177,6 @@ cudaError_t launch_count_kept(int n, int nprob, const double* w, long long strid
                               int32_t* m, int32_t* status, cudaStream_t st);
 cudaError_t launch_hermitize(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA,
                              cudaStream_t st);
-cudaError_t launch_copy_real(int n, int nprob, const int32_t* size, const double* src, int lds, long long sstride,
-                             double* dst, int ldd, long long dstride, cudaStream_t st);
 cudaError_t launch_write_eps(int n, int nprob, const int32_t* m, const double* w, long long strideV,
                              double* eps, cudaStream_t st);
 cudaError_t launch_zero_cols(int n, int nprob, int nb, const int32_t* m, z64* C, cudaStream_t st);
