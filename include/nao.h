@@ -68,6 +68,11 @@ size_t nao_workspace_bytes(const nao_ctx* ctx);
 /* Select the product method of this context's band-step calls (default NAO_GEMM_TC).    */
 int nao_set_gemm_method(nao_ctx* ctx, int method);
 
+/* Ritz refinement sweeps after a mixed-precision nao_gen_eig: 1 (default; eigenvalues to
+ * the mixed-mode bound), 2 (eigenvectors to FP64 accuracy too) or 0 (none: raw mixed
+ * results).  Returns NAO_E_INVALID for other values.  No effect on NAO_FP64 calls.        */
+int nao_set_refinement(nao_ctx* ctx, int sweeps);
+
 /* Batched complex GEMM (the products of Parts 3, 4 and 6):
  *   C[p] = alpha op(A[p]) op(B[p]) + beta C[p],  p = 0..nprob-1, real alpha and beta.
  * Row-major storage: A[p] at A + p*strideA with leading dimension lda (elements); op(X) is
@@ -103,7 +108,17 @@ int nao_bloch_sum(nao_ctx* ctx, int n, int nR, const int32_t* R, int nmat, const
  *             identity map (then nS = nprob).  Each distinct S is reduced once.
  *   nS        number of S matrices (ignored when s_of_prob is NULL)
  *   s_cut     absolute cutoff on the eigenvalues of S (e.g. 1e-10)
- *   precision NAO_FP64 (others reserved: NAO_E_INVALID)
+ *   precision NAO_FP64: every product FP64-accurate (ten-digit tensor-core products, or
+ *             FP64 CUDA cores with NAO_GEMM_FP64).
+ *             NAO_MIXED_BF16X3: the back-transformations, X^H H X, the rank-2k updates of H'
+ *             and X V use 24-bit tensor-core products (four BF16 digit planes); the reduction
+ *             of S, the tridiagonal solves and s^{-1/2} stay FP64.  Then one Ritz refinement
+ *             sweep (Ogita-Aishima in the S inner product, FP64-accurate products of the
+ *             input H and S; not in the paper) restores the accuracy: eps are the Rayleigh
+ *             quotients of the refined vectors, sorted.  nao_set_refinement chooses 0-2
+ *             sweeps (default 1).
+ *             NAO_MIXED_TF32: rejected (NAO_E_INVALID): 12-bit products leave errors that
+ *             one sweep does not remove.
  *   nb        eigenvector columns wanted, 1 <= nb <= n
  *   eps       float64 [nprob][n] out: ascending eigenvalues; entries j >= m are +inf
  *   C         complex128 [nprob][n][nb] out (may be NULL): column j is the eigenvector of

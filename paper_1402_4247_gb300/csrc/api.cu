@@ -134,12 +134,14 @@ __global__ void finish_status_kernel(int nprob, const int32_t* mP, const int32_t
 
 // One batched complex product of the band step, on the tensor cores (digit planes) when the
 // context asks for it and the contraction length allows, else on the FP64 CUDA cores.
+// digits: NAO_OZ_DIGITS_FP64, or NAO_OZ_DIGITS_MIXED for the products the mixed mode
+// computes to 24 bits (the FP64 CUDA-core route ignores it).
 cudaError_t run_zgemm(nao_ctx* ctx, const char* stage, int nprob, GemmDims d, double alpha, GemmOperand A,
                       GemmOperand B, double beta, z64* C, long long Cbs, long long Crs, long long Ccs, void* ozws,
-                      cudaStream_t st) {
+                      cudaStream_t st, int digits = NAO_OZ_DIGITS_FP64) {
   if (ctx->gemm_method == NAO_GEMM_TC && ozws && zgemm_oz_supported(d)) {
     NaoStage stage_(ctx, stage, st, 3);
-    return launch_zgemm_oz(nprob, d, alpha, A, B, beta, C, Cbs, Crs, Ccs, ozws, ctx->dev_flags, st);
+    return launch_zgemm_oz(nprob, d, alpha, A, B, beta, C, Cbs, Crs, Ccs, ozws, ctx->dev_flags, st, digits);
   }
   NaoStage stage_(ctx, stage, st, 1);
   return launch_zgemm(nprob, d, zmk(alpha, 0.0), A, B, zmk(beta, 0.0), C, Cbs, Crs, Ccs, st);
@@ -163,7 +165,8 @@ cudaError_t run_dgemm(nao_ctx* ctx, const char* stage, int nprob, GemmDims d, do
 // (W = V^H U, W = T W, U -= V W) plus its Gram matrix V^H V for T.
 cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, const int32_t* ncols, const z64* A,
                                   const z64* tau, const double* Z, const double* w, int use_rsqrt, z64* U, z64* Vf,
-                                  z64* tauc, z64* G, z64* T, z64* W, z64* W2, void* ozws, cudaStream_t st) {
+                                  z64* tauc, z64* G, z64* T, z64* W, z64* W2, void* ozws, cudaStream_t st,
+                                  int digits) {
   const int nb = NAO_WY_NB;
   const int ncolv = (n + nb - 1) / nb * nb;
   const long long snn = (long long)n * n, svf = (long long)n * ncolv, snb2 = (long long)nb * nb,
@@ -182,7 +185,7 @@ cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t*
     const z64* Vj = Vf + R0 + (size_t)j * nb * n;  // V_j(r, c) at Vj[r + c n]
     GemmDims dg{nb, nb, rows, nullptr, nullptr, nullptr, 0};
     e = run_zgemm(ctx, "backtransform", nprob, dg, 1.0, GemmOperand{Vj, svf, n, 1, 1, nullptr},
-                  GemmOperand{Vj, svf, 1, n, 0, nullptr}, 0.0, G, snb2, nb, 1, ozws, st);
+                  GemmOperand{Vj, svf, 1, n, 0, nullptr}, 0.0, G, snb2, nb, 1, ozws, st, digits);
     if (e != cudaSuccess) return e;
     {
       NaoStage stage_(ctx, "backtransform", st, 1);
@@ -191,15 +194,15 @@ cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t*
     }
     GemmDims dw{nb, n, rows, nullptr, ncols, nullptr, 0};
     e = run_zgemm(ctx, "backtransform", nprob, dw, 1.0, GemmOperand{Vj, svf, n, 1, 1, nullptr},
-                  GemmOperand{U + R0, snn, 1, n, 0, nullptr}, 0.0, W, snbn, n, 1, ozws, st);
+                  GemmOperand{U + R0, snn, 1, n, 0, nullptr}, 0.0, W, snbn, n, 1, ozws, st, digits);
     if (e != cudaSuccess) return e;
     GemmDims dt{nb, n, nb, nullptr, ncols, nullptr, 0};
     e = run_zgemm(ctx, "backtransform", nprob, dt, 1.0, GemmOperand{T, snb2, nb, 1, 0, nullptr},
-                  GemmOperand{W, snbn, n, 1, 0, nullptr}, 0.0, W2, snbn, n, 1, ozws, st);
+                  GemmOperand{W, snbn, n, 1, 0, nullptr}, 0.0, W2, snbn, n, 1, ozws, st, digits);
     if (e != cudaSuccess) return e;
     GemmDims du{rows, n, nb, nullptr, ncols, nullptr, 0};
     e = run_zgemm(ctx, "backtransform", nprob, du, -1.0, GemmOperand{Vj, svf, 1, n, 0, nullptr},
-                  GemmOperand{W2, snbn, n, 1, 0, nullptr}, 1.0, U + R0, snn, 1, n, ozws, st);
+                  GemmOperand{W2, snbn, n, 1, 0, nullptr}, 1.0, U + R0, snn, 1, n, ozws, st, digits);
     if (e != cudaSuccess) return e;
   }
   NaoStage stage_(ctx, "backtransform", st, 1);
@@ -210,7 +213,7 @@ cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t*
 // followed by the deferred update A(r0:, r0:) -= V W^H + W V^H of the rest (lower triangle,
 // one rank-2 NB product).  VW: [nprob][n][3 NB] workspace.
 cudaError_t hetrd_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, z64* A, double* d, double* e, z64* tau,
-                          z64* VW, void* ozws, cudaStream_t st) {
+                          z64* VW, void* ozws, cudaStream_t st, int digits) {
   const int NB = NAO_HT_NB;
   const int cl = hetrd_cluster_size(n, nprob, ctx->num_sms);
   const long long snn = (long long)n * n, svw = (long long)n * 3 * NB;
@@ -227,7 +230,7 @@ cudaError_t hetrd_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, z
     GemmDims dd{rows, rows, 2 * NB, nullptr, nullptr, nullptr, 1};
     err = run_zgemm(ctx, "hetrd_update", nprob, dd, -1.0, GemmOperand{VW + (size_t)r0 * 3 * NB, svw, 3 * NB, 1, 0, nullptr},
                     GemmOperand{VW + (size_t)r0 * 3 * NB + NB, svw, 1, 3 * NB, 1, nullptr}, 1.0,
-                    A + r0 + (size_t)r0 * n, snn, 1, n, ozws, st);
+                    A + r0 + (size_t)r0 * n, snn, 1, n, ozws, st, digits);
     if (err != cudaSuccess) return err;
   }
   return cudaSuccess;
@@ -319,6 +322,13 @@ int nao_set_gemm_method(nao_ctx* ctx, int method) {
   return NAO_OK;
 }
 
+int nao_set_refinement(nao_ctx* ctx, int sweeps) {
+  if (!ctx) return nao_fail(nullptr, NAO_E_INVALID, "nao_set_refinement: ctx is NULL");
+  if (sweeps < 0 || sweeps > 2) return nao_fail(ctx, NAO_E_INVALID, "nao_set_refinement: sweeps must be 0, 1 or 2");
+  ctx->refine_sweeps = sweeps;
+  return NAO_OK;
+}
+
 int nao_zgemm(nao_ctx* ctx, int method, int nprob, int M, int N, int K, double alpha, const nao_c128* A, int lda,
               long long strideA, int transA, const nao_c128* B, int ldb, long long strideB, int transB, double beta,
               nao_c128* C, int ldc, long long strideC, void* stream) {
@@ -369,7 +379,12 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   if (n < 1 || nprob < 1) return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig: n and nprob must be >= 1");
   if (n > 4096) return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig: n = %d above the supported 4096", n);
   if (!H || !S || !eps || !m_kept || !status) return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig: NULL array");
-  if (precision != NAO_FP64) return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig: precision %d not available", precision);
+  if (precision == NAO_MIXED_TF32)
+    return nao_fail(ctx, NAO_E_INVALID,
+                    "nao_gen_eig: NAO_MIXED_TF32 not available (12-bit products leave errors one refinement sweep "
+                    "does not remove); use NAO_MIXED_BF16X3");
+  if (precision != NAO_FP64 && precision != NAO_MIXED_BF16X3)
+    return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig: unknown precision %d", precision);
   if (nb < 1 || nb > n) return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig: nb must be in [1, n]");
   if (s_of_prob && nS < 1) return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig: nS must be >= 1 with a map");
   if (!(s_cut >= 0.0)) return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig: s_cut must be >= 0");
@@ -422,10 +437,16 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   z64 *Vf = (z64*)(ws + oVf), *tauc = (z64*)(ws + oTc), *Gw = (z64*)(ws + oG2), *Tw = (z64*)(ws + oT2),
       *Ww = (z64*)(ws + oW), *W2w = (z64*)(ws + oW2), *VWp = (z64*)(ws + oVW);
   const long long snn = (long long)nn;
+  // Mixed mode: the back-transformations, X^H H X, the rank-2k updates of H' and X V run with
+  // 24-bit products; the reduction of S, the tridiagonal solves (with their Newton-Schulz
+  // step) and s^{-1/2} stay FP64-accurate, and one Ritz refinement sweep with FP64-accurate
+  // products follows.
+  const bool mixed = precision != NAO_FP64;
+  const int dig = mixed ? NAO_OZ_DIGITS_MIXED : NAO_OZ_DIGITS_FP64;
 
   // ---- Part 2: Eigen_HH(S) -> s, U;  X = U_m s_m^{-1/2}
   NAO_STAGE("herm_fill", 1, launch_herm_fill(n, nSe, (const z64*)S, snn, nullptr, AS, n, snn, st));
-  NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nSe, nullptr, AS, dS, eS, tauS, VWp, ozws, st));
+  NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nSe, nullptr, AS, dS, eS, tauS, VWp, ozws, st, NAO_OZ_DIGITS_FP64));
   NAO_STAGE("stein", 1, launch_stein(n, nSe, nullptr, dS, eS, n, wS, Z, n, snn, scr, stS, st));
   NAO_STAGE("misc", 1, launch_count_kept(n, nSe, wS, n, s_cut, mS, stS, st));
   {  // one Newton-Schulz step: Z2 = Z (3I - Z^T Z)/2 = Z - Z (Z^T Z - I)/2
@@ -436,7 +457,7 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
     NAO_CUDA_TRY(ctx, launch_ns_correct(n, nSe, nullptr, Z, G, n, snn, Z2, st));
   }
   NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nSe, nullptr, mS, AS, tauS, Z2, wS, 1, X, Vf, tauc, Gw, Tw, Ww, W2w,
-                                          ozws, st));
+                                          ozws, st, dig));
   {
     NaoStage stage_(ctx, "misc", st, 1);
     gather_m_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(nprob, s_of_prob, mS, stS, nb, mP, nbP, stP);
@@ -448,15 +469,15 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   {
     GemmDims d{n, n, n, nullptr, mP, nullptr};  // Y = Hf X : n x m
     NAO_CUDA_TRY(ctx, run_zgemm(ctx, "zgemm_HX", nprob, d, 1.0, GemmOperand{Hf, snn, 1, n, 0, nullptr},
-                                GemmOperand{X, snn, 1, n, 0, s_of_prob}, 0.0, Y, snn, 1, n, ozws, st));
+                                GemmOperand{X, snn, 1, n, 0, s_of_prob}, 0.0, Y, snn, 1, n, ozws, st, dig));
     GemmDims d2{n, n, n, mP, mP, nullptr, 1};  // Hp = X^H Y : m x m, lower triangle
     NAO_CUDA_TRY(ctx, run_zgemm(ctx, "zgemm_XHY", nprob, d2, 1.0, GemmOperand{X, snn, n, 1, 1, s_of_prob},
-                                GemmOperand{Y, snn, 1, n, 0, nullptr}, 0.0, Hp, snn, 1, n, ozws, st));
+                                GemmOperand{Y, snn, 1, n, 0, nullptr}, 0.0, Hp, snn, 1, n, ozws, st, dig));
   }
   NAO_STAGE("misc", 1, launch_hermitize(n, nprob, mP, Hp, n, snn, st));
 
   // ---- Part 4: Eigen_HH(H') -> eps, V;  C = X V
-  NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nprob, mP, Hp, dH, eH, tauH, VWp, ozws, st));
+  NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nprob, mP, Hp, dH, eH, tauH, VWp, ozws, st, dig));
   NAO_STAGE("stein", 1, launch_stein(n, nprob, mP, dH, eH, n, wH, Z, n, snn, scr, stH, st));
   {
     GemmDims d{n, n, n, mP, mP, mP, 1};
@@ -466,15 +487,59 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
     NAO_CUDA_TRY(ctx, launch_ns_correct(n, nprob, mP, Z, G, n, snn, Z2, st));
   }
   NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nprob, mP, mP, Hp, tauH, Z2, wH, 0, V, Vf, tauc, Gw, Tw, Ww, W2w, ozws,
-                                          st));
-  if (C) {
-    GemmDims d{n, nb, n, nullptr, nbP, mP};  // C = X V(:, :nb) : n x nb, row-major [n][nb]
-    NAO_CUDA_TRY(ctx, run_zgemm(ctx, "zgemm_XV", nprob, d, 1.0, GemmOperand{X, snn, 1, n, 0, s_of_prob},
-                                GemmOperand{V, snn, 1, n, 0, nullptr}, 0.0, (z64*)C, (long long)n * nb, nb, 1, ozws,
-                                st));
-    NAO_STAGE("misc", 1, launch_zero_cols(n, nprob, nb, mP, (z64*)C, st));
+                                          st, dig));
+  if (mixed && ctx->refine_sweeps > 0) {
+    // C^ = X V (all m columns, column-major in Hp), then Ritz refinement sweeps with
+    // FP64-accurate products (csrc/refine.cu):  R' = C^H S C^, G = C^H H C^ -> I + F,
+    // C = C^ (I + F); after the last sweep eps = Rayleigh quotients of C, columns
+    // S-normalised, sorted.
+    const long long svf = (long long)n * ncolv;
+    int32_t* perm = (int32_t*)scr;
+    GemmDims dc{n, n, n, nullptr, mP, mP};
+    NAO_CUDA_TRY(ctx, run_zgemm(ctx, "zgemm_XV", nprob, dc, 1.0, GemmOperand{X, snn, 1, n, 0, s_of_prob},
+                                GemmOperand{V, snn, 1, n, 0, nullptr}, 0.0, Hp, snn, 1, n, ozws, st, dig));
+    NAO_STAGE("refine", 1, launch_herm_fill(n, nSe, (const z64*)S, snn, nullptr, AS, n, snn, st));
+    const GemmDims dw{n, n, n, nullptr, mP, nullptr};  // n x m, contraction over n
+    const GemmDims dr{n, n, n, mP, mP, nullptr, 1};     // m x m lower triangle, contraction over n
+    const GemmDims du{n, n, n, nullptr, mP, mP};        // n x m, contraction over m
+    for (int sw = 0; sw < ctx->refine_sweeps; ++sw) {
+      if (sw > 0) {  // the previous sweep's C (Vf) is the next C^ (Hp)
+        NaoStage stage_(ctx, "refine", st, 0);
+        NAO_CUDA_TRY(ctx, cudaMemcpy2DAsync(Hp, (size_t)snn * sizeof(z64), Vf, (size_t)svf * sizeof(z64),
+                                            nn * sizeof(z64), nprob, cudaMemcpyDeviceToDevice, st));
+      }
+      NAO_CUDA_TRY(ctx, run_zgemm(ctx, "refine", nprob, dw, 1.0, GemmOperand{AS, snn, 1, n, 0, s_of_prob},
+                                  GemmOperand{Hp, snn, 1, n, 0, nullptr}, 0.0, Y, snn, 1, n, ozws, st));
+      NAO_CUDA_TRY(ctx, run_zgemm(ctx, "refine", nprob, dw, 1.0, GemmOperand{Hf, snn, 1, n, 0, nullptr},
+                                  GemmOperand{Hp, snn, 1, n, 0, nullptr}, 0.0, Vf, svf, 1, n, ozws, st));
+      NAO_CUDA_TRY(ctx, run_zgemm(ctx, "refine", nprob, dr, 1.0, GemmOperand{Hp, snn, n, 1, 1, nullptr},
+                                  GemmOperand{Y, snn, 1, n, 0, nullptr}, 0.0, V, snn, 1, n, ozws, st));
+      NAO_CUDA_TRY(ctx, run_zgemm(ctx, "refine", nprob, dr, 1.0, GemmOperand{Hp, snn, n, 1, 1, nullptr},
+                                  GemmOperand{Vf, svf, 1, n, 0, nullptr}, 0.0, Y, snn, 1, n, ozws, st));
+      NAO_STAGE("refine", 1, launch_hermitize(n, nprob, mP, V, n, snn, st));
+      NAO_STAGE("refine", 1, launch_hermitize(n, nprob, mP, Y, n, snn, st));
+      NAO_STAGE("refine", 1, launch_oa_lambda(n, nprob, mP, V, Y, n, snn, wH, n, st));
+      NAO_STAGE("refine", 1, launch_oa_f(n, nprob, mP, V, Y, n, snn, wH, n, st));
+      NAO_CUDA_TRY(ctx, run_zgemm(ctx, "refine", nprob, du, 1.0, GemmOperand{Hp, snn, 1, n, 0, nullptr},
+                                  GemmOperand{Y, snn, 1, n, 0, nullptr}, 0.0, Vf, svf, 1, n, ozws, st));
+    }
+    NAO_CUDA_TRY(ctx, run_zgemm(ctx, "refine", nprob, dw, 1.0, GemmOperand{AS, snn, 1, n, 0, s_of_prob},
+                                GemmOperand{Vf, svf, 1, n, 0, nullptr}, 0.0, Y, snn, 1, n, ozws, st));
+    NAO_CUDA_TRY(ctx, run_zgemm(ctx, "refine", nprob, dw, 1.0, GemmOperand{Hf, snn, 1, n, 0, nullptr},
+                                GemmOperand{Vf, svf, 1, n, 0, nullptr}, 0.0, Hp, snn, 1, n, ozws, st));
+    NAO_STAGE("refine", 1, launch_oa_rq(n, nprob, mP, Vf, n, svf, Y, Hp, n, snn, wH, n, st));
+    NAO_STAGE("refine", 1, launch_oa_sort(n, nprob, mP, wH, n, eps, perm, st));
+    if (C) NAO_STAGE("refine", 1, launch_oa_gather(n, nprob, nb, perm, Vf, n, svf, (z64*)C, st));
+  } else {
+    if (C) {
+      GemmDims d{n, nb, n, nullptr, nbP, mP};  // C = X V(:, :nb) : n x nb, row-major [n][nb]
+      NAO_CUDA_TRY(ctx, run_zgemm(ctx, "zgemm_XV", nprob, d, 1.0, GemmOperand{X, snn, 1, n, 0, s_of_prob},
+                                  GemmOperand{V, snn, 1, n, 0, nullptr}, 0.0, (z64*)C, (long long)n * nb, nb, 1, ozws,
+                                  st, dig));
+      NAO_STAGE("misc", 1, launch_zero_cols(n, nprob, nb, mP, (z64*)C, st));
+    }
+    NAO_STAGE("misc", 1, launch_write_eps(n, nprob, mP, wH, n, eps, st));
   }
-  NAO_STAGE("misc", 1, launch_write_eps(n, nprob, mP, wH, n, eps, st));
   {
     NaoStage stage_(ctx, "misc", st, 1);
     finish_status_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(nprob, mP, stP, stH, ctx->dev_flags, m_kept, status);

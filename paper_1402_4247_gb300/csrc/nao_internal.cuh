@@ -51,6 +51,7 @@ struct nao_ctx {
   std::vector<NaoPending> pending;
   std::vector<cudaEvent_t> event_pool;
   int gemm_method = NAO_GEMM_TC;
+  int refine_sweeps = 1;     // Ritz refinement sweeps after a mixed-precision solve (0, 1 or 2)
   int* dev_flags = nullptr;  // [0]: a bounded wait in a tensor-core kernel expired
 };
 
@@ -160,17 +161,37 @@ cudaError_t launch_ns_correct(int n, int nprob, const int32_t* size, const doubl
 
 // FP64-accurate complex GEMM on the BF16 tensor cores (digit-plane splitting): C = alpha
 // op(A) op(B) + beta C with real alpha, beta.  Requires 2K <= 1792.  ws: zgemm_oz_workspace
-// bytes; err: device int set to 1 if a bounded wait expired.
+// bytes; err: device int set to 1 if a bounded wait expired.  digits: NAO_OZ_DIGITS_FP64
+// (ten base-64 planes, FP64 accuracy) or NAO_OZ_DIGITS_MIXED (four planes: 24 bits, the
+// accuracy of an FP32 / three-term BF16 split product, ~5x fewer tensor-core operations).
+constexpr int NAO_OZ_DIGITS_FP64 = 10;
+constexpr int NAO_OZ_DIGITS_MIXED = 4;
 bool zgemm_oz_supported(GemmDims dims);
 size_t zgemm_oz_workspace(int nprob, GemmDims dims);
 cudaError_t launch_zgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta, z64* C,
-                            long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st);
+                            long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st,
+                            int digits = NAO_OZ_DIGITS_FP64);
 
 // The same method for real float64 operands (C = alpha op(A) op(B) + beta C, K <= 1792);
 // fits in the workspace of a complex product of the same M, N, K.
 bool dgemm_oz_supported(GemmDims dims);
 cudaError_t launch_dgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta, double* C,
-                            long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st);
+                            long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st,
+                            int digits = NAO_OZ_DIGITS_FP64);
+
+// Ritz refinement (csrc/refine.cu): Rayleigh quotients G_ii / R'_ii; I + F in place over G;
+// Rayleigh quotients of the refined columns (W1 = S C, W2 = H C) with S-normalisation;
+// ascending sort with permutation; gather of the first nb sorted columns into C [n][nb].
+cudaError_t launch_oa_lambda(int n, int nprob, const int32_t* size, const z64* Rp, const z64* G, int ld,
+                             long long stride, double* lam, long long lstride, cudaStream_t st);
+cudaError_t launch_oa_f(int n, int nprob, const int32_t* size, const z64* Rp, z64* G, int ld, long long stride,
+                        const double* lam, long long lstride, cudaStream_t st);
+cudaError_t launch_oa_rq(int n, int nprob, const int32_t* size, z64* Cn, int ldc, long long cstride, const z64* W1,
+                         const z64* W2, int ldw, long long wstride, double* lam, long long lstride, cudaStream_t st);
+cudaError_t launch_oa_sort(int n, int nprob, const int32_t* size, const double* lam, long long lstride, double* eps,
+                           int32_t* perm, cudaStream_t st);
+cudaError_t launch_oa_gather(int n, int nprob, int nb, const int32_t* perm, const z64* Cn, int ldc, long long cstride,
+                             z64* C, cudaStream_t st);
 
 // Small helpers of the gen-eig chain.
 cudaError_t launch_count_kept(int n, int nprob, const double* w, long long strideV, double s_cut,

@@ -34,17 +34,15 @@
 
 namespace {
 
-constexpr int OZ_S = 10;             // digit planes per operand (60 bits)
+constexpr int OZ_S = 10;             // digit planes per operand for FP64 accuracy (60 bits); the most
+                                     // any product uses (the workspace is sized for it)
 constexpr int OZ_BM = 128;           // tile rows (C'' rows)
 constexpr int OZ_BN = 64;            // tile columns (C'' columns = 32 complex columns)
 constexpr int OZ_BK = 16;            // K' per MMA step
 constexpr int OZ_TILE_A = OZ_BM * OZ_BK * 2;  // bytes of one A plane tile (4096)
 constexpr int OZ_TILE_B = OZ_BN * OZ_BK * 2;  // bytes of one B plane tile (2048)
-constexpr int OZ_STAGE = OZ_S * (OZ_TILE_A + OZ_TILE_B);  // bytes per pipeline stage
 constexpr int OZ_STAGES = 3;
 constexpr int OZ_THREADS = 256;
-constexpr int OZ_NACC = 8;
-constexpr int OZ_TMEM_COLS = 512;
 constexpr long long OZ_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 constexpr int OZ_MAX_K2 = 1792;      // 2K bound for exact FP32 group sums (group 8: 9 2^10 per k)
 
@@ -69,13 +67,14 @@ __device__ __forceinline__ int oz_tile_off(int row, int k) {
 // biased exponent field of x (0 for zero / subnormal)
 __device__ __forceinline__ int exp_field(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7ff); }
 
-// q = round(x * 2^{6 OZ_S - e}) for |x| < 2^e, by integer arithmetic on the bits of x
+// q = round(x * 2^{6 S - e}) for |x| < 2^e, by integer arithmetic on the bits of x
+template <int S>
 __device__ __forceinline__ long long oz_fixed(double x, int e) {
   const long long bits = __double_as_longlong(x);
   const int b = (int)((bits >> 52) & 0x7ff);
   if (b == 0) return 0;  // zero (subnormals are far below any row scale used here)
   long long m = (bits & 0xFFFFFFFFFFFFFll) | 0x10000000000000ll;  // 53-bit integer mantissa
-  const int sh = b - 1075 + 6 * OZ_S - e;                           // x 2^{6S-e} = m 2^{sh}
+  const int sh = b - 1075 + 6 * S - e;                              // x 2^{6S-e} = m 2^{sh}
   long long q;
   if (sh >= 0) q = m << sh;
   else if (sh <= -62) q = 0;
@@ -83,16 +82,17 @@ __device__ __forceinline__ long long oz_fixed(double x, int e) {
   return bits < 0 ? -q : q;
 }
 
-// OZ_S signed base-64 digits of q (|q| < 2^{6 OZ_S}): q = sum_s d_s 2^{6(OZ_S-s)}
+// S signed base-64 digits of q (|q| < 2^{6 S}): q = sum_s d_s 2^{6(S-s)}
+template <int S>
 __device__ __forceinline__ void oz_digits(long long q, int* d) {
 #pragma unroll
-  for (int s = 0; s < OZ_S - 1; ++s) {
-    const int sh = 6 * (OZ_S - 1 - s);
+  for (int s = 0; s < S - 1; ++s) {
+    const int sh = 6 * (S - 1 - s);
     const long long ds = (q + (1ll << (sh - 1))) >> sh;
     d[s] = (int)ds;
     q -= ds * (1ll << sh);
   }
-  d[OZ_S - 1] = (int)q;
+  d[S - 1] = (int)q;
 }
 
 // ---------------------------------------------------------------------------- split kernels
@@ -107,7 +107,7 @@ __device__ __forceinline__ void oz_digits(long long q, int* d) {
 // each of its 16-byte plane chunks is contiguous and a warp stores 512 contiguous bytes per
 // plane.  Pass 1 takes the row's largest exponent (the power-of-two row scale), pass 2 writes
 // the digits.  Complex rows 2j and 2j+1 of B see the same set of values, hence one scale.
-template <bool IS_B, bool REAL>
+template <bool IS_B, bool REAL, int S>
 __global__ void __launch_bounds__(256) oz_split(int nprob, GemmDims dims, GemmOperand X, int Rp, int K2p,
                                                  __nv_bfloat16* __restrict__ planes, int* __restrict__ xexp) {
   constexpr int TR = IS_B ? OZ_BN : OZ_BM;            // rows per plane tile
@@ -164,12 +164,12 @@ __global__ void __launch_bounds__(256) oz_split(int nprob, GemmDims dims, GemmOp
   const int KK = REAL ? K : 2 * K;
   const int nks = K2p / OZ_BK;
   const size_t plane_bytes = (size_t)(Rp / TR) * nks * TB;
-  unsigned char* base = (unsigned char*)planes + (size_t)p * OZ_S * plane_bytes +
+  unsigned char* base = (unsigned char*)planes + (size_t)p * S * plane_bytes +
                         (size_t)(row / TR) * nks * TB + oz_tile_off(row % TR, kh * 8);
   for (int c = warp; c < nks; c += 8) {
-    uint32_t pk[OZ_S][4];
+    uint32_t pk[S][4];
 #pragma unroll
-    for (int s = 0; s < OZ_S; ++s) pk[s][0] = pk[s][1] = pk[s][2] = pk[s][3] = 0u;
+    for (int s = 0; s < S; ++s) pk[s][0] = pk[s][1] = pk[s][2] = pk[s][3] = 0u;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int kk = c * OZ_BK + kh * 8 + e;
@@ -186,16 +186,16 @@ __global__ void __launch_bounds__(256) oz_split(int nprob, GemmDims dims, GemmOp
           else v = hi ? z.x : z.y;                    // (Im b ; Re b)
         }
       }
-      int d[OZ_S];
-      oz_digits(oz_fixed(v, ex), d);
+      int d[S];
+      oz_digits<S>(oz_fixed<S>(v, ex), d);
 #pragma unroll
-      for (int s = 0; s < OZ_S; ++s) {
+      for (int s = 0; s < S; ++s) {
         const __nv_bfloat16 b = __float2bfloat16_rn(ldexpf((float)d[s], SCALE0 - 6 * s));
         pk[s][e >> 1] |= (uint32_t)__bfloat16_as_ushort(b) << (16 * (e & 1));
       }
     }
 #pragma unroll
-    for (int s = 0; s < OZ_S; ++s)
+    for (int s = 0; s < S; ++s)
       *(uint4*)(base + (size_t)s * plane_bytes + (size_t)c * TB) = make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
   }
 }
@@ -234,11 +234,17 @@ __device__ __forceinline__ void oz_bulk_copy(void* dst_smem, const void* src_gme
 //   warp 1 / lane 0 (MMA issuer): waits for a full stage, issues the 55 MMAs, commits them
 //     to the stage's empty barrier, and after the last stage to the "done" barrier;
 //   all 8 warps: wait for "done", then run the epilogue from TMEM.
-template <bool REAL>
+template <bool REAL, int S>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_bfloat16* __restrict__ Ap,
                const __nv_bfloat16* __restrict__ Bp, const int* __restrict__ rexp, const int* __restrict__ cexp, int Mp,
                int N2p, int K2p, void* __restrict__ Cv, long long Cbs, long long Crs, long long Ccs, int* __restrict__ err) {
+  // exact FP32 groups g = 2 .. NEX+1, one TMEM accumulator each; groups above 8 share one
+  constexpr int NEX = (S + 1 <= 8) ? S : 7;
+  constexpr bool MERGED = S + 1 > 8;
+  constexpr int NACC = NEX + (MERGED ? 1 : 0);
+  constexpr int TMEM_COLS = NACC * OZ_BN <= 128 ? 128 : (NACC * OZ_BN <= 256 ? 256 : 512);
+  constexpr int STAGE = S * (OZ_TILE_A + OZ_TILE_B);  // bytes per pipeline stage
   extern __shared__ __align__(1024) unsigned char oz_smem[];
   __shared__ uint64_t full_bar[OZ_STAGES], empty_bar[OZ_STAGES], done_bar;
   __shared__ uint32_t tbase;
@@ -260,12 +266,12 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
   const int nks_p = max(1, min(nks, ((REAL ? 1 : 2) * Kprob + OZ_BK - 1) / OZ_BK));
   const size_t aplane = (size_t)(Mp / OZ_BM) * nks * (OZ_TILE_A / 2);
   const size_t bplane = (size_t)(N2p / OZ_BN) * nks * (OZ_TILE_B / 2);
-  const unsigned char* Abase = (const unsigned char*)(Ap + (size_t)p * OZ_S * aplane) + (size_t)rb * nks * OZ_TILE_A;
-  const unsigned char* Bbase = (const unsigned char*)(Bp + (size_t)p * OZ_S * bplane) + (size_t)cb * nks * OZ_TILE_B;
+  const unsigned char* Abase = (const unsigned char*)(Ap + (size_t)p * S * aplane) + (size_t)rb * nks * OZ_TILE_A;
+  const unsigned char* Bbase = (const unsigned char*)(Bp + (size_t)p * S * bplane) + (size_t)cb * nks * OZ_TILE_B;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&tbase)), "r"(OZ_TMEM_COLS));
+                 :: "r"(smem_u32(&tbase)), "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -292,15 +298,15 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
         break;
       }
       if (s_fail) break;
-      unsigned char* sdst = stage0 + st * OZ_STAGE;
-      oz_expect_tx(&full_bar[st], OZ_STAGE);
+      unsigned char* sdst = stage0 + st * STAGE;
+      oz_expect_tx(&full_bar[st], STAGE);
 #pragma unroll
-      for (int s = 0; s < OZ_S; ++s)
+      for (int s = 0; s < S; ++s)
         oz_bulk_copy(sdst + s * OZ_TILE_A, Abase + (size_t)s * aplane * 2 + (size_t)ks * OZ_TILE_A, OZ_TILE_A,
                      &full_bar[st]);
 #pragma unroll
-      for (int t = 0; t < OZ_S; ++t)
-        oz_bulk_copy(sdst + OZ_S * OZ_TILE_A + t * OZ_TILE_B, Bbase + (size_t)t * bplane * 2 + (size_t)ks * OZ_TILE_B,
+      for (int t = 0; t < S; ++t)
+        oz_bulk_copy(sdst + S * OZ_TILE_A + t * OZ_TILE_B, Bbase + (size_t)t * bplane * 2 + (size_t)ks * OZ_TILE_B,
                      OZ_TILE_B, &full_bar[st]);
     }
     s_issued = ks;
@@ -316,15 +322,15 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
       }
       if (s_fail) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      unsigned char* ssrc = stage0 + st * OZ_STAGE;
-      const uint32_t sa = smem_u32(ssrc), sb = smem_u32(ssrc + OZ_S * OZ_TILE_A);
+      unsigned char* ssrc = stage0 + st * STAGE;
+      const uint32_t sa = smem_u32(ssrc), sb = smem_u32(ssrc + S * OZ_TILE_A);
 #pragma unroll
-      for (int s = 0; s < OZ_S; ++s) {
+      for (int s = 0; s < S; ++s) {
 #pragma unroll
-        for (int t = 0; t < OZ_S; ++t) {
+        for (int t = 0; t < S; ++t) {
           const int g = (s + 1) + (t + 1);
-          if (g > OZ_S + 1) continue;
-          const int acc = g <= 8 ? g - 2 : OZ_NACC - 1;
+          if (g > S + 1) continue;
+          const int acc = g - 2 < NEX ? g - 2 : NEX;
           const uint32_t on = (init_mask >> acc) & 1u;
           oz_mma(tmem + acc * OZ_BN, oz_desc(sa + s * OZ_TILE_A), oz_desc(sb + t * OZ_TILE_B), on);
           init_mask |= 1u << acc;
@@ -359,9 +365,9 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
     const int erow = (gi < M) ? rexp[(size_t)p * Mp + gi] : 0;
     for (int cc = 0; cc < OZ_BN / 4; cc += 4) {  // 8 C'' columns per round
       const int col0 = half * (OZ_BN / 2) + 2 * cc;
-      uint32_t v[OZ_NACC][8];
+      uint32_t v[NACC][8];
 #pragma unroll
-      for (int a = 0; a < OZ_NACC; ++a) {
+      for (int a = 0; a < NACC; ++a) {
         const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + a * OZ_BN + col0;
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                      : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]), "=r"(v[a][5]),
@@ -373,16 +379,17 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
       double part[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
-        // exact groups g = 2..8 (accumulator g-2): G_g = n_g 2^{6(7-g)} with integer n_g;
-        // hi = sum_g n_g 2^{6(8-g)} counts in units of group 8 (2^-6)
+        // exact groups g = 2..NEX+1 (accumulator g-2): G_g = n_g 2^{42-6g} with integer n_g;
+        // hi = sum_g n_g 2^{6(NEX+1-g)} counts in units of the last exact group, 2^{36-6 NEX}
         long long hi = 0;
 #pragma unroll
-        for (int a = 0; a < OZ_NACC - 1; ++a) {
+        for (int a = 0; a < NEX; ++a) {
           const float gv = __uint_as_float(v[a][c]);
           const long long ng = (long long)__float2int_rn(ldexpf(gv, -6 * (5 - a)));
-          hi += ng * (1ll << (6 * (6 - a)));
+          hi += ng * (1ll << (6 * (NEX - 1 - a)));
         }
-        part[c] = (double)hi * 0x1p-6 + (double)__uint_as_float(v[OZ_NACC - 1][c]);
+        part[c] = ldexp((double)hi, 36 - 6 * NEX);
+        if (MERGED) part[c] += (double)__uint_as_float(v[NEX][c]);
       }
       if (REAL) {
         double* Cp = (double*)Cv + (size_t)p * Cbs;
@@ -422,10 +429,40 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
   __syncthreads();
   asm volatile("tcgen05.fence::before_thread_sync;");
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(OZ_TMEM_COLS));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS));
 }
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Split both operands into S digit planes and run the tensor kernel.  The plane buffers are
+// laid out for OZ_S planes (the workspace size), whatever S is used.
+template <bool REAL, int S>
+cudaError_t launch_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta, void* C,
+                      long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st) {
+  if (nprob <= 0 || dims.M <= 0 || dims.N <= 0) return cudaSuccess;
+  const int w2 = REAL ? 1 : 2;
+  const int Mp = round_up(dims.M, OZ_BM), N2p = round_up(w2 * dims.N, OZ_BN), K2p = round_up(w2 * dims.K, OZ_BK);
+  unsigned char* w = (unsigned char*)ws;
+  __nv_bfloat16* Apl = (__nv_bfloat16*)w;
+  w += (size_t)nprob * OZ_S * Mp * K2p * 2;
+  __nv_bfloat16* Bpl = (__nv_bfloat16*)w;
+  w += (size_t)nprob * OZ_S * N2p * K2p * 2;
+  int* rexp = (int*)w;
+  int* cexp = rexp + (size_t)nprob * Mp;
+  oz_split<false, REAL, S><<<dim3(Mp / 16, nprob), 256, 0, st>>>(nprob, dims, A, Mp, K2p, Apl, rexp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  oz_split<true, REAL, S><<<dim3(N2p / 16, nprob), 256, 0, st>>>(nprob, dims, B, N2p, K2p, Bpl, cexp);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = OZ_STAGES * (size_t)S * (OZ_TILE_A + OZ_TILE_B) + 1024;
+  e = cudaFuncSetAttribute(oz_gemm_kernel<REAL, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(N2p / OZ_BN, Mp / OZ_BM, nprob);
+  oz_gemm_kernel<REAL, S><<<grid, OZ_THREADS, smem, st>>>(nprob, dims, alpha, beta, Apl, Bpl, rexp, cexp, Mp, N2p,
+                                                           K2p, C, Cbs, Crs, Ccs, err);
+  return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -438,55 +475,19 @@ size_t zgemm_oz_workspace(int nprob, GemmDims dims) {
 }
 
 cudaError_t launch_zgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta, z64* C,
-                            long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st) {
-  if (nprob <= 0 || dims.M <= 0 || dims.N <= 0) return cudaSuccess;
-  const int Mp = round_up(dims.M, OZ_BM), N2p = round_up(2 * dims.N, OZ_BN), K2p = round_up(2 * dims.K, OZ_BK);
-  unsigned char* w = (unsigned char*)ws;
-  __nv_bfloat16* Apl = (__nv_bfloat16*)w;
-  w += (size_t)nprob * OZ_S * Mp * K2p * 2;
-  __nv_bfloat16* Bpl = (__nv_bfloat16*)w;
-  w += (size_t)nprob * OZ_S * N2p * K2p * 2;
-  int* rexp = (int*)w;
-  int* cexp = rexp + (size_t)nprob * Mp;
-  oz_split<false, false><<<dim3(Mp / 16, nprob), 256, 0, st>>>(nprob, dims, A, Mp, K2p, Apl, rexp);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  oz_split<true, false><<<dim3(N2p / 16, nprob), 256, 0, st>>>(nprob, dims, B, N2p, K2p, Bpl, cexp);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const size_t smem = OZ_STAGES * (size_t)OZ_STAGE + 1024;
-  e = cudaFuncSetAttribute(oz_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  dim3 grid(N2p / OZ_BN, Mp / OZ_BM, nprob);
-  oz_gemm_kernel<false><<<grid, OZ_THREADS, smem, st>>>(nprob, dims, alpha, beta, Apl, Bpl, rexp, cexp, Mp, N2p, K2p,
-                                                         (void*)C, Cbs, Crs, Ccs, err);
-  return cudaGetLastError();
+                            long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st,
+                            int digits) {
+  if (digits == NAO_OZ_DIGITS_MIXED)
+    return launch_oz<false, NAO_OZ_DIGITS_MIXED>(nprob, dims, alpha, A, B, beta, (void*)C, Cbs, Crs, Ccs, ws, err, st);
+  return launch_oz<false, OZ_S>(nprob, dims, alpha, A, B, beta, (void*)C, Cbs, Crs, Ccs, ws, err, st);
 }
 
 bool dgemm_oz_supported(GemmDims dims) { return (long long)dims.K <= OZ_MAX_K2 && dims.M > 0 && dims.N > 0; }
 
 cudaError_t launch_dgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta, double* C,
-                            long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st) {
-  if (nprob <= 0 || dims.M <= 0 || dims.N <= 0) return cudaSuccess;
-  const int Mp = round_up(dims.M, OZ_BM), N2p = round_up(dims.N, OZ_BN), K2p = round_up(dims.K, OZ_BK);
-  unsigned char* w = (unsigned char*)ws;
-  __nv_bfloat16* Apl = (__nv_bfloat16*)w;
-  w += (size_t)nprob * OZ_S * Mp * K2p * 2;
-  __nv_bfloat16* Bpl = (__nv_bfloat16*)w;
-  w += (size_t)nprob * OZ_S * N2p * K2p * 2;
-  int* rexp = (int*)w;
-  int* cexp = rexp + (size_t)nprob * Mp;
-  oz_split<false, true><<<dim3(Mp / 16, nprob), 256, 0, st>>>(nprob, dims, A, Mp, K2p, Apl, rexp);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  oz_split<true, true><<<dim3(N2p / 16, nprob), 256, 0, st>>>(nprob, dims, B, N2p, K2p, Bpl, cexp);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const size_t smem = OZ_STAGES * (size_t)OZ_STAGE + 1024;
-  e = cudaFuncSetAttribute(oz_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  dim3 grid(N2p / OZ_BN, Mp / OZ_BM, nprob);
-  oz_gemm_kernel<true><<<grid, OZ_THREADS, smem, st>>>(nprob, dims, alpha, beta, Apl, Bpl, rexp, cexp, Mp, N2p, K2p,
-                                                        (void*)C, Cbs, Crs, Ccs, err);
-  return cudaGetLastError();
+                            long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st,
+                            int digits) {
+  if (digits == NAO_OZ_DIGITS_MIXED)
+    return launch_oz<true, NAO_OZ_DIGITS_MIXED>(nprob, dims, alpha, A, B, beta, (void*)C, Cbs, Crs, Ccs, ws, err, st);
+  return launch_oz<true, OZ_S>(nprob, dims, alpha, A, B, beta, (void*)C, Cbs, Crs, Ccs, ws, err, st);
 }

@@ -30,7 +30,7 @@ NAO_MIXED_BF16X3 = 2
 #: every symbol include/nao.h declares
 EXPORTS = ("nao_init", "nao_destroy", "nao_last_error", "nao_workspace_bytes", "nao_bloch_sum",
            "nao_gen_eig", "nao_density_matrix", "nao_profile_enable", "nao_profile_read", "nao_launch_count",
-           "nao_fermi_level_noalloc", "nao_set_gemm_method", "nao_zgemm")
+           "nao_fermi_level_noalloc", "nao_set_gemm_method", "nao_set_refinement", "nao_zgemm")
 NAO_GEMM_FP64 = 0
 NAO_GEMM_TC = 1
 
@@ -75,6 +75,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.nao_launch_count.restype = ctypes.c_int64
     lib.nao_set_gemm_method.argtypes = [vp, i32]
     lib.nao_set_gemm_method.restype = i32
+    lib.nao_set_refinement.argtypes = [vp, i32]
+    lib.nao_set_refinement.restype = i32
     i64 = ctypes.c_longlong
     lib.nao_zgemm.argtypes = [vp, i32, i32, i32, i32, i32, f64, vp, i32, i64, i32, vp, i32, i64, i32, f64, vp, i32,
                               i64, vp]
@@ -131,6 +133,10 @@ class Context:
 
     def nao_set_gemm_method(self, method: int):
         self._check(self.lib.nao_set_gemm_method(self.handle, int(method)), "nao_set_gemm_method")
+
+    def nao_set_refinement(self, sweeps: int):
+        """Ritz refinement sweeps after a mixed-precision nao_gen_eig (0, 1 or 2)."""
+        self._check(self.lib.nao_set_refinement(self.handle, int(sweeps)), "nao_set_refinement")
 
     def nao_zgemm(self, A, B, C=None, alpha=1.0, beta=0.0, transA=0, transB=0, method=NAO_GEMM_TC, stream=None):
         """Batched C[p] = alpha op(A[p]) op(B[p]) + beta C[p] (complex128, row-major, 3-d tensors)."""

@@ -20,13 +20,13 @@ def to_dev(inp, torch, dev):
                 w=torch.from_numpy(inp.wk).to(dev))
 
 
-def gpu_band_step(ctx, inp, torch, dev, nb=None, s_cut=1e-10, density=True):
+def gpu_band_step(ctx, inp, torch, dev, nb=None, s_cut=1e-10, density=True, precision=0):
     t = to_dev(inp, torch, dev)
     n = inp.n
     Hk = ctx.nao_bloch_sum(t["HR"], t["R"], t["k"]).reshape(-1, n, n)
     Sk = ctx.nao_bloch_sum(t["SR"], t["R"], t["k"])[0]
     smap = torch.arange(inp.nprob, dtype=torch.int32, device=dev) % inp.nk
-    eps, C, m, st = ctx.nao_gen_eig(Hk, Sk, s_of_prob=smap, s_cut=s_cut, nb=nb)
+    eps, C, m, st = ctx.nao_gen_eig(Hk, Sk, s_of_prob=smap, s_cut=s_cut, nb=nb, precision=precision)
     out = dict(Hk=Hk, Sk=Sk, eps=eps, C=C, m=m, status=st)
     if density:
         mu, eb, f, rho, rst = ctx.nao_density_matrix(t["w"], t["k"], eps, C, m, inp.n_electrons, inp.kT, t["R"],
