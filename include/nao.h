@@ -111,7 +111,7 @@ int nao_bloch_sum(nao_ctx* ctx, int n, int nR, const int32_t* R, int nmat, const
  *   precision NAO_FP64: every product FP64-accurate (ten-digit tensor-core products, or
  *             FP64 CUDA cores with NAO_GEMM_FP64).
  *             NAO_MIXED_BF16X3: the back-transformations, X^H H X, the rank-2k updates of H'
- *             and X V use 24-bit tensor-core products (four BF16 digit planes); the reduction
+ *             and X V use 30-bit tensor-core products (five BF16 digit planes); the reduction
  *             of S, the tridiagonal solves and s^{-1/2} stay FP64.  Then one Ritz refinement
  *             sweep (Ogita-Aishima in the S inner product, FP64-accurate products of the
  *             input H and S; not in the paper) restores the accuracy: eps are the Rayleigh

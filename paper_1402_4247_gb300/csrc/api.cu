@@ -135,7 +135,7 @@ __global__ void finish_status_kernel(int nprob, const int32_t* mP, const int32_t
 // One batched complex product of the band step, on the tensor cores (digit planes) when the
 // context asks for it and the contraction length allows, else on the FP64 CUDA cores.
 // digits: NAO_OZ_DIGITS_FP64, or NAO_OZ_DIGITS_MIXED for the products the mixed mode
-// computes to 24 bits (the FP64 CUDA-core route ignores it).
+// computes to 30 bits (the FP64 CUDA-core route ignores it).
 cudaError_t run_zgemm(nao_ctx* ctx, const char* stage, int nprob, GemmDims d, double alpha, GemmOperand A,
                       GemmOperand B, double beta, z64* C, long long Cbs, long long Crs, long long Ccs, void* ozws,
                       cudaStream_t st, int digits = NAO_OZ_DIGITS_FP64) {
@@ -438,7 +438,7 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
       *Ww = (z64*)(ws + oW), *W2w = (z64*)(ws + oW2), *VWp = (z64*)(ws + oVW);
   const long long snn = (long long)nn;
   // Mixed mode: the back-transformations, X^H H X, the rank-2k updates of H' and X V run with
-  // 24-bit products; the reduction of S, the tridiagonal solves (with their Newton-Schulz
+  // 30-bit products; the reduction of S, the tridiagonal solves (with their Newton-Schulz
   // step) and s^{-1/2} stay FP64-accurate, and one Ritz refinement sweep with FP64-accurate
   // products follows.
   const bool mixed = precision != NAO_FP64;

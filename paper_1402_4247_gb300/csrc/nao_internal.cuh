@@ -162,10 +162,10 @@ cudaError_t launch_ns_correct(int n, int nprob, const int32_t* size, const doubl
 // FP64-accurate complex GEMM on the BF16 tensor cores (digit-plane splitting): C = alpha
 // op(A) op(B) + beta C with real alpha, beta.  Requires 2K <= 1792.  ws: zgemm_oz_workspace
 // bytes; err: device int set to 1 if a bounded wait expired.  digits: NAO_OZ_DIGITS_FP64
-// (ten base-64 planes, FP64 accuracy) or NAO_OZ_DIGITS_MIXED (four planes: 24 bits, the
-// accuracy of an FP32 / three-term BF16 split product, ~5x fewer tensor-core operations).
+// (ten base-64 planes, FP64 accuracy) or NAO_OZ_DIGITS_MIXED (five planes: 30 bits, a little
+// above an FP32 or three-term BF16 split product; 15 tensor-core products instead of 55).
 constexpr int NAO_OZ_DIGITS_FP64 = 10;
-constexpr int NAO_OZ_DIGITS_MIXED = 4;
+constexpr int NAO_OZ_DIGITS_MIXED = 5;
 bool zgemm_oz_supported(GemmDims dims);
 size_t zgemm_oz_workspace(int nprob, GemmDims dims);
 cudaError_t launch_zgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta, z64* C,

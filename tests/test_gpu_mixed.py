@@ -1,7 +1,7 @@
 """Mixed-precision band step vs the CPU oracle (GPU only).
 
 The mixed mode runs the back-transformations, X^H H X, the rank-2k updates of H' and X V
-with 24-bit tensor-core products and then one Ritz refinement sweep (Ogita-Aishima in the S
+with 30-bit tensor-core products and then one Ritz refinement sweep (Ogita-Aishima in the S
 inner product, FP64-accurate products).  The workload statement bounds it by |d eps| <= 1e-9
 Ha over all kept eigenvalues of every problem.  Each case runs with 0, 1 and 2 sweeps: one
 sweep meets the eigenvalue bound, and each sweep squares the vector error (up to a factor
@@ -72,7 +72,7 @@ def test_mixed_refined_matches_oracle(ctx, maker):
     # quadratically (e_{k+1} <= C e_k^2 with C ~ ||H'|| / gap, at most ~1e2 on these cells)
     (de0, res0, orth0), (de1, res1, orth1), (de2, res2, orth2) = err[0], err[1], err[2]
     assert de1 <= TOL_MIXED_EPS_HA and de2 <= TOL_MIXED_EPS_HA, f"refined eigenvalues differ by {de1:.3e} Ha"
-    assert orth1 <= 1e3 * orth0 ** 2 and orth2 <= 1e3 * orth1 ** 2 + 1e-13
+    assert orth1 <= 1e3 * orth0 ** 2 + 1e-12 and orth2 <= 1e3 * orth1 ** 2 + 1e-12  # + rounding floor
     assert res2 < res1 < res0
     # Parts 5-6 on the twice-refined eigenpairs: rho to the FP64 bound, or to the first
     # order of the remaining vector error where that is larger
