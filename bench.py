@@ -262,11 +262,11 @@ def run_ours(args, rank, world, local_rank):
     smap = (torch.arange(nprob, dtype=torch.int32) % nk).to(dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(src):
+    def step(src, precision=0, eps_out=eps):
         ctx.nao_bloch_sum(src["SR"], src["R"], src["k"], out=Sk)
         ctx.nao_bloch_sum(src["HR"], src["R"], src["k"], out=Hk)
-        ctx.nao_gen_eig(Hk.view(nprob, n, n), Sk[0], s_of_prob=smap, out=(eps, C, m, st))
-        ctx.nao_density_matrix(src["w"], src["k"], eps, C, m, inp.n_electrons, inp.kT, src["R"], nspin,
+        ctx.nao_gen_eig(Hk.view(nprob, n, n), Sk[0], s_of_prob=smap, precision=precision, out=(eps_out, C, m, st))
+        ctx.nao_density_matrix(src["w"], src["k"], eps_out, C, m, inp.n_electrons, inp.kT, src["R"], nspin,
                                out=(mu, eb, f, rho, rst))
 
     def barrier():
@@ -322,6 +322,26 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     e2e_ms = x0.elapsed_time(x1) / k_e2e
 
+    # the mixed-precision form of the same step: 30-bit products where the mixed mode allows
+    # them, then one Ritz refinement sweep (NAO_MIXED_BF16X3); its eigenvalues are compared
+    # with the FP64 step's
+    eps_mx = torch.empty_like(eps)
+    step(d_in, 2, eps_mx)
+    barrier()
+    y0, y1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    y0.record(stream)
+    for _ in range(args.steps):
+        step(d_in, 2, eps_mx)
+    y1.record(stream)
+    barrier()
+    mixed_ms = y0.elapsed_time(y1) / args.steps
+    fin = torch.isfinite(eps)
+    mixed = {"value": nprob * world / (mixed_ms * 1e-3), "unit": UNIT, "ms_per_step": mixed_ms,
+             "precision": "NAO_MIXED_BF16X3: five BF16 digit planes (30 bits) for the back-transformations, "
+                          "X^H H X, the H' rank-2k updates and X V; one Ritz refinement sweep",
+             "max_abs_deps_vs_fp64_Ha": float((eps_mx - eps)[fin].abs().max()),
+             "status_ok": bool(int(st.abs().sum()) == 0 and int(rst[0]) == 0)}
+
     t_max = ms_total
     e2e_max = e2e_ms
     if dist is not None:
@@ -365,7 +385,7 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roof, "stages": stages,
             "e2e": {"value": nprob * world / (e2e_max * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
+            "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu, "mixed": mixed,
             "status_ok": bool(int(st.abs().sum()) == 0 and int(rst[0]) == 0),
         }
         print(json.dumps(line), flush=True)
