@@ -185,6 +185,69 @@ int nao_fermi_level_noalloc(int n, int nspin, int nk, const double* wk, const do
                             double* f_out, double* mu_out, double* eband_out, int32_t* status,
                             void* stream);
 
+/* Workspace bytes that nao_gen_eig (precision as given) allocates in this context for n,
+ * nprob problems and nS overlap matrices (nS = nprob without a map).  *bytes out.       */
+int nao_gen_eig_workspace(nao_ctx* ctx, int n, int nprob, int nS, int precision, size_t* bytes);
+
+/* ---- Serving: continuous batching of band steps (not in the paper) ------------------- *
+ * A request is one band step (Parts 1-6) of its own cell: real-space H(R), S(R), images R,
+ * its k-points and weights.  nao_serve_submit copies the inputs (host or device memory) and
+ * returns at once with a ticket.  A scheduler thread inside the context:
+ *   - groups queued requests of equal (n, precision, nb, s_cut), in arrival order, into one
+ *     batch of at most max_batch_problems (spin, k) problems, solved by one nao_gen_eig;
+ *   - runs each batch on a free slot (a stream with its own workspace), so batches of
+ *     different sizes overlap on the GPU, and admits a batch only when its device bytes
+ *     (inputs, outputs, workspace growth) fit in hbm_budget_bytes next to what running
+ *     batches and unreleased results hold;
+ *   - keeps each result on the device until nao_serve_release.
+ * A request that alone exceeds the budget fails with NAO_E_NOMEM.                         */
+typedef struct {
+  int n, nspin, nk, nR;
+  const double* HR;    /* float64 [nspin][nR][n][n] (host or device) */
+  const double* SR;    /* float64 [nR][n][n] */
+  const int32_t* R;    /* int32 [nR][3] integer image vectors */
+  const double* kpts;  /* float64 [nk][3] fractional */
+  const double* wk;    /* float64 [nk] weights */
+  double n_electrons, kT, s_cut;
+  int precision;       /* NAO_FP64 or NAO_MIXED_BF16X3 */
+  int nb;              /* eigenvector columns per problem, 1..n; 0 means n */
+  int want_rho;        /* 1: Parts 5-6 (mu, f, E_band, rho) as well */
+} nao_request;
+
+typedef struct {
+  int status;          /* NAO_OK; NAO_E_BUSY: not finished within the poll's timeout;
+                          otherwise the code the request failed with */
+  int n, nprob, nb, nspin, nR;
+  const double* eps;             /* device [nprob][n], as from nao_gen_eig */
+  const nao_c128* C;             /* device [nprob][n][nb] */
+  const int32_t* m_kept;         /* device [nprob] */
+  const int32_t* prob_status;    /* device [nprob] */
+  const double* mu;              /* device [1]; NULL unless want_rho (also eband, f, rho) */
+  const double* eband;           /* device [1] */
+  const double* f;               /* device [nprob][n] */
+  const double* rho;             /* device [nspin][nR][n][n] */
+  const int32_t* rho_status;     /* device [1] */
+  double queue_ms;     /* submit -> its batch was launched (host clock) */
+  double latency_ms;   /* submit -> its batch finished on the GPU */
+  int batch_requests;  /* requests that shared its nao_gen_eig launch */
+} nao_result;
+
+/* Scheduler settings; call before the first submit (or when nothing is queued or running).
+ * Defaults: 80 % of the free device memory at the first submit, 256 problems, 2 slots.   */
+int nao_serve_config(nao_ctx* ctx, size_t hbm_budget_bytes, int max_batch_problems, int slots);
+/* Hold (on = 1) or resume (on = 0) admission: while held, requests queue but none starts;
+ * running batches finish.  For draining a device or assembling a batch deliberately.     */
+int nao_serve_pause(nao_ctx* ctx, int on);
+/* Queue a request; *ticket receives its id.  NAO_E_INVALID for bad sizes or pointers.     */
+int nao_serve_submit(nao_ctx* ctx, const nao_request* req, uint64_t* ticket);
+/* Wait up to timeout_us (0: do not wait; < 0: no limit) for the request, then fill *out.
+ * Returns out->status.  Device pointers stay valid until nao_serve_release.               */
+int nao_serve_poll(nao_ctx* ctx, uint64_t ticket, int timeout_us, nao_result* out);
+/* Free a finished request's device memory (NAO_E_BUSY while it is queued or running).    */
+int nao_serve_release(nao_ctx* ctx, uint64_t ticket);
+/* Device bytes held by the scheduler now and at most so far, requests queued / running.   */
+int nao_serve_stats(nao_ctx* ctx, size_t* used_bytes, size_t* peak_bytes, int* queued, int* running);
+
 #ifdef __cplusplus
 }
 #endif

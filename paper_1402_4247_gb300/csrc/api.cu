@@ -159,6 +159,81 @@ cudaError_t run_dgemm(nao_ctx* ctx, const char* stage, int nprob, GemmDims d, do
   return launch_dgemm(nprob, d, alpha, A, B, beta, C, Cbs, Crs, Ccs, st);
 }
 
+// Workspace layout of nao_gen_eig (byte offsets into the context's arena) and its size.
+struct GenEigPlan {
+  size_t oAS, oTauS, odS, oeS, owS, oZ, oZ2, oG, oScr, omS, ostS, oX, oHf, oY, oHp, oV, oTauH, odH, oeH, owH, omP, onbP, ostP, ostH, oOz, oVf, oTc, oG2, oT2, oW, oW2, oVW;
+  size_t bytes;
+};
+
+GenEigPlan plan_gen_eig(int n, int nprob, int nSe, bool use_tc) {
+  GenEigPlan W;
+  WsPlan P;
+  const size_t nn = (size_t)n * n;
+  const int nmax = nSe > nprob ? nSe : nprob;
+  // overlap chain
+  W.oAS = P.take<z64>(nn * nSe);
+  W.oTauS = P.take<z64>((size_t)n * nSe);
+  W.odS = P.take<double>((size_t)n * nSe);
+  W.oeS = P.take<double>((size_t)n * nSe);
+  W.owS = P.take<double>((size_t)n * nSe);
+  W.omS = P.take<int32_t>(nSe);
+  W.ostS = P.take<int32_t>(nSe);
+  W.oX = P.take<z64>(nn * nSe);
+  // tridiagonal eigenvectors, Newton-Schulz, inverse-iteration scratch (both chains)
+  W.oZ = P.take<double>(nn * nmax);
+  W.oZ2 = P.take<double>(nn * nmax);
+  W.oG = P.take<double>(nn * nmax);
+  W.oScr = P.take<double>(stein_scratch_doubles(n, nmax));
+  // Hamiltonian chain
+  W.oHf = P.take<z64>(nn * nprob);
+  W.oY = P.take<z64>(nn * nprob);
+  W.oHp = P.take<z64>(nn * nprob);
+  W.oV = P.take<z64>(nn * nprob);
+  W.oTauH = P.take<z64>((size_t)n * nprob);
+  W.odH = P.take<double>((size_t)n * nprob);
+  W.oeH = P.take<double>((size_t)n * nprob);
+  W.owH = P.take<double>((size_t)n * nprob);
+  W.omP = P.take<int32_t>(nprob);
+  W.onbP = P.take<int32_t>(nprob);
+  W.ostP = P.take<int32_t>(nprob);
+  W.ostH = P.take<int32_t>(nprob);
+  // digit planes of the largest product: n x n x n, or the back-transform's nb-wide ones
+  const int nd = n > NAO_WY_NB ? n : NAO_WY_NB;
+  const GemmDims dmax{nd, nd, nd, nullptr, nullptr, nullptr, 0};
+  W.oOz = P.take<char>(use_tc ? zgemm_oz_workspace(nmax, dmax) : 1);
+  // compact WY operands and the Householder panel's [V | W | V]
+  const int ncolv = (n + NAO_WY_NB - 1) / NAO_WY_NB * NAO_WY_NB;
+  W.oVf = P.take<z64>((size_t)n * ncolv * nmax);
+  W.oTc = P.take<z64>((size_t)ncolv * nmax);
+  W.oG2 = P.take<z64>((size_t)NAO_WY_NB * NAO_WY_NB * nmax);
+  W.oT2 = P.take<z64>((size_t)NAO_WY_NB * NAO_WY_NB * nmax);
+  W.oW = P.take<z64>((size_t)NAO_WY_NB * n * nmax);
+  W.oW2 = P.take<z64>((size_t)NAO_WY_NB * n * nmax);
+  W.oVW = P.take<z64>((size_t)3 * NAO_HT_NB * n * nmax);
+  W.bytes = P.off;
+  return W;
+}
+
+// Workspace layout of nao_density_matrix.
+struct DensityPlan {
+  size_t of, onocc, oscr, ost, oCs, oP, oOz;
+  size_t bytes;
+};
+
+DensityPlan plan_density(int n, int nprob, int nb, int num_sms, bool use_tc) {
+  DensityPlan W;
+  WsPlan P;
+  W.of = P.take<double>((size_t)nprob * n);
+  W.onocc = P.take<int32_t>(nprob);
+  W.oscr = P.take<double>(fermi_scratch_doubles(num_sms));
+  W.ost = P.take<int32_t>(1);
+  W.oCs = P.take<z64>((size_t)nprob * n * nb);
+  W.oP = P.take<z64>((size_t)n * n * nprob);
+  W.oOz = P.take<char>(use_tc ? zgemm_oz_workspace(nprob, GemmDims{n, n, nb, nullptr, nullptr, nullptr, 0}) : 1);
+  W.bytes = P.off;
+  return W;
+}
+
 // Eigen_HH steps 3-4 in blocked form: U(:, c) = Q Z(:, m - nc + c) for c < nc (nc = ncols[p]),
 // normalised (times 1/sqrt(w) when use_rsqrt), with Q = prod_j (I - V_j T_j V_j^H) applied from
 // the last block of NAO_WY_NB reflectors to the first; every block costs three products
@@ -247,6 +322,17 @@ bool is_device_ptr(const void* p) {
 
 }  // namespace
 
+size_t gen_eig_ws_bytes(const nao_ctx* ctx, int n, int nprob, int nSe) {
+  const bool use_tc = ctx->gemm_method == NAO_GEMM_TC && zgemm_oz_supported(GemmDims{n, n, n, nullptr, nullptr, nullptr, 0});
+  return plan_gen_eig(n, nprob, nSe, use_tc).bytes;
+}
+
+size_t density_ws_bytes(const nao_ctx* ctx, int n, int nprob, int nb) {
+  const bool use_tc =
+      ctx->gemm_method == NAO_GEMM_TC && zgemm_oz_supported(GemmDims{n, n, nb, nullptr, nullptr, nullptr, 0});
+  return plan_density(n, nprob, nb, ctx->num_sms, use_tc).bytes;
+}
+
 extern "C" {
 
 int nao_init(nao_ctx** out, int device) {
@@ -279,6 +365,7 @@ int nao_init(nao_ctx** out, int device) {
 
 void nao_destroy(nao_ctx* ctx) {
   if (!ctx) return;
+  serve_shutdown(ctx);
   {
     DeviceGuard g(ctx->device);
     drain_pending(ctx);
@@ -319,6 +406,16 @@ int nao_set_gemm_method(nao_ctx* ctx, int method) {
   if (method != NAO_GEMM_FP64 && method != NAO_GEMM_TC)
     return nao_fail(ctx, NAO_E_INVALID, "nao_set_gemm_method: unknown method %d", method);
   ctx->gemm_method = method;
+  return NAO_OK;
+}
+
+int nao_gen_eig_workspace(nao_ctx* ctx, int n, int nprob, int nS, int precision, size_t* bytes) {
+  if (!ctx || !bytes) return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig_workspace: NULL argument");
+  if (n < 1 || nprob < 1 || nS < 1) return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig_workspace: sizes must be >= 1");
+  if (precision != NAO_FP64 && precision != NAO_MIXED_BF16X3)
+    return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig_workspace: precision %d not available", precision);
+  const size_t b = gen_eig_ws_bytes(ctx, n, nprob, nS);
+  *bytes = b + b / 8;  // the arena keeps 1/8 headroom
   return NAO_OK;
 }
 
@@ -394,48 +491,26 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   const size_t nn = (size_t)n * n;
   const int nmax = nSe > nprob ? nSe : nprob;
 
-  WsPlan P;
-  const size_t oAS = P.take<z64>(nn * nSe), oTauS = P.take<z64>((size_t)n * nSe);
-  const size_t odS = P.take<double>((size_t)n * nSe), oeS = P.take<double>((size_t)n * nSe),
-               owS = P.take<double>((size_t)n * nSe);
-  const size_t oZ = P.take<double>(nn * nmax), oZ2 = P.take<double>(nn * nmax), oG = P.take<double>(nn * nmax);
-  const size_t oScr = P.take<double>(stein_scratch_doubles(n, nmax));
-  const size_t omS = P.take<int32_t>(nSe), ostS = P.take<int32_t>(nSe);
-  const size_t oX = P.take<z64>(nn * nSe);
-  const size_t oHf = P.take<z64>(nn * nprob), oY = P.take<z64>(nn * nprob), oHp = P.take<z64>(nn * nprob),
-               oV = P.take<z64>(nn * nprob);
-  const size_t oTauH = P.take<z64>((size_t)n * nprob), odH = P.take<double>((size_t)n * nprob),
-               oeH = P.take<double>((size_t)n * nprob), owH = P.take<double>((size_t)n * nprob);
-  const size_t omP = P.take<int32_t>(nprob), onbP = P.take<int32_t>(nprob), ostP = P.take<int32_t>(nprob),
-               ostH = P.take<int32_t>(nprob);
-  // largest product of the step: n x n x n, or the blocked back-transform's nb-wide ones
-  const int nd = n > NAO_WY_NB ? n : NAO_WY_NB;
-  const GemmDims dmax{nd, nd, nd, nullptr, nullptr, nullptr, 0};
   const bool use_tc = ctx->gemm_method == NAO_GEMM_TC && zgemm_oz_supported(GemmDims{n, n, n, nullptr, nullptr, nullptr, 0});
-  const size_t oOz = P.take<char>(use_tc ? zgemm_oz_workspace(nmax, dmax) : 1);
+  const GenEigPlan W = plan_gen_eig(n, nprob, nSe, use_tc);
   const int ncolv = (n + NAO_WY_NB - 1) / NAO_WY_NB * NAO_WY_NB;
-  const size_t oVf = P.take<z64>((size_t)n * ncolv * nmax), oTc = P.take<z64>((size_t)ncolv * nmax),
-               oG2 = P.take<z64>((size_t)NAO_WY_NB * NAO_WY_NB * nmax),
-               oT2 = P.take<z64>((size_t)NAO_WY_NB * NAO_WY_NB * nmax),
-               oW = P.take<z64>((size_t)NAO_WY_NB * n * nmax), oW2 = P.take<z64>((size_t)NAO_WY_NB * n * nmax),
-               oVW = P.take<z64>((size_t)3 * NAO_HT_NB * n * nmax);
-  int rc = nao_ws_reserve(ctx, P.off);
+  int rc = nao_ws_reserve(ctx, W.bytes);
   if (rc) return rc;
   char* ws = (char*)ctx->ws;
-  z64* AS = (z64*)(ws + oAS);
-  z64* tauS = (z64*)(ws + oTauS);
-  double *dS = (double*)(ws + odS), *eS = (double*)(ws + oeS), *wS = (double*)(ws + owS);
-  double *Z = (double*)(ws + oZ), *Z2 = (double*)(ws + oZ2), *G = (double*)(ws + oG), *scr = (double*)(ws + oScr);
-  int32_t *mS = (int32_t*)(ws + omS), *stS = (int32_t*)(ws + ostS);
-  z64* X = (z64*)(ws + oX);
-  z64 *Hf = (z64*)(ws + oHf), *Y = (z64*)(ws + oY), *Hp = (z64*)(ws + oHp), *V = (z64*)(ws + oV);
-  z64* tauH = (z64*)(ws + oTauH);
-  double *dH = (double*)(ws + odH), *eH = (double*)(ws + oeH), *wH = (double*)(ws + owH);
-  int32_t *mP = (int32_t*)(ws + omP), *nbP = (int32_t*)(ws + onbP), *stP = (int32_t*)(ws + ostP),
-          *stH = (int32_t*)(ws + ostH);
-  void* ozws = use_tc ? (void*)(ws + oOz) : nullptr;
-  z64 *Vf = (z64*)(ws + oVf), *tauc = (z64*)(ws + oTc), *Gw = (z64*)(ws + oG2), *Tw = (z64*)(ws + oT2),
-      *Ww = (z64*)(ws + oW), *W2w = (z64*)(ws + oW2), *VWp = (z64*)(ws + oVW);
+  z64* AS = (z64*)(ws + W.oAS);
+  z64* tauS = (z64*)(ws + W.oTauS);
+  double *dS = (double*)(ws + W.odS), *eS = (double*)(ws + W.oeS), *wS = (double*)(ws + W.owS);
+  double *Z = (double*)(ws + W.oZ), *Z2 = (double*)(ws + W.oZ2), *G = (double*)(ws + W.oG), *scr = (double*)(ws + W.oScr);
+  int32_t *mS = (int32_t*)(ws + W.omS), *stS = (int32_t*)(ws + W.ostS);
+  z64* X = (z64*)(ws + W.oX);
+  z64 *Hf = (z64*)(ws + W.oHf), *Y = (z64*)(ws + W.oY), *Hp = (z64*)(ws + W.oHp), *V = (z64*)(ws + W.oV);
+  z64* tauH = (z64*)(ws + W.oTauH);
+  double *dH = (double*)(ws + W.odH), *eH = (double*)(ws + W.oeH), *wH = (double*)(ws + W.owH);
+  int32_t *mP = (int32_t*)(ws + W.omP), *nbP = (int32_t*)(ws + W.onbP), *stP = (int32_t*)(ws + W.ostP),
+          *stH = (int32_t*)(ws + W.ostH);
+  void* ozws = use_tc ? (void*)(ws + W.oOz) : nullptr;
+  z64 *Vf = (z64*)(ws + W.oVf), *tauc = (z64*)(ws + W.oTc), *Gw = (z64*)(ws + W.oG2), *Tw = (z64*)(ws + W.oT2),
+      *Ww = (z64*)(ws + W.oW), *W2w = (z64*)(ws + W.oW2), *VWp = (z64*)(ws + W.oVW);
   const long long snn = (long long)nn;
   // Mixed mode: the back-transformations, X^H H X, the rank-2k updates of H' and X V run with
   // 30-bit products; the reduction of S, the tridiagonal solves (with their Newton-Schulz
@@ -564,14 +639,11 @@ int nao_density_matrix(nao_ctx* ctx, int n, int nspin, int nk, const double* wk,
   const int nprob = nspin * nk;
   const size_t nn = (size_t)n * n;
   const double gdeg = (nspin == 1) ? 2.0 : 1.0;
-  WsPlan P;
-  const size_t of = P.take<double>((size_t)nprob * n), onocc = P.take<int32_t>(nprob),
-               oscr = P.take<double>(fermi_scratch_doubles(ctx->num_sms)), ost = P.take<int32_t>(1),
-               oCs = P.take<z64>((size_t)nprob * n * nb), oP = P.take<z64>(nn * nprob);
   const GemmDims dP{n, n, nb, nullptr, nullptr, nullptr, 0};
   const bool use_tc = ctx->gemm_method == NAO_GEMM_TC && zgemm_oz_supported(dP);
-  const size_t oOz = P.take<char>(use_tc ? zgemm_oz_workspace(nprob, dP) : 1);
-  int rc = nao_ws_reserve(ctx, P.off);
+  const DensityPlan W = plan_density(n, nprob, nb, ctx->num_sms, use_tc);
+  const size_t of = W.of, onocc = W.onocc, oscr = W.oscr, ost = W.ost, oCs = W.oCs, oP = W.oP, oOz = W.oOz;
+  int rc = nao_ws_reserve(ctx, W.bytes);
   if (rc) return rc;
   char* ws = (char*)ctx->ws;
   double* f = f_out ? f_out : (double*)(ws + of);

@@ -53,7 +53,15 @@ struct nao_ctx {
   int gemm_method = NAO_GEMM_TC;
   int refine_sweeps = 1;     // Ritz refinement sweeps after a mixed-precision solve (0, 1 or 2)
   int* dev_flags = nullptr;  // [0]: a bounded wait in a tensor-core kernel expired
+  struct NaoServer* server = nullptr;  // request scheduler (csrc/serve.cu), made on first use
 };
+
+// Workspace bytes nao_gen_eig / nao_density_matrix reserve on this context (before the
+// arena's 1/8 headroom); the scheduler's admission test uses them.
+size_t gen_eig_ws_bytes(const nao_ctx* ctx, int n, int nprob, int nSe);
+size_t density_ws_bytes(const nao_ctx* ctx, int n, int nprob, int nb);
+// Stops the scheduler thread of ctx (if any), waits for its batches, frees its memory.
+void serve_shutdown(nao_ctx* ctx);
 
 // Stage bracketing for tracing (no-ops unless profiling is on).
 struct NaoStage {

@@ -30,7 +30,9 @@ NAO_MIXED_BF16X3 = 2
 #: every symbol include/nao.h declares
 EXPORTS = ("nao_init", "nao_destroy", "nao_last_error", "nao_workspace_bytes", "nao_bloch_sum",
            "nao_gen_eig", "nao_density_matrix", "nao_profile_enable", "nao_profile_read", "nao_launch_count",
-           "nao_fermi_level_noalloc", "nao_set_gemm_method", "nao_set_refinement", "nao_zgemm")
+           "nao_fermi_level_noalloc", "nao_set_gemm_method", "nao_set_refinement", "nao_zgemm",
+           "nao_gen_eig_workspace", "nao_serve_config", "nao_serve_pause", "nao_serve_submit", "nao_serve_poll",
+           "nao_serve_release", "nao_serve_stats")
 NAO_GEMM_FP64 = 0
 NAO_GEMM_TC = 1
 
@@ -39,6 +41,33 @@ _lib = None
 
 class NaoError(RuntimeError):
     pass
+
+
+class NaoRequest(ctypes.Structure):
+    """``nao_request`` of include/nao.h."""
+    _fields_ = [("n", ctypes.c_int), ("nspin", ctypes.c_int), ("nk", ctypes.c_int), ("nR", ctypes.c_int),
+                ("HR", ctypes.c_void_p), ("SR", ctypes.c_void_p), ("R", ctypes.c_void_p),
+                ("kpts", ctypes.c_void_p), ("wk", ctypes.c_void_p),
+                ("n_electrons", ctypes.c_double), ("kT", ctypes.c_double), ("s_cut", ctypes.c_double),
+                ("precision", ctypes.c_int), ("nb", ctypes.c_int), ("want_rho", ctypes.c_int)]
+
+
+class NaoResult(ctypes.Structure):
+    """``nao_result`` of include/nao.h."""
+    _fields_ = [("status", ctypes.c_int), ("n", ctypes.c_int), ("nprob", ctypes.c_int), ("nb", ctypes.c_int),
+                ("nspin", ctypes.c_int), ("nR", ctypes.c_int),
+                ("eps", ctypes.c_void_p), ("C", ctypes.c_void_p), ("m_kept", ctypes.c_void_p),
+                ("prob_status", ctypes.c_void_p), ("mu", ctypes.c_void_p), ("eband", ctypes.c_void_p),
+                ("f", ctypes.c_void_p), ("rho", ctypes.c_void_p), ("rho_status", ctypes.c_void_p),
+                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("batch_requests", ctypes.c_int)]
+
+
+class _DeviceView:
+    """A device array the library owns, seen by torch through __cuda_array_interface__."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
 
 
 def load_library(path: str | None = None) -> ctypes.CDLL:
@@ -83,6 +112,21 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.nao_zgemm.restype = i32
     lib.nao_fermi_level_noalloc.argtypes = [i32, i32, i32, vp, vp, vp, i32, f64, f64, vp, vp, vp, vp, vp]
     lib.nao_fermi_level_noalloc.restype = i32
+    lib.nao_gen_eig_workspace.argtypes = [vp, i32, i32, i32, i32, ctypes.POINTER(sz)]
+    lib.nao_gen_eig_workspace.restype = i32
+    lib.nao_serve_config.argtypes = [vp, sz, i32, i32]
+    lib.nao_serve_config.restype = i32
+    lib.nao_serve_pause.argtypes = [vp, i32]
+    lib.nao_serve_pause.restype = i32
+    lib.nao_serve_submit.argtypes = [vp, ctypes.POINTER(NaoRequest), ctypes.POINTER(ctypes.c_uint64)]
+    lib.nao_serve_submit.restype = i32
+    lib.nao_serve_poll.argtypes = [vp, ctypes.c_uint64, i32, ctypes.POINTER(NaoResult)]
+    lib.nao_serve_poll.restype = i32
+    lib.nao_serve_release.argtypes = [vp, ctypes.c_uint64]
+    lib.nao_serve_release.restype = i32
+    lib.nao_serve_stats.argtypes = [vp, ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(i32),
+                                    ctypes.POINTER(i32)]
+    lib.nao_serve_stats.restype = i32
     _lib = lib
     return lib
 
@@ -204,6 +248,74 @@ class Context:
                                   int(precision), nb, _ptr(eps), _ptr(C), _ptr(m), _ptr(st), _stream(stream))
         self._check(rc, "nao_gen_eig")
         return eps, C, m, st
+
+    def nao_gen_eig_workspace(self, n, nprob, nS, precision=NAO_FP64) -> int:
+        b = ctypes.c_size_t()
+        self._check(self.lib.nao_gen_eig_workspace(self.handle, int(n), int(nprob), int(nS), int(precision),
+                                                   ctypes.byref(b)), "nao_gen_eig_workspace")
+        return int(b.value)
+
+    # ------------------------------------------------------------------ serving
+    def nao_serve_config(self, hbm_budget_bytes: int, max_batch_problems: int = 256, slots: int = 2):
+        self._check(self.lib.nao_serve_config(self.handle, int(hbm_budget_bytes), int(max_batch_problems),
+                                              int(slots)), "nao_serve_config")
+
+    def nao_serve_pause(self, on: bool):
+        self._check(self.lib.nao_serve_pause(self.handle, 1 if on else 0), "nao_serve_pause")
+
+    def nao_serve_submit(self, HR, SR, R, kpts, wk, n_electrons, kT, s_cut=1e-10, precision=NAO_FP64, nb=0,
+                         want_rho=True) -> int:
+        """Queue one band step.  HR float64 [nspin][nR][n][n], SR [nR][n][n], R int32 [nR][3],
+        kpts [nk][3], wk [nk]: contiguous torch tensors on the host or the device (copied
+        before the call returns).  Returns the ticket."""
+        for t in (HR, SR, R, kpts, wk):
+            if not t.is_contiguous():
+                raise ValueError("expected contiguous tensors")
+        nspin, nR, n, _ = HR.shape
+        q = NaoRequest(n=n, nspin=nspin, nk=kpts.shape[0], nR=nR, HR=HR.data_ptr(), SR=SR.data_ptr(),
+                       R=R.data_ptr(), kpts=kpts.data_ptr(), wk=wk.data_ptr(), n_electrons=float(n_electrons),
+                       kT=float(kT), s_cut=float(s_cut), precision=int(precision), nb=int(nb),
+                       want_rho=1 if want_rho else 0)
+        t = ctypes.c_uint64()
+        self._check(self.lib.nao_serve_submit(self.handle, ctypes.byref(q), ctypes.byref(t)), "nao_serve_submit")
+        return int(t.value)
+
+    def nao_serve_poll(self, ticket: int, timeout_us: int = -1) -> NaoResult:
+        """Wait (timeout_us < 0: without limit) and return the ``NaoResult``; its status is
+        NAO_E_BUSY while the request is still queued or running."""
+        res = NaoResult()
+        rc = self.lib.nao_serve_poll(self.handle, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(res))
+        if rc not in (NAO_OK, NAO_E_BUSY) and res.n == 0:
+            self._check(rc, "nao_serve_poll")
+        return res
+
+    def serve_result_tensors(self, res: NaoResult) -> dict:
+        """Copies (torch, on the device) of a finished request's results."""
+        n, P, nb, ns, nR = res.n, res.nprob, res.nb, res.nspin, res.nR
+        dev = torch.device("cuda", self.device)
+
+        def view(ptr, shape, typestr, dtype):
+            if not ptr:
+                return None
+            return torch.as_tensor(_DeviceView(ptr, shape, typestr), device=dev).view(dtype).clone()
+
+        return {"eps": view(res.eps, (P, n), "<f8", torch.float64),
+                "C": view(res.C, (P, n, 2 * nb), "<f8", torch.float64).view(torch.complex128) if res.C else None,
+                "m": view(res.m_kept, (P,), "<i4", torch.int32),
+                "status": view(res.prob_status, (P,), "<i4", torch.int32),
+                "mu": view(res.mu, (1,), "<f8", torch.float64), "eband": view(res.eband, (1,), "<f8", torch.float64),
+                "f": view(res.f, (P, n), "<f8", torch.float64), "rho": view(res.rho, (ns, nR, n, n), "<f8", torch.float64),
+                "rstatus": view(res.rho_status, (1,), "<i4", torch.int32)}
+
+    def nao_serve_release(self, ticket: int):
+        self._check(self.lib.nao_serve_release(self.handle, ctypes.c_uint64(ticket)), "nao_serve_release")
+
+    def nao_serve_stats(self):
+        """-> (used_bytes, peak_bytes, queued, running)"""
+        u, pk, q, r = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.nao_serve_stats(self.handle, ctypes.byref(u), ctypes.byref(pk), ctypes.byref(q),
+                                             ctypes.byref(r)), "nao_serve_stats")
+        return int(u.value), int(pk.value), int(q.value), int(r.value)
 
     # ------------------------------------------------------------------ Parts 5-6
     def nao_density_matrix(self, wk, kpts, eps, C, m_kept, n_electrons, kT, R, nspin, want_f=True, out=None,
