@@ -188,6 +188,87 @@ def _load_traffic(stage, units_per_launch):
         return None
 
 
+def run_serve(local_rank, n_requests=48, seed=5):
+    """Serving stream (a scaled-down form of the serving workload: fewer requests, n up to 768):
+    cells with n log-uniform in [128, 768], 1-8 random k-points mirrored to +-k (Gamma added
+    when odd), 1 or 2 spins, FP64 or mixed precision.  First the offline capacity (all
+    requests queued at once), then Poisson arrivals at 0.7x that rate; latencies are the
+    library's submit -> finished-on-GPU times."""
+    import numpy as np
+    import torch
+    from paper_1402_4247_gb300 import synth
+    from paper_1402_4247_gb300.nao import Context
+
+    rng = np.random.default_rng(seed)
+    cells = []
+    for i in range(6):
+        nt = float(np.exp(rng.uniform(np.log(128), np.log(768))))
+        h, l = max(1, round(nt / 25)), max(1, round(3 * nt / 50))
+        cells.append(synth.small_cell(500 + i, h, l, kgrid=(1, 1, 1), nspin=2))
+    reqs = []
+    for _ in range(n_requests):
+        c = cells[int(rng.integers(len(cells)))]
+        nk = int(rng.integers(1, 9))
+        half = rng.uniform(-0.5, 0.5, size=(nk // 2, 3))
+        k = np.concatenate([half, -half] + ([np.zeros((1, 3))] if nk % 2 else []))
+        nspin = int(rng.integers(1, 3))
+        reqs.append(dict(HR=torch.from_numpy(np.ascontiguousarray(c.HR[:nspin])), SR=torch.from_numpy(c.SR),
+                         R=torch.from_numpy(c.R), k=torch.from_numpy(k), w=torch.full((nk,), 1.0 / nk, dtype=torch.float64),
+                         ne=c.n_electrons, kT=c.kT, prec=int(rng.integers(0, 2)) * 2, nprob=nspin * nk, n=c.n))
+    ctx = Context(local_rank)
+
+    def submit(q):
+        return ctx.nao_serve_submit(q["HR"], q["SR"], q["R"], q["k"], q["w"], q["ne"], q["kT"], precision=q["prec"])
+
+    # warm-up: one request of every cell (workspaces, allocator pool)
+    for c in cells:
+        q = dict(reqs[0], HR=torch.from_numpy(c.HR[:1].copy()), SR=torch.from_numpy(c.SR), R=torch.from_numpy(c.R),
+                 ne=c.n_electrons, kT=c.kT)
+        t = submit(q)
+        ctx.nao_serve_poll(t, -1)
+        ctx.nao_serve_release(t)
+    ok = True
+    # offline capacity
+    ctx.nao_serve_pause(True)
+    tickets = [submit(q) for q in reqs]
+    t0 = time.perf_counter()
+    ctx.nao_serve_pause(False)
+    batch = []
+    for t in tickets:
+        r = ctx.nao_serve_poll(t, -1)
+        ok = ok and r.status == 0
+        batch.append(r.batch_requests)
+        ctx.nao_serve_release(t)
+    t_off = time.perf_counter() - t0
+    cap = n_requests / t_off
+    # online: Poisson arrivals at 0.7x capacity
+    rate = 0.7 * cap
+    gaps = rng.exponential(1.0 / rate, size=n_requests)
+    tickets = []
+    t0 = time.perf_counter()
+    due = t0
+    for q, g in zip(reqs, gaps):
+        due += g
+        while time.perf_counter() < due:
+            time.sleep(min(1e-3, max(0.0, due - time.perf_counter())))
+        tickets.append(submit(q))
+    lat = []
+    for t in tickets:
+        r = ctx.nao_serve_poll(t, -1)
+        ok = ok and r.status == 0
+        lat.append(r.latency_ms)
+        ctx.nao_serve_release(t)
+    _, peak, _, _ = ctx.nao_serve_stats()
+    ctx.close()
+    return {"workload": f"{n_requests} requests: n log-uniform in [128, 768] over 6 cells (n = "
+                        + ", ".join(str(c.n) for c in cells) + "), 1-8 mirrored random k-points, 1-2 spins, "
+                        "FP64 or mixed 50/50, Parts 1-6 each; 2 slots, batches up to 256 problems",
+            "requests": n_requests, "capacity_req_per_s": cap,
+            "solves_per_s_offline": sum(q["nprob"] for q in reqs) / t_off,
+            "rate_req_per_s": rate, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_batch_requests_offline": float(np.mean(batch)), "peak_hbm_bytes": peak, "status_ok": ok}
+
+
 # ------------------------------------------------------------------------------ arms
 
 def run_reference(args, rank, world):
@@ -342,6 +423,8 @@ def run_ours(args, rank, world, local_rank):
              "max_abs_deps_vs_fp64_Ha": float((eps_mx - eps)[fin].abs().max()),
              "status_ok": bool(int(st.abs().sum()) == 0 and int(rst[0]) == 0)}
 
+    serve = run_serve(local_rank) if (world == 1 and not args.no_serve) else None
+
     t_max = ms_total
     e2e_max = e2e_ms
     if dist is not None:
@@ -385,7 +468,7 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roof, "stages": stages,
             "e2e": {"value": nprob * world / (e2e_max * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu, "mixed": mixed,
+            "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu, "mixed": mixed, "serve": serve,
             "status_ok": bool(int(st.abs().sum()) == 0 and int(rst[0]) == 0),
         }
         print(json.dumps(line), flush=True)
@@ -401,6 +484,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-stream measurement")
     ap.add_argument("--cpu-cores", type=int, default=16)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

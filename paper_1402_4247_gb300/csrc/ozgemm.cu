@@ -64,6 +64,9 @@ __device__ __forceinline__ int oz_tile_off(int row, int k) {
   return (row >> 3) * 256 + ((k >> 3) & 1) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
+// 2^e for a compile-time e (|e| < 1000)
+__host__ __device__ constexpr double oz_pow2(int e) { return e == 0 ? 1.0 : (e > 0 ? 2.0 * oz_pow2(e - 1) : 0.5 * oz_pow2(e + 1)); }
+
 // biased exponent field of x (0 for zero / subnormal)
 __device__ __forceinline__ int exp_field(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7ff); }
 
@@ -245,6 +248,7 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
   constexpr int NACC = NEX + (MERGED ? 1 : 0);
   constexpr int TMEM_COLS = NACC * OZ_BN <= 128 ? 128 : (NACC * OZ_BN <= 256 ? 256 : 512);
   constexpr int STAGE = S * (OZ_TILE_A + OZ_TILE_B);  // bytes per pipeline stage
+  constexpr double kUnit = oz_pow2(36 - 6 * NEX);     // value of one unit of the last exact group
   extern __shared__ __align__(1024) unsigned char oz_smem[];
   __shared__ uint64_t full_bar[OZ_STAGES], empty_bar[OZ_STAGES], done_bar;
   __shared__ uint32_t tbase;
@@ -388,7 +392,7 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
           const long long ng = (long long)__float2int_rn(ldexpf(gv, -6 * (5 - a)));
           hi += ng * (1ll << (6 * (NEX - 1 - a)));
         }
-        part[c] = ldexp((double)hi, 36 - 6 * NEX);
+        part[c] = (double)hi * kUnit;
         if (MERGED) part[c] += (double)__uint_as_float(v[NEX][c]);
       }
       if (REAL) {
