@@ -50,7 +50,7 @@ enum {
   NAO_GEMM_FP64 = 0,  /* FP64 FMA on the CUDA cores                                        */
   NAO_GEMM_TC = 1     /* BF16 tensor cores on exact 6-bit digit planes of the FP64 operands
                          (60-bit splitting, FP32-exact partial sums; FP64-level accuracy);
-                         used where the contraction length allows (2K <= 1792), else FP64 */
+                         contractions longer than 896 run as chunks summed in FP64         */
 };
 
 /* Library / context ------------------------------------------------------------------ */
@@ -77,8 +77,8 @@ int nao_set_refinement(nao_ctx* ctx, int sweeps);
  *   C[p] = alpha op(A[p]) op(B[p]) + beta C[p],  p = 0..nprob-1, real alpha and beta.
  * Row-major storage: A[p] at A + p*strideA with leading dimension lda (elements); op(X) is
  * X (trans = 0), X^T (1) or X^H (2).  op(A) is M x K, op(B) is K x N, C[p] is M x N with
- * leading dimension ldc.  method: NAO_GEMM_FP64 or NAO_GEMM_TC (NAO_E_INVALID if 2K > 1792
- * for NAO_GEMM_TC).  Device arrays; stream-ordered.                                       */
+ * leading dimension ldc.  method: NAO_GEMM_FP64 or NAO_GEMM_TC.  Device arrays;
+ * stream-ordered.                                                                         */
 int nao_zgemm(nao_ctx* ctx, int method, int nprob, int M, int N, int K, double alpha,
               const nao_c128* A, int lda, long long strideA, int transA,
               const nao_c128* B, int ldb, long long strideB, int transB, double beta,

@@ -93,13 +93,23 @@ def householder_tridiagonalize(A: np.ndarray):
 # Eigen_HH step 2: the LAPACK tridiagonal eigensolver
 # --------------------------------------------------------------------------------------
 
-def tridiagonal_eigensolve(d: np.ndarray, e: np.ndarray):
+def tridiagonal_eigensolve(d: np.ndarray, e: np.ndarray, method: str = "mrrr"):
     """Sec. 3, Eigen_HH step 2: all eigenpairs of the real symmetric tridiagonal
-    tridiag(e, d, e) by a LAPACK routine (MRRR, dstemr), eigenvalues ascending."""
+    tridiag(e, d, e) by a LAPACK routine, eigenvalues ascending.  The paper allows dstevx,
+    dstedc or dstegr.  method "mrrr" (default): MRRR (dstemr, the successor of dstegr); when
+    MRRR reports failure (it can on spectra with hundreds of eigenvalues packed within
+    ~1e-7 |T|, as the overlap of an ill-conditioned basis has), the implicit QL/QR routine
+    (dstev) gives the same eigenpairs by another route.  method "bisection": bisection and
+    inverse iteration (dstebz + dstein, the method of dstevx)."""
     n = d.shape[0]
     if n == 1:
         return d.copy(), np.ones((1, 1))
-    w, Z = scipy.linalg.eigh_tridiagonal(d, e, lapack_driver="stemr")
+    if method == "bisection":
+        return scipy.linalg.eigh_tridiagonal(d, e, lapack_driver="stebz")
+    try:
+        w, Z = scipy.linalg.eigh_tridiagonal(d, e, lapack_driver="stemr")
+    except np.linalg.LinAlgError:
+        w, Z = scipy.linalg.eigh_tridiagonal(d, e, lapack_driver="stev")
     return w, Z
 
 
@@ -121,10 +131,10 @@ def rearrange_eigenvectors(Z: np.ndarray, us, hs, delta) -> np.ndarray:
     return V
 
 
-def eigen_hh(A: np.ndarray):
+def eigen_hh(A: np.ndarray, method: str = "mrrr"):
     """Sec. 3 Eigen_HH: eigenvalues (ascending) and orthonormal eigenvectors of Hermitian A."""
     d, e, us, hs, delta = householder_tridiagonalize(A)
-    w, Z = tridiagonal_eigensolve(d, e)
+    w, Z = tridiagonal_eigensolve(d, e, method)
     return w, rearrange_eigenvectors(Z, us, hs, delta)
 
 
@@ -132,14 +142,14 @@ def eigen_hh(A: np.ndarray):
 # Parts 2-4: the generalized eigenproblem H C = S C eps
 # --------------------------------------------------------------------------------------
 
-def generalized_eigensolve(H: np.ndarray, S: np.ndarray, s_cut: float = 1e-10):
+def generalized_eigensolve(H: np.ndarray, S: np.ndarray, s_cut: float = 1e-10, method: str = "mrrr"):
     """Sec. 3 Parts 2-4.
 
     Part 2: Eigen_HH(S) -> s, U; X = U_m s_m^{-1/2} over s_j >= s_cut.
     Part 3: H' = X^H H X (made exactly Hermitian from its lower triangle).
     Part 4: Eigen_HH(H') -> eps, V; C = X V.
     Returns (eps [m], C [n, m], m, s [n])."""
-    s, U = eigen_hh(S)
+    s, U = eigen_hh(S, method)
     keep = s >= s_cut
     X = U[:, keep] / np.sqrt(s[keep])[None, :]
     Hp = X.conj().T @ H @ X
@@ -148,7 +158,7 @@ def generalized_eigensolve(H: np.ndarray, S: np.ndarray, s_cut: float = 1e-10):
     m = int(keep.sum())
     if m == 0:
         return np.zeros(0), np.zeros((H.shape[0], 0), dtype=np.complex128), 0, s
-    eps, V = eigen_hh(Hp)
+    eps, V = eigen_hh(Hp, method)
     return eps, X @ V, m, s
 
 

@@ -438,7 +438,6 @@ int nao_zgemm(nao_ctx* ctx, int method, int nprob, int M, int N, int K, double a
   GemmOperand b{B, strideB, transB ? 1 : ldb, transB ? ldb : 1, transB == 2, nullptr};
   GemmDims d{M, N, K, nullptr, nullptr, nullptr, 0};
   if (method == NAO_GEMM_TC) {
-    if (!zgemm_oz_supported(d)) return nao_fail(ctx, NAO_E_INVALID, "nao_zgemm: K = %d too long for NAO_GEMM_TC", K);
     WsPlan P;
     const size_t o = P.take<char>(zgemm_oz_workspace(nprob, d));
     int rc = nao_ws_reserve(ctx, P.off);

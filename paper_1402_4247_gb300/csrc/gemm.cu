@@ -40,7 +40,7 @@ gemm_kernel(GemmDims dims, T alpha, GemmOperand A, GemmOperand B, T beta, T* __r
   const int p = blockIdx.z;
   const int M = dims.Mp ? dims.Mp[p] : dims.M;
   const int Nn = dims.Np ? dims.Np[p] : dims.N;
-  const int K = dims.Kp ? dims.Kp[p] : dims.K;
+  const int K = gemm_k(dims, p);
   const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
   if (i0 >= M || j0 >= Nn) return;
   if (dims.lower && j0 > i0 + BM - 1) return;  // tile entirely above the diagonal

@@ -154,7 +154,15 @@ struct GemmDims {
   int M, N, K;                          // maxima (grid sizing) / fixed values
   const int32_t *Mp, *Np, *Kp;          // per-problem overrides (nullable)
   int lower = 0;                        // 1: only output tiles that meet the lower triangle
+  int k0 = 0;                           // contraction chunk start: with Kp, problem p's length
+                                        // is min(max(Kp[p] - k0, 0), K)
 };
+// per-problem contraction length of a (possibly chunked) product
+__host__ __device__ inline int gemm_k(const GemmDims& d, int p) {
+  if (!d.Kp) return d.K;
+  const int k = d.Kp[p] - d.k0;
+  return k < 0 ? 0 : (k > d.K ? d.K : k);
+}
 cudaError_t launch_zgemm(int nprob, GemmDims dims, z64 alpha, GemmOperand A, GemmOperand B, z64 beta,
                          z64* C, long long Cbs, long long Crs, long long Ccs, cudaStream_t st);
 cudaError_t launch_dgemm(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta,
@@ -168,7 +176,8 @@ cudaError_t launch_ns_correct(int n, int nprob, const int32_t* size, const doubl
                               long long stride, double* Z2, cudaStream_t st);
 
 // FP64-accurate complex GEMM on the BF16 tensor cores (digit-plane splitting): C = alpha
-// op(A) op(B) + beta C with real alpha, beta.  Requires 2K <= 1792.  ws: zgemm_oz_workspace
+// op(A) op(B) + beta C with real alpha, beta.  Contractions longer than 896 (1792 real) run
+// as chunks whose FP32 group sums stay exact, accumulated in FP64.  ws: zgemm_oz_workspace
 // bytes; err: device int set to 1 if a bounded wait expired.  digits: NAO_OZ_DIGITS_FP64
 // (ten base-64 planes, FP64 accuracy) or NAO_OZ_DIGITS_MIXED (five planes: 30 bits, a little
 // above an FP32 or three-term BF16 split product; 15 tensor-core products instead of 55).

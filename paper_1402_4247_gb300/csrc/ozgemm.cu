@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(256) oz_split(int nprob, GemmDims dims, GemmOp
   const int kh = (lane >> 3) & 1;
   const int row = blockIdx.x * 16 + lr;
   const int R = IS_B ? (dims.Np ? dims.Np[p] : dims.N) : (dims.Mp ? dims.Mp[p] : dims.M);
-  const int K = dims.Kp ? dims.Kp[p] : dims.K;
+  const int K = gemm_k(dims, p);
   const int rows_live = (IS_B && !REAL) ? 2 * R : R;
   const bool live = row < rows_live;
   const int x = (IS_B && !REAL) ? row >> 1 : row;  // row (A) or column (B) of op(X)
@@ -266,7 +266,7 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
   unsigned char* stage0 = (unsigned char*)(((uintptr_t)oz_smem + 1023) & ~(uintptr_t)1023);
   const int nks = K2p / OZ_BK;  // plane layout (all problems)
   // this problem's digit planes are zero beyond column 2 K_p (K_p when real): stop the K loop there
-  const int Kprob = dims.Kp ? dims.Kp[p] : dims.K;
+  const int Kprob = gemm_k(dims, p);
   const int nks_p = max(1, min(nks, ((REAL ? 1 : 2) * Kprob + OZ_BK - 1) / OZ_BK));
   const size_t aplane = (size_t)(Mp / OZ_BM) * nks * (OZ_TILE_A / 2);
   const size_t bplane = (size_t)(N2p / OZ_BN) * nks * (OZ_TILE_B / 2);
@@ -468,12 +468,43 @@ cudaError_t launch_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, Gem
   return cudaGetLastError();
 }
 
+// Longest contraction of one exact chunk: 2K' <= OZ_MAX_K2 (complex) or K' <= OZ_MAX_K2 (real).
+constexpr int OZ_CHUNK_C = OZ_MAX_K2 / 2, OZ_CHUNK_R = OZ_MAX_K2;
+
+// Products longer than one chunk: C = alpha sum_c op(A)(:, c) op(B)(c, :) + beta C, every
+// chunk FP64-accurate, the sum accumulated in FP64 through beta = 1.
+template <bool REAL>
+cudaError_t launch_oz_chunked(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta,
+                              void* C, long long Cbs, long long Crs, long long Ccs, void* ws, int* err,
+                              cudaStream_t st, int digits) {
+  const int chunk = REAL ? OZ_CHUNK_R : OZ_CHUNK_C;
+  const size_t esz = REAL ? sizeof(double) : sizeof(z64);
+  for (int k0 = 0; k0 < dims.K || k0 == 0; k0 += chunk) {
+    GemmDims d = dims;
+    d.K = dims.K - k0 < chunk ? dims.K - k0 : chunk;
+    d.k0 = dims.k0 + k0;
+    GemmOperand a = A, b = B;
+    a.ptr = (const char*)A.ptr + (long long)k0 * A.cs * (long long)esz;  // op(A)(i, k) at i rs + k cs
+    b.ptr = (const char*)B.ptr + (long long)k0 * B.rs * (long long)esz;  // op(B)(k, j) at k rs + j cs
+    const double bt = k0 == 0 ? beta : 1.0;
+    cudaError_t e;
+    if (digits == NAO_OZ_DIGITS_MIXED)
+      e = launch_oz<REAL, NAO_OZ_DIGITS_MIXED>(nprob, d, alpha, a, b, bt, C, Cbs, Crs, Ccs, ws, err, st);
+    else
+      e = launch_oz<REAL, OZ_S>(nprob, d, alpha, a, b, bt, C, Cbs, Crs, Ccs, ws, err, st);
+    if (e != cudaSuccess) return e;
+    if (dims.K <= chunk) break;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace
 
-bool zgemm_oz_supported(GemmDims dims) { return 2 * (long long)dims.K <= OZ_MAX_K2 && dims.M > 0 && dims.N > 0; }
+bool zgemm_oz_supported(GemmDims dims) { return dims.M > 0 && dims.N > 0 && dims.K > 0; }
 
 size_t zgemm_oz_workspace(int nprob, GemmDims dims) {
-  const int Mp = round_up(dims.M, OZ_BM), N2p = round_up(2 * dims.N, OZ_BN), K2p = round_up(2 * dims.K, OZ_BK);
+  const int Kc = dims.K < OZ_CHUNK_C ? dims.K : OZ_CHUNK_C;
+  const int Mp = round_up(dims.M, OZ_BM), N2p = round_up(2 * dims.N, OZ_BN), K2p = round_up(2 * Kc, OZ_BK);
   const size_t a = (size_t)nprob * OZ_S * Mp * K2p * 2, b = (size_t)nprob * OZ_S * N2p * K2p * 2;
   return a + b + (size_t)nprob * (Mp + N2p) * sizeof(int) + 4096;
 }
@@ -481,17 +512,13 @@ size_t zgemm_oz_workspace(int nprob, GemmDims dims) {
 cudaError_t launch_zgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta, z64* C,
                             long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st,
                             int digits) {
-  if (digits == NAO_OZ_DIGITS_MIXED)
-    return launch_oz<false, NAO_OZ_DIGITS_MIXED>(nprob, dims, alpha, A, B, beta, (void*)C, Cbs, Crs, Ccs, ws, err, st);
-  return launch_oz<false, OZ_S>(nprob, dims, alpha, A, B, beta, (void*)C, Cbs, Crs, Ccs, ws, err, st);
+  return launch_oz_chunked<false>(nprob, dims, alpha, A, B, beta, (void*)C, Cbs, Crs, Ccs, ws, err, st, digits);
 }
 
-bool dgemm_oz_supported(GemmDims dims) { return (long long)dims.K <= OZ_MAX_K2 && dims.M > 0 && dims.N > 0; }
+bool dgemm_oz_supported(GemmDims dims) { return dims.M > 0 && dims.N > 0 && dims.K > 0; }
 
 cudaError_t launch_dgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta, double* C,
                             long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st,
                             int digits) {
-  if (digits == NAO_OZ_DIGITS_MIXED)
-    return launch_oz<true, NAO_OZ_DIGITS_MIXED>(nprob, dims, alpha, A, B, beta, (void*)C, Cbs, Crs, Ccs, ws, err, st);
-  return launch_oz<true, OZ_S>(nprob, dims, alpha, A, B, beta, (void*)C, Cbs, Crs, Ccs, ws, err, st);
+  return launch_oz_chunked<true>(nprob, dims, alpha, A, B, beta, (void*)C, Cbs, Crs, Ccs, ws, err, st, digits);
 }

@@ -24,6 +24,10 @@
 //   against the earlier members of a TIGHT cluster (gap < 1e-7 |T|_1), whose leader walks the
 //   cluster in order.  Wider near-degeneracies leave overlaps of order eps|T|/gap <= ~1e-9,
 //   which the caller removes with one Newton-Schulz step Z <- Z (3I - Z^T Z)/2.
+//   A tight cluster of more than BIG members (the near-null spectrum of an ill-conditioned
+//   overlap matrix can chain hundreds) is handed to kernel 3: one block per cluster, the
+//   same iteration with the reorthogonalisation done by the whole block (classical
+//   Gram-Schmidt applied twice) while one thread runs the tridiagonal solves.
 // * Output: eigenvalues ascending (across blocks), eigenvectors in matching columns,
 //   unit 2-norm, largest component positive.  All loops are bounded.
 #include <cfloat>
@@ -37,6 +41,7 @@ constexpr int MAXITS = 5;         // inverse-iteration solves before giving up
 constexpr int EXTRA = 2;          // extra solves after the growth test passes
 constexpr double TIGHT = 1e-7;
 constexpr int NARR = 6;           // scratch arrays per eigenvalue: L, U0inv, U1, U2, PIV, X
+constexpr int BIG = 32;           // tight clusters with more members go to stein_cluster_kernel
 
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
@@ -294,7 +299,7 @@ __global__ void __launch_bounds__(ST_THREADS)
 stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ dbase, const double* __restrict__ ebase,
                  long long strideV, const double* __restrict__ wslot, double* __restrict__ wbase,
                  double* __restrict__ Zbase, int ldz, long long strideZ, double* __restrict__ scratch,
-                 int32_t* __restrict__ status) {
+                 int32_t* __restrict__ status, int* __restrict__ biglist, int bigcap) {
   extern __shared__ double smd[];
   double* d = smd;
   double* e = smd + n;
@@ -334,9 +339,19 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
   if (j < m) {
     const int b0 = bst[j], b1 = ben[j];
     const bool leader = !(j > b0 && w[j] - w[j - 1] < tight);
-    if (leader) {
-      int jend = j + 1;
+    int jend = j + 1;
+    if (leader)
       while (jend < b1 && w[jend] - w[jend - 1] < tight) ++jend;
+    if (leader && jend - j > BIG) {  // hand the cluster to kernel 3
+      const int slot = atomicAdd(&biglist[0], 1);
+      if (slot < bigcap) {
+        biglist[1 + 3 * slot] = p;
+        biglist[2 + 3 * slot] = j;
+        biglist[3 + 3 * slot] = jend;
+      } else {
+        s_fail = 1;
+      }
+    } else if (leader) {
       const int bs = b1 - b0;
       double* Lr = scr + 0 * nn;
       double* U0i = scr + 1 * nn;
@@ -480,9 +495,237 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
   if (threadIdx.x == 0 && s_fail && status) atomicExch(&status[p], NAO_E_NOCONV);
 }
 
+// ---------------------------------------------------------------- kernel 3: big tight clusters
+// One block per cluster listed by kernel 2: members in ascending order; thread 0 factors
+// T - lambda I and runs the solves (as kernel 2), the block re-orthogonalises each iterate
+// against the earlier members (classical Gram-Schmidt, twice) and takes the norms.
+__device__ __forceinline__ double block_sum1(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int k = 0; k < nw; ++k) r += red[k];
+  return r;
+}
+
+__device__ __forceinline__ double block_max1(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int k = 0; k < nw; ++k) r = fmax(r, red[k]);
+  return r;
+}
+
+constexpr int SC_THREADS = 256;
+
+__global__ void __launch_bounds__(SC_THREADS)
+stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ dbase,
+                     const double* __restrict__ ebase, long long strideV, const double* __restrict__ wslot,
+                     double* __restrict__ Zbase, int ldz, long long strideZ, double* __restrict__ scratch,
+                     int32_t* __restrict__ status, const int* __restrict__ biglist, int bigcap) {
+  extern __shared__ double smc[];
+  double* d = smc;
+  double* e = smc + n;
+  double* e2 = smc + 2 * n;
+  double* w = smc + 3 * n;
+  double* sx = smc + 4 * n;
+  double* dots = e2;  // e^2 is not needed after the load: it holds the Gram-Schmidt coefficients
+  int* bst = (int*)(smc + 5 * n);
+  int* ben = bst + n;
+  int* rnk = ben + n;
+  __shared__ double red[96];
+  __shared__ int s_go, s_ok;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int count = min(biglist[0], bigcap);
+  for (int ent = blockIdx.x; ent < count; ent += gridDim.x) {
+    const int p = biglist[1 + 3 * ent], j = biglist[2 + 3 * ent], jend = biglist[3 + 3 * ent];
+    const int m = size ? size[p] : n;
+    __syncthreads();
+    const TriInfo T = load_tridiag(m, dbase + (size_t)p * strideV, ebase + (size_t)p * strideV, d, e, e2, bst, ben, red);
+    const double* ws = wslot + (size_t)p * n;
+    for (int i = tid; i < m; i += nt) w[i] = ws[i];
+    __syncthreads();
+    for (int q = j + tid; q < jend; q += nt) {  // ranks of the members (global ascending order)
+      const double wq = w[q];
+      int r = 0;
+      for (int t = 0; t < m; ++t) r += (w[t] < wq) || (w[t] == wq && t < q);
+      rnk[q - j] = r;
+    }
+    __syncthreads();
+    double* Z = Zbase + (size_t)p * strideZ;
+    double* scr = scratch + (size_t)p * NARR * n * n;
+    const double eps = DBL_EPSILON * 0.5;
+    const double pivtol = eps * T.tnorm;
+    const size_t nn = (size_t)n * n;
+    const int b0 = bst[j], b1 = ben[j], bs = b1 - b0;
+    double* Lr = scr + 0 * nn;
+    double* U0i = scr + 1 * nn;
+    double* U1 = scr + 2 * nn;
+    double* U2 = scr + 3 * nn;
+    double* PV = scr + 4 * nn;
+    double lamprev = 0.0, ulast = 0.0;
+    bool fail = false;
+    for (int q = j; q < jend; ++q) {
+      const int sl = q;
+#define AT(arr, i) arr[(size_t)(i) * n + sl]
+      if (tid == 0) {  // LU with partial pivoting of T[b0:b1) - lam I (as kernel 2)
+        double lam = w[q];
+        if (q > j) {
+          const double pertol = 10.0 * fabs(eps * lam);
+          if (lam - lamprev < pertol) lam = lamprev + pertol;
+        }
+        lamprev = lam;
+        double al = d[b0] - lam, be = e[b0];
+        for (int k = b0; k < b1 - 1; ++k) {
+          const double c = e[k];
+          const double an = d[k + 1] - lam;
+          const double bn = (k + 1 < b1 - 1) ? e[k + 1] : 0.0;
+          double u0, u1, u2, l, piv, al2, be2;
+          if (fabs(al) >= fabs(c)) {
+            piv = 0.0;
+            u0 = al;
+            u1 = be;
+            u2 = 0.0;
+            l = (al != 0.0) ? c / al : 0.0;
+            al2 = an - l * be;
+            be2 = bn;
+          } else {
+            piv = 1.0;
+            u0 = c;
+            u1 = an;
+            u2 = bn;
+            l = al / c;
+            al2 = be - l * an;
+            be2 = -l * bn;
+          }
+          if (fabs(u0) < pivtol) u0 = copysign(pivtol, u0);
+          AT(U0i, k) = 1.0 / u0;
+          AT(U1, k) = u1;
+          AT(U2, k) = u2;
+          AT(Lr, k) = l;
+          AT(PV, k) = piv;
+          al = al2;
+          be = be2;
+        }
+        if (fabs(al) < pivtol) al = copysign(pivtol, al);
+        ulast = al;
+        AT(U0i, b1 - 1) = 1.0 / al;
+      }
+      for (int i = b0 + tid; i < b1; i += nt)
+        sx[i] = hash_uniform(((unsigned long long)p << 40) ^ ((unsigned long long)q << 20) ^ (unsigned long long)i);
+      __syncthreads();
+      int its = 0, nrmchk = 0;
+      bool ok = false;
+      while (its < MAXITS + EXTRA) {
+        ++its;
+        double a1 = 0.0;
+        for (int i = b0 + tid; i < b1; i += nt) a1 += fabs(sx[i]);
+        const double x1 = block_sum1(a1, red);
+        if (tid == 0) {  // scaled right-hand side, forward and back substitution
+          const double scl = (double)bs * T.onenrm * fmax(eps, fabs(ulast)) / fmax(x1, DBL_MIN);
+          double r = sx[b0] * scl;
+          for (int k = b0; k < b1 - 1; ++k) {
+            const double xn = sx[k + 1] * scl;
+            const double l = AT(Lr, k);
+            if (AT(PV, k) == 0.0) {
+              sx[k] = r;
+              r = xn - l * r;
+            } else {
+              sx[k] = xn;
+              r = r - l * xn;
+            }
+          }
+          double x2 = 0.0, x1v = r * AT(U0i, b1 - 1);
+          sx[b1 - 1] = x1v;
+          for (int k = b1 - 2; k >= b0; --k) {
+            const double xv = (sx[k] - AT(U1, k) * x1v - AT(U2, k) * x2) * AT(U0i, k);
+            sx[k] = xv;
+            x2 = x1v;
+            x1v = xv;
+          }
+        }
+        __syncthreads();
+        const int np = q - j;  // earlier members
+        for (int pass = 0; pass < 2 && np > 0; ++pass) {
+          for (int t = wid; t < np; t += nw) {
+            const double* zt = Z + (size_t)rnk[t] * ldz;
+            double dt = 0.0;
+            for (int i = b0 + lane; i < b1; i += 32) dt = fma(sx[i], zt[i], dt);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dt += __shfl_xor_sync(0xffffffffu, dt, o);
+            if (lane == 0) dots[t] = dt;
+          }
+          __syncthreads();
+          for (int i = b0 + tid; i < b1; i += nt) {
+            double v = sx[i];
+            for (int t = 0; t < np; ++t) v = fma(-dots[t], Z[(size_t)rnk[t] * ldz + i], v);
+            sx[i] = v;
+          }
+          __syncthreads();
+        }
+        double am = 0.0;
+        bool fin = true;
+        for (int i = b0 + tid; i < b1; i += nt) {
+          const double a = fabs(sx[i]);
+          fin = fin && (a <= DBL_MAX);
+          am = fmax(am, a);
+        }
+        const double xinf = block_max1(fin ? am : INFINITY, red);
+        if (!(xinf <= DBL_MAX)) break;
+        if (its > MAXITS && nrmchk == 0) break;
+        if (xinf < sqrt(0.1 / bs)) continue;
+        ++nrmchk;
+        if (nrmchk < EXTRA + 1) continue;
+        ok = true;
+        break;
+      }
+      if (!ok) fail = true;
+      // normalise, sign: largest component positive (first of equal magnitude)
+      double a2 = 0.0, big = 0.0;
+      int jm = b1;
+      for (int i = b0 + tid; i < b1; i += nt) {
+        const double a = sx[i];
+        a2 = fma(a, a, a2);
+        if (fabs(a) > big) {
+          big = fabs(a);
+          jm = i;
+        }
+      }
+      const double nrm2 = block_sum1(a2, red);
+      const double bigmax = block_max1(big, red);
+      if (tid == 0) s_go = b1;
+      __syncthreads();
+      if (big == bigmax && bigmax > 0.0) atomicMin(&s_go, jm);
+      __syncthreads();
+      double sc = (nrm2 > 0.0 && nrm2 <= DBL_MAX) ? 1.0 / sqrt(nrm2) : 0.0;
+      if (s_go < b1 && sx[s_go] < 0.0) sc = -sc;
+      double* zc = Z + (size_t)rnk[q - j] * ldz;
+      for (int i = tid; i < m; i += nt) zc[i] = (i >= b0 && i < b1) ? sx[i] * sc : 0.0;
+      if (sc == 0.0 && tid == 0) zc[b0 + (q - b0) % bs] = 1.0;
+      __syncthreads();
+#undef AT
+    }
+    if (tid == 0) s_ok = fail ? 0 : 1;
+    __syncthreads();
+    if (tid == 0 && !s_ok && status) atomicExch(&status[p], NAO_E_NOCONV);
+  }
+}
+
 }  // namespace
 
-size_t stein_scratch_doubles(int n, int nprob) { return (size_t)NARR * n * n * nprob + (size_t)n * nprob; }
+// scratch: NARR n^2 doubles per problem, the eigenvalue slots (n per problem), and the
+// big-cluster list (count + 3 ints per cluster, at most n / (BIG + 1) clusters per problem)
+static int big_capacity(int n, int nprob) { return nprob * (n / (BIG + 1) + 1); }
+
+size_t stein_scratch_doubles(int n, int nprob) {
+  return (size_t)NARR * n * n * nprob + (size_t)n * nprob + (3 * (size_t)big_capacity(n, nprob) + 2) / 2 + 1;
+}
 
 cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d, const double* e, long long strideV,
                          double* w, double* Z, int ld, long long strideZ, double* scratch, int32_t* status,
@@ -495,9 +738,25 @@ cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d,
   stebz_kernel<<<grid, ST_THREADS, smem1, st>>>(n, size, d, e, strideV, wslot, status);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
+  int* biglist = (int*)(wslot + (size_t)n * nprob);
+  const int bigcap = big_capacity(n, nprob);
+  err = cudaMemsetAsync(biglist, 0, sizeof(int), st);
+  if (err != cudaSuccess) return err;
   const size_t smem2 = sizeof(double) * 4 * (size_t)n + sizeof(int) * 2 * (size_t)n;
   err = cudaFuncSetAttribute(stein_vec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
   if (err != cudaSuccess) return err;
-  stein_vec_kernel<<<grid, ST_THREADS, smem2, st>>>(n, size, d, e, strideV, wslot, w, Z, ld, strideZ, scratch, status);
+  stein_vec_kernel<<<grid, ST_THREADS, smem2, st>>>(n, size, d, e, strideV, wslot, w, Z, ld, strideZ, scratch, status,
+                                                    biglist, bigcap);
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  // kernel 3: a grid that stays resident; blocks without a listed cluster exit at once
+  const size_t smem3 = sizeof(double) * 5 * (size_t)n + sizeof(int) * 3 * (size_t)n;
+  err = cudaFuncSetAttribute(stein_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3);
+  if (err != cudaSuccess) return err;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  stein_cluster_kernel<<<sms, SC_THREADS, smem3, st>>>(n, size, d, e, strideV, wslot, Z, ld, strideZ, scratch, status,
+                                                       biglist, bigcap);
   return cudaGetLastError();
 }

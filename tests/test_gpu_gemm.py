@@ -80,12 +80,20 @@ def test_tc_exact_on_integers(ctx):
         assert np.array_equal(_run(ctx, A, B, 0, 0, method), ref)
 
 
-def test_tc_rejects_long_k(ctx):
-    from paper_1402_4247_gb300.nao import NaoError
-    A = torch.zeros((1, 4, 897), dtype=torch.complex128, device=DEV)
-    B = torch.zeros((1, 897, 4), dtype=torch.complex128, device=DEV)
-    with pytest.raises(NaoError):
-        ctx.nao_zgemm(A, B, method=1)
+@pytest.mark.parametrize("K", [897, 2000])
+def test_tc_long_k_in_chunks(ctx, K):
+    """Contractions past one exact chunk (896) run as several, summed in FP64: as accurate as
+    the FP64 product against extended precision, and within the FP64 error bound."""
+    rng = np.random.Generator(np.random.PCG64(K))
+    A = rng.normal(size=(2, 70, K)) + 1j * rng.normal(size=(2, 70, K))
+    B = rng.normal(size=(2, K, 50)) + 1j * rng.normal(size=(2, K, 50))
+    A[:, :, :5] *= 1e-7
+    ref = np.matmul(A.astype(np.clongdouble), B.astype(np.clongdouble))
+    got = _run(ctx, A, B, 0, 0, 1)
+    e_fp64 = np.linalg.norm((_run(ctx, A, B, 0, 0, 0) - ref).astype(np.complex128))
+    e_tc = np.linalg.norm((got - ref).astype(np.complex128))
+    assert e_tc <= 2.0 * e_fp64 + 1e-300, (e_tc, e_fp64)
+    assert np.all(np.abs(got - ref.astype(np.complex128)) <= _bound(A, B, 0, 0))
 
 
 @pytest.mark.parametrize("M,N,K,tA", [(96, 64, 568, 2), (130, 50, 890, 0), (64, 130, 300, 1)])
