@@ -134,19 +134,22 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
  * Problem p = sigma * nk + q (spin-major), as produced by nao_gen_eig on H(k) from
  * nao_bloch_sum.  g = 2 when nspin = 1, else 1.  Fermi-Dirac occupations
  * f = 1 / (1 + exp((eps - mu)/kT)); mu solves g sum_p wk[q] sum_{j<m_p} f = n_electrons
- * (Sec. 3 Part 5); E_band = g sum_p wk[q] sum_j f eps.  Density matrix (Part 6):
+ * (Sec. 3 Part 5); E_band = g sum_p wk[q] sum_j f eps.  Charge and energy density
+ * matrices (Part 6):
  *   rhoR[sigma][r][i][j] = Re[ g sum_q wk[q] sum_{j'} f c_{i j'} conj(c_{j j'})
- *                              exp(-2 pi i kpts[q].R[r]) ].
+ *                              exp(-2 pi i kpts[q].R[r]) ],
+ *   edmR: the same with weights f eps instead of f.
  *   eps, C, m_kept as written by nao_gen_eig (C [nprob][n][nb]); bands j >= nb must be
  *     unoccupied (f <= 1e-16), else status NAO_E_INVALID is written.
  *   mu_out, eband_out  float64 [1] out (device);  f_out float64 [nprob][n] out or NULL
  *   rhoR   float64 [nspin][nR][n][n] out (device)
+ *   edmR   float64 [nspin][nR][n][n] out (device), or NULL to skip it
  *   status int32 [1] out (device): 0, NAO_E_RANGE or NAO_E_INVALID                    */
 int nao_density_matrix(nao_ctx* ctx, int n, int nspin, int nk, const double* wk,
                        const double* kpts, const double* eps, const nao_c128* C, int nb,
                        const int32_t* m_kept, double n_electrons, double kT, int nR,
                        const int32_t* R, double* mu_out, double* eband_out, double* f_out,
-                       double* rhoR, int32_t* status, void* stream);
+                       double* rhoR, double* edmR, int32_t* status, void* stream);
 
 /* Tracing ------------------------------------------------------------------------------ *
  * With profiling on, every stage of the calls above is bracketed by CUDA events recorded

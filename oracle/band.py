@@ -231,7 +231,8 @@ def band_step(HR, SR, R, kpts, wk, n_electrons: float, kT: float, s_cut: float =
               problems=None):
     """Sec. 3 Band_DFT_Col on real-space inputs HR [nspin][nR][n][n], SR [nR][n][n].
 
-    Problem p = sigma * nk + k.  Returns a dict with Hk, Sk, eps, C, m, mu, f, eband, rho.
+    Problem p = sigma * nk + k.  Returns a dict with Hk, Sk, eps, C, m, mu, f, eband, rho
+    and edm (the energy density matrix).
     ``problems`` restricts Parts 2-4 to a subset (then mu/f/rho are not computed)."""
     nspin = HR.shape[0]
     nk = kpts.shape[0]
@@ -253,5 +254,11 @@ def band_step(HR, SR, R, kpts, wk, n_electrons: float, kT: float, s_cut: float =
                        [wk[p % nk] for p in ps if p // nk == sg], [kpts[p % nk] for p in ps if p // nk == sg],
                        R, g)
         for sg in range(nspin)])
-    out.update(mu=mu, f={p: f[i] for i, p in enumerate(ps)}, eband=eband, rho=rho, g=g)
+    # Part 6's second output, the energy density matrix: the same sum with weights f eps
+    edm = np.stack([
+        density_matrix([C[p] for p in ps if p // nk == sg], [f[p] * eps[p] for p in ps if p // nk == sg],
+                       [wk[p % nk] for p in ps if p // nk == sg], [kpts[p % nk] for p in ps if p // nk == sg],
+                       R, g)
+        for sg in range(nspin)])
+    out.update(mu=mu, f={p: f[i] for i, p in enumerate(ps)}, eband=eband, rho=rho, edm=edm, g=g)
     return out

@@ -216,11 +216,11 @@ GenEigPlan plan_gen_eig(int n, int nprob, int nSe, bool use_tc) {
 
 // Workspace layout of nao_density_matrix.
 struct DensityPlan {
-  size_t of, onocc, oscr, ost, oCs, oP, oOz;
+  size_t of, onocc, oscr, ost, oCs, oCe, oP, oOz;
   size_t bytes;
 };
 
-DensityPlan plan_density(int n, int nprob, int nb, int num_sms, bool use_tc) {
+DensityPlan plan_density(int n, int nprob, int nb, int num_sms, bool use_tc, bool edm) {
   DensityPlan W;
   WsPlan P;
   W.of = P.take<double>((size_t)nprob * n);
@@ -228,6 +228,7 @@ DensityPlan plan_density(int n, int nprob, int nb, int num_sms, bool use_tc) {
   W.oscr = P.take<double>(fermi_scratch_doubles(num_sms));
   W.ost = P.take<int32_t>(1);
   W.oCs = P.take<z64>((size_t)nprob * n * nb);
+  W.oCe = P.take<z64>(edm ? (size_t)nprob * n * nb : 1);
   W.oP = P.take<z64>((size_t)n * n * nprob);
   W.oOz = P.take<char>(use_tc ? zgemm_oz_workspace(nprob, GemmDims{n, n, nb, nullptr, nullptr, nullptr, 0}) : 1);
   W.bytes = P.off;
@@ -330,7 +331,7 @@ size_t gen_eig_ws_bytes(const nao_ctx* ctx, int n, int nprob, int nSe) {
 size_t density_ws_bytes(const nao_ctx* ctx, int n, int nprob, int nb) {
   const bool use_tc =
       ctx->gemm_method == NAO_GEMM_TC && zgemm_oz_supported(GemmDims{n, n, nb, nullptr, nullptr, nullptr, 0});
-  return plan_density(n, nprob, nb, ctx->num_sms, use_tc).bytes;
+  return plan_density(n, nprob, nb, ctx->num_sms, use_tc, false).bytes;
 }
 
 extern "C" {
@@ -625,7 +626,7 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
 int nao_density_matrix(nao_ctx* ctx, int n, int nspin, int nk, const double* wk, const double* kpts,
                        const double* eps, const nao_c128* C, int nb, const int32_t* m_kept, double n_electrons,
                        double kT, int nR, const int32_t* R, double* mu_out, double* eband_out, double* f_out,
-                       double* rhoR, int32_t* status, void* stream) {
+                       double* rhoR, double* edmR, int32_t* status, void* stream) {
   if (!ctx) return nao_fail(nullptr, NAO_E_INVALID, "nao_density_matrix: ctx is NULL");
   if (n < 1 || nk < 1 || nR < 1 || nb < 1 || nb > n || (nspin != 1 && nspin != 2))
     return nao_fail(ctx, NAO_E_INVALID, "nao_density_matrix: bad sizes");
@@ -640,7 +641,7 @@ int nao_density_matrix(nao_ctx* ctx, int n, int nspin, int nk, const double* wk,
   const double gdeg = (nspin == 1) ? 2.0 : 1.0;
   const GemmDims dP{n, n, nb, nullptr, nullptr, nullptr, 0};
   const bool use_tc = ctx->gemm_method == NAO_GEMM_TC && zgemm_oz_supported(dP);
-  const DensityPlan W = plan_density(n, nprob, nb, ctx->num_sms, use_tc);
+  const DensityPlan W = plan_density(n, nprob, nb, ctx->num_sms, use_tc, edmR != nullptr);
   const size_t of = W.of, onocc = W.onocc, oscr = W.oscr, ost = W.ost, oCs = W.oCs, oP = W.oP, oOz = W.oOz;
   int rc = nao_ws_reserve(ctx, W.bytes);
   if (rc) return rc;
@@ -662,6 +663,15 @@ int nao_density_matrix(nao_ctx* ctx, int n, int nspin, int nk, const double* wk,
                                 use_tc ? (void*)(ws + oOz) : nullptr, st));
   }
   NAO_STAGE("rho_phase", 1, launch_rho_phase_sum(n, nspin, nk, nR, R, kpts, wk, gdeg, Pk, rhoR, st));
+  if (edmR) {  // Part 6's energy density matrix: P_E(k) = Cs diag(eps) Cs^H, the same phase sum
+    z64* Ce = (z64*)(ws + W.oCe);
+    NAO_STAGE("misc", 1, launch_scale_cols_eps(n, nprob, nb, Cs, f, eps, Ce, st));
+    GemmDims d{n, n, nb, nullptr, nullptr, nocc};
+    NAO_CUDA_TRY(ctx, run_zgemm(ctx, "zgemm_P", nprob, d, 1.0, GemmOperand{Ce, (long long)n * nb, nb, 1, 0, nullptr},
+                                GemmOperand{Cs, (long long)n * nb, 1, nb, 1, nullptr}, 0.0, Pk, (long long)nn, n, 1,
+                                use_tc ? (void*)(ws + oOz) : nullptr, st));
+    NAO_STAGE("rho_phase", 1, launch_rho_phase_sum(n, nspin, nk, nR, R, kpts, wk, gdeg, Pk, edmR, st));
+  }
   return NAO_OK;
 }
 

@@ -66,6 +66,17 @@ __global__ void scale_cols_sqrt_kernel(int n, int nprob, int nb, const z64* __re
   Cs[idx] = zscale(C[idx], fj > 0.0 ? sqrt(fj) : 0.0);
 }
 
+// Ce = Cs diag(eps) over the occupied columns (eps is +inf where f = 0: those stay zero)
+__global__ void scale_cols_eps_kernel(int n, int nprob, int nb, const z64* __restrict__ Cs, const double* __restrict__ f,
+                                      const double* __restrict__ eps, z64* __restrict__ Ce) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * nb * nprob) return;
+  const int p = (int)(idx / ((size_t)n * nb));
+  const int j = (int)(idx % nb);
+  const double fj = f[(size_t)p * n + j];
+  Ce[idx] = fj > 0.0 ? zscale(Cs[idx], eps[(size_t)p * n + j]) : zmk(0.0, 0.0);
+}
+
 }  // namespace
 
 cudaError_t launch_count_kept(int n, int nprob, const double* w, long long strideV, double s_cut, int32_t* m,
@@ -90,6 +101,13 @@ cudaError_t launch_write_eps(int n, int nprob, const int32_t* m, const double* w
 cudaError_t launch_zero_cols(int n, int nprob, int nb, const int32_t* m, z64* C, cudaStream_t st) {
   const size_t tot = (size_t)n * nb * nprob;
   zero_cols_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, nprob, nb, m, C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_cols_eps(int n, int nprob, int nb, const z64* Cs, const double* f, const double* eps, z64* Ce,
+                                  cudaStream_t st) {
+  const size_t tot = (size_t)n * nb * nprob;
+  scale_cols_eps_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, nprob, nb, Cs, f, eps, Ce);
   return cudaGetLastError();
 }
 

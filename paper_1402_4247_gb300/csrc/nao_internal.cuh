@@ -227,8 +227,11 @@ cudaError_t launch_fermi(int num_sms, int n, int nprob, int nk, double g, const 
                          double* mu, double* eband, int32_t* status, double* scratch, cudaStream_t st);
 size_t fermi_scratch_doubles(int num_sms);
 
-// Part 6 helpers: Cs = C diag(sqrt f) and the inverse phase sum to rho(R).
+// Part 6 helpers: Cs = C diag(sqrt f), Ce = Cs diag(eps) (occupied columns), and the inverse
+// phase sum to rho(R).
 cudaError_t launch_scale_cols_sqrt(int n, int nprob, int nb, const z64* C, const double* f, z64* Cs,
                                    cudaStream_t st);
+cudaError_t launch_scale_cols_eps(int n, int nprob, int nb, const z64* Cs, const double* f, const double* eps, z64* Ce,
+                                  cudaStream_t st);
 cudaError_t launch_rho_phase_sum(int n, int nspin, int nk, int nR, const int32_t* R, const double* kpts,
                                  const double* wk, double g, const z64* P, double* rho, cudaStream_t st);

@@ -271,7 +271,7 @@ void NaoServerCore::launch(ServeSlot* slot, std::vector<ServeReq*> rs) {
                             (const nao_c128*)b->C.p + (size_t)r->prob_off * n * nb, nb,
                             (const int32_t*)b->m.p + r->prob_off, q.n_electrons, q.kT, q.nR,
                             (const int32_t*)r->dR.p, (double*)r->dmu.p, (double*)r->deb.p, (double*)r->df.p,
-                            (double*)r->drho.p, (int32_t*)r->drst.p, st);
+                            (double*)r->drho.p, nullptr, (int32_t*)r->drst.p, st);
   }
   const size_t ws_now = slot->sub->ws_bytes;
   bool enqueued = false;

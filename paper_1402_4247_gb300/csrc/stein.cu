@@ -295,7 +295,7 @@ stebz_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__
 }
 
 // ---------------------------------------------------------------- kernel 2: eigenvectors
-__global__ void __launch_bounds__(ST_THREADS)
+__global__ void __launch_bounds__(ST_THREADS, 5)  // 5 blocks per SM: 640 blocks (128 problems) in one wave
 stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ dbase, const double* __restrict__ ebase,
                  long long strideV, const double* __restrict__ wslot, double* __restrict__ wbase,
                  double* __restrict__ Zbase, int ldz, long long strideZ, double* __restrict__ scratch,

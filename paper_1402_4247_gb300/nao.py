@@ -93,7 +93,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.nao_gen_eig.argtypes = [vp, i32, i32, vp, vp, vp, i32, f64, i32, i32, vp, vp, vp, vp, vp]
     lib.nao_gen_eig.restype = i32
     lib.nao_density_matrix.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, i32, vp, f64, f64, i32, vp, vp, vp,
-                                       vp, vp, vp, vp]
+                                       vp, vp, vp, vp, vp]
     lib.nao_density_matrix.restype = i32
     lib.nao_profile_enable.argtypes = [vp, i32]
     lib.nao_profile_enable.restype = i32
@@ -319,8 +319,10 @@ class Context:
 
     # ------------------------------------------------------------------ Parts 5-6
     def nao_density_matrix(self, wk, kpts, eps, C, m_kept, n_electrons, kT, R, nspin, want_f=True, out=None,
-                           stream=None):
-        """-> (mu [1], eband [1], f [nprob][n] or None, rho [nspin][nR][n][n], status [1])."""
+                           stream=None, edm=None):
+        """-> (mu [1], eband [1], f [nprob][n] or None, rho [nspin][nR][n][n], status [1]).
+        ``edm``: a float64 [nspin][nR][n][n] device tensor that receives the energy density
+        matrix (Part 6's second output), or None."""
         nprob, n, nb = C.shape
         nk = wk.shape[0]
         nR = R.shape[0]
@@ -335,7 +337,7 @@ class Context:
             mu, eb, f, rho, st = out
         rc = self.lib.nao_density_matrix(self.handle, n, nspin, nk, _ptr(wk), _ptr(kpts), _ptr(eps), _ptr(C), nb,
                                          _ptr(m_kept), float(n_electrons), float(kT), nR, _ptr(R), _ptr(mu),
-                                         _ptr(eb), _ptr(f), _ptr(rho), _ptr(st), _stream(stream))
+                                         _ptr(eb), _ptr(f), _ptr(rho), _ptr(edm), _ptr(st), _stream(stream))
         self._check(rc, "nao_density_matrix")
         return mu, eb, f, rho, st
 

@@ -29,9 +29,10 @@ def gpu_band_step(ctx, inp, torch, dev, nb=None, s_cut=1e-10, density=True, prec
     eps, C, m, st = ctx.nao_gen_eig(Hk, Sk, s_of_prob=smap, s_cut=s_cut, nb=nb, precision=precision)
     out = dict(Hk=Hk, Sk=Sk, eps=eps, C=C, m=m, status=st)
     if density:
+        edm = torch.empty((inp.nspin, inp.nR, n, n), dtype=torch.float64, device=dev)
         mu, eb, f, rho, rst = ctx.nao_density_matrix(t["w"], t["k"], eps, C, m, inp.n_electrons, inp.kT, t["R"],
-                                                     inp.nspin)
-        out.update(mu=mu, eband=eb, f=f, rho=rho, rstatus=rst)
+                                                     inp.nspin, edm=edm)
+        out.update(mu=mu, eband=eb, f=f, rho=rho, edm=edm, rstatus=rst)
     torch.cuda.synchronize()
     return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in out.items()}
 

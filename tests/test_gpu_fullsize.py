@@ -50,6 +50,14 @@ def test_magnetite_full_step_sampled(ctx):
     assert abs(eb - g["eband"][0]) <= 1e-9 * max(1.0, abs(eb))
     ehr = sum(np.sum(rho[s] * inp.HR[s]) for s in range(inp.nspin))
     assert abs(ehr - eb) <= 1e-8 * max(1.0, abs(eb)), (ehr, eb)
+    # energy density matrix: sum E(R) S(R) = E_band, sum E(R) H(R) = g sum w f eps^2
+    edm = g["edm"]
+    es = sum(np.sum(edm[s] * inp.SR) for s in range(inp.nspin))
+    eh = sum(np.sum(edm[s] * inp.HR[s]) for s in range(inp.nspin))
+    m2 = gdeg * sum(inp.wk[p % inp.nk] * np.sum(g["f"][p] * np.where(fin[p], g["eps"][p], 0.0) ** 2)
+                    for p in range(inp.nprob))
+    assert abs(es - eb) <= 1e-8 * max(1.0, abs(eb)), (es, eb)
+    assert abs(eh - m2) <= 1e-8 * max(1.0, abs(m2)), (eh, m2)
 
 
 @pytest.mark.parametrize("ill", [False, True], ids=["n1000", "n1000-ill"])

@@ -88,6 +88,9 @@ def test_band_step_matches_oracle(ctx, maker):
     assert abs(g["eband"][0] - ref["eband"]) <= 1e-9 * max(1.0, abs(ref["eband"]))
     drho = np.abs(g["rho"] - ref["rho"]).max()
     assert drho <= TOL_RHO * max(1.0, np.abs(ref["rho"]).max()), f"rho differs by {drho:.3e}"
+    # Part 6's energy density matrix, elementwise with the same relative bound
+    dedm = np.abs(g["edm"] - ref["edm"]).max()
+    assert dedm <= TOL_RHO * max(1.0, np.abs(ref["edm"]).max()), f"energy density matrix differs by {dedm:.3e}"
 
 
 def test_nb_subset_and_zero_padding(ctx):

@@ -176,6 +176,14 @@ def test_invariants_tiny_cell():
     for p in range(inp.nprob):
         f = out["f"][p]
         assert np.all((f >= 0) & (f <= 1))
+    # energy density matrix (Part 6): sum E(R) S(R) = E_band and sum E(R) H(R) = g sum w f eps^2
+    # (c^H S c = 1 and c^H H c = eps for each eigenvector)
+    edm = out["edm"]
+    es = sum((edm[0, r] * inp.SR[r]).sum() for r in range(inp.nR))
+    eh = sum((edm[0, r] * inp.HR[0, r]).sum() for r in range(inp.nR))
+    m2 = 2.0 * sum(inp.wk[p] * np.sum(out["f"][p] * out["eps"][p] ** 2) for p in range(inp.nprob))
+    assert abs(es - out["eband"]) < 1e-9 * max(1.0, abs(out["eband"]))
+    assert abs(eh - m2) < 1e-9 * max(1.0, abs(m2))
 
 
 def test_two_spin_identities():
@@ -231,3 +239,8 @@ def test_density_matrix_plane_waves(N, k):
     for ir, Rv in enumerate(inp.R):
         want = (2.0 * P * np.exp(-2j * np.pi * k * Rv[0])).real
         assert np.abs(out["rho"][0, ir] - want).max() < 1e-12
+    # the energy density matrix: the same plane waves weighted by f_j eps_j
+    PE = ((fj * ej)[None, None, :] * np.exp(1j * t[None, None, :] * (a[:, None, None] - a[None, :, None]))).sum(-1) / N
+    for ir, Rv in enumerate(inp.R):
+        want = (2.0 * PE * np.exp(-2j * np.pi * k * Rv[0])).real
+        assert np.abs(out["edm"][0, ir] - want).max() < 1e-12
