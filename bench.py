@@ -423,6 +423,33 @@ def run_ours(args, rank, world, local_rank):
              "max_abs_deps_vs_fp64_Ha": float((eps_mx - eps)[fin].abs().max()),
              "status_ok": bool(int(st.abs().sum()) == 0 and int(rst[0]) == 0)}
 
+    # the paper's two-pass form: eigenvectors only for the bands the density matrix uses
+    # (the most occupied bands of any problem on the FP64 step, plus a margin of 8)
+    nb_sub = min(n, int((f > 1e-16).sum(1).max()) + 8)
+    C_sub = torch.empty((nprob, n, nb_sub), dtype=torch.complex128, device=dev)
+    eps_sub = torch.empty_like(eps)
+
+    def step_sub(src):
+        ctx.nao_bloch_sum(src["SR"], src["R"], src["k"], out=Sk)
+        ctx.nao_bloch_sum(src["HR"], src["R"], src["k"], out=Hk)
+        ctx.nao_gen_eig(Hk.view(nprob, n, n), Sk[0], s_of_prob=smap, nb=nb_sub, out=(eps_sub, C_sub, m, st))
+        ctx.nao_density_matrix(src["w"], src["k"], eps_sub, C_sub, m, inp.n_electrons, inp.kT, src["R"], nspin,
+                               out=(mu, eb, f, rho, rst))
+
+    step_sub(d_in)
+    barrier()
+    z0, z1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    z0.record(stream)
+    for _ in range(args.steps):
+        step_sub(d_in)
+    z1.record(stream)
+    barrier()
+    sub_ms = z0.elapsed_time(z1) / args.steps
+    subset = {"value": nprob * world / (sub_ms * 1e-3), "unit": UNIT, "ms_per_step": sub_ms, "nb": nb_sub,
+              "note": "eigenvectors of H' only for the lowest nb bands (most occupied bands of any problem + 8), "
+                      "eigenvalues all; the density-matrix status confirms no occupied band lies beyond nb",
+              "status_ok": bool(int(st.abs().sum()) == 0 and int(rst[0]) == 0)}
+
     serve = run_serve(local_rank) if (world == 1 and not args.no_serve) else None
 
     t_max = ms_total
@@ -468,7 +495,7 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roof, "stages": stages,
             "e2e": {"value": nprob * world / (e2e_max * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu, "mixed": mixed, "serve": serve,
+            "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu, "mixed": mixed, "subset": subset, "serve": serve,
             "status_ok": bool(int(st.abs().sum()) == 0 and int(rst[0]) == 0),
         }
         print(json.dumps(line), flush=True)

@@ -235,14 +235,15 @@ DensityPlan plan_density(int n, int nprob, int nb, int num_sms, bool use_tc, boo
   return W;
 }
 
-// Eigen_HH steps 3-4 in blocked form: U(:, c) = Q Z(:, m - nc + c) for c < nc (nc = ncols[p]),
+// Eigen_HH steps 3-4 in blocked form: U(:, c) = Q Z(:, m - nc + c) for c < nc (nc = ncols[p];
+// Z(:, c) when lowest),
 // normalised (times 1/sqrt(w) when use_rsqrt), with Q = prod_j (I - V_j T_j V_j^H) applied from
 // the last block of NAO_WY_NB reflectors to the first; every block costs three products
 // (W = V^H U, W = T W, U -= V W) plus its Gram matrix V^H V for T.
 cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, const int32_t* ncols, const z64* A,
                                   const z64* tau, const double* Z, const double* w, int use_rsqrt, z64* U, z64* Vf,
                                   z64* tauc, z64* G, z64* T, z64* W, z64* W2, void* ozws, cudaStream_t st,
-                                  int digits) {
+                                  int digits, int lowest) {
   const int nb = NAO_WY_NB;
   const int ncolv = (n + nb - 1) / nb * nb;
   const long long snn = (long long)n * n, svf = (long long)n * ncolv, snb2 = (long long)nb * nb,
@@ -251,7 +252,7 @@ cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t*
   {
     NaoStage stage_(ctx, "backtransform", st, 2);
     e = launch_extract_v(n, nprob, size, A, n, snn, tau, n, ncolv, Vf, n, svf, tauc, st);
-    if (e == cudaSuccess) e = launch_init_u(n, nprob, size, ncols, Z, n, snn, U, n, snn, st);
+    if (e == cudaSuccess) e = launch_init_u(n, nprob, size, ncols, Z, n, snn, U, n, snn, lowest, st);
     if (e != cudaSuccess) return e;
   }
   const int nblk = (n - 1 + nb - 1) / nb;
@@ -522,17 +523,17 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   // ---- Part 2: Eigen_HH(S) -> s, U;  X = U_m s_m^{-1/2}
   NAO_STAGE("herm_fill", 1, launch_herm_fill(n, nSe, (const z64*)S, snn, nullptr, AS, n, snn, st));
   NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nSe, nullptr, AS, dS, eS, tauS, VWp, ozws, st, NAO_OZ_DIGITS_FP64));
-  NAO_STAGE("stein", 1, launch_stein(n, nSe, nullptr, dS, eS, n, wS, Z, n, snn, scr, stS, st));
+  NAO_STAGE("stein", 1, launch_stein(n, nSe, nullptr, dS, eS, n, wS, Z, n, snn, scr, stS, nullptr, n, st));
   NAO_STAGE("misc", 1, launch_count_kept(n, nSe, wS, n, s_cut, mS, stS, st));
   {  // one Newton-Schulz step: Z2 = Z (3I - Z^T Z)/2 = Z - Z (Z^T Z - I)/2
     GemmDims d{n, n, n, nullptr, nullptr, nullptr, 1};
     NAO_CUDA_TRY(ctx, run_dgemm(ctx, "ortho_ns", nSe, d, 1.0, GemmOperand{Z, snn, n, 1, 0, nullptr},
                                 GemmOperand{Z, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, ozws, st));
     NaoStage stage_(ctx, "ortho_ns", st, 1);
-    NAO_CUDA_TRY(ctx, launch_ns_correct(n, nSe, nullptr, Z, G, n, snn, Z2, st));
+    NAO_CUDA_TRY(ctx, launch_ns_correct(n, nSe, nullptr, nullptr, Z, G, n, snn, Z2, st));
   }
   NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nSe, nullptr, mS, AS, tauS, Z2, wS, 1, X, Vf, tauc, Gw, Tw, Ww, W2w,
-                                          ozws, st, dig));
+                                          ozws, st, dig, 0));
   {
     NaoStage stage_(ctx, "misc", st, 1);
     gather_m_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(nprob, s_of_prob, mS, stS, nb, mP, nbP, stP);
@@ -553,16 +554,24 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
 
   // ---- Part 4: Eigen_HH(H') -> eps, V;  C = X V
   NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nprob, mP, Hp, dH, eH, tauH, VWp, ozws, st, dig));
-  NAO_STAGE("stein", 1, launch_stein(n, nprob, mP, dH, eH, n, wH, Z, n, snn, scr, stH, st));
-  {
-    GemmDims d{n, n, n, mP, mP, mP, 1};
-    NAO_CUDA_TRY(ctx, run_dgemm(ctx, "ortho_ns", nprob, d, 1.0, GemmOperand{Z, snn, n, 1, 0, nullptr},
-                                GemmOperand{Z, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, ozws, st));
-    NaoStage stage_(ctx, "ortho_ns", st, 1);
-    NAO_CUDA_TRY(ctx, launch_ns_correct(n, nprob, mP, Z, G, n, snn, Z2, st));
+  // Eigenvectors of H' only where they are used (the paper's second pass, dstevx's index
+  // range): the lowest nb per problem for C, all m for the mixed-mode refinement, none when
+  // the caller asks for eigenvalues only (C = NULL).
+  const bool all_vecs = mixed && ctx->refine_sweeps > 0;
+  const int32_t* nvP = all_vecs ? mP : nbP;
+  const int nv_max = (C || all_vecs) ? n : 0;
+  NAO_STAGE("stein", 1, launch_stein(n, nprob, mP, dH, eH, n, wH, Z, n, snn, scr, stH, nvP, nv_max, st));
+  if (nv_max > 0) {
+    {
+      GemmDims d{n, n, n, nvP, nvP, mP, 1};
+      NAO_CUDA_TRY(ctx, run_dgemm(ctx, "ortho_ns", nprob, d, 1.0, GemmOperand{Z, snn, n, 1, 0, nullptr},
+                                  GemmOperand{Z, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, ozws, st));
+      NaoStage stage_(ctx, "ortho_ns", st, 1);
+      NAO_CUDA_TRY(ctx, launch_ns_correct(n, nprob, mP, nvP, Z, G, n, snn, Z2, st));
+    }
+    NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nprob, mP, nvP, Hp, tauH, Z2, wH, 0, V, Vf, tauc, Gw, Tw, Ww, W2w,
+                                            ozws, st, dig, 1));
   }
-  NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nprob, mP, mP, Hp, tauH, Z2, wH, 0, V, Vf, tauc, Gw, Tw, Ww, W2w, ozws,
-                                          st, dig));
   if (mixed && ctx->refine_sweeps > 0) {
     // C^ = X V (all m columns, column-major in Hp), then Ritz refinement sweeps with
     // FP64-accurate products (csrc/refine.cu):  R' = C^H S C^, G = C^H H C^ -> I + F,

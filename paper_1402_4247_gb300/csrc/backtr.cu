@@ -144,10 +144,11 @@ __global__ void extract_v_kernel(int n, const int32_t* __restrict__ size, const 
   if (r == 0) taucbase[(size_t)p * ncolv + i] = (i < m - 1) ? taubase[(size_t)p * strideV + i] : zmk(0.0, 0.0);
 }
 
-// U(:, c) = Z(:, m - nc + c) as complex for c < nc, rows < m; zero elsewhere (n x n).
+// U(:, c) = Z(:, m - nc + c) (or Z(:, c) when lowest) as complex for c < nc, rows < m; zero
+// elsewhere (n x n).
 __global__ void init_u_kernel(int n, const int32_t* __restrict__ size, const int32_t* __restrict__ ncols,
                               const double* __restrict__ Zbase, int ldz, long long strideZ, z64* __restrict__ Ubase,
-                              int ldu, long long strideU) {
+                              int ldu, long long strideU, int lowest) {
   const int p = blockIdx.z;
   const int m = size ? size[p] : n;
   const int nc = ncols ? ncols[p] : m;
@@ -155,7 +156,7 @@ __global__ void init_u_kernel(int n, const int32_t* __restrict__ size, const int
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   double v = 0.0;
-  if (c < nc && r < m) v = Zbase[(size_t)p * strideZ + (size_t)(m - nc + c) * ldz + r];
+  if (c < nc && r < m) v = Zbase[(size_t)p * strideZ + (size_t)(lowest ? c : m - nc + c) * ldz + r];
   Ubase[(size_t)p * strideU + (size_t)c * ldu + r] = zmk(v, 0.0);
 }
 
@@ -212,9 +213,9 @@ cudaError_t launch_extract_v(int n, int nprob, const int32_t* size, const z64* A
 }
 
 cudaError_t launch_init_u(int n, int nprob, const int32_t* size, const int32_t* ncols, const double* Z, int ldz,
-                          long long strideZ, z64* U, int ldu, long long strideU, cudaStream_t st) {
+                          long long strideZ, z64* U, int ldu, long long strideU, int lowest, cudaStream_t st) {
   dim3 grid((n + 127) / 128, n, nprob);
-  init_u_kernel<<<grid, 128, 0, st>>>(n, size, ncols, Z, ldz, strideZ, U, ldu, strideU);
+  init_u_kernel<<<grid, 128, 0, st>>>(n, size, ncols, Z, ldz, strideZ, U, ldu, strideU, lowest);
   return cudaGetLastError();
 }
 

@@ -129,14 +129,16 @@ cudaError_t launch_gemm_t(int nprob, GemmDims dims, T alpha, GemmOperand A, Gemm
 // Z2 = Z - 0.5 Z (G - I), G symmetric from its lower triangle; FP32 product.
 constexpr int NB = 64, NK = 16;
 __global__ void __launch_bounds__(256)
-ns_correct_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ Zb, const double* __restrict__ Gb,
-                  int ld, long long stride, double* __restrict__ Z2b) {
+ns_correct_kernel(int n, const int32_t* __restrict__ size, const int32_t* __restrict__ ncols,
+                  const double* __restrict__ Zb, const double* __restrict__ Gb, int ld, long long stride,
+                  double* __restrict__ Z2b) {
   __shared__ float Zs[NK][NB + 1];
   __shared__ float Es[NK][NB + 1];
   const int p = blockIdx.z;
   const int m = size ? size[p] : n;
+  const int nc = ncols ? ncols[p] : m;  // columns of Z (and order of G)
   const int i0 = blockIdx.y * NB, j0 = blockIdx.x * NB;
-  if (i0 >= m || j0 >= m) return;
+  if (i0 >= m || j0 >= nc) return;
   const double* Z = Zb + (size_t)p * stride;
   const double* G = Gb + (size_t)p * stride;
   double* Z2 = Z2b + (size_t)p * stride;
@@ -146,17 +148,17 @@ ns_correct_kernel(int n, const int32_t* __restrict__ size, const double* __restr
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-  for (int k0 = 0; k0 < m; k0 += NK) {
+  for (int k0 = 0; k0 < nc; k0 += NK) {
 #pragma unroll
     for (int s = 0; s < (NB * NK) / 256; ++s) {
       const int e = tid + 256 * s;
       const int row = e % NB, kk = e / NB;  // Z(i0+row, k0+kk): column-major, rows fast
       const int gi = i0 + row, gk = k0 + kk;
-      Zs[kk][row] = (gi < m && gk < m) ? (float)Z[(size_t)gk * ld + gi] : 0.f;
+      Zs[kk][row] = (gi < m && gk < nc) ? (float)Z[(size_t)gk * ld + gi] : 0.f;
       const int col = e % NB, kk2 = e / NB;  // E(k0+kk2, j0+col)
       const int gj = j0 + col, gk2 = k0 + kk2;
       float ev = 0.f;
-      if (gj < m && gk2 < m) {
+      if (gj < nc && gk2 < nc) {
         double g = (gk2 >= gj) ? G[(size_t)gj * ld + gk2] : G[(size_t)gk2 * ld + gj];
         if (gk2 == gj) g -= 1.0;
         ev = (float)g;
@@ -185,7 +187,7 @@ ns_correct_kernel(int n, const int32_t* __restrict__ size, const double* __restr
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int gj = j0 + tx + 16 * b;
-      if (gj >= m) continue;
+      if (gj >= nc) continue;
       const size_t o = (size_t)gj * ld + gi;
       Z2[o] = Z[o] - 0.5 * (double)acc[a][b];
     }
@@ -194,10 +196,10 @@ ns_correct_kernel(int n, const int32_t* __restrict__ size, const double* __restr
 
 }  // namespace
 
-cudaError_t launch_ns_correct(int n, int nprob, const int32_t* size, const double* Z, const double* G, int ld,
-                              long long stride, double* Z2, cudaStream_t st) {
+cudaError_t launch_ns_correct(int n, int nprob, const int32_t* size, const int32_t* ncols, const double* Z,
+                              const double* G, int ld, long long stride, double* Z2, cudaStream_t st) {
   dim3 grid((n + NB - 1) / NB, (n + NB - 1) / NB, nprob);
-  ns_correct_kernel<<<grid, 256, 0, st>>>(n, size, Z, G, ld, stride, Z2);
+  ns_correct_kernel<<<grid, 256, 0, st>>>(n, size, ncols, Z, G, ld, stride, Z2);
   return cudaGetLastError();
 }
 

@@ -124,17 +124,20 @@ cudaError_t launch_hetrd_panel(int n, int nprob, const int32_t* size, z64* A, in
 // Eigen_HH step 2: eigenvalues w (ascending) and orthonormal eigenvectors Z (column-major,
 // ld) of tridiag(e, d, e) by bisection + inverse iteration.  scratch: see stein_scratch_doubles.
 size_t stein_scratch_doubles(int n, int nprob);
+// nvec (nullable: all) and nvec_max bound the eigenvectors computed per problem to the lowest
+// min(nvec[p], nvec_max); the eigenvalues are always all computed.
 cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d, const double* e,
                          long long strideV, double* w, double* Z, int ld, long long strideZ,
-                         double* scratch, int32_t* status, cudaStream_t st);
+                         double* scratch, int32_t* status, const int32_t* nvec, int nvec_max, cudaStream_t st);
 
 // Blocked (compact WY) back-transformation helpers, see backtr.cu.
 constexpr int NAO_WY_NB = 128;
 cudaError_t launch_extract_v(int n, int nprob, const int32_t* size, const z64* A, int lda, long long strideA,
                              const z64* tau, long long strideV, int ncolv, z64* V, int ldv, long long strideVf,
                              z64* tauc, cudaStream_t st);
+// init_u: column c of U takes Z's column m - nc + c (the top nc) or, when lowest, column c.
 cudaError_t launch_init_u(int n, int nprob, const int32_t* size, const int32_t* ncols, const double* Z, int ldz,
-                          long long strideZ, z64* U, int ldu, long long strideU, cudaStream_t st);
+                          long long strideZ, z64* U, int ldu, long long strideU, int lowest, cudaStream_t st);
 cudaError_t launch_build_t(int nb, int nprob, const z64* G, const z64* tauc, int ncolv, int j0, z64* T,
                            cudaStream_t st);
 cudaError_t launch_normalize_cols(int n, int nprob, const int32_t* size, const int32_t* ncols, const double* w,
@@ -172,8 +175,8 @@ cudaError_t launch_dgemm(int nprob, GemmDims dims, double alpha, GemmOperand A, 
 // = Z^T Z given by its lower triangle (column-major, ld).  E is ~1e-9, so the product runs
 // in FP32 on the FP32 pipe; its rounding (~1e-7 relative of a 1e-9 term) stays below FP64
 // rounding of Z.
-cudaError_t launch_ns_correct(int n, int nprob, const int32_t* size, const double* Z, const double* G, int ld,
-                              long long stride, double* Z2, cudaStream_t st);
+cudaError_t launch_ns_correct(int n, int nprob, const int32_t* size, const int32_t* ncols, const double* Z,
+                              const double* G, int ld, long long stride, double* Z2, cudaStream_t st);
 
 // FP64-accurate complex GEMM on the BF16 tensor cores (digit-plane splitting): C = alpha
 // op(A) op(B) + beta C with real alpha, beta.  Contractions longer than 896 (1792 real) run

@@ -299,7 +299,8 @@ __global__ void __launch_bounds__(ST_THREADS, 5)  // 5 blocks per SM: 640 blocks
 stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ dbase, const double* __restrict__ ebase,
                  long long strideV, const double* __restrict__ wslot, double* __restrict__ wbase,
                  double* __restrict__ Zbase, int ldz, long long strideZ, double* __restrict__ scratch,
-                 int32_t* __restrict__ status, int* __restrict__ biglist, int bigcap) {
+                 int32_t* __restrict__ status, int* __restrict__ biglist, int bigcap,
+                 const int32_t* __restrict__ nvec, int nvec_max) {
   extern __shared__ double smd[];
   double* d = smd;
   double* e = smd + n;
@@ -318,6 +319,7 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
   if (threadIdx.x == 0) s_fail = 0;
   __syncthreads();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nv = min(nvec ? nvec[p] : m, nvec_max);  // vectors of the lowest nv eigenvalues only
   double* wout = wbase + (size_t)p * strideV;
   double* Z = Zbase + (size_t)p * strideZ;
   double* scr = scratch + (size_t)p * NARR * n * n;
@@ -370,6 +372,7 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
           const double wt = w[t];
           rq += (wt < wq) || (wt == wq && t < q);
         }
+        if (rq >= nv) break;  // members ascend: the rest of the cluster is not wanted either
         double* zc = Z + (size_t)rq * ldz;
         if (bs == 1) {
           for (int i = 0; i < m; ++i) zc[i] = (i == b0) ? 1.0 : 0.0;
@@ -528,7 +531,8 @@ __global__ void __launch_bounds__(SC_THREADS)
 stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ dbase,
                      const double* __restrict__ ebase, long long strideV, const double* __restrict__ wslot,
                      double* __restrict__ Zbase, int ldz, long long strideZ, double* __restrict__ scratch,
-                     int32_t* __restrict__ status, const int* __restrict__ biglist, int bigcap) {
+                     int32_t* __restrict__ status, const int* __restrict__ biglist, int bigcap,
+                     const int32_t* __restrict__ nvec, int nvec_max) {
   extern __shared__ double smc[];
   double* d = smc;
   double* e = smc + n;
@@ -571,7 +575,9 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
     double* PV = scr + 4 * nn;
     double lamprev = 0.0, ulast = 0.0;
     bool fail = false;
+    const int nv = min(nvec ? nvec[p] : m, nvec_max);
     for (int q = j; q < jend; ++q) {
+      if (rnk[q - j] >= nv) break;  // uniform: ranks ascend with q
       const int sl = q;
 #define AT(arr, i) arr[(size_t)(i) * n + sl]
       if (tid == 0) {  // LU with partial pivoting of T[b0:b1) - lam I (as kernel 2)
@@ -729,7 +735,7 @@ size_t stein_scratch_doubles(int n, int nprob) {
 
 cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d, const double* e, long long strideV,
                          double* w, double* Z, int ld, long long strideZ, double* scratch, int32_t* status,
-                         cudaStream_t st) {
+                         const int32_t* nvec, int nvec_max, cudaStream_t st) {
   double* wslot = scratch + (size_t)NARR * n * n * nprob;
   const size_t smem1 = sizeof(double) * 3 * (size_t)n + sizeof(float) * 2 * (size_t)n + sizeof(int) * 2 * (size_t)n;
   cudaError_t err = cudaFuncSetAttribute(stebz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
@@ -746,7 +752,7 @@ cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d,
   err = cudaFuncSetAttribute(stein_vec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
   if (err != cudaSuccess) return err;
   stein_vec_kernel<<<grid, ST_THREADS, smem2, st>>>(n, size, d, e, strideV, wslot, w, Z, ld, strideZ, scratch, status,
-                                                    biglist, bigcap);
+                                                    biglist, bigcap, nvec, nvec_max);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   // kernel 3: a grid that stays resident; blocks without a listed cluster exit at once
@@ -757,6 +763,6 @@ cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d,
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   stein_cluster_kernel<<<sms, SC_THREADS, smem3, st>>>(n, size, d, e, strideV, wslot, Z, ld, strideZ, scratch, status,
-                                                       biglist, bigcap);
+                                                       biglist, bigcap, nvec, nvec_max);
   return cudaGetLastError();
 }
