@@ -204,10 +204,15 @@ __global__ void __launch_bounds__(256) oz_split(int nprob, GemmDims dims, GemmOp
 }
 
 // ---------------------------------------------------------------------------- tensor kernel
-__device__ __forceinline__ void oz_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+// instruction descriptor for N = nn output columns (a multiple of 16, <= 256)
+__device__ __forceinline__ uint32_t oz_idesc(int nn) {
+  return (OZ_IDESC & ~(0x3Fu << 17)) | ((uint32_t)(nn >> 3) << 17);
+}
+
+__device__ __forceinline__ void oz_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
   asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-               :: "r"(dtmem), "l"(adesc), "l"(bdesc), "r"(OZ_IDESC), "r"(acc));
+               :: "r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ bool oz_wait(uint64_t* mbar, uint32_t parity) {
@@ -234,7 +239,7 @@ __device__ __forceinline__ void oz_bulk_copy(void* dst_smem, const void* src_gme
 //   warp 0 / lane 0 (producer): waits until a stage is free (its "empty" barrier, arrived
 //     by the MMA commit), then loads it with 20 bulk copies (cp.async.bulk, the 1-D TMA)
 //     that complete on the stage's "full" barrier;
-//   warp 1 / lane 0 (MMA issuer): waits for a full stage, issues the 55 MMAs, commits them
+//   warp 1 / lane 0 (MMA issuer): waits for a full stage, issues the 37 MMAs (55 digit products), commits them
 //     to the stage's empty barrier, and after the last stage to the "done" barrier;
 //   all 8 warps: wait for "done", then run the epilogue from TMEM.
 template <bool REAL, int S>
@@ -328,16 +333,30 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
       asm volatile("tcgen05.fence::after_thread_sync;");
       unsigned char* ssrc = stage0 + st * STAGE;
       const uint32_t sa = smem_u32(ssrc), sb = smem_u32(ssrc + S * OZ_TILE_A);
+      // Digit products A_s B_t (0-based; group s + t + 2).  The exact groups have adjacent
+      // accumulators and the B planes adjacent tiles, so for each s the planes t0..t0+w-1
+      // stack into one operand of 64 w rows: one MMA with N = 64 w (w <= 4) feeds w
+      // accumulators and reads A_s from shared memory once instead of w times.  The merged
+      // groups (one accumulator) take one N = 64 MMA each.  A window's accumulators are all
+      // fresh or all written, so one accumulate flag serves it.
 #pragma unroll
       for (int s = 0; s < S; ++s) {
+        const uint64_t ad = oz_desc(sa + s * OZ_TILE_A);
 #pragma unroll
-        for (int t = 0; t < S; ++t) {
-          const int g = (s + 1) + (t + 1);
-          if (g > S + 1) continue;
-          const int acc = g - 2 < NEX ? g - 2 : NEX;
-          const uint32_t on = (init_mask >> acc) & 1u;
-          oz_mma(tmem + acc * OZ_BN, oz_desc(sa + s * OZ_TILE_A), oz_desc(sb + t * OZ_TILE_B), on);
-          init_mask |= 1u << acc;
+        for (int t0 = 0; t0 < NEX - s && t0 < S; t0 += 4) {
+          const int tend = min(min(NEX - s, S), t0 + 4);
+          const int w = tend - t0, acc0 = s + t0;
+          const uint32_t on = (init_mask >> acc0) & 1u;
+          oz_mma(tmem + acc0 * OZ_BN, ad, oz_desc(sb + t0 * OZ_TILE_B), oz_idesc(w * OZ_BN), on);
+          init_mask |= ((1u << w) - 1u) << acc0;
+        }
+        if (MERGED) {
+#pragma unroll
+          for (int t = (NEX - s > 0 ? NEX - s : 0); t < S && s + t + 2 <= S + 1; ++t) {
+            const uint32_t on = (init_mask >> NEX) & 1u;
+            oz_mma(tmem + NEX * OZ_BN, ad, oz_desc(sb + t * OZ_TILE_B), oz_idesc(OZ_BN), on);
+            init_mask |= 1u << NEX;
+          }
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"

@@ -36,7 +36,9 @@
 
 namespace {
 
-constexpr int ST_THREADS = 128;   // = slots per block
+constexpr int ST_THREADS = 128;   // = slots per block (eigenvectors)
+constexpr int SZ_THREADS = 64;    // = slots per block (eigenvalues): ~8 blocks per SM for 128 problems
+                                  // of n = 568, so the SMs' FP64 pipes finish within one block of each other
 constexpr int MAXITS = 5;         // inverse-iteration solves before giving up
 constexpr int EXTRA = 2;          // extra solves after the growth test passes
 constexpr double TIGHT = 1e-7;
@@ -191,7 +193,7 @@ __device__ __forceinline__ double hash_uniform(unsigned long long key) {
 }
 
 // ---------------------------------------------------------------- kernel 1: eigenvalues
-__global__ void __launch_bounds__(ST_THREADS)
+__global__ void __launch_bounds__(SZ_THREADS)
 stebz_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ dbase, const double* __restrict__ ebase,
              long long strideV, double* __restrict__ wslot, int32_t* __restrict__ status) {
   extern __shared__ double smd[];
@@ -740,8 +742,9 @@ cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d,
   const size_t smem1 = sizeof(double) * 3 * (size_t)n + sizeof(float) * 2 * (size_t)n + sizeof(int) * 2 * (size_t)n;
   cudaError_t err = cudaFuncSetAttribute(stebz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
   if (err != cudaSuccess) return err;
+  dim3 grid1((n + SZ_THREADS - 1) / SZ_THREADS, nprob);
+  stebz_kernel<<<grid1, SZ_THREADS, smem1, st>>>(n, size, d, e, strideV, wslot, status);
   dim3 grid((n + ST_THREADS - 1) / ST_THREADS, nprob);
-  stebz_kernel<<<grid, ST_THREADS, smem1, st>>>(n, size, d, e, strideV, wslot, status);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   int* biglist = (int*)(wslot + (size_t)n * nprob);
