@@ -205,8 +205,9 @@ GenEigPlan plan_gen_eig(int n, int nprob, int nSe, bool use_tc) {
   const int ncolv = (n + NAO_WY_NB - 1) / NAO_WY_NB * NAO_WY_NB;
   W.oVf = P.take<z64>((size_t)n * ncolv * nmax);
   W.oTc = P.take<z64>((size_t)ncolv * nmax);
-  W.oG2 = P.take<z64>((size_t)NAO_WY_NB * NAO_WY_NB * nmax);
-  W.oT2 = P.take<z64>((size_t)NAO_WY_NB * NAO_WY_NB * nmax);
+  const int nblk = n > 1 ? (n - 1 + NAO_WY_NB - 1) / NAO_WY_NB : 1;  // WY blocks: G_j and T_j of all
+  W.oG2 = P.take<z64>((size_t)NAO_WY_NB * NAO_WY_NB * nmax * nblk);
+  W.oT2 = P.take<z64>((size_t)NAO_WY_NB * NAO_WY_NB * nmax * nblk);
   W.oW = P.take<z64>((size_t)NAO_WY_NB * n * nmax);
   W.oW2 = P.take<z64>((size_t)NAO_WY_NB * n * nmax);
   W.oVW = P.take<z64>((size_t)3 * NAO_HT_NB * n * nmax);
@@ -239,7 +240,8 @@ DensityPlan plan_density(int n, int nprob, int nb, int num_sms, bool use_tc, boo
 // Z(:, c) when lowest),
 // normalised (times 1/sqrt(w) when use_rsqrt), with Q = prod_j (I - V_j T_j V_j^H) applied from
 // the last block of NAO_WY_NB reflectors to the first; every block costs three products
-// (W = V^H U, W = T W, U -= V W) plus its Gram matrix V^H V for T.
+// (W = V^H U, W = T W, U -= V W).  The Gram matrices V_j^H V_j of all blocks come first and
+// all T_j are built in one launch (they do not depend on U), so that launch fills the GPU.
 cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, const int32_t* ncols, const z64* A,
                                   const z64* tau, const double* Z, const double* w, int use_rsqrt, z64* U, z64* Vf,
                                   z64* tauc, z64* G, z64* T, z64* W, z64* W2, void* ozws, cudaStream_t st,
@@ -256,25 +258,31 @@ cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t*
     if (e != cudaSuccess) return e;
   }
   const int nblk = (n - 1 + nb - 1) / nb;
-  for (int j = nblk - 1; j >= 0; --j) {
+  for (int j = 0; j < nblk; ++j) {  // Gram matrices of all blocks
     const int R0 = j * nb + 1, rows = n - R0;
-    if (rows <= 0) continue;
     const z64* Vj = Vf + R0 + (size_t)j * nb * n;  // V_j(r, c) at Vj[r + c n]
     GemmDims dg{nb, nb, rows, nullptr, nullptr, nullptr, 0};
     e = run_zgemm(ctx, "backtransform", nprob, dg, 1.0, GemmOperand{Vj, svf, n, 1, 1, nullptr},
-                  GemmOperand{Vj, svf, 1, n, 0, nullptr}, 0.0, G, snb2, nb, 1, ozws, st, digits);
+                  GemmOperand{Vj, svf, 1, n, 0, nullptr}, 0.0, G + (size_t)j * nprob * snb2, snb2, nb, 1, ozws,
+                  st, digits);
     if (e != cudaSuccess) return e;
-    {
-      NaoStage stage_(ctx, "backtransform", st, 1);
-      e = launch_build_t(nb, nprob, G, tauc, ncolv, j * nb, T, st);
-      if (e != cudaSuccess) return e;
-    }
+  }
+  if (nblk > 0) {
+    NaoStage stage_(ctx, "backtransform", st, 1);
+    e = launch_build_t(nb, nprob, nblk, G, tauc, ncolv, T, st);
+    if (e != cudaSuccess) return e;
+  }
+  for (int j = nblk - 1; j >= 0; --j) {
+    const int R0 = j * nb + 1, rows = n - R0;
+    if (rows <= 0) continue;
+    const z64* Vj = Vf + R0 + (size_t)j * nb * n;
+    const z64* Tj = T + (size_t)j * nprob * snb2;
     GemmDims dw{nb, n, rows, nullptr, ncols, nullptr, 0};
     e = run_zgemm(ctx, "backtransform", nprob, dw, 1.0, GemmOperand{Vj, svf, n, 1, 1, nullptr},
                   GemmOperand{U + R0, snn, 1, n, 0, nullptr}, 0.0, W, snbn, n, 1, ozws, st, digits);
     if (e != cudaSuccess) return e;
     GemmDims dt{nb, n, nb, nullptr, ncols, nullptr, 0};
-    e = run_zgemm(ctx, "backtransform", nprob, dt, 1.0, GemmOperand{T, snb2, nb, 1, 0, nullptr},
+    e = run_zgemm(ctx, "backtransform", nprob, dt, 1.0, GemmOperand{Tj, snb2, nb, 1, 0, nullptr},
                   GemmOperand{W, snbn, n, 1, 0, nullptr}, 0.0, W2, snbn, n, 1, ozws, st, digits);
     if (e != cudaSuccess) return e;
     GemmDims du{rows, n, nb, nullptr, ncols, nullptr, 0};

@@ -160,27 +160,34 @@ __global__ void init_u_kernel(int n, const int32_t* __restrict__ size, const int
   Ubase[(size_t)p * strideU + (size_t)c * ldu + r] = zmk(v, 0.0);
 }
 
-// T (nb x nb, row-major, upper triangular) of block j0..j0+nb-1 from G = V^H V (row-major):
+// T (nb x nb, row-major, upper triangular) of block j from G = V^H V (row-major, Hermitian):
 // T_ii = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) G(0:i, i).  One block of nb threads per
-// problem; T is built in shared memory, packed by columns (column c holds rows 0..c).
-__global__ void build_t_kernel(int nb, const z64* __restrict__ Gbase, const z64* __restrict__ taucbase, int ncolv, int j0,
-                               z64* __restrict__ Tbase) {
-  extern __shared__ z64 tp[];  // nb (nb + 1) / 2
-  const int p = blockIdx.x;
+// (block j, problem p); thread r owns row r of T, which it writes and reads back itself (in
+// global memory, cached), so only G's current column is shared (2 KB of shared memory: many
+// blocks per SM).  G and T of block j of problem p at (j nprob + p) nb^2.
+__global__ void build_t_kernel(int nb, int nprob, const z64* __restrict__ Gbase, const z64* __restrict__ taucbase,
+                               int ncolv, z64* __restrict__ Tbase) {
+  extern __shared__ z64 gcol[];  // nb
+  const int p = blockIdx.x % nprob, j = blockIdx.x / nprob;
   const int r = threadIdx.x;
-  const z64* G = Gbase + (size_t)p * nb * nb;
-  const z64* tau = taucbase + (size_t)p * ncolv + j0;
-  z64* T = Tbase + (size_t)p * nb * nb;
+  const z64* G = Gbase + (size_t)blockIdx.x * nb * nb;
+  const z64* tau = taucbase + (size_t)p * ncolv + (size_t)j * nb;
+  z64* Tr = Tbase + (size_t)blockIdx.x * nb * nb + (size_t)r * nb;  // row r
+  for (int c = 0; c < r; ++c) Tr[c] = zmk(0.0, 0.0);
   for (int i = 0; i < nb; ++i) {
-    const z64 ti = tau[i];
-    z64 acc = zmk(0.0, 0.0);
-    if (r < i)
-      for (int c = r; c < i; ++c) acc = zfma(tp[c * (c + 1) / 2 + r], G[(size_t)c * nb + i], acc);
-    if (r < i) tp[i * (i + 1) / 2 + r] = zmul(zmk(-ti.x, -ti.y), acc);
-    else if (r == i) tp[i * (i + 1) / 2 + r] = ti;
+    // G(0:i, i) = conj(G(i, 0:i)) (G is Hermitian): one coalesced load of row i
+    if (r < i) gcol[r] = zconj(G[(size_t)i * nb + r]);
+    __syncthreads();
+    if (r < i) {
+      z64 acc = zmk(0.0, 0.0);
+      for (int c = r; c < i; ++c) acc = zfma(Tr[c], gcol[c], acc);
+      const z64 ti = tau[i];
+      Tr[i] = zmul(zmk(-ti.x, -ti.y), acc);
+    } else if (r == i) {
+      Tr[i] = tau[i];
+    }
     __syncthreads();
   }
-  for (int c = 0; c < nb; ++c) T[(size_t)r * nb + c] = (c >= r) ? tp[c * (c + 1) / 2 + r] : zmk(0.0, 0.0);
 }
 
 // column c < nc: U(:, c) /= ||U(:, c)||, times 1/sqrt(w[m - nc + c]) when use_rsqrt
@@ -219,12 +226,10 @@ cudaError_t launch_init_u(int n, int nprob, const int32_t* size, const int32_t* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_t(int nb, int nprob, const z64* G, const z64* tauc, int ncolv, int j0, z64* T,
+cudaError_t launch_build_t(int nb, int nprob, int nblk, const z64* G, const z64* tauc, int ncolv, z64* T,
                            cudaStream_t st) {
-  const size_t smem = (size_t)nb * (nb + 1) / 2 * sizeof(z64);
-  cudaError_t e = cudaFuncSetAttribute(build_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  build_t_kernel<<<nprob, nb, smem, st>>>(nb, G, tauc, ncolv, j0, T);
+  const size_t smem = (size_t)nb * sizeof(z64);
+  build_t_kernel<<<nprob * nblk, nb, smem, st>>>(nb, nprob, G, tauc, ncolv, T);
   return cudaGetLastError();
 }
 

@@ -138,7 +138,8 @@ cudaError_t launch_extract_v(int n, int nprob, const int32_t* size, const z64* A
 // init_u: column c of U takes Z's column m - nc + c (the top nc) or, when lowest, column c.
 cudaError_t launch_init_u(int n, int nprob, const int32_t* size, const int32_t* ncols, const double* Z, int ldz,
                           long long strideZ, z64* U, int ldu, long long strideU, int lowest, cudaStream_t st);
-cudaError_t launch_build_t(int nb, int nprob, const z64* G, const z64* tauc, int ncolv, int j0, z64* T,
+// T_j of every WY block j < nblk and problem p at once: G_j, T_j at (j nprob + p) nb^2.
+cudaError_t launch_build_t(int nb, int nprob, int nblk, const z64* G, const z64* tauc, int ncolv, z64* T,
                            cudaStream_t st);
 cudaError_t launch_normalize_cols(int n, int nprob, const int32_t* size, const int32_t* ncols, const double* w,
                                   long long strideV, int use_rsqrt, z64* U, int ldu, long long strideU,

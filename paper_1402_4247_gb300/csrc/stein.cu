@@ -12,12 +12,10 @@
 //     1. bisection in FP32 (64x the FP64 rate on this GPU) to ~1e-7 |T|, counting negative
 //        pivots of the LDL^T form with a fast reciprocal;
 //     2. the FP32 bracket, widened by 64 eps_32 |T| (an FP32 count is exact for a matrix
-//        within a few eps_32 |T| of T), is verified with two FP64 counts; if it holds exactly
-//        this one eigenvalue, safeguarded Newton on p_n (derivative from the same
-//        recurrence) converges in a few steps to the rounding noise of p_n, and a bracket of
-//        a few noise widths around it, verified by two FP64 counts, replaces the FP32 one;
-//     3. FP64 bisection closes the bracket to eps |T| (tight clusters and failed
-//        verifications take this path from the wider bracket).
+//        within a few eps_32 |T| of T), is verified with two FP64 counts (the full
+//        Gershgorin interval replaces it if a count disagrees);
+//     3. FP64 bisection closes the bracket to eps |T| in a number of steps that is nearly the
+//        same for every lane.
 // * Eigenvectors (kernel 2, same block split): inverse iteration with a partially pivoted LU
 //   of T - lambda I (tiny pivots perturbed to eps |T|), a scaled right-hand side, the growth
 //   test |x|_inf >= sqrt(0.1/blocksize) plus two extra solves, and modified Gram-Schmidt
@@ -246,45 +244,11 @@ stebz_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__
       lo = T.gl;
       hi = T.gu;
     }
-    const bool isolated = (clo == idx && chi == idx + 1);
-    if (isolated) {
-      // safeguarded Newton on p_n; its step bottoms out at the rounding noise of p_n, so
-      // it only narrows the bracket, which bisection then closes to eps |T|
-      double x = 0.5 * (lo + hi), last = hi - lo, prev = hi - lo;
-      bool conv = false;
-      for (int it = 0; it < 10; ++it) {
-        double pn = 0.0, dpn = 0.0;
-        const int c = sturm64(d, e2, b0, b1, x, true, &pn, &dpn);
-        if (c > idx) hi = x;
-        else lo = x;
-        if (dpn == 0.0) break;
-        const double step = pn / dpn, cand = x - step;
-        if (!(cand > lo && cand < hi)) break;
-        x = cand;
-        last = fabs(step);
-        // converged to ~1e-11 |T|, or stalled at the rounding noise of p_n (no longer
-        // shrinking quadratically)
-        if (last <= 1e-11 * T.tnorm || last >= 0.25 * prev) {
-          conv = true;
-          break;
-        }
-        prev = last;
-      }
-      if (conv) {
-        double del = 16.0 * last + 8.0 * eps * T.tnorm;
-        for (int tries = 0; tries < 3; ++tries, del *= 16.0) {
-          const double l2 = fmax(x - del, lo), h2 = fmin(x + del, hi);
-          const int cl = sturm64(d, e2, b0, b1, l2, false, nullptr, nullptr);
-          const int ch = sturm64(d, e2, b0, b1, h2, false, nullptr, nullptr);
-          if (cl <= idx && idx < ch) {
-            lo = l2;
-            hi = h2;
-            break;
-          }
-        }
-      }
-    }
-    for (int it = 0; it < 128; ++it) {  // FP64 bisection to eps |T|
+    // FP64 bisection to eps |T|.  Every lane starts from a bracket of the same width (the
+    // verified FP32 one), so the lanes of a warp run the same number of steps: the FP64 pipe
+    // (1/64 of FP32 here) sees full warps.  (A Newton shortcut for isolated eigenvalues took
+    // fewer steps per lane but left ~2/3 of the lanes idle through divergence.)
+    for (int it = 0; it < 128; ++it) {
       const double mid = 0.5 * (lo + hi);
       const double tol = fmax(2.0 * eps * fmax(fabs(lo), fabs(hi)), eps * T.tnorm);
       if (hi - lo <= tol || mid <= lo || mid >= hi) break;
