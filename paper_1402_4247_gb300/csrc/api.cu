@@ -161,7 +161,7 @@ cudaError_t run_dgemm(nao_ctx* ctx, const char* stage, int nprob, GemmDims d, do
 
 // Workspace layout of nao_gen_eig (byte offsets into the context's arena) and its size.
 struct GenEigPlan {
-  size_t oAS, oTauS, odS, oeS, owS, oZ, oZ2, oG, oScr, omS, ostS, oX, oHf, oY, oHp, oV, oTauH, odH, oeH, owH, omP, onbP, ostP, ostH, oOz, oVf, oTc, oG2, oT2, oW, oW2, oVW;
+  size_t oAS, oTauS, odS, oeS, owS, oZ, oZ2, oG, oScr, omS, ostS, oX, oHf, oY, oHp, oV, oTauH, odH, oeH, owH, omP, onbP, ostP, ostH, oOz, oVf, oTc, oG2, oT2, oW, oW2, oVW, oDig, oErow;
   size_t bytes;
 };
 
@@ -211,6 +211,9 @@ GenEigPlan plan_gen_eig(int n, int nprob, int nSe, bool use_tc) {
   W.oW = P.take<z64>((size_t)NAO_WY_NB * n * nmax);
   W.oW2 = P.take<z64>((size_t)NAO_WY_NB * n * nmax);
   W.oVW = P.take<z64>((size_t)3 * NAO_HT_NB * n * nmax);
+  // 8-bit digit planes of the Householder trailing matrix (tensor-core product method)
+  W.oDig = P.take<char>(use_tc ? hetrd_digits_bytes(n, nmax) : 16);
+  W.oErow = P.take<int>((size_t)(n > 1 ? n - 1 : 1) * nmax);
   W.bytes = P.off;
   return W;
 }
@@ -298,15 +301,20 @@ cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t*
 // followed by the deferred update A(r0:, r0:) -= V W^H + W V^H of the rest (lower triangle,
 // one rank-2 NB product).  VW: [nprob][n][3 NB] workspace.
 cudaError_t hetrd_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, z64* A, double* d, double* e, z64* tau,
-                          z64* VW, void* ozws, cudaStream_t st, int digits) {
+                          z64* VW, void* ozws, cudaStream_t st, int digits, void* dig, int* erow) {
+  // exact integer matrix-vector products with the tensor-core method; FP64 FMAs otherwise
+  const bool use_dig = ctx->gemm_method == NAO_GEMM_TC && dig != nullptr;
   const int NB = NAO_HT_NB;
   const int cl = hetrd_cluster_size(n, nprob, ctx->num_sms);
   const long long snn = (long long)n * n, svw = (long long)n * 3 * NB;
   for (int i0 = 0; i0 < n; i0 += NB) {
-    cudaError_t err;
+    cudaError_t err = cudaSuccess;
     {
-      NaoStage stage_(ctx, "hetrd", st, 1);
-      err = launch_hetrd_panel(n, nprob, size, A, n, snn, d, e, tau, n, VW, svw, i0, cl, st);
+      NaoStage stage_(ctx, "hetrd", st, use_dig ? 2 : 1);
+      if (use_dig) err = launch_hetrd_digits(n, nprob, size, A, n, snn, i0, dig, erow, st);
+      if (err == cudaSuccess)
+        err = launch_hetrd_panel(n, nprob, size, A, n, snn, d, e, tau, n, VW, svw, i0, cl, use_dig ? dig : nullptr,
+                                 erow, st);
     }
     if (err != cudaSuccess) return err;
     const int r0 = i0 + NB;
@@ -520,6 +528,8 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   void* ozws = use_tc ? (void*)(ws + W.oOz) : nullptr;
   z64 *Vf = (z64*)(ws + W.oVf), *tauc = (z64*)(ws + W.oTc), *Gw = (z64*)(ws + W.oG2), *Tw = (z64*)(ws + W.oT2),
       *Ww = (z64*)(ws + W.oW), *W2w = (z64*)(ws + W.oW2), *VWp = (z64*)(ws + W.oVW);
+  void* digp = use_tc ? (void*)(ws + W.oDig) : nullptr;
+  int* erowp = (int*)(ws + W.oErow);
   const long long snn = (long long)nn;
   // Mixed mode: the back-transformations, X^H H X, the rank-2k updates of H' and X V run with
   // 30-bit products; the reduction of S, the tridiagonal solves (with their Newton-Schulz
@@ -530,7 +540,7 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
 
   // ---- Part 2: Eigen_HH(S) -> s, U;  X = U_m s_m^{-1/2}
   NAO_STAGE("herm_fill", 1, launch_herm_fill(n, nSe, (const z64*)S, snn, nullptr, AS, n, snn, st));
-  NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nSe, nullptr, AS, dS, eS, tauS, VWp, ozws, st, NAO_OZ_DIGITS_FP64));
+  NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nSe, nullptr, AS, dS, eS, tauS, VWp, ozws, st, NAO_OZ_DIGITS_FP64, digp, erowp));
   NAO_STAGE("stein", 1, launch_stein(n, nSe, nullptr, dS, eS, n, wS, Z, n, snn, scr, stS, nullptr, n, st));
   NAO_STAGE("misc", 1, launch_count_kept(n, nSe, wS, n, s_cut, mS, stS, st));
   {  // one Newton-Schulz step: Z2 = Z (3I - Z^T Z)/2 = Z - Z (Z^T Z - I)/2
@@ -561,7 +571,7 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   NAO_STAGE("misc", 1, launch_hermitize(n, nprob, mP, Hp, n, snn, st));
 
   // ---- Part 4: Eigen_HH(H') -> eps, V;  C = X V
-  NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nprob, mP, Hp, dH, eH, tauH, VWp, ozws, st, dig));
+  NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nprob, mP, Hp, dH, eH, tauH, VWp, ozws, st, dig, digp, erowp));
   // Eigenvectors of H' only where they are used (the paper's second pass, dstevx's index
   // range): the lowest nb per problem for C, all m for the mixed-mode refinement, none when
   // the caller asks for eigenvalues only (C = NULL).

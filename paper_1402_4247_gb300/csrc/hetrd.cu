@@ -60,6 +60,135 @@ __device__ __forceinline__ double2 block_sum2(double a, double b, double* red) {
 }
 
 
+// ---------------------------------------------------------------------------------------
+// Exact integer form of the panel's Hermitian matrix-vector product (used with the
+// tensor-core product method).  On this GPU FP64 runs at 2 FMA/clk/SM while the integer
+// 4-way dot product (DP4A) runs at 60/clk/SM (240 8-bit MACs), so the product
+// p = A22 v, which dominates the reduction, is formed from 8-bit digits:
+//  * once per panel, every row r of the Hermitian trailing matrix (both triangles) is scaled
+//    by its own power of two 2^{e_r} (|a| < 2^{e_r}) and q = round(a 2^{62 - e_r}) written in
+//    eight balanced base-256 digits d_0..d_7 in [-128, 127] (62 bits: FP64 accuracy with
+//    margin for entries below their row maximum), real and imaginary parts separately;
+//  * per column, v is split the same way with one scale 2^f;
+//  * DP4A sums digit products of one order G = s + t exactly in int32 (|d d'| <= 2^14, two
+//    products per pair, at most 8 pairs per order, K <= 4096: below 2^30): RR_G collects
+//    Re a Re v + Im a (-Im v) (-Im v is split as its own
+//    value, so no digit is negated), RI_G the cross terms, for G <= 7 (the orders beyond are
+//    below 2^-68 of the row scale);
+//  * p_r = 2^{e_r + f - 12} sum_G (RR_G + i RI_G) 2^{-8 G}, combined in FP64.
+// Digit layout: dig[p][rr][w][16 words], rr = r - (i0 + 1), word w holds columns
+// i0 + 1 + 4w .. +3 (4 int8 lanes) of plane s, part t at word index 2 s + t.
+constexpr int HD_S = 8;      // digits per value
+constexpr int HD_G = 8;      // digit orders kept (G = 0..7)
+// words (4 columns) per digit row: rows and columns i0 + 1 .. n - 1
+__host__ __device__ inline int hd_words(int n) { return n > 1 ? (n - 1 + 3) / 4 : 1; }
+
+__device__ __forceinline__ int hd_exp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7ff); }
+
+// q = round(x 2^{62 - e}) for |x| < 2^e (integer arithmetic on the bits of x)
+__device__ __forceinline__ long long hd_fixed(double x, int e) {
+  const long long bits = __double_as_longlong(x);
+  const int b = (int)((bits >> 52) & 0x7ff);
+  if (b == 0) return 0;
+  long long m = (bits & 0xFFFFFFFFFFFFFll) | 0x10000000000000ll;
+  const int sh = b - 1075 + 62 - e;
+  long long q;
+  if (sh >= 0) q = m << sh;
+  else if (sh <= -62) q = 0;
+  else q = (m + (1ll << (-sh - 1))) >> (-sh);
+  return bits < 0 ? -q : q;
+}
+
+// balanced base-256 digits of q (|q| < 2^62), most significant first, as unsigned bytes
+__device__ __forceinline__ void hd_digits(long long q, unsigned int* d) {
+#pragma unroll
+  for (int s = HD_S - 1; s >= 1; --s) {
+    const int ds = (int)((q + 128) & 255) - 128;
+    d[s] = (unsigned int)(ds & 255);
+    q = (q - ds) >> 8;
+  }
+  d[0] = (unsigned int)((int)q & 255);
+}
+
+// digit words of 4 complex values x[0..3]: out[2 s + t] = plane s of part t (t = 0 re, 1 im)
+__device__ __forceinline__ void hd_pack4(const z64* x, int e, uint4* out4) {
+  unsigned int w[2 * HD_S];
+#pragma unroll
+  for (int k = 0; k < 2 * HD_S; ++k) w[k] = 0u;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    unsigned int dr[HD_S], di[HD_S];
+    hd_digits(hd_fixed(x[l].x, e), dr);
+    hd_digits(hd_fixed(x[l].y, e), di);
+#pragma unroll
+    for (int s = 0; s < HD_S; ++s) {
+      w[2 * s] |= dr[s] << (8 * l);
+      w[2 * s + 1] |= di[s] << (8 * l);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) out4[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+}
+
+// digit words of v's 4 values: out[3 t + k], k = 0: Re v, 1: Im v, 2: -Im v (plane t)
+__device__ __forceinline__ void hd_pack4v(const z64* x, int e, unsigned int* out) {
+#pragma unroll
+  for (int k = 0; k < 3 * HD_S; ++k) out[k] = 0u;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    unsigned int dr[HD_S], di[HD_S], dn[HD_S];
+    hd_digits(hd_fixed(x[l].x, e), dr);
+    hd_digits(hd_fixed(x[l].y, e), di);
+    hd_digits(hd_fixed(-x[l].y, e), dn);
+#pragma unroll
+    for (int t = 0; t < HD_S; ++t) {
+      out[3 * t] |= dr[t] << (8 * l);
+      out[3 * t + 1] |= di[t] << (8 * l);
+      out[3 * t + 2] |= dn[t] << (8 * l);
+    }
+  }
+}
+
+// element (r, c) of the Hermitian matrix stored as its lower triangle (column-major)
+__device__ __forceinline__ z64 herm_at(const z64* A, int ld, int r, int c) {
+  return c <= r ? A[(size_t)c * ld + r] : zconj(A[(size_t)r * ld + c]);
+}
+
+// Digits of the trailing matrix rows/columns i0+1 .. m-1 at the start of a panel.  One warp
+// per row; lanes over words.  Lmax rows x W words per problem.
+__global__ void __launch_bounds__(256)
+hetrd_digits_kernel(int n, const int32_t* __restrict__ size, const z64* __restrict__ Abase, int ld,
+                    long long strideA, int i0, int Lmax, int W, uint4* __restrict__ dig, int* __restrict__ erow) {
+  const int p = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int rr = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int m = size ? size[p] : n;
+  const int L = m - i0 - 1;
+  if (rr >= Lmax || rr >= L || L <= 0) return;
+  const z64* A = Abase + (size_t)p * strideA;
+  const int r = i0 + 1 + rr;
+  int bmax = 0;
+  for (int c = lane; c < L; c += 32) {
+    const z64 a = herm_at(A, ld, r, i0 + 1 + c);
+    bmax = max(bmax, max(hd_exp(a.x), hd_exp(a.y)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+  const int e = bmax == 0 ? -1100 : bmax - 1022;
+  if (lane == 0) erow[(size_t)p * Lmax + rr] = e;
+  uint4* row = dig + ((size_t)p * Lmax + rr) * W * 4;
+  const int Wp = (L + 3) >> 2;
+  for (int w = lane; w < Wp; w += 32) {
+    z64 x[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int c = 4 * w + l;
+      x[l] = c < L ? herm_at(A, ld, r, i0 + 1 + c) : zmk(0.0, 0.0);
+    }
+    hd_pack4(x, e, row + (size_t)w * 4);
+  }
+}
+
 // first pair index of block k when npairs pairs are dealt to C blocks
 __device__ __forceinline__ int pair_start(int k, int npairs, int C) { return (int)(((long long)k * npairs) / C); }
 
@@ -73,7 +202,8 @@ __device__ __forceinline__ int pair_start(int k, int npairs, int C) { return (in
 __global__ void __launch_bounds__(HT_THREADS)
 hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Abase, int ld, long long strideA,
                    double* __restrict__ dbase, double* __restrict__ ebase, z64* __restrict__ taubase, long long strideV,
-                   z64* __restrict__ VWbase, long long strideVW, int i0) {
+                   z64* __restrict__ VWbase, long long strideVW, int i0, const uint4* __restrict__ dig,
+                   const int* __restrict__ erow, int Lmax, int W) {
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
@@ -84,6 +214,8 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
   z64* w = sm + n;           // [n] p, then w
   z64* pown = sm + 2 * n;    // [n] corrected p for this block's rows (read by the others)
   z64* part = sm + 3 * n;    // [2 * HT_THREADS] partial sums of the K threads of each pair
+  unsigned int* vd = (unsigned int*)(sm + 3 * n + 2 * HT_THREADS);  // [24][W] digit words of v
+  __shared__ int ired[32];
   __shared__ z64 ypart[2 * NB], yfull[2 * NB];
   __shared__ double red[64];
   __shared__ z64 s_tau, s_scale;
@@ -170,7 +302,94 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
     const int P = g1 - g0;
     int K = P > 0 ? nt / P : 1;
     K = K < 1 ? 1 : (K > HT_MAXK ? HT_MAXK : K);
-    if (active) {
+    if (active && dig) {
+      // (c) with 8-bit digits and DP4A (see the note above hetrd_digits_kernel)
+      int bm = 0;
+      for (int c = tid; c < mt; c += nt) bm = max(bm, max(hd_exp(v[c].x), hd_exp(v[c].y)));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) bm = max(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+      if (lane == 0) ired[wid] = bm;
+      __syncthreads();
+      bm = 0;
+      for (int k = 0; k < nw; ++k) bm = max(bm, ired[k]);
+      const int f = bm == 0 ? -1100 : bm - 1022;
+      const int kk0 = i - i0;  // column i + 1 relative to i0 + 1
+      const int w0 = kk0 >> 2, Wp = (m - i0 - 1 + 3) >> 2;
+      for (int w = w0 + tid; w < Wp; w += nt) {
+        z64 x[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const int c = 4 * w + l - kk0;
+          x[l] = (c >= 0 && c < mt) ? v[c] : zmk(0.0, 0.0);
+        }
+        unsigned int t[3 * HD_S];
+        hd_pack4v(x, f, t);
+#pragma unroll
+        for (int k = 0; k < 3 * HD_S; ++k) vd[k * W + w] = t[k];
+      }
+      __syncthreads();
+      // rows of this block's pairs: four rows per warp, eight lanes per row
+      const int nrows = 2 * P, rslot = lane >> 3, wl = lane & 7;
+      for (int q0 = wid * 4; q0 < nrows; q0 += nw * 4) {
+        const int qq = q0 + rslot;
+        int r = -1;
+        if (qq < nrows) {
+          const int g = g0 + (qq >> 1);
+          r = (qq & 1) ? mt - 1 - g : g;
+          if ((qq & 1) && r == g) r = -1;
+        }
+        int RR[HD_G], RI[HD_G];
+#pragma unroll
+        for (int G = 0; G < HD_G; ++G) RR[G] = RI[G] = 0;
+        const int rr = r + kk0;  // digit row
+        if (r >= 0) {
+          const uint4* row = dig + ((size_t)p * Lmax + rr) * W * 4;
+          for (int w = w0 + wl; w < Wp; w += 8) {
+            unsigned int a[2 * HD_S];
+            const uint4* aw = row + (size_t)w * 4;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const uint4 q4 = aw[k];
+              a[4 * k] = q4.x;
+              a[4 * k + 1] = q4.y;
+              a[4 * k + 2] = q4.z;
+              a[4 * k + 3] = q4.w;
+            }
+#pragma unroll
+            for (int t2 = 0; t2 < HD_G; ++t2) {
+              const int bre = (int)vd[(3 * t2) * W + w], bim = (int)vd[(3 * t2 + 1) * W + w],
+                        bni = (int)vd[(3 * t2 + 2) * W + w];
+#pragma unroll
+              for (int s2 = 0; s2 + t2 < HD_G; ++s2) {
+                const int G = s2 + t2;
+                RR[G] = __dp4a((int)a[2 * s2], bre, RR[G]);      // Re a Re v
+                RR[G] = __dp4a((int)a[2 * s2 + 1], bni, RR[G]);  // Im a (-Im v)
+                RI[G] = __dp4a((int)a[2 * s2], bim, RI[G]);      // Re a Im v
+                RI[G] = __dp4a((int)a[2 * s2 + 1], bre, RI[G]);  // Im a Re v
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+          for (int G = 0; G < HD_G; ++G) {
+            RR[G] += __shfl_xor_sync(0xffffffffu, RR[G], o);
+            RI[G] += __shfl_xor_sync(0xffffffffu, RI[G], o);
+          }
+        if (r >= 0 && wl == 0) {
+          double hr = 0.0, hi = 0.0;
+#pragma unroll
+          for (int G = HD_G - 1; G >= 0; --G) {
+            hr = fma(hr, 0x1p-8, (double)RR[G]);
+            hi = fma(hi, 0x1p-8, (double)RI[G]);
+          }
+          const double sc = ldexp(1.0, erow[(size_t)p * Lmax + rr] + f - 12);
+          pown[r] = zmk(hr * sc, hi * sc);
+        }
+      }
+    }
+    if (active && !dig) {
       for (int tt = tid; tt < K * P; tt += nt) {
         const int k = tt / P, gl = tt - k * P, g = g0 + gl;
         const int c0 = (int)(((long long)k * mt) / K), c1 = (int)(((long long)(k + 1) * mt) / K);
@@ -187,6 +406,8 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
           part[(size_t)k * 2 * P + 2 * gl + h] = acc;
         }
       }
+    }
+    if (active) {
       // partial y over this block's rows: warp-strided over the 2j entries
       for (int jj = wid; jj < 2 * j; jj += nw) {
         const int cidx = jj < j ? NB + jj : jj - j;  // W column jj, or V column jj - j
@@ -209,14 +430,15 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
         if (lane == 0) ypart[jj] = zmk(sre, sim);
       }
       __syncthreads();
-      for (int tt = tid; tt < 2 * P; tt += nt) {
-        const int gl = tt >> 1, h = tt & 1, g = g0 + gl;
-        const int r = h ? mt - 1 - g : g;
-        if (h && r == g) continue;
-        z64 acc = zmk(0.0, 0.0);
-        for (int k = 0; k < K; ++k) acc = zadd(acc, part[(size_t)k * 2 * P + tt]);
-        pown[r] = acc;
-      }
+      if (!dig)
+        for (int tt = tid; tt < 2 * P; tt += nt) {
+          const int gl = tt >> 1, h = tt & 1, g = g0 + gl;
+          const int r = h ? mt - 1 - g : g;
+          if (h && r == g) continue;
+          z64 acc = zmk(0.0, 0.0);
+          for (int k = 0; k < K; ++k) acc = zadd(acc, part[(size_t)k * 2 * P + tt]);
+          pown[r] = acc;
+        }
     }
     cluster.sync();  // S2: partial results ready; every block is done reading column i
     if (rank == 0) {  // Procedure 3: keep v below the subdiagonal of column i, and in V
@@ -288,8 +510,12 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
 
 // Largest cluster size C (1..8, at most one block per 128 rows) for which the nprob clusters
 // of C blocks are all resident at once, as the occupancy calculator reports for this kernel.
+static size_t panel_smem(int n) {
+  return sizeof(z64) * (3 * (size_t)n + 2 * HT_THREADS) + sizeof(unsigned int) * 3 * HD_S * hd_words(n);
+}
+
 int hetrd_cluster_size(int n, int nprob, int num_sms) {
-  const size_t smem = sizeof(z64) * (3 * (size_t)n + 2 * HT_THREADS);
+  const size_t smem = panel_smem(n);
   if (cudaFuncSetAttribute(hetrd_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       cudaFuncSetAttribute(hetrd_panel_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 0) != cudaSuccess) {
     cudaGetLastError();
@@ -321,8 +547,8 @@ int hetrd_cluster_size(int n, int nprob, int num_sms) {
 
 cudaError_t launch_hetrd_panel(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA, double* d,
                                double* e, z64* tau, long long strideV, z64* VW, long long strideVW, int i0, int cluster,
-                               cudaStream_t st) {
-  size_t smem = sizeof(z64) * (3 * (size_t)n + 2 * HT_THREADS);
+                               const void* dig, const int* erow, cudaStream_t st) {
+  size_t smem = panel_smem(n);
   cudaError_t err = cudaFuncSetAttribute(hetrd_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   cudaLaunchConfig_t cfg = {};
@@ -337,5 +563,20 @@ cudaError_t launch_hetrd_panel(int n, int nprob, const int32_t* size, z64* A, in
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, hetrd_panel_kernel, n, size, A, ld, strideA, d, e, tau, strideV, VW, strideVW, i0);
+  return cudaLaunchKernelEx(&cfg, hetrd_panel_kernel, n, size, A, ld, strideA, d, e, tau, strideV, VW, strideVW, i0,
+                            (const uint4*)dig, erow, n > 1 ? n - 1 : 1, hd_words(n));
+}
+
+size_t hetrd_digits_bytes(int n, int nprob) {
+  const size_t L = n > 1 ? n - 1 : 1;
+  return L * hd_words(n) * 64 * (size_t)nprob;
+}
+
+cudaError_t launch_hetrd_digits(int n, int nprob, const int32_t* size, const z64* A, int ld, long long strideA, int i0,
+                                void* dig, int* erow, cudaStream_t st) {
+  const int Lmax = n > 1 ? n - 1 : 1, L = n - i0 - 1;
+  if (L <= 0) return cudaSuccess;
+  dim3 grid((L + 7) / 8, nprob);
+  hetrd_digits_kernel<<<grid, 256, 0, st>>>(n, size, A, ld, strideA, i0, Lmax, hd_words(n), (uint4*)dig, erow);
+  return cudaGetLastError();
 }

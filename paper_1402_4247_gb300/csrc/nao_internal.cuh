@@ -117,9 +117,15 @@ cudaError_t launch_herm_fill(int n, int nprob, const z64* src, long long src_str
 // applies A(i0+NB:, i0+NB:) -= V W^H + W V^H before the next panel.
 constexpr int NAO_HT_NB = 32;
 int hetrd_cluster_size(int n, int nprob, int num_sms);
+// dig / erow (nullable): 8-bit digit planes of the trailing matrix made by launch_hetrd_digits
+// for this panel; with them the panel forms its Hermitian matrix-vector products exactly with
+// integer dot products (DP4A) instead of FP64 FMAs.
 cudaError_t launch_hetrd_panel(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA, double* d,
                                double* e, z64* tau, long long strideV, z64* VW, long long strideVW, int i0, int cluster,
-                               cudaStream_t st);
+                               const void* dig, const int* erow, cudaStream_t st);
+size_t hetrd_digits_bytes(int n, int nprob);  // digit planes (row exponents: (n - 1) nprob ints)
+cudaError_t launch_hetrd_digits(int n, int nprob, const int32_t* size, const z64* A, int ld, long long strideA, int i0,
+                                void* dig, int* erow, cudaStream_t st);
 
 // Eigen_HH step 2: eigenvalues w (ascending) and orthonormal eigenvectors Z (column-major,
 // ld) of tridiag(e, d, e) by bisection + inverse iteration.  scratch: see stein_scratch_doubles.
