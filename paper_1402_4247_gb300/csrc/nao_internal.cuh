@@ -115,7 +115,7 @@ cudaError_t launch_herm_fill(int n, int nprob, const z64* src, long long src_str
 // One launch reduces the panel of columns i0 .. i0+NAO_HT_NB-1; VW ([nprob][n][3 NB],
 // per row [V | W | V]) receives the panel's reflectors and update vectors, and the caller
 // applies A(i0+NB:, i0+NB:) -= V W^H + W V^H before the next panel.
-constexpr int NAO_HT_NB = 32;
+constexpr int NAO_HT_NB = 16;
 int hetrd_cluster_size(int n, int nprob, int num_sms);
 // dig / erow (nullable): 8-bit digit planes of the trailing matrix made by launch_hetrd_digits
 // for this panel; with them the panel forms its Hermitian matrix-vector products exactly with
