@@ -149,6 +149,25 @@ __device__ __forceinline__ void hd_pack4v(const z64* x, int e, unsigned int* out
   }
 }
 
+// sum_G R[G] 2^{-8 G} 2^ex as a double, in integer arithmetic: the orders G < 4 and G >= 4
+// are combined exactly in two int64 words (|R[G]| < 2^31 gives |.| < 2^56 each), which are
+// then joined in one 63-bit integer, with a rounding of the low word far below the result's
+// last bit, and converted with one rounding
+__device__ __forceinline__ double hd_combine(const int* R, int ex) {
+  long long hi = 0, lo = 0;
+#pragma unroll
+  for (int G = 0; G < 4; ++G) hi += (long long)R[G] * (1ll << (8 * (3 - G)));
+#pragma unroll
+  for (int G = 4; G < HD_G; ++G) lo += (long long)R[G] * (1ll << (8 * (7 - G)));
+  // value = (hi 2^32 + lo) 2^{ex - 56}; shift hi up by s <= 32 so that |hi 2^s| < 2^61
+  const unsigned long long ah = hi < 0 ? 0ull - (unsigned long long)hi : (unsigned long long)hi;
+  const int s = min(max(__clzll((long long)ah) - 3, 0), 32);
+  long long t = (long long)((unsigned long long)hi << s);
+  if (s == 32) t += lo;
+  else t += (lo + (1ll << (31 - s))) >> (32 - s);
+  return fix_to_double(t, ex - 56 - s + 32, false);
+}
+
 // element (r, c) of the Hermitian matrix stored as its lower triangle (column-major)
 __device__ __forceinline__ z64 herm_at(const z64* A, int ld, int r, int c) {
   return c <= r ? A[(size_t)c * ld + r] : zconj(A[(size_t)r * ld + c]);
@@ -240,8 +259,8 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
         const z64* Vr = VW + (size_t)r * LDVW;
         const z64* Vi = VW + (size_t)i * LDVW;
         for (int jj = 0; jj < j; ++jj) {
-          acc = zsub(acc, zmul(Vr[jj], zconj(Vi[NB + jj])));  // V(r,jj) conj(W(i,jj))
-          acc = zsub(acc, zmul(Vr[NB + jj], zconj(Vi[jj])));  // W(r,jj) conj(V(i,jj))
+          acc = zfmsc(Vr[jj], Vi[NB + jj], acc);  // - V(r,jj) conj(W(i,jj))
+          acc = zfmsc(Vr[NB + jj], Vi[jj], acc);  // - W(r,jj) conj(V(i,jj))
         }
         if (r == i) acc.y = 0.0;
         A[(size_t)i * ld + r] = acc;
@@ -377,15 +396,9 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
             RR[G] += __shfl_xor_sync(0xffffffffu, RR[G], o);
             RI[G] += __shfl_xor_sync(0xffffffffu, RI[G], o);
           }
-        if (r >= 0 && wl == 0) {
-          double hr = 0.0, hi = 0.0;
-#pragma unroll
-          for (int G = HD_G - 1; G >= 0; --G) {
-            hr = fma(hr, 0x1p-8, (double)RR[G]);
-            hi = fma(hi, 0x1p-8, (double)RI[G]);
-          }
-          const double sc = ldexp(1.0, erow[(size_t)p * Lmax + rr] + f - 12);
-          pown[r] = zmk(hr * sc, hi * sc);
+        if (r >= 0 && wl < 2) {  // lane 0 the real part, lane 1 the imaginary part
+          double* dst = (double*)&pown[r] + wl;
+          *dst = hd_combine(wl ? RI : RR, erow[(size_t)p * Lmax + rr] + f - 12);
         }
       }
     }
@@ -411,22 +424,13 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
       // partial y over this block's rows: warp-strided over the 2j entries
       for (int jj = wid; jj < 2 * j; jj += nw) {
         const int cidx = jj < j ? NB + jj : jj - j;  // W column jj, or V column jj - j
-        double sre = 0.0, sim = 0.0;
+        z64 acc = zmk(0.0, 0.0);
         for (int g = g0 + lane; g < g1; g += 32) {
           const int ra = g, rb = mt - 1 - g;
-          const z64 a = VW[(size_t)(i + 1 + ra) * LDVW + cidx];
-          const z64 ca = zcfma(a, v[ra], zmk(0.0, 0.0));
-          sre += ca.x;
-          sim += ca.y;
-          if (rb != ra) {
-            const z64 b = VW[(size_t)(i + 1 + rb) * LDVW + cidx];
-            const z64 cb = zcfma(b, v[rb], zmk(0.0, 0.0));
-            sre += cb.x;
-            sim += cb.y;
-          }
+          acc = zcfma(VW[(size_t)(i + 1 + ra) * LDVW + cidx], v[ra], acc);
+          if (rb != ra) acc = zcfma(VW[(size_t)(i + 1 + rb) * LDVW + cidx], v[rb], acc);
         }
-        sre = warp_sum(sre);
-        sim = warp_sum(sim);
+        const double sre = warp_sum(acc.x), sim = warp_sum(acc.y);
         if (lane == 0) ypart[jj] = zmk(sre, sim);
       }
       __syncthreads();
@@ -467,8 +471,8 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
           const z64* row = VW + (size_t)(i + 1 + r) * LDVW;
           z64 acc = pown[r];
           for (int jj = 0; jj < j; ++jj) {
-            acc = zsub(acc, zmul(row[jj], yfull[jj]));           // V(r,jj) (W^H v)_jj
-            acc = zsub(acc, zmul(row[NB + jj], yfull[j + jj]));  // W(r,jj) (V^H v)_jj
+            acc = zfms(row[jj], yfull[jj], acc);           // - V(r,jj) (W^H v)_jj
+            acc = zfms(row[NB + jj], yfull[j + jj], acc);  // - W(r,jj) (V^H v)_jj
           }
           pown[r] = acc;
         }
@@ -476,7 +480,7 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
     cluster.sync();  // S3: corrected pieces of p ready
     if (active) {
       // (e) Procedure 5: w = tau p - (tau/2) ((tau p)^H v) v on the full vector
-      double dre = 0.0, dim = 0.0;
+      z64 dacc = zmk(0.0, 0.0);
       for (int g = tid; g < npairs; g += nt) {
         int k = 0;
         while (k + 1 < C && pair_start(k + 1, npairs, C) <= g) ++k;
@@ -484,18 +488,14 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
         const int ra = g, rb = mt - 1 - g;
         const z64 pa = zmul(t, src[ra]);
         w[ra] = pa;
-        const z64 c1 = zcfma(pa, v[ra], zmk(0.0, 0.0));
-        dre += c1.x;
-        dim += c1.y;
+        dacc = zcfma(pa, v[ra], dacc);
         if (rb != ra) {
           const z64 pb = zmul(t, src[rb]);
           w[rb] = pb;
-          const z64 c2 = zcfma(pb, v[rb], zmk(0.0, 0.0));
-          dre += c2.x;
-          dim += c2.y;
+          dacc = zcfma(pb, v[rb], dacc);
         }
       }
-      const double2 dot = block_sum2(dre, dim, red);
+      const double2 dot = block_sum2(dacc.x, dacc.y, red);
       const z64 alpha2 = zscale(zmul(t, zmk(dot.x, dot.y)), -0.5);
       for (int r = tid; r < mt; r += nt) w[r] = zfma(alpha2, v[r], w[r]);
       __syncthreads();

@@ -27,7 +27,35 @@ __host__ __device__ __forceinline__ z64 zfma(z64 a, z64 b, z64 acc) {
 __host__ __device__ __forceinline__ z64 zcfma(z64 a, z64 b, z64 acc) {
   return zmk(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y)));
 }
+// acc - a*b
+__host__ __device__ __forceinline__ z64 zfms(z64 a, z64 b, z64 acc) {
+  return zmk(fma(-a.x, b.x, fma(a.y, b.y, acc.x)), fma(-a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+// acc - a*conj(b)
+__host__ __device__ __forceinline__ z64 zfmsc(z64 a, z64 b, z64 acc) {
+  return zmk(fma(-a.x, b.x, fma(-a.y, b.y, acc.x)), fma(-a.y, b.x, fma(a.x, b.y, acc.y)));
+}
 __host__ __device__ __forceinline__ double zabs2(z64 a) { return a.x * a.x + a.y * a.y; }
+
+// The double nearest to t 2^ex (ties to even), negated if neg, by integer operations (on
+// this GPU the FP64 pipe, which the int64 -> double conversion and a scaling multiply
+// would use, runs at 1/64 of the integer rate).  Results outside the normal range (not met by the
+// operands of this method) take an FP64 ldexp (a subnormal result may then round twice).
+__device__ __forceinline__ double fix_to_double(long long t, int ex, bool neg) {
+  if (t == 0) return 0.0;
+  const unsigned long long sgn = ((unsigned long long)t >> 63 ^ (neg ? 1ull : 0ull)) << 63;
+  unsigned long long u = t < 0 ? 0ull - (unsigned long long)t : (unsigned long long)t;
+  const int nlz = __clzll((long long)u);
+  u <<= nlz;                                          // leading one at bit 63
+  unsigned long long mant = u >> 11;                  // 53 bits
+  const unsigned int rest = (unsigned int)u & 0x7ffu;  // the 11 bits below them
+  if (rest > 0x400u || (rest == 0x400u && (mant & 1ull))) ++mant;
+  const int e = 63 - nlz + ex;  // exponent of the leading one; a carry out of the rounding
+  if (e >= -1022 && e <= 1022)  // moves it up by one, through the add into the exponent field
+    return __longlong_as_double((long long)((((unsigned long long)(e + 1022) << 52) + mant) | sgn));
+  const double r = ldexp((double)mant, e - 52);
+  return sgn ? -r : r;
+}
 
 // ---------------------------------------------------------------- context
 struct NaoStageStat {
@@ -115,7 +143,7 @@ cudaError_t launch_herm_fill(int n, int nprob, const z64* src, long long src_str
 // One launch reduces the panel of columns i0 .. i0+NAO_HT_NB-1; VW ([nprob][n][3 NB],
 // per row [V | W | V]) receives the panel's reflectors and update vectors, and the caller
 // applies A(i0+NB:, i0+NB:) -= V W^H + W V^H before the next panel.
-constexpr int NAO_HT_NB = 16;
+constexpr int NAO_HT_NB = 32;
 int hetrd_cluster_size(int n, int nprob, int num_sms);
 // dig / erow (nullable): 8-bit digit planes of the trailing matrix made by launch_hetrd_digits
 // for this panel; with them the panel forms its Hermitian matrix-vector products exactly with

@@ -85,6 +85,20 @@ __device__ __forceinline__ long long oz_fixed(double x, int e) {
   return bits < 0 ? -q : q;
 }
 
+// round(x 2^k) for a float x with |x 2^k| < 2^62, by integer arithmetic on the bits of x
+__device__ __forceinline__ long long oz_f32_fixed(float x, int k) {
+  const int b = __float_as_int(x);
+  const int f = (b >> 23) & 0xff;
+  if (f == 0) return 0;  // zero (subnormal sums are below any unit used here)
+  const long long m = (b & 0x7fffff) | 0x800000;  // x = m 2^{f - 150}
+  const int sh = f - 150 + k;
+  long long q;
+  if (sh >= 0) q = m << sh;
+  else if (sh <= -26) q = 0;
+  else q = (m + (1ll << (-sh - 1))) >> (-sh);
+  return b < 0 ? -q : q;
+}
+
 // S signed base-64 digits of q (|q| < 2^{6 S}): q = sum_s d_s 2^{6(S-s)}
 template <int S>
 __device__ __forceinline__ void oz_digits(long long q, int* d) {
@@ -253,7 +267,7 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
   constexpr int NACC = NEX + (MERGED ? 1 : 0);
   constexpr int TMEM_COLS = NACC * OZ_BN <= 128 ? 128 : (NACC * OZ_BN <= 256 ? 256 : 512);
   constexpr int STAGE = S * (OZ_TILE_A + OZ_TILE_B);  // bytes per pipeline stage
-  constexpr double kUnit = oz_pow2(36 - 6 * NEX);     // value of one unit of the last exact group
+  constexpr int kUnitExp = 36 - 6 * NEX;              // one unit of the last exact group is 2^kUnitExp
   extern __shared__ __align__(1024) unsigned char oz_smem[];
   __shared__ uint64_t full_bar[OZ_STAGES], empty_bar[OZ_STAGES], done_bar;
   __shared__ uint32_t tbase;
@@ -386,6 +400,12 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
     const int gi = rb * OZ_BM + row;
     const int half = warp >> 2;
     const int erow = (gi < M) ? rexp[(size_t)p * Mp + gi] : 0;
+    // alpha = +-2^ae goes into the exponent; any other alpha takes one FP64 multiply
+    const long long abits = __double_as_longlong(alpha);
+    const int afield = (int)((abits >> 52) & 0x7ff);
+    const bool amul = (abits & 0xFFFFFFFFFFFFFll) != 0 || afield == 0 || afield == 0x7ff;
+    const int ae = amul ? 0 : afield - 1023;
+    const bool aneg = !amul && abits < 0;
     for (int cc = 0; cc < OZ_BN / 4; cc += 4) {  // 8 C'' columns per round
       const int col0 = half * (OZ_BN / 2) + 2 * cc;
       uint32_t v[NACC][8];
@@ -399,7 +419,10 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
       }
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       if (gi >= M) continue;
-      double part[8];
+      // every output as one exact fixed-point integer t (value t 2^{kUnitExp - sh}), turned
+      // into a double by integer operations: no FP64 instruction unless beta != 0
+      long long t[8];
+      int sh[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         // exact groups g = 2..NEX+1 (accumulator g-2): G_g = n_g 2^{42-6g} with integer n_g;
@@ -411,8 +434,17 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
           const long long ng = (long long)__float2int_rn(ldexpf(gv, -6 * (5 - a)));
           hi += ng * (1ll << (6 * (NEX - 1 - a)));
         }
-        part[c] = (double)hi * kUnit;
-        if (MERGED) part[c] += (double)__uint_as_float(v[NEX][c]);
+        if (MERGED) {
+          // |hi| < 2^59 (2K' <= 1792); shift it up to just below 2^60 and add the merged
+          // groups (|.| < 2^13 in units of 1) rounded to the new unit, which stays below 2^62
+          const unsigned long long ah = hi < 0 ? 0ull - (unsigned long long)hi : (unsigned long long)hi;
+          const int s = min(max(__clzll((long long)ah) - 4, 0), 40);
+          t[c] = (long long)((unsigned long long)hi << s) + oz_f32_fixed(__uint_as_float(v[NEX][c]), s - kUnitExp);
+          sh[c] = s;
+        } else {
+          t[c] = hi;
+          sh[c] = 0;
+        }
       }
       if (REAL) {
         double* Cp = (double*)Cv + (size_t)p * Cbs;
@@ -420,11 +452,10 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
         for (int c = 0; c < 8; ++c) {
           const int gj = cb * OZ_BN + col0 + c;
           if (gj >= N) continue;
-          int E = erow + cexp[(size_t)p * N2p + gj] - 42;
-          E = E < -1022 ? -1022 : (E > 1023 ? 1023 : E);
-          const double sc = __longlong_as_double((long long)(E + 1023) << 52) * alpha;
+          const int ex = erow + cexp[(size_t)p * N2p + gj] - 42 + kUnitExp + ae;
           double* cp = Cp + (long long)gi * Crs + (long long)gj * Ccs;
-          double r = part[c] * sc;
+          double r = fix_to_double(t[c], ex - sh[c], aneg);
+          if (amul) r *= alpha;
           if (beta != 0.0) r = fma(beta, *cp, r);
           *cp = r;
         }
@@ -434,11 +465,14 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
         for (int q = 0; q < 4; ++q) {
           const int gj = cb * (OZ_BN / 2) + half * (OZ_BN / 4) + cc + q;  // complex column
           if (gj >= N) continue;
-          int E = erow + cexp[(size_t)p * (N2p / 2) + gj] - 42;
-          E = E < -1022 ? -1022 : (E > 1023 ? 1023 : E);
-          const double sc = __longlong_as_double((long long)(E + 1023) << 52) * alpha;
+          const int ex = erow + cexp[(size_t)p * (N2p / 2) + gj] - 42 + kUnitExp + ae;
           z64* cp = Cp + (long long)gi * Crs + (long long)gj * Ccs;
-          z64 r = zmk(part[2 * q] * sc, part[2 * q + 1] * sc);
+          z64 r = zmk(fix_to_double(t[2 * q], ex - sh[2 * q], aneg),
+                      fix_to_double(t[2 * q + 1], ex - sh[2 * q + 1], aneg));
+          if (amul) {
+            r.x *= alpha;
+            r.y *= alpha;
+          }
           if (beta != 0.0) {
             const z64 old = *cp;
             r.x = fma(beta, old.x, r.x);
