@@ -90,9 +90,14 @@ int nao_zgemm(nao_ctx* ctx, int method, int nprob, int M, int N, int K, double a
  * when MR[a][r][i][j] = MR[a][r'][j][i] for the image r' = -R[r] (caller's contract).
  *   n     basis size (>= 1);  nR images (>= 1);  nmat matrices (e.g. spin channels, >= 1)
  *   R     int32 [nR][3] integer cell vectors (device)
- *   MR    float64 [nmat][nR][n][n] real-space blocks (device); only i >= j is read
+ *   MR    float64 [nmat][nR][n][n] real-space blocks (device); only i >= j enters the
+ *         result (the tensor-core form reads all n^2 entries and discards the upper ones)
  *   kpts  float64 [nk][3] fractional k-points (device)
- *   Mk    complex128 [nmat][nk][n][n] output (device)                                    */
+ *   Mk    complex128 [nmat][nk][n][n] output (device)
+ * With NAO_GEMM_TC (the default) and nk >= 8 the sum is one FP64-accurate tensor-core
+ * product per chunk of rows (phase matrix [cos; sin] times the element columns; the
+ * context's workspace grows by up to 256 MB); otherwise FP64 FMAs.  A tensor-core wait that
+ * expired shows as NAO_E_TIMEOUT in the status of the context's next nao_gen_eig.          */
 int nao_bloch_sum(nao_ctx* ctx, int n, int nR, const int32_t* R, int nmat, const double* MR,
                   int nk, const double* kpts, nao_c128* Mk, void* stream);
 
@@ -139,6 +144,8 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
  *   rhoR[sigma][r][i][j] = Re[ g sum_q wk[q] sum_{j'} f c_{i j'} conj(c_{j j'})
  *                              exp(-2 pi i kpts[q].R[r]) ],
  *   edmR: the same with weights f eps instead of f.
+ * The k sum runs, like Part 1's, as FP64-accurate tensor-core products (cos Re P + sin Im P)
+ * with NAO_GEMM_TC and nk >= 8, else with FP64 FMAs.
  *   eps, C, m_kept as written by nao_gen_eig (C [nprob][n][nb]); bands j >= nb must be
  *     unoccupied (f <= 1e-16), else status NAO_E_INVALID is written.
  *   mu_out, eband_out  float64 [1] out (device);  f_out float64 [nprob][n] out or NULL

@@ -78,6 +78,11 @@ NaoStage::NaoStage(nao_ctx* c, const char* name, cudaStream_t s, int nlaunch) : 
   cudaEventRecord(a, s);
 }
 
+void NaoStage::add_launches(int k) {
+  ctx->launches += k;
+  if (idx >= 0) ctx->stages[idx].launches += k;
+}
+
 NaoStage::~NaoStage() {
   if (idx < 0 || !a) return;
   cudaEvent_t b = take_event(ctx);
@@ -224,7 +229,10 @@ struct DensityPlan {
   size_t bytes;
 };
 
-DensityPlan plan_density(int n, int nprob, int nb, int num_sms, bool use_tc, bool edm) {
+// The phase sum of Part 6 (rho_tc: on the tensor cores) reuses the product workspace oOz:
+// it runs after the P(k) product, in stream order.
+DensityPlan plan_density(int n, int nspin, int nk, int nR, int nb, int num_sms, bool use_tc, bool rho_tc, bool edm) {
+  const int nprob = nspin * nk;
   DensityPlan W;
   WsPlan P;
   W.of = P.take<double>((size_t)nprob * n);
@@ -234,7 +242,12 @@ DensityPlan plan_density(int n, int nprob, int nb, int num_sms, bool use_tc, boo
   W.oCs = P.take<z64>((size_t)nprob * n * nb);
   W.oCe = P.take<z64>(edm ? (size_t)nprob * n * nb : 1);
   W.oP = P.take<z64>((size_t)n * n * nprob);
-  W.oOz = P.take<char>(use_tc ? zgemm_oz_workspace(nprob, GemmDims{n, n, nb, nullptr, nullptr, nullptr, 0}) : 1);
+  size_t oz = use_tc ? zgemm_oz_workspace(nprob, GemmDims{n, n, nb, nullptr, nullptr, nullptr, 0}) : 1;
+  if (rho_tc) {
+    const size_t r = rho_phase_tc_ws_bytes(n, nspin, nk, nR);
+    if (r > oz) oz = r;
+  }
+  W.oOz = P.take<char>(oz);
   W.bytes = P.off;
   return W;
 }
@@ -345,10 +358,14 @@ size_t gen_eig_ws_bytes(const nao_ctx* ctx, int n, int nprob, int nSe) {
   return plan_gen_eig(n, nprob, nSe, use_tc).bytes;
 }
 
-size_t density_ws_bytes(const nao_ctx* ctx, int n, int nprob, int nb) {
+size_t density_ws_bytes(const nao_ctx* ctx, int n, int nspin, int nk, int nR, int nb) {
   const bool use_tc =
       ctx->gemm_method == NAO_GEMM_TC && zgemm_oz_supported(GemmDims{n, n, nb, nullptr, nullptr, nullptr, 0});
-  return plan_density(n, nprob, nb, ctx->num_sms, use_tc, false).bytes;
+  return plan_density(n, nspin, nk, nR, nb, ctx->num_sms, use_tc, use_tc && nk >= NAO_PHASE_TC_MIN_NK, false).bytes;
+}
+
+size_t bloch_ws_bytes(const nao_ctx* ctx, int n, int nR, int nmat, int nk) {
+  return ctx->gemm_method == NAO_GEMM_TC && nk >= NAO_PHASE_TC_MIN_NK ? bloch_tc_ws_bytes(n, nR, nmat, nk) : 0;
 }
 
 extern "C" {
@@ -482,6 +499,16 @@ int nao_bloch_sum(nao_ctx* ctx, int n, int nR, const int32_t* R, int nmat, const
   if ((size_t)8 * nR * 2 > 200 * 1024) return nao_fail(ctx, NAO_E_INVALID, "nao_bloch_sum: nR too large");
   DeviceGuard g(ctx->device);
   cudaStream_t st = as_stream(stream);
+  if (ctx->gemm_method == NAO_GEMM_TC && nk >= NAO_PHASE_TC_MIN_NK) {
+    const int rc = nao_ws_reserve(ctx, bloch_tc_ws_bytes(n, nR, nmat, nk));
+    if (rc) return rc;
+    NaoStage stage_(ctx, "bloch_sum", st, 0);
+    int nl = 0;
+    const cudaError_t e = launch_bloch_sum_tc(n, nR, R, nmat, MR, nk, kpts, (z64*)Mk, ctx->ws, ctx->dev_flags, st, &nl);
+    stage_.add_launches(nl);
+    NAO_CUDA_TRY(ctx, e);
+    return NAO_OK;
+  }
   NAO_STAGE("bloch_sum", 1, launch_bloch_sum(n, nR, R, nmat, MR, nk, kpts, (z64*)Mk, st));
   return NAO_OK;
 }
@@ -668,7 +695,8 @@ int nao_density_matrix(nao_ctx* ctx, int n, int nspin, int nk, const double* wk,
   const double gdeg = (nspin == 1) ? 2.0 : 1.0;
   const GemmDims dP{n, n, nb, nullptr, nullptr, nullptr, 0};
   const bool use_tc = ctx->gemm_method == NAO_GEMM_TC && zgemm_oz_supported(dP);
-  const DensityPlan W = plan_density(n, nprob, nb, ctx->num_sms, use_tc, edmR != nullptr);
+  const bool rho_tc = use_tc && nk >= NAO_PHASE_TC_MIN_NK;
+  const DensityPlan W = plan_density(n, nspin, nk, nR, nb, ctx->num_sms, use_tc, rho_tc, edmR != nullptr);
   const size_t of = W.of, onocc = W.onocc, oscr = W.oscr, ost = W.ost, oCs = W.oCs, oP = W.oP, oOz = W.oOz;
   int rc = nao_ws_reserve(ctx, W.bytes);
   if (rc) return rc;
@@ -689,7 +717,19 @@ int nao_density_matrix(nao_ctx* ctx, int n, int nspin, int nk, const double* wk,
                                 GemmOperand{Cs, (long long)n * nb, 1, nb, 1, nullptr}, 0.0, Pk, (long long)nn, n, 1,
                                 use_tc ? (void*)(ws + oOz) : nullptr, st));
   }
-  NAO_STAGE("rho_phase", 1, launch_rho_phase_sum(n, nspin, nk, nR, R, kpts, wk, gdeg, Pk, rhoR, st));
+  auto phase_sum = [&](double* out) -> cudaError_t {
+    if (!rho_tc) {
+      NaoStage stage_(ctx, "rho_phase", st, 1);
+      return launch_rho_phase_sum(n, nspin, nk, nR, R, kpts, wk, gdeg, Pk, out, st);
+    }
+    NaoStage stage_(ctx, "rho_phase", st, 0);
+    int nl = 0;
+    const cudaError_t e = launch_rho_phase_tc(n, nspin, nk, nR, R, kpts, wk, gdeg, Pk, out, ws + oOz, ctx->dev_flags,
+                                              st, &nl);
+    stage_.add_launches(nl);
+    return e;
+  };
+  NAO_CUDA_TRY(ctx, phase_sum(rhoR));
   if (edmR) {  // Part 6's energy density matrix: P_E(k) = Cs diag(eps) Cs^H, the same phase sum
     z64* Ce = (z64*)(ws + W.oCe);
     NAO_STAGE("misc", 1, launch_scale_cols_eps(n, nprob, nb, Cs, f, eps, Ce, st));
@@ -697,7 +737,7 @@ int nao_density_matrix(nao_ctx* ctx, int n, int nspin, int nk, const double* wk,
     NAO_CUDA_TRY(ctx, run_zgemm(ctx, "zgemm_P", nprob, d, 1.0, GemmOperand{Ce, (long long)n * nb, nb, 1, 0, nullptr},
                                 GemmOperand{Cs, (long long)n * nb, 1, nb, 1, nullptr}, 0.0, Pk, (long long)nn, n, 1,
                                 use_tc ? (void*)(ws + oOz) : nullptr, st));
-    NAO_STAGE("rho_phase", 1, launch_rho_phase_sum(n, nspin, nk, nR, R, kpts, wk, gdeg, Pk, edmR, st));
+    NAO_CUDA_TRY(ctx, phase_sum(edmR));
   }
   return NAO_OK;
 }

@@ -75,7 +75,7 @@ __device__ __forceinline__ double2 block_sum2(double a, double b, double* red) {
 //    Re a Re v + Im a (-Im v) (-Im v is split as its own
 //    value, so no digit is negated), RI_G the cross terms, for G <= 7 (the orders beyond are
 //    below 2^-68 of the row scale);
-//  * p_r = 2^{e_r + f - 12} sum_G (RR_G + i RI_G) 2^{-8 G}, combined in FP64.
+//  * p_r = 2^{e_r + f - 12} sum_G (RR_G + i RI_G) 2^{-8 G}, combined in integer arithmetic.
 // Digit layout: dig[p][rr][w][16 words], rr = r - (i0 + 1), word w holds columns
 // i0 + 1 + 4w .. +3 (4 int8 lanes) of plane s, part t at word index 2 s + t.
 constexpr int HD_S = 8;      // digits per value

@@ -87,7 +87,8 @@ struct nao_ctx {
 // Workspace bytes nao_gen_eig / nao_density_matrix reserve on this context (before the
 // arena's 1/8 headroom); the scheduler's admission test uses them.
 size_t gen_eig_ws_bytes(const nao_ctx* ctx, int n, int nprob, int nSe);
-size_t density_ws_bytes(const nao_ctx* ctx, int n, int nprob, int nb);
+size_t density_ws_bytes(const nao_ctx* ctx, int n, int nspin, int nk, int nR, int nb);
+size_t bloch_ws_bytes(const nao_ctx* ctx, int n, int nR, int nmat, int nk);  // 0: no workspace
 // Stops the scheduler thread of ctx (if any), waits for its batches, frees its memory.
 void serve_shutdown(nao_ctx* ctx);
 
@@ -99,6 +100,7 @@ struct NaoStage {
   cudaEvent_t a = nullptr;
   NaoStage(nao_ctx* c, const char* name, cudaStream_t s, int nlaunch);
   ~NaoStage();
+  void add_launches(int k);  // kernels counted after the stage began
 };
 
 // Bump allocator over the context's workspace (256-byte aligned slices).
@@ -230,6 +232,7 @@ cudaError_t launch_zgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand 
 // The same method for real float64 operands (C = alpha op(A) op(B) + beta C, K <= 1792);
 // fits in the workspace of a complex product of the same M, N, K.
 bool dgemm_oz_supported(GemmDims dims);
+size_t dgemm_oz_workspace(int nprob, GemmDims dims);  // bytes of ws for launch_dgemm_oz
 cudaError_t launch_dgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta, double* C,
                             long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st,
                             int digits = NAO_OZ_DIGITS_FP64);
@@ -273,3 +276,13 @@ cudaError_t launch_scale_cols_eps(int n, int nprob, int nb, const z64* Cs, const
                                   cudaStream_t st);
 cudaError_t launch_rho_phase_sum(int n, int nspin, int nk, int nR, const int32_t* R, const double* kpts,
                                  const double* wk, double g, const z64* P, double* rho, cudaStream_t st);
+// The same two phase sums as FP64-accurate tensor-core GEMMs (digit planes), for k grids
+// of at least NAO_PHASE_TC_MIN_NK points; ws holds *_ws_bytes; *nlaunch counts the kernels.
+constexpr int NAO_PHASE_TC_MIN_NK = 8;
+size_t bloch_tc_ws_bytes(int n, int nR, int nmat, int nk);
+cudaError_t launch_bloch_sum_tc(int n, int nR, const int32_t* R, int nmat, const double* MR, int nk,
+                                const double* kpts, z64* Mk, void* ws, int* err, cudaStream_t st, int* nlaunch);
+size_t rho_phase_tc_ws_bytes(int n, int nspin, int nk, int nR);
+cudaError_t launch_rho_phase_tc(int n, int nspin, int nk, int nR, const int32_t* R, const double* kpts,
+                                const double* wk, double g, const z64* P, double* rho, void* ws, int* err,
+                                cudaStream_t st, int* nlaunch);

@@ -570,6 +570,12 @@ cudaError_t launch_zgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand 
 
 bool dgemm_oz_supported(GemmDims dims) { return dims.M > 0 && dims.N > 0 && dims.K > 0; }
 
+size_t dgemm_oz_workspace(int nprob, GemmDims dims) {
+  const int Kc = dims.K < OZ_CHUNK_R ? dims.K : OZ_CHUNK_R;
+  const int Mp = round_up(dims.M, OZ_BM), Np = round_up(dims.N, OZ_BN), Kp = round_up(Kc, OZ_BK);
+  return (size_t)nprob * OZ_S * ((size_t)Mp + Np) * Kp * 2 + (size_t)nprob * ((size_t)Mp + Np) * sizeof(int) + 4096;
+}
+
 cudaError_t launch_dgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta, double* C,
                             long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st,
                             int digits) {

@@ -155,7 +155,7 @@ void CUDART_CB slot_done_cb(void* arg) {
 size_t NaoServerCore::batch_bytes(const std::vector<ServeReq*>& rs, size_t* req_bytes, size_t* ws_need) const {
   const int n = rs[0]->rq.n, nb = rs[0]->nb;
   size_t rb = 0;
-  int P = 0, NS = 0, maxp = 0;
+  int P = 0, NS = 0;
   for (ServeReq* r : rs) {
     const nao_request& q = r->rq;
     size_t b = elems_bytes((size_t)q.nspin * q.nR * n * n, 8) + elems_bytes((size_t)q.nR * n * n, 8) +
@@ -165,13 +165,17 @@ size_t NaoServerCore::batch_bytes(const std::vector<ServeReq*>& rs, size_t* req_
     rb += b;
     P += r->nprob;
     NS += q.nk;
-    if (r->nprob > maxp) maxp = r->nprob;
   }
   size_t bb = elems_bytes((size_t)P * n * n, 16) + elems_bytes((size_t)NS * n * n, 16) + elems_bytes(P, 4) +
               elems_bytes((size_t)P * n, 8) + elems_bytes((size_t)P * n * nb, 16) + 2 * elems_bytes(P, 4);
   size_t ws = gen_eig_ws_bytes(owner, n, P, NS);
-  const size_t wd = density_ws_bytes(owner, n, maxp, nb);
-  if (wd > ws) ws = wd;
+  for (ServeReq* r : rs) {  // Parts 1 and 5-6 run per request in the same workspace
+    const nao_request& q = r->rq;
+    const size_t wd = density_ws_bytes(owner, n, q.nspin, q.nk, q.nR, nb);
+    const size_t wb = bloch_ws_bytes(owner, n, q.nR, q.nspin, q.nk);
+    if (wd > ws) ws = wd;
+    if (wb > ws) ws = wb;
+  }
   *req_bytes = rb;
   *ws_need = ws + ws / 8;
   return rb + bb;

@@ -37,8 +37,11 @@ def _compare_all(inp, g, ref, nb=None):
         assert int(g["status"][p]) == 0
 
 
-def test_bloch_sum_matches_oracle(ctx):
-    inp = synth.small_cell(21, 2, 3, kgrid=(3, 2, 1), nspin=2)
+@pytest.mark.parametrize("kgrid", [(3, 2, 1), (3, 3, 2), (5, 5, 3)], ids=["nk6", "nk18", "nk75"])
+def test_bloch_sum_matches_oracle(ctx, kgrid):
+    # nk >= 8 takes the tensor-core form with the tc context: 2 nk = 36 rows (one ragged
+    # tile) and 150 rows (two tiles)
+    inp = synth.small_cell(21, 2, 3, kgrid=kgrid, nspin=2)
     g = gpu_band_step(ctx, inp, torch, DEV, density=False)
     Hk = oracle.bloch_sum(inp.HR, inp.R, inp.kpts).reshape(-1, inp.n, inp.n)
     Sk = oracle.bloch_sum(inp.SR, inp.R, inp.kpts)
@@ -68,7 +71,8 @@ def test_bloch_sum_hand_values(ctx):
     lambda: synth.small_cell(31, 1, 2, kgrid=(2, 1, 1), nspin=2),       # n = 29
     lambda: synth.small_cell(32, 3, 5, kgrid=(2, 2, 1), nspin=1),       # n = 79
     lambda: synth.small_cell(33, 5, 8, kgrid=(1, 2, 1), nspin=2),       # n = 129: several tiles + ragged tail
-], ids=["tiny64", "n29", "n79", "n129"])
+    lambda: synth.small_cell(37, 2, 4, kgrid=(3, 3, 1), nspin=2),       # nk = 9: tensor-core phase sums
+], ids=["tiny64", "n29", "n79", "n129", "nk9"])
 def test_band_step_matches_oracle(ctx, maker):
     inp = maker()
     g = gpu_band_step(ctx, inp, torch, DEV)
