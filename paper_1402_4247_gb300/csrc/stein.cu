@@ -14,8 +14,10 @@
 //     2. the FP32 bracket, widened by 64 eps_32 |T| (an FP32 count is exact for a matrix
 //        within a few eps_32 |T| of T), is verified with two FP64 counts (the full
 //        Gershgorin interval replaces it if a count disagrees);
-//     3. FP64 bisection closes the bracket to eps |T| in a number of steps that is nearly the
-//        same for every lane.
+//     3. an eigenvalue that the bracket isolates is finished by safeguarded Newton steps on
+//        the characteristic polynomial and confirmed by two FP64 counts; the others (and
+//        any unconfirmed one) are queued and bisected in FP64 to eps |T| by a second kernel,
+//        one thread per queue entry, so that its warps are full.
 // * Eigenvectors (kernel 2, same block split): inverse iteration with a partially pivoted LU
 //   of T - lambda I (tiny pivots perturbed to eps |T|), a scaled right-hand side, the growth
 //   test |x|_inf >= sqrt(0.1/blocksize) plus two extra solves, and modified Gram-Schmidt
@@ -42,6 +44,7 @@ constexpr int EXTRA = 2;          // extra solves after the growth test passes
 constexpr double TIGHT = 1e-7;
 constexpr int NARR = 6;           // scratch arrays per eigenvalue: L, U0inv, U1, U2, PIV, X
 constexpr int BIG = 32;           // tight clusters with more members go to stein_cluster_kernel
+constexpr int NEWTON_MAX = 6;     // Newton steps on an isolated eigenvalue before it is queued
 
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
@@ -190,10 +193,44 @@ __device__ __forceinline__ double hash_uniform(unsigned long long key) {
   return (double)(key >> 11) * 0x1p-52 - 1.0;
 }
 
+// Safeguarded Newton steps on p_n inside a bracket [lo, hi] that isolates eigenvalue idx of
+// T[b0:b1) (count(lo) = idx, count(hi) = idx + 1); every evaluation's count narrows the
+// bracket.  True when lam is confirmed by two FP64 counts within 2 tol, tol = max(2 eps |x|,
+// eps |T|) (the bisection's final bracket width; the margin covers the counts' own backward
+// error of a few eps |T|).  A step within rounding of the root may leave the one-sided
+// bracket, so convergence is tested before the step is kept inside it.
+__device__ bool newton_finish(const double* __restrict__ d, const double* __restrict__ e2, int b0, int b1, int idx,
+                              double tnorm, double& lo, double& hi, int& clo, int& chi, double& lam) {
+  const double eps = DBL_EPSILON * 0.5;
+  double x = 0.5 * (lo + hi);
+  for (int it = 0; it < NEWTON_MAX; ++it) {
+    double pn, dpn;
+    const int c = sturm64(d, e2, b0, b1, x, true, &pn, &dpn);
+    if (c > idx) {
+      hi = x;
+      chi = c;
+    } else {
+      lo = x;
+      clo = c;
+    }
+    const double tol = fmax(2.0 * eps * fabs(x), eps * tnorm);
+    double xn = x - pn / dpn;
+    if (fabs(xn - x) <= tol) {
+      lam = xn;
+      return sturm64(d, e2, b0, b1, xn - 2.0 * tol, false, nullptr, nullptr) <= idx &&
+             sturm64(d, e2, b0, b1, xn + 2.0 * tol, false, nullptr, nullptr) > idx;
+    }
+    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);  // outside, or not finite: bisect
+    x = xn;
+  }
+  return false;
+}
+
 // ---------------------------------------------------------------- kernel 1: eigenvalues
 __global__ void __launch_bounds__(SZ_THREADS)
 stebz_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ dbase, const double* __restrict__ ebase,
-             long long strideV, double* __restrict__ wslot, int32_t* __restrict__ status) {
+             long long strideV, double* __restrict__ wslot, int32_t* __restrict__ status, int* __restrict__ qcount,
+             int* __restrict__ qslot, double* __restrict__ qlo, double* __restrict__ qhi) {
   extern __shared__ double smd[];
   double* d = smd;
   double* e = smd + n;
@@ -244,20 +281,64 @@ stebz_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__
       lo = T.gl;
       hi = T.gu;
     }
-    // FP64 bisection to eps |T|.  Every lane starts from a bracket of the same width (the
-    // verified FP32 one), so the lanes of a warp run the same number of steps: the FP64 pipe
-    // (1/64 of FP32 here) sees full warps.  (A Newton shortcut for isolated eigenvalues took
-    // fewer steps per lane but left ~2/3 of the lanes idle through divergence.)
-    for (int it = 0; it < 128; ++it) {
-      const double mid = 0.5 * (lo + hi);
-      const double tol = fmax(2.0 * eps * fmax(fabs(lo), fabs(hi)), eps * T.tnorm);
-      if (hi - lo <= tol || mid <= lo || mid >= hi) break;
-      if (sturm64(d, e2, b0, b1, mid, false, nullptr, nullptr) > idx) hi = mid;
-      else lo = mid;
+    // 3. An eigenvalue that the bracket isolates is finished by newton_finish.  Every other
+    //    one (a cluster the FP32 bracket does not split, or no confirmed convergence) goes
+    //    to a queue that a second kernel bisects with full warps: bisecting it here would
+    //    hold the whole warp for ~40 FP64 steps.
+    int cl = clo, ch = chi;
+    if (!(cl <= idx && idx < ch)) {
+      cl = 0;
+      ch = b1 - b0;
     }
-    lam = 0.5 * (lo + hi);
+    bool ok = false;
+    if (cl == idx && ch == idx + 1) ok = newton_finish(d, e2, b0, b1, idx, T.tnorm, lo, hi, cl, ch, lam);
+    if (!ok) {
+      const int k = atomicAdd(&qcount[p], 1);
+      const size_t o = (size_t)p * n + k;
+      qslot[o] = j;
+      qlo[o] = lo;
+      qhi[o] = hi;
+      return;
+    }
   }
   wslot[(size_t)p * n + j] = lam;
+}
+
+// Kernel 1b: FP64 bisection of the queued eigenvalues of each problem, one thread per queue
+// entry, so that the warps are full.  Entries carry their verified bracket.  (Switching a
+// lane to Newton once its bracket isolates the eigenvalue was measured slower: the lanes of
+// a warp reach isolation at different steps, so the two paths serialise.)
+__global__ void __launch_bounds__(SZ_THREADS)
+stebz_bisect_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ dbase,
+                    const double* __restrict__ ebase, long long strideV, double* __restrict__ wslot,
+                    const int* __restrict__ qcount, const int* __restrict__ qslot, const double* __restrict__ qlo,
+                    const double* __restrict__ qhi) {
+  extern __shared__ double smd[];
+  double* d = smd;
+  double* e = smd + n;
+  double* e2 = smd + 2 * n;
+  int* bst = (int*)(smd + 3 * n);
+  int* ben = bst + n;
+  __shared__ double red[96];
+  const int p = blockIdx.y;
+  const int m = size ? size[p] : n;
+  const int nq = qcount[p];
+  if (m <= 0 || (int)(blockIdx.x * blockDim.x) >= nq) return;  // uniform per block
+  const TriInfo T = load_tridiag(m, dbase + (size_t)p * strideV, ebase + (size_t)p * strideV, d, e, e2, bst, ben, red);
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const double eps = DBL_EPSILON * 0.5;
+  const int j = qslot[(size_t)p * n + q];
+  const int b0 = bst[j], b1 = ben[j], idx = j - b0;
+  double lo = qlo[(size_t)p * n + q], hi = qhi[(size_t)p * n + q];
+  for (int it = 0; it < 128; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    const double tol = fmax(2.0 * eps * fmax(fabs(lo), fabs(hi)), eps * T.tnorm);
+    if (hi - lo <= tol || mid <= lo || mid >= hi) break;
+    if (sturm64(d, e2, b0, b1, mid, false, nullptr, nullptr) > idx) hi = mid;
+    else lo = mid;
+  }
+  wslot[(size_t)p * n + j] = 0.5 * (lo + hi);
 }
 
 // ---------------------------------------------------------------- kernel 2: eigenvectors
@@ -706,8 +787,21 @@ cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d,
   const size_t smem1 = sizeof(double) * 3 * (size_t)n + sizeof(float) * 2 * (size_t)n + sizeof(int) * 2 * (size_t)n;
   cudaError_t err = cudaFuncSetAttribute(stebz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
   if (err != cudaSuccess) return err;
+  // the bisection queue lives in the inverse-iteration scratch, unused until kernel 2
+  double* qlo = scratch;
+  double* qhi = qlo + (size_t)n * nprob;
+  int* qslot = (int*)(qhi + (size_t)n * nprob);
+  int* qcount = qslot + (size_t)n * nprob;
+  err = cudaMemsetAsync(qcount, 0, sizeof(int) * nprob, st);
+  if (err != cudaSuccess) return err;
   dim3 grid1((n + SZ_THREADS - 1) / SZ_THREADS, nprob);
-  stebz_kernel<<<grid1, SZ_THREADS, smem1, st>>>(n, size, d, e, strideV, wslot, status);
+  stebz_kernel<<<grid1, SZ_THREADS, smem1, st>>>(n, size, d, e, strideV, wslot, status, qcount, qslot, qlo, qhi);
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const size_t smem1b = sizeof(double) * 3 * (size_t)n + sizeof(int) * 2 * (size_t)n;
+  err = cudaFuncSetAttribute(stebz_bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1b);
+  if (err != cudaSuccess) return err;
+  stebz_bisect_kernel<<<grid1, SZ_THREADS, smem1b, st>>>(n, size, d, e, strideV, wslot, qcount, qslot, qlo, qhi);
   dim3 grid((n + ST_THREADS - 1) / ST_THREADS, nprob);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
