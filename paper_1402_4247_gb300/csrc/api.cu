@@ -322,12 +322,14 @@ cudaError_t hetrd_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, z
   const long long snn = (long long)n * n, svw = (long long)n * 3 * NB;
   for (int i0 = 0; i0 < n; i0 += NB) {
     cudaError_t err = cudaSuccess;
-    {
-      NaoStage stage_(ctx, "hetrd", st, use_dig ? 2 : 1);
-      if (use_dig) err = launch_hetrd_digits(n, nprob, size, A, n, snn, i0, dig, erow, st);
-      if (err == cudaSuccess)
-        err = launch_hetrd_panel(n, nprob, size, A, n, snn, d, e, tau, n, VW, svw, i0, cl, use_dig ? dig : nullptr,
-                                 erow, st);
+    if (use_dig) {
+      NaoStage stage_(ctx, "hetrd_digits", st, 1);
+      err = launch_hetrd_digits(n, nprob, size, A, n, snn, i0, dig, erow, st);
+    }
+    if (err == cudaSuccess) {
+      NaoStage stage_(ctx, "hetrd", st, 1);
+      err = launch_hetrd_panel(n, nprob, size, A, n, snn, d, e, tau, n, VW, svw, i0, cl, use_dig ? dig : nullptr,
+                               erow, st);
     }
     if (err != cudaSuccess) return err;
     const int r0 = i0 + NB;
