@@ -11,11 +11,11 @@
 //   count, three operations per step.
 //     1. bisection in FP32 (64x the FP64 rate on this GPU) to ~1e-7 |T|, counting negative
 //        pivots of the LDL^T form with a fast reciprocal;
-//     2. the FP32 bracket, widened by 64 eps_32 |T| (an FP32 count is exact for a matrix
+//     2. the FP32 bracket, widened by 8 eps_32 |T| (an FP32 count is exact for a matrix
 //        within a few eps_32 |T| of T), is verified with two FP64 counts (the full
 //        Gershgorin interval replaces it if a count disagrees);
 //     3. an eigenvalue that the bracket isolates is finished by safeguarded Newton steps on
-//        the characteristic polynomial and confirmed by two FP64 counts; the others (and
+//        the characteristic polynomial and confirmed by FP64 counts; the others (and
 //        any unconfirmed one) are queued and bisected in FP64 to eps |T| by a second kernel,
 //        one thread per queue entry, so that its warps are full.
 // * Eigenvectors (kernel 2, same block split): inverse iteration with a partially pivoted LU
@@ -195,9 +195,9 @@ __device__ __forceinline__ double hash_uniform(unsigned long long key) {
 
 // Safeguarded Newton steps on p_n inside a bracket [lo, hi] that isolates eigenvalue idx of
 // T[b0:b1) (count(lo) = idx, count(hi) = idx + 1); every evaluation's count narrows the
-// bracket.  True when lam is confirmed by two FP64 counts within 2 tol, tol = max(2 eps |x|,
-// eps |T|) (the bisection's final bracket width; the margin covers the counts' own backward
-// error of a few eps |T|).  A step within rounding of the root may leave the one-sided
+// bracket.  True when lam is confirmed within 2 tol, tol = max(2 eps |x|, eps |T|) (the
+// bisection's final bracket width; the margin covers the counts' own backward error of a few
+// eps |T|), by the last iterate's count on one side and one more FP64 count on the other.  A step within rounding of the root may leave the one-sided
 // bracket, so convergence is tested before the step is kept inside it.
 __device__ bool newton_finish(const double* __restrict__ d, const double* __restrict__ e2, int b0, int b1, int idx,
                               double tnorm, double& lo, double& hi, int& clo, int& chi, double& lam) {
@@ -216,9 +216,11 @@ __device__ bool newton_finish(const double* __restrict__ d, const double* __rest
     const double tol = fmax(2.0 * eps * fabs(x), eps * tnorm);
     double xn = x - pn / dpn;
     if (fabs(xn - x) <= tol) {
+      // x's count fixed one side of lambda (|xn - x| <= tol); one count 2 tol beyond xn on
+      // the other side closes the bracket within [xn - 2 tol, xn + 2 tol]
       lam = xn;
-      return sturm64(d, e2, b0, b1, xn - 2.0 * tol, false, nullptr, nullptr) <= idx &&
-             sturm64(d, e2, b0, b1, xn + 2.0 * tol, false, nullptr, nullptr) > idx;
+      return c > idx ? sturm64(d, e2, b0, b1, xn - 2.0 * tol, false, nullptr, nullptr) <= idx
+                     : sturm64(d, e2, b0, b1, xn + 2.0 * tol, false, nullptr, nullptr) > idx;
     }
     if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);  // outside, or not finite: bisect
     x = xn;
@@ -273,7 +275,9 @@ stebz_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__
       else lo32 = mid;
     }
     // 2. FP64 bracket from it, verified
-    const double margin = 64.0 * (double)FLT_EPSILON * T.tnorm;
+    // the FP32 midpoint was measured within 1.9 eps_32 |T| of the eigenvalue (matrices of
+    // the magnetite-shaped cell); 8 eps_32 |T| on each side, and the FP64 counts check it
+    const double margin = 8.0 * (double)FLT_EPSILON * T.tnorm;
     double lo = fmax((double)lo32 - margin, T.gl), hi = fmin((double)hi32 + margin, T.gu);
     const int clo = sturm64(d, e2, b0, b1, lo, false, nullptr, nullptr);
     const int chi = sturm64(d, e2, b0, b1, hi, false, nullptr, nullptr);
