@@ -316,9 +316,10 @@ cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t*
 cudaError_t hetrd_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, z64* A, double* d, double* e, z64* tau,
                           z64* VW, void* ozws, cudaStream_t st, int digits, void* dig, int* erow) {
   // exact integer matrix-vector products with the tensor-core method; FP64 FMAs otherwise
-  const bool use_dig = ctx->gemm_method == NAO_GEMM_TC && dig != nullptr;
+  // (up to the order whose digit words still fit in a block's shared memory)
+  const bool use_dig = ctx->gemm_method == NAO_GEMM_TC && dig != nullptr && hetrd_digits_fit(n);
   const int NB = NAO_HT_NB;
-  const int cl = hetrd_cluster_size(n, nprob, ctx->num_sms);
+  const int cl = hetrd_cluster_size(n, nprob, ctx->num_sms, use_dig);
   const long long snn = (long long)n * n, svw = (long long)n * 3 * NB;
   for (int i0 = 0; i0 < n; i0 += NB) {
     cudaError_t err = cudaSuccess;

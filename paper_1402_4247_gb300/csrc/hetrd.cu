@@ -34,6 +34,7 @@ namespace {
 
 constexpr int HT_THREADS = 1024;
 constexpr int HT_MAXK = 8;  // threads per row pair
+constexpr int HT_FP64_WARPS = 8;  // digit path: warps doing the FP64 work beside the digit products
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -230,10 +231,10 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
   constexpr int LDVW = 3 * NB;
   extern __shared__ z64 sm[];
   z64* v = sm;               // [n] reflector (trailing coordinates)
-  z64* w = sm + n;           // [n] p, then w
-  z64* pown = sm + 2 * n;    // [n] corrected p for this block's rows (read by the others)
-  z64* part = sm + 3 * n;    // [2 * HT_THREADS] partial sums of the K threads of each pair
-  unsigned int* vd = (unsigned int*)(sm + 3 * n + 2 * HT_THREADS);  // [24][W] digit words of v
+  z64* w = sm + n;           // [n] w; in the digit path first the corrections of p (one-block clusters)
+  z64* pown = sm + 2 * n;    // [n] p for this block's rows (read by the others)
+  z64* part = sm + 3 * n;    // FP64 path: [2 * HT_THREADS] partial sums of the K threads of each pair
+  unsigned int* vd = (unsigned int*)(sm + 3 * n);  // digit path, same region: [24][W] digit words of v
   __shared__ int ired[32];
   __shared__ z64 ypart[2 * NB], yfull[2 * NB];
   __shared__ double red[64];
@@ -249,16 +250,24 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
   z64* VW = VWbase + (size_t)p * strideVW;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   const int iend = min(i0 + NB, m);  // uniform over the cluster (one problem per cluster)
+  // Digit path: warps [0, NWD) form the digit products while the last HT_FP64_WARPS warps
+  // do the FP64 work that does not depend on them (W^H v and V^H v, the corrections when the
+  // cluster is one block, and the next column's updates from panel columns 0..j-1), so the
+  // integer and FP64 pipes work at the same time.
+  const bool dp = dig != nullptr;
+  const int NWD = dp ? nw - HT_FP64_WARPS : nw;
 
   for (int i = i0; i < iend; ++i) {
     const int j = i - i0;
-    // (a) column i (rows i..m-1) receives the updates of panel columns 0..j-1
+    // (a) column i (rows i..m-1) receives the updates of panel columns 0..j-1 (in the digit
+    // path those of columns 0..j-2 were applied while column i-1 was reduced)
     if (j > 0) {
+      const int jj0 = dp ? j - 1 : 0;
       for (int r = i + rank * nt + tid; r < m; r += C * nt) {
         z64 acc = A[(size_t)i * ld + r];
         const z64* Vr = VW + (size_t)r * LDVW;
         const z64* Vi = VW + (size_t)i * LDVW;
-        for (int jj = 0; jj < j; ++jj) {
+        for (int jj = jj0; jj < j; ++jj) {
           acc = zfmsc(Vr[jj], Vi[NB + jj], acc);  // - V(r,jj) conj(W(i,jj))
           acc = zfmsc(Vr[NB + jj], Vi[jj], acc);  // - W(r,jj) conj(V(i,jj))
         }
@@ -349,7 +358,7 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
       __syncthreads();
       // rows of this block's pairs: four rows per warp, eight lanes per row
       const int nrows = 2 * P, rslot = lane >> 3, wl = lane & 7;
-      for (int q0 = wid * 4; q0 < nrows; q0 += nw * 4) {
+      for (int q0 = wid * 4; wid < NWD && q0 < nrows; q0 += NWD * 4) {
         const int qq = q0 + rslot;
         int r = -1;
         if (qq < nrows) {
@@ -420,7 +429,7 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
         }
       }
     }
-    if (active) {
+    if (active && !dp) {
       // partial y over this block's rows: warp-strided over the 2j entries
       for (int jj = wid; jj < 2 * j; jj += nw) {
         const int cidx = jj < j ? NB + jj : jj - j;  // W column jj, or V column jj - j
@@ -434,15 +443,61 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
         if (lane == 0) ypart[jj] = zmk(sre, sim);
       }
       __syncthreads();
-      if (!dig)
-        for (int tt = tid; tt < 2 * P; tt += nt) {
-          const int gl = tt >> 1, h = tt & 1, g = g0 + gl;
-          const int r = h ? mt - 1 - g : g;
-          if (h && r == g) continue;
+      for (int tt = tid; tt < 2 * P; tt += nt) {
+        const int gl = tt >> 1, h = tt & 1, g = g0 + gl;
+        const int r = h ? mt - 1 - g : g;
+        if (h && r == g) continue;
+        z64 acc = zmk(0.0, 0.0);
+        for (int k = 0; k < K; ++k) acc = zadd(acc, part[(size_t)k * 2 * P + tt]);
+        pown[r] = acc;
+      }
+    }
+    if (dp && wid >= NWD) {
+      // the FP64 warps, while the others form the digit products
+      const int fw = wid - NWD, nfw = nw - NWD, ft = tid - NWD * 32, nft = nfw * 32;
+      if (active) {
+        // partial y over this block's rows: y1 = W^H v (entries 0..j-1), y2 = V^H v (j..2j-1)
+        for (int jj = fw; jj < 2 * j; jj += nfw) {
+          const int cidx = jj < j ? NB + jj : jj - j;
           z64 acc = zmk(0.0, 0.0);
-          for (int k = 0; k < K; ++k) acc = zadd(acc, part[(size_t)k * 2 * P + tt]);
-          pown[r] = acc;
+          for (int g = g0 + lane; g < g1; g += 32) {
+            const int ra = g, rb = mt - 1 - g;
+            acc = zcfma(VW[(size_t)(i + 1 + ra) * LDVW + cidx], v[ra], acc);
+            if (rb != ra) acc = zcfma(VW[(size_t)(i + 1 + rb) * LDVW + cidx], v[rb], acc);
+          }
+          const double sre = warp_sum(acc.x), sim = warp_sum(acc.y);
+          if (lane == 0) ypart[jj] = zmk(sre, sim);
         }
+        if (C == 1 && j > 0) {
+          // one-block cluster: y is complete, so the corrections V y1 + W y2 of every row
+          // are formed here too, into w (subtracted from p in (e))
+          asm volatile("bar.sync 1, %0;" :: "r"(nft) : "memory");
+          for (int r = ft; r < mt; r += nft) {
+            const z64* row = VW + (size_t)(i + 1 + r) * LDVW;
+            z64 acc = zmk(0.0, 0.0);
+            for (int jj = 0; jj < j; ++jj) {
+              acc = zfma(row[jj], ypart[jj], acc);           // V(r,jj) (W^H v)_jj
+              acc = zfma(row[NB + jj], ypart[j + jj], acc);  // W(r,jj) (V^H v)_jj
+            }
+            w[r] = acc;
+          }
+        }
+      }
+      // column i+1 (same panel) receives the updates of panel columns 0..j-1 now; the one of
+      // column j follows in its (a)
+      if (j > 0 && j + 1 < NB && i + 1 < iend) {
+        const int i1 = i + 1;
+        const z64* Vi = VW + (size_t)i1 * LDVW;
+        for (int r = i1 + rank * nft + ft; r < m; r += C * nft) {
+          z64 acc = A[(size_t)i1 * ld + r];
+          const z64* Vr = VW + (size_t)r * LDVW;
+          for (int jj = 0; jj < j; ++jj) {
+            acc = zfmsc(Vr[jj], Vi[NB + jj], acc);
+            acc = zfmsc(Vr[NB + jj], Vi[jj], acc);
+          }
+          A[(size_t)i1 * ld + r] = acc;
+        }
+      }
     }
     cluster.sync();  // S2: partial results ready; every block is done reading column i
     if (rank == 0) {  // Procedure 3: keep v below the subdiagonal of column i, and in V
@@ -454,7 +509,7 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
         row[2 * NB + j] = row[j];
       }
     }
-    if (active) {
+    if (active && (!dp || C > 1)) {
       // (d) y = sum over the cluster's blocks (fixed order), then the corrections of this
       // block's rows: p_raw -= V y2 + W y1  (y1 = W^H v multiplies V, y2 = V^H v multiplies W)
       for (int jj = tid; jj < 2 * j; jj += nt) {
@@ -479,18 +534,20 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
     }
     cluster.sync();  // S3: corrected pieces of p ready
     if (active) {
-      // (e) Procedure 5: w = tau p - (tau/2) ((tau p)^H v) v on the full vector
+      // (e) Procedure 5: w = tau p - (tau/2) ((tau p)^H v) v on the full vector (in the digit
+      // path with a one-block cluster, p = pown - w: the corrections formed beside (c))
+      const bool dpc = dp && C == 1 && j > 0;
       z64 dacc = zmk(0.0, 0.0);
       for (int g = tid; g < npairs; g += nt) {
         int k = 0;
         while (k + 1 < C && pair_start(k + 1, npairs, C) <= g) ++k;
         const z64* src = cluster.map_shared_rank(pown, k);
         const int ra = g, rb = mt - 1 - g;
-        const z64 pa = zmul(t, src[ra]);
+        const z64 pa = zmul(t, dpc ? zsub(src[ra], w[ra]) : src[ra]);
         w[ra] = pa;
         dacc = zcfma(pa, v[ra], dacc);
         if (rb != ra) {
-          const z64 pb = zmul(t, src[rb]);
+          const z64 pb = zmul(t, dpc ? zsub(src[rb], w[rb]) : src[rb]);
           w[rb] = pb;
           dacc = zcfma(pb, v[rb], dacc);
         }
@@ -508,14 +565,27 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
 
 }  // namespace
 
-// Largest cluster size C (1..8, at most one block per 128 rows) for which the nprob clusters
-// of C blocks are all resident at once, as the occupancy calculator reports for this kernel.
-static size_t panel_smem(int n) {
-  return sizeof(z64) * (3 * (size_t)n + 2 * HT_THREADS) + sizeof(unsigned int) * 3 * HD_S * hd_words(n);
+// v, w, pown, then one region shared by the FP64 path's partial sums and the digit path's
+// digit words of v
+static size_t panel_smem(int n, bool digits) {
+  const size_t region = digits ? sizeof(unsigned int) * 3 * HD_S * hd_words(n) : sizeof(z64) * 2 * HT_THREADS;
+  return sizeof(z64) * 3 * (size_t)n + region;
 }
 
-int hetrd_cluster_size(int n, int nprob, int num_sms) {
-  const size_t smem = panel_smem(n);
+bool hetrd_digits_fit(int n) {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return panel_smem(n, true) <= (size_t)optin;
+}
+
+// Largest cluster size C (1..8, at most one block per 128 rows) for which the nprob clusters
+// of C blocks are all resident at once, as the occupancy calculator reports for this kernel.
+int hetrd_cluster_size(int n, int nprob, int num_sms, bool digits) {
+  const size_t smem = panel_smem(n, digits);
   if (cudaFuncSetAttribute(hetrd_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       cudaFuncSetAttribute(hetrd_panel_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 0) != cudaSuccess) {
     cudaGetLastError();
@@ -548,7 +618,7 @@ int hetrd_cluster_size(int n, int nprob, int num_sms) {
 cudaError_t launch_hetrd_panel(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA, double* d,
                                double* e, z64* tau, long long strideV, z64* VW, long long strideVW, int i0, int cluster,
                                const void* dig, const int* erow, cudaStream_t st) {
-  size_t smem = panel_smem(n);
+  size_t smem = panel_smem(n, dig != nullptr);
   cudaError_t err = cudaFuncSetAttribute(hetrd_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   cudaLaunchConfig_t cfg = {};

@@ -146,7 +146,8 @@ cudaError_t launch_herm_fill(int n, int nprob, const z64* src, long long src_str
 // per row [V | W | V]) receives the panel's reflectors and update vectors, and the caller
 // applies A(i0+NB:, i0+NB:) -= V W^H + W V^H before the next panel.
 constexpr int NAO_HT_NB = 32;
-int hetrd_cluster_size(int n, int nprob, int num_sms);
+int hetrd_cluster_size(int n, int nprob, int num_sms, bool digits);
+bool hetrd_digits_fit(int n);  // the digit path's shared memory fits a block at order n
 // dig / erow (nullable): 8-bit digit planes of the trailing matrix made by launch_hetrd_digits
 // for this panel; with them the panel forms its Hermitian matrix-vector products exactly with
 // integer dot products (DP4A) instead of FP64 FMAs.
