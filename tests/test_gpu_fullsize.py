@@ -5,13 +5,14 @@
   by one; rho through the electron-count and band-energy identities, which hold at any size.
 * Large-basis cells (n = 1000: contractions past one exact tensor-core chunk): a
   well-conditioned cell against the oracle with the literal bounds, and the ill-conditioned
-  one (eta ~ 1e-8, one orbital in 50 duplicated) whose cut count m = n - n/50 is exact."""
+  one (eta ~ 1e-8, one orbital in 50 duplicated) whose cut count m = n - n/50 is exact.
+* Orders at the Householder panel's shared-memory limits (n = 2900 and 3300)."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_1402_4247_gb300 import synth
-from tests.gpu_helpers import check_problem, gpu_band_step
+from tests.gpu_helpers import TOL_EPS, TOL_ORTH, TOL_RES, check_problem, gpu_band_step
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -97,3 +98,31 @@ def test_large_basis_n1000(ctx, ill):
     be_x = backward(C_x[:, :m_x], e_x[:m_x])
     print(f"\nn1000-ill backward error: GPU {be.max():.2e}, LAPACK bisection + inverse iteration {be_x.max():.2e}")
     assert be.max() <= 10 * be_x.max(), (be.max(), be_x.max())
+
+
+@pytest.mark.parametrize("n", [2900, 3300], ids=["n2900-digit-panel", "n3300-fp64-panel"])
+def test_large_order_launch_limits(ctx, n):
+    """Orders near the shared-memory limits of the Householder panel: n = 2900 keeps the
+    digit path (its block needs 72 n bytes), n = 3300 is past it and takes the FP64 panel.  A seeded
+    well-conditioned pencil (S = I + 0.1 G G^H / n, H Hermitian), one problem, against
+    scipy's generalized eigensolver as a host witness, with the literal bounds."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(n)
+    G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    S = np.eye(n) + 0.1 * (G @ G.conj().T) / n
+    B = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    H = (B + B.conj().T) / (2.0 * np.sqrt(n))
+    Hd = torch.from_numpy(H[None]).to(DEV)
+    Sd = torch.from_numpy(S[None]).to(DEV)
+    eps, C, m, st = ctx.nao_gen_eig(Hd, Sd, nb=n)
+    torch.cuda.synchronize()
+    assert int(st[0]) == 0 and int(m[0]) == n
+    e = eps.cpu().numpy()[0]
+    Cn = C.cpu().numpy()[0]
+    e_ref = scipy_linalg.eigh(H, S, eigvals_only=True)
+    hn = np.abs(e_ref).max()
+    assert np.abs(e - e_ref).max() <= TOL_EPS * hn
+    res = np.linalg.norm(H @ Cn - S @ Cn * e[None, :]) / (n * np.linalg.norm(H, 2))
+    assert res <= TOL_RES, res
+    orth = np.abs(Cn.conj().T @ S @ Cn - np.eye(n)).max()
+    assert orth <= TOL_ORTH, orth
