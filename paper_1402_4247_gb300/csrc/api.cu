@@ -186,7 +186,7 @@ GenEigPlan plan_gen_eig(int n, int nprob, int nSe, bool use_tc) {
   W.oX = P.take<z64>(nn * nSe);
   // tridiagonal eigenvectors, Newton-Schulz, inverse-iteration scratch (both chains)
   W.oZ = P.take<double>(nn * nmax);
-  W.oZ2 = P.take<double>(nn * nmax);
+  W.oZ2 = P.take<double>(use_tc ? 1 : nn * nmax);  // the tensor-core Newton-Schulz step works in place
   W.oG = P.take<double>(nn * nmax);
   W.oScr = P.take<double>(stein_scratch_doubles(n, nmax));
   // Hamiltonian chain
@@ -343,6 +343,29 @@ cudaError_t hetrd_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, z
     if (err != cudaSuccess) return err;
   }
   return cudaSuccess;
+}
+
+// The second half of the Newton-Schulz step, Z - Z (G - I)/2 with G = Z^T Z given by its
+// lower triangle (Z: rows size[p], columns ncols[p]).  Tensor-core method: G - I made full,
+// then one five-plane (30-bit) product with alpha = -1/2 and beta = 1 in place on Z (the
+// operands are split before the product reads them); the term is ~1e-9 of Z, so 30 bits
+// of it are far below Z's own rounding.  Otherwise the FP32 SIMT correction into Z2.
+// Returns the array that holds the result.
+double* ns_correct(nao_ctx* ctx, int n, int nprob, const int32_t* size, const int32_t* ncols, double* Z, double* G,
+                   double* Z2, void* ozws, cudaStream_t st, cudaError_t* err) {
+  const long long snn = (long long)n * n;
+  const GemmDims d{n, n, n, size, ncols, ncols};
+  if (ctx->gemm_method == NAO_GEMM_TC && ozws && dgemm_oz_supported(d)) {
+    NaoStage stage_(ctx, "ortho_ns", st, 4);
+    *err = launch_sym_minus_identity(n, nprob, ncols, G, n, snn, st);
+    if (*err == cudaSuccess)
+      *err = launch_dgemm_oz(nprob, d, -0.5, GemmOperand{Z, snn, 1, n, 0, nullptr}, GemmOperand{G, snn, 1, n, 0, nullptr},
+                             1.0, Z, snn, 1, n, ozws, ctx->dev_flags, st, NAO_OZ_DIGITS_MIXED);
+    return Z;
+  }
+  NaoStage stage_(ctx, "ortho_ns", st, 1);
+  *err = launch_ns_correct(n, nprob, size, ncols, Z, G, n, snn, Z2, st);
+  return Z2;
 }
 
 bool is_device_ptr(const void* p) {
@@ -573,14 +596,16 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nSe, nullptr, AS, dS, eS, tauS, VWp, ozws, st, NAO_OZ_DIGITS_FP64, digp, erowp));
   NAO_STAGE("stein", 1, launch_stein(n, nSe, nullptr, dS, eS, n, wS, Z, n, snn, scr, stS, nullptr, n, st));
   NAO_STAGE("misc", 1, launch_count_kept(n, nSe, wS, n, s_cut, mS, stS, st));
-  {  // one Newton-Schulz step: Z2 = Z (3I - Z^T Z)/2 = Z - Z (Z^T Z - I)/2
+  double* Zo = Z2;  // the Newton-Schulz result (Z itself on the tensor-core method)
+  {  // one Newton-Schulz step: Z (3I - Z^T Z)/2 = Z - Z (Z^T Z - I)/2
     GemmDims d{n, n, n, nullptr, nullptr, nullptr, 1};
     NAO_CUDA_TRY(ctx, run_dgemm(ctx, "ortho_ns", nSe, d, 1.0, GemmOperand{Z, snn, n, 1, 0, nullptr},
                                 GemmOperand{Z, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, ozws, st));
-    NaoStage stage_(ctx, "ortho_ns", st, 1);
-    NAO_CUDA_TRY(ctx, launch_ns_correct(n, nSe, nullptr, nullptr, Z, G, n, snn, Z2, st));
+    cudaError_t e = cudaSuccess;
+    Zo = ns_correct(ctx, n, nSe, nullptr, nullptr, Z, G, Z2, ozws, st, &e);
+    NAO_CUDA_TRY(ctx, e);
   }
-  NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nSe, nullptr, mS, AS, tauS, Z2, wS, 1, X, Vf, tauc, Gw, Tw, Ww, W2w,
+  NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nSe, nullptr, mS, AS, tauS, Zo, wS, 1, X, Vf, tauc, Gw, Tw, Ww, W2w,
                                           ozws, st, dig, 0));
   {
     NaoStage stage_(ctx, "misc", st, 1);
@@ -614,10 +639,11 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
       GemmDims d{n, n, n, nvP, nvP, mP, 1};
       NAO_CUDA_TRY(ctx, run_dgemm(ctx, "ortho_ns", nprob, d, 1.0, GemmOperand{Z, snn, n, 1, 0, nullptr},
                                   GemmOperand{Z, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, ozws, st));
-      NaoStage stage_(ctx, "ortho_ns", st, 1);
-      NAO_CUDA_TRY(ctx, launch_ns_correct(n, nprob, mP, nvP, Z, G, n, snn, Z2, st));
+      cudaError_t e = cudaSuccess;
+      Zo = ns_correct(ctx, n, nprob, mP, nvP, Z, G, Z2, ozws, st, &e);
+      NAO_CUDA_TRY(ctx, e);
     }
-    NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nprob, mP, nvP, Hp, tauH, Z2, wH, 0, V, Vf, tauc, Gw, Tw, Ww, W2w,
+    NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nprob, mP, nvP, Hp, tauH, Zo, wH, 0, V, Vf, tauc, Gw, Tw, Ww, W2w,
                                             ozws, st, dig, 1));
   }
   if (mixed && ctx->refine_sweeps > 0) {

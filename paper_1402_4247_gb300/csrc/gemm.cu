@@ -194,7 +194,38 @@ ns_correct_kernel(int n, const int32_t* __restrict__ size, const int32_t* __rest
   }
 }
 
+// E = G - I made full in place from G = Z^T Z given by its lower triangle (column-major, ld):
+// the upper triangle mirrored from the lower, 1 subtracted on the diagonal; order ncols[p]
+// (n when ncols is null).  A block owns one 32 x 32 tile on or above the diagonal and reads
+// its mirror through shared memory, so that both the read and the write are coalesced.
+__global__ void sym_minus_identity_kernel(int n, const int32_t* __restrict__ ncols, double* __restrict__ Gb, int ld,
+                                          long long stride) {
+  __shared__ double tile[32][33];
+  const int p = blockIdx.z;
+  const int nc = ncols ? ncols[p] : n;
+  const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;  // target rows bi.., columns bj..
+  if (bi > bj || bj >= nc) return;                        // uniform per block
+  double* G = Gb + (size_t)p * stride;
+  const int tx = threadIdx.x, ty = threadIdx.y;           // 32 x 8
+  for (int c = ty; c < 32; c += 8) {  // source G(j, i), j = bj + tx, i = bi + c: contiguous in j
+    const int i = bi + c, j = bj + tx;
+    tile[c][tx] = (i < nc && j < nc && j >= i) ? G[(size_t)i * ld + j] : 0.0;
+  }
+  __syncthreads();
+  for (int c = ty; c < 32; c += 8) {  // target E(i, j), i = bi + tx, j = bj + c: contiguous in i
+    const int i = bi + tx, j = bj + c;
+    if (i < nc && j < nc && i <= j) G[(size_t)j * ld + i] = (i == j) ? tile[tx][c] - 1.0 : tile[tx][c];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_sym_minus_identity(int n, int nprob, const int32_t* ncols, double* G, int ld, long long stride,
+                                      cudaStream_t st) {
+  dim3 grid((n + 31) / 32, (n + 31) / 32, nprob), block(32, 8);
+  sym_minus_identity_kernel<<<grid, block, 0, st>>>(n, ncols, G, ld, stride);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ns_correct(int n, int nprob, const int32_t* size, const int32_t* ncols, const double* Z,
                               const double* G, int ld, long long stride, double* Z2, cudaStream_t st) {

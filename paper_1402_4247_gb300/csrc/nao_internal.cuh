@@ -213,6 +213,9 @@ cudaError_t launch_dgemm(int nprob, GemmDims dims, double alpha, GemmOperand A, 
 // = Z^T Z given by its lower triangle (column-major, ld).  E is ~1e-9, so the product runs
 // in FP32 on the FP32 pipe; its rounding (~1e-7 relative of a 1e-9 term) stays below FP64
 // rounding of Z.
+// E = G - I made full in place (upper triangle mirrored from the lower), order ncols[p] or n.
+cudaError_t launch_sym_minus_identity(int n, int nprob, const int32_t* ncols, double* G, int ld, long long stride,
+                                      cudaStream_t st);
 cudaError_t launch_ns_correct(int n, int nprob, const int32_t* size, const int32_t* ncols, const double* Z,
                               const double* G, int ld, long long stride, double* Z2, cudaStream_t st);
 
