@@ -232,7 +232,8 @@ __device__ bool newton_finish(const double* __restrict__ d, const double* __rest
 __global__ void __launch_bounds__(SZ_THREADS)
 stebz_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ dbase, const double* __restrict__ ebase,
              long long strideV, double* __restrict__ wslot, int32_t* __restrict__ status, int* __restrict__ qcount,
-             int* __restrict__ qslot, double* __restrict__ qlo, double* __restrict__ qhi) {
+             int4* __restrict__ qent, double* __restrict__ qlo, double* __restrict__ qhi, double* __restrict__ e2g,
+             double* __restrict__ tng) {
   extern __shared__ double smd[];
   double* d = smd;
   double* e = smd + n;
@@ -254,11 +255,14 @@ stebz_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     d32[i] = (float)d[i];
     e232[i] = (float)e2[i];
+    if (blockIdx.x == 0) e2g[(size_t)p * n + i] = e2[i];  // the split e^2, for the queue kernel
   }
   __syncthreads();
-  if (blockIdx.x == 0 && threadIdx.x == 0 && status) status[p] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (status) status[p] = 0;
+    tng[p] = T.tnorm;
+  }
   if (j >= m) return;
-  const double eps = DBL_EPSILON * 0.5;
   const int b0 = bst[j], b1 = ben[j];
   double lam;
   if (b1 - b0 == 1) {
@@ -297,47 +301,38 @@ stebz_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__
     bool ok = false;
     if (cl == idx && ch == idx + 1) ok = newton_finish(d, e2, b0, b1, idx, T.tnorm, lo, hi, cl, ch, lam);
     if (!ok) {
-      const int k = atomicAdd(&qcount[p], 1);
-      const size_t o = (size_t)p * n + k;
-      qslot[o] = j;
-      qlo[o] = lo;
-      qhi[o] = hi;
+      const int k = atomicAdd(qcount, 1);  // one queue over all problems
+      qent[k] = make_int4(p, j, b0, b1);
+      qlo[k] = lo;
+      qhi[k] = hi;
       return;
     }
   }
   wslot[(size_t)p * n + j] = lam;
 }
 
-// Kernel 1b: FP64 bisection of the queued eigenvalues of each problem, one thread per queue
-// entry, so that the warps are full.  Entries carry their verified bracket.  (Switching a
-// lane to Newton once its bracket isolates the eigenvalue was measured slower: the lanes of
-// a warp reach isolation at different steps, so the two paths serialise.)
+// Kernel 1b: FP64 bisection of the queued eigenvalues of all problems, one thread per queue
+// entry, so that the warps are full however few entries each problem has.  An entry carries
+// its problem, slot, split block and verified bracket; d and the split e^2 are read from
+// global memory (each lane streams its own problem's arrays).  (Switching a lane to Newton
+// once its bracket isolates the eigenvalue was measured slower: the lanes of a warp reach
+// isolation at different steps, so the two paths serialise.)
 __global__ void __launch_bounds__(SZ_THREADS)
-stebz_bisect_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ dbase,
-                    const double* __restrict__ ebase, long long strideV, double* __restrict__ wslot,
-                    const int* __restrict__ qcount, const int* __restrict__ qslot, const double* __restrict__ qlo,
-                    const double* __restrict__ qhi) {
-  extern __shared__ double smd[];
-  double* d = smd;
-  double* e = smd + n;
-  double* e2 = smd + 2 * n;
-  int* bst = (int*)(smd + 3 * n);
-  int* ben = bst + n;
-  __shared__ double red[96];
-  const int p = blockIdx.y;
-  const int m = size ? size[p] : n;
-  const int nq = qcount[p];
-  if (m <= 0 || (int)(blockIdx.x * blockDim.x) >= nq) return;  // uniform per block
-  const TriInfo T = load_tridiag(m, dbase + (size_t)p * strideV, ebase + (size_t)p * strideV, d, e, e2, bst, ben, red);
+stebz_bisect_kernel(int n, const double* __restrict__ dbase, long long strideV, const double* __restrict__ e2g,
+                    const double* __restrict__ tng, double* __restrict__ wslot, const int* __restrict__ qcount,
+                    const int4* __restrict__ qent, const double* __restrict__ qlo, const double* __restrict__ qhi) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nq) return;
+  if (q >= *qcount) return;
+  const int4 en = qent[q];
+  const int p = en.x, j = en.y, b0 = en.z, b1 = en.w, idx = j - b0;
+  const double* d = dbase + (size_t)p * strideV;
+  const double* e2 = e2g + (size_t)p * n;
+  const double tn = tng[p];
   const double eps = DBL_EPSILON * 0.5;
-  const int j = qslot[(size_t)p * n + q];
-  const int b0 = bst[j], b1 = ben[j], idx = j - b0;
-  double lo = qlo[(size_t)p * n + q], hi = qhi[(size_t)p * n + q];
+  double lo = qlo[q], hi = qhi[q];
   for (int it = 0; it < 128; ++it) {
     const double mid = 0.5 * (lo + hi);
-    const double tol = fmax(2.0 * eps * fmax(fabs(lo), fabs(hi)), eps * T.tnorm);
+    const double tol = fmax(2.0 * eps * fmax(fabs(lo), fabs(hi)), eps * tn);
     if (hi - lo <= tol || mid <= lo || mid >= hi) break;
     if (sturm64(d, e2, b0, b1, mid, false, nullptr, nullptr) > idx) hi = mid;
     else lo = mid;
@@ -781,7 +776,9 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
 static int big_capacity(int n, int nprob) { return nprob * (n / (BIG + 1) + 1); }
 
 size_t stein_scratch_doubles(int n, int nprob) {
-  return (size_t)NARR * n * n * nprob + (size_t)n * nprob + (3 * (size_t)big_capacity(n, nprob) + 2) / 2 + 1;
+  // the bisection queue (5 n + 1 doubles per problem, + 1) fits in the first NARR n^2 per
+  // problem for n >= 2; the pad covers n = 1
+  return (size_t)NARR * n * n * nprob + (size_t)n * nprob + (3 * (size_t)big_capacity(n, nprob) + 2) / 2 + 1 + nprob + 2;
 }
 
 cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d, const double* e, long long strideV,
@@ -791,21 +788,25 @@ cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d,
   const size_t smem1 = sizeof(double) * 3 * (size_t)n + sizeof(float) * 2 * (size_t)n + sizeof(int) * 2 * (size_t)n;
   cudaError_t err = cudaFuncSetAttribute(stebz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
   if (err != cudaSuccess) return err;
-  // the bisection queue lives in the inverse-iteration scratch, unused until kernel 2
+  // the bisection queue (all problems) and the split e^2 live in the inverse-iteration
+  // scratch, unused until kernel 2
+  const size_t cap = (size_t)n * nprob;
   double* qlo = scratch;
-  double* qhi = qlo + (size_t)n * nprob;
-  int* qslot = (int*)(qhi + (size_t)n * nprob);
-  int* qcount = qslot + (size_t)n * nprob;
-  err = cudaMemsetAsync(qcount, 0, sizeof(int) * nprob, st);
+  double* qhi = qlo + cap;
+  int4* qent = (int4*)(qhi + cap);
+  double* e2g = (double*)(qent + cap);
+  double* tng = e2g + cap;                                            // 5 cap + nprob <= NARR n^2 nprob
+  int* qcount = (int*)(scratch + stein_scratch_doubles(n, nprob) - 2);  // the pad at the end
+  err = cudaMemsetAsync(qcount, 0, sizeof(int), st);
   if (err != cudaSuccess) return err;
   dim3 grid1((n + SZ_THREADS - 1) / SZ_THREADS, nprob);
-  stebz_kernel<<<grid1, SZ_THREADS, smem1, st>>>(n, size, d, e, strideV, wslot, status, qcount, qslot, qlo, qhi);
+  stebz_kernel<<<grid1, SZ_THREADS, smem1, st>>>(n, size, d, e, strideV, wslot, status, qcount, qent, qlo, qhi, e2g,
+                                                 tng);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  const size_t smem1b = sizeof(double) * 3 * (size_t)n + sizeof(int) * 2 * (size_t)n;
-  err = cudaFuncSetAttribute(stebz_bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1b);
-  if (err != cudaSuccess) return err;
-  stebz_bisect_kernel<<<grid1, SZ_THREADS, smem1b, st>>>(n, size, d, e, strideV, wslot, qcount, qslot, qlo, qhi);
+  stebz_bisect_kernel<<<(unsigned)((cap + SZ_THREADS - 1) / SZ_THREADS), SZ_THREADS, 0, st>>>(n, d, strideV, e2g, tng,
+                                                                                             wslot, qcount, qent, qlo,
+                                                                                             qhi);
   dim3 grid((n + ST_THREADS - 1) / ST_THREADS, nprob);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
