@@ -37,11 +37,15 @@ namespace {
 constexpr int OZ_S = 10;             // digit planes per operand for FP64 accuracy (60 bits); the most
                                      // any product uses (the workspace is sized for it)
 constexpr int OZ_BM = 128;           // tile rows (C'' rows)
-constexpr int OZ_BN = 64;            // tile columns (C'' columns = 32 complex columns)
+constexpr int OZ_BN = 64;            // tile columns (C'' columns = 32 complex columns); B plane tile rows
 constexpr int OZ_BK = 16;            // K' per MMA step
 constexpr int OZ_TILE_A = OZ_BM * OZ_BK * 2;  // bytes of one A plane tile (4096)
 constexpr int OZ_TILE_B = OZ_BN * OZ_BK * 2;  // bytes of one B plane tile (2048)
 constexpr int OZ_STAGES = 3;
+// Short contractions (at most OZ_SHORT_KSTEPS K steps) use tiles of 32 columns, 256 TMEM
+// columns and 2 stages (102 KB), so that two CTAs share an SM and one's epilogue overlaps
+// the other's MMAs; their B tiles are the contiguous 32-row halves of the 64-row plane tiles.
+constexpr int OZ_SHORT_KSTEPS = 16;
 constexpr int OZ_THREADS = 256;
 constexpr long long OZ_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 constexpr int OZ_MAX_K2 = 1792;      // 2K bound for exact FP32 group sums (group 8: 9 2^10 per k)
@@ -256,8 +260,8 @@ __device__ __forceinline__ void oz_bulk_copy(void* dst_smem, const void* src_gme
 //   warp 1 / lane 0 (MMA issuer): waits for a full stage, issues the 37 MMAs (55 digit products), commits them
 //     to the stage's empty barrier, and after the last stage to the "done" barrier;
 //   all 8 warps: wait for "done", then run the epilogue from TMEM.
-template <bool REAL, int S>
-__global__ void __launch_bounds__(OZ_THREADS, 1)
+template <bool REAL, int S, int BN, int NST>
+__global__ void __launch_bounds__(OZ_THREADS, BN == OZ_BN ? 1 : 2)
 oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_bfloat16* __restrict__ Ap,
                const __nv_bfloat16* __restrict__ Bp, const int* __restrict__ rexp, const int* __restrict__ cexp, int Mp,
                int N2p, int K2p, void* __restrict__ Cv, long long Cbs, long long Crs, long long Ccs, int* __restrict__ err) {
@@ -265,11 +269,12 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
   constexpr int NEX = (S + 1 <= 8) ? S : 7;
   constexpr bool MERGED = S + 1 > 8;
   constexpr int NACC = NEX + (MERGED ? 1 : 0);
-  constexpr int TMEM_COLS = NACC * OZ_BN <= 128 ? 128 : (NACC * OZ_BN <= 256 ? 256 : 512);
-  constexpr int STAGE = S * (OZ_TILE_A + OZ_TILE_B);  // bytes per pipeline stage
+  constexpr int TMEM_COLS = NACC * BN <= 128 ? 128 : (NACC * BN <= 256 ? 256 : 512);
+  constexpr int TILE_B = BN * OZ_BK * 2;              // bytes of one B tile in shared memory
+  constexpr int STAGE = S * (OZ_TILE_A + TILE_B);     // bytes per pipeline stage
   constexpr int kUnitExp = 36 - 6 * NEX;              // one unit of the last exact group is 2^kUnitExp
   extern __shared__ __align__(1024) unsigned char oz_smem[];
-  __shared__ uint64_t full_bar[OZ_STAGES], empty_bar[OZ_STAGES], done_bar;
+  __shared__ uint64_t full_bar[NST], empty_bar[NST], done_bar;
   __shared__ uint32_t tbase;
   __shared__ volatile int s_fail;
   __shared__ int s_issued;
@@ -279,7 +284,7 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
   const int N = dims.Np ? dims.Np[p] : dims.N;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // uniform early exits (before any barrier or allocation)
-  const int CPT = REAL ? OZ_BN : OZ_BN / 2;  // output columns per tile
+  const int CPT = REAL ? BN : BN / 2;  // output columns per tile
   if (rb * OZ_BM >= M || cb * CPT >= N) return;
   if (dims.lower && cb * CPT > rb * OZ_BM + OZ_BM - 1) return;
   unsigned char* stage0 = (unsigned char*)(((uintptr_t)oz_smem + 1023) & ~(uintptr_t)1023);
@@ -290,7 +295,9 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
   const size_t aplane = (size_t)(Mp / OZ_BM) * nks * (OZ_TILE_A / 2);
   const size_t bplane = (size_t)(N2p / OZ_BN) * nks * (OZ_TILE_B / 2);
   const unsigned char* Abase = (const unsigned char*)(Ap + (size_t)p * S * aplane) + (size_t)rb * nks * OZ_TILE_A;
-  const unsigned char* Bbase = (const unsigned char*)(Bp + (size_t)p * S * bplane) + (size_t)cb * nks * OZ_TILE_B;
+  // B rows cb BN .. +BN-1: plane tile (cb BN) / 64, from its row (cb BN) % 64 on (contiguous)
+  const unsigned char* Bbase = (const unsigned char*)(Bp + (size_t)p * S * bplane) +
+                               (size_t)((cb * BN) / OZ_BN) * nks * OZ_TILE_B + (((cb * BN) % OZ_BN) >> 3) * 256;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -300,7 +307,7 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
   if (tid == 0) {
     s_fail = 0;
     s_issued = 0;
-    for (int st = 0; st < OZ_STAGES; ++st) {
+    for (int st = 0; st < NST; ++st) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full_bar[st])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty_bar[st])));
     }
@@ -315,8 +322,8 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
     // ---------------- producer
     int ks = 0;
     for (; ks < nks_p; ++ks) {
-      const int st = ks % OZ_STAGES;
-      if (ks >= OZ_STAGES && !oz_wait(&empty_bar[st], ((ks / OZ_STAGES) - 1) & 1)) {
+      const int st = ks % NST;
+      if (ks >= NST && !oz_wait(&empty_bar[st], ((ks / NST) - 1) & 1)) {
         s_fail = 1;
         break;
       }
@@ -329,8 +336,8 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
                      &full_bar[st]);
 #pragma unroll
       for (int t = 0; t < S; ++t)
-        oz_bulk_copy(sdst + S * OZ_TILE_A + t * OZ_TILE_B, Bbase + (size_t)t * bplane * 2 + (size_t)ks * OZ_TILE_B,
-                     OZ_TILE_B, &full_bar[st]);
+        oz_bulk_copy(sdst + S * OZ_TILE_A + t * TILE_B, Bbase + (size_t)t * bplane * 2 + (size_t)ks * OZ_TILE_B,
+                     TILE_B, &full_bar[st]);
     }
     s_issued = ks;
   } else if (warp == 1 && lane == 0) {
@@ -338,8 +345,8 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
     uint32_t init_mask = 0;  // accumulators written at least once
     int ks = 0;
     for (; ks < nks_p; ++ks) {
-      const int st = ks % OZ_STAGES;
-      if (!oz_wait(&full_bar[st], (ks / OZ_STAGES) & 1)) {
+      const int st = ks % NST;
+      if (!oz_wait(&full_bar[st], (ks / NST) & 1)) {
         s_fail = 1;
         break;
       }
@@ -361,14 +368,14 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
           const int tend = min(min(NEX - s, S), t0 + 4);
           const int w = tend - t0, acc0 = s + t0;
           const uint32_t on = (init_mask >> acc0) & 1u;
-          oz_mma(tmem + acc0 * OZ_BN, ad, oz_desc(sb + t0 * OZ_TILE_B), oz_idesc(w * OZ_BN), on);
+          oz_mma(tmem + acc0 * BN, ad, oz_desc(sb + t0 * TILE_B), oz_idesc(w * BN), on);
           init_mask |= ((1u << w) - 1u) << acc0;
         }
         if (MERGED) {
 #pragma unroll
           for (int t = (NEX - s > 0 ? NEX - s : 0); t < S && s + t + 2 <= S + 1; ++t) {
             const uint32_t on = (init_mask >> NEX) & 1u;
-            oz_mma(tmem + NEX * OZ_BN, ad, oz_desc(sb + t * OZ_TILE_B), oz_idesc(OZ_BN), on);
+            oz_mma(tmem + NEX * BN, ad, oz_desc(sb + t * TILE_B), oz_idesc(BN), on);
             init_mask |= 1u << NEX;
           }
         }
@@ -390,8 +397,8 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
       atomicExch(err, 1);
       // let every bulk copy that was issued land before the block (and its shared memory) goes
       const int issued = s_issued;
-      for (int ks = (issued > OZ_STAGES ? issued - OZ_STAGES : 0); ks < issued; ++ks)
-        oz_wait(&full_bar[ks % OZ_STAGES], (ks / OZ_STAGES) & 1);
+      for (int ks = (issued > NST ? issued - NST : 0); ks < issued; ++ks)
+        oz_wait(&full_bar[ks % NST], (ks / NST) & 1);
     }
   } else {
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows); warps 0-3 take
@@ -406,12 +413,12 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
     const bool amul = (abits & 0xFFFFFFFFFFFFFll) != 0 || afield == 0 || afield == 0x7ff;
     const int ae = amul ? 0 : afield - 1023;
     const bool aneg = !amul && abits < 0;
-    for (int cc = 0; cc < OZ_BN / 4; cc += 4) {  // 8 C'' columns per round
-      const int col0 = half * (OZ_BN / 2) + 2 * cc;
+    for (int cc = 0; cc < BN / 4; cc += 4) {  // 8 C'' columns per round
+      const int col0 = half * (BN / 2) + 2 * cc;
       uint32_t v[NACC][8];
 #pragma unroll
       for (int a = 0; a < NACC; ++a) {
-        const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + a * OZ_BN + col0;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + a * BN + col0;
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                      : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]), "=r"(v[a][5]),
                        "=r"(v[a][6]), "=r"(v[a][7])
@@ -450,7 +457,7 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
         double* Cp = (double*)Cv + (size_t)p * Cbs;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          const int gj = cb * OZ_BN + col0 + c;
+          const int gj = cb * BN + col0 + c;
           if (gj >= N) continue;
           const int ex = erow + cexp[(size_t)p * N2p + gj] - 42 + kUnitExp + ae;
           double* cp = Cp + (long long)gi * Crs + (long long)gj * Ccs;
@@ -463,7 +470,7 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
         z64* Cp = (z64*)Cv + (size_t)p * Cbs;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int gj = cb * (OZ_BN / 2) + half * (OZ_BN / 4) + cc + q;  // complex column
+          const int gj = cb * (BN / 2) + half * (BN / 4) + cc + q;  // complex column
           if (gj >= N) continue;
           const int ex = erow + cexp[(size_t)p * (N2p / 2) + gj] - 42 + kUnitExp + ae;
           z64* cp = Cp + (long long)gi * Crs + (long long)gj * Ccs;
@@ -512,12 +519,23 @@ cudaError_t launch_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, Gem
   oz_split<true, REAL, S><<<dim3(N2p / 16, nprob), 256, 0, st>>>(nprob, dims, B, N2p, K2p, Bpl, cexp);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (K2p / OZ_BK <= OZ_SHORT_KSTEPS) {
+    constexpr int BN = OZ_BN / 2, NST = 2;
+    const size_t smem = NST * (size_t)S * (OZ_TILE_A + BN * OZ_BK * 2) + 1024;
+    e = cudaFuncSetAttribute(oz_gemm_kernel<REAL, S, BN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(N2p / BN, Mp / OZ_BM, nprob);
+    oz_gemm_kernel<REAL, S, BN, NST><<<grid, OZ_THREADS, smem, st>>>(nprob, dims, alpha, beta, Apl, Bpl, rexp, cexp, Mp,
+                                                                     N2p, K2p, C, Cbs, Crs, Ccs, err);
+    return cudaGetLastError();
+  }
   const size_t smem = OZ_STAGES * (size_t)S * (OZ_TILE_A + OZ_TILE_B) + 1024;
-  e = cudaFuncSetAttribute(oz_gemm_kernel<REAL, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(oz_gemm_kernel<REAL, S, OZ_BN, OZ_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(N2p / OZ_BN, Mp / OZ_BM, nprob);
-  oz_gemm_kernel<REAL, S><<<grid, OZ_THREADS, smem, st>>>(nprob, dims, alpha, beta, Apl, Bpl, rexp, cexp, Mp, N2p,
-                                                           K2p, C, Cbs, Crs, Ccs, err);
+  oz_gemm_kernel<REAL, S, OZ_BN, OZ_STAGES><<<grid, OZ_THREADS, smem, st>>>(nprob, dims, alpha, beta, Apl, Bpl, rexp,
+                                                                           cexp, Mp, N2p, K2p, C, Cbs, Crs, Ccs, err);
   return cudaGetLastError();
 }
 

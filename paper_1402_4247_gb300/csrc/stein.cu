@@ -437,26 +437,28 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
           const double c = e[k];
           const double an = d[k + 1] - lam;
           const double bn = (k + 1 < b1 - 1) ? e[k + 1] : 0.0;
-          double u0, u1, u2, l, piv, al2, be2;
+          // the pivot (perturbed when tiny) serves both the multiplier l = num / u0 and
+          // the stored 1/u0: one FP64 reciprocal instead of two divisions
+          double u0, u1, u2, num, piv;
           if (fabs(al) >= fabs(c)) {
             piv = 0.0;
             u0 = al;
             u1 = be;
             u2 = 0.0;
-            l = (al != 0.0) ? c / al : 0.0;
-            al2 = an - l * be;
-            be2 = bn;
+            num = c;
           } else {
             piv = 1.0;
             u0 = c;
             u1 = an;
             u2 = bn;
-            l = al / c;
-            al2 = be - l * an;
-            be2 = -l * bn;
+            num = al;
           }
           if (fabs(u0) < pivtol) u0 = copysign(pivtol, u0);
-          AT(U0i, k) = 1.0 / u0;
+          const double rinv = 1.0 / u0;
+          const double l = num * rinv;
+          const double al2 = piv == 0.0 ? an - l * be : be - l * an;
+          const double be2 = piv == 0.0 ? bn : -l * bn;
+          AT(U0i, k) = rinv;
           AT(U1, k) = u1;
           AT(U2, k) = u2;
           AT(Lr, k) = l;
@@ -638,26 +640,28 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
           const double c = e[k];
           const double an = d[k + 1] - lam;
           const double bn = (k + 1 < b1 - 1) ? e[k + 1] : 0.0;
-          double u0, u1, u2, l, piv, al2, be2;
+          // the pivot (perturbed when tiny) serves both the multiplier l = num / u0 and
+          // the stored 1/u0: one FP64 reciprocal instead of two divisions
+          double u0, u1, u2, num, piv;
           if (fabs(al) >= fabs(c)) {
             piv = 0.0;
             u0 = al;
             u1 = be;
             u2 = 0.0;
-            l = (al != 0.0) ? c / al : 0.0;
-            al2 = an - l * be;
-            be2 = bn;
+            num = c;
           } else {
             piv = 1.0;
             u0 = c;
             u1 = an;
             u2 = bn;
-            l = al / c;
-            al2 = be - l * an;
-            be2 = -l * bn;
+            num = al;
           }
           if (fabs(u0) < pivtol) u0 = copysign(pivtol, u0);
-          AT(U0i, k) = 1.0 / u0;
+          const double rinv = 1.0 / u0;
+          const double l = num * rinv;
+          const double al2 = piv == 0.0 ? an - l * be : be - l * an;
+          const double be2 = piv == 0.0 ? bn : -l * bn;
+          AT(U0i, k) = rinv;
           AT(U1, k) = u1;
           AT(U2, k) = u2;
           AT(Lr, k) = l;
