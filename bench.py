@@ -362,10 +362,14 @@ def run_ours(args, rank, world, local_rank):
     smap = (torch.arange(nprob, dtype=torch.int32) % nk).to(dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(src, precision=0, eps_out=eps):
+    def step(src, precision=0, eps_out=eps, before_eig=None, before_density=None):
         ctx.nao_bloch_sum(src["SR"], src["R"], src["k"], out=Sk)
         ctx.nao_bloch_sum(src["HR"], src["R"], src["k"], out=Hk)
+        if before_eig:
+            before_eig()
         ctx.nao_gen_eig(Hk.view(nprob, n, n), Sk[0], s_of_prob=smap, precision=precision, out=(eps_out, C, m, st))
+        if before_density:
+            before_density()
         ctx.nao_density_matrix(src["w"], src["k"], eps_out, C, m, inp.n_electrons, inp.kT, src["R"], nspin,
                                out=(mu, eb, f, rho, rst))
 
@@ -402,23 +406,60 @@ def run_ours(args, rank, world, local_rank):
              "rho": torch.empty_like(rho, device="cpu").pin_memory()}
     h2d = sum(v.numel() * v.element_size() for v in h_in.values())
     d2h = sum(v.numel() * v.element_size() for v in out_h.values())
-    d_e2e = {k_: torch.empty_like(v) for k_, v in d_in.items()}
+    # Pipelined: a copy stream brings step i+1's inputs into the other of two device input
+    # slots while step i computes, and copies step i's results out while step i+1 runs (its
+    # eigensolve waits for the small results' copy, its density matrix for rho's).  Every
+    # step still copies its own inputs in and reads its own results back, inside the timed
+    # region, which ends when the last step's results are on the host.
+    d_e2e = [{k_: torch.empty_like(v) for k_, v in d_in.items()} for _ in range(2)]
     k_e2e = max(1, min(args.steps, 3))
+    cs = torch.cuda.Stream(dev)
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_used = [torch.cuda.Event() for _ in range(2)]
+    ev_small, ev_rho = torch.cuda.Event(), torch.cuda.Event()
+
+    def copy_in(slot):
+        with torch.cuda.stream(cs):
+            for k_, v in h_in.items():
+                d_e2e[slot][k_].copy_(v, non_blocking=True)
+            ev_in[slot].record(cs)
+
+    def copy_out():
+        ev_done = torch.cuda.Event()
+        ev_done.record(stream)
+        with torch.cuda.stream(cs):
+            cs.wait_event(ev_done)
+            for k_, v in (("eps", eps), ("m", m), ("mu", mu), ("eb", eb)):
+                out_h[k_].copy_(v, non_blocking=True)
+            ev_small.record(cs)
+            out_h["rho"].copy_(rho, non_blocking=True)
+            ev_rho.record(cs)
+
     barrier()
     x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     x0.record(stream)
-    for _ in range(k_e2e):
-        for k_, v in h_in.items():
-            d_e2e[k_].copy_(v, non_blocking=True)
-        step(d_e2e)
-        out_h["eps"].copy_(eps, non_blocking=True)
-        out_h["m"].copy_(m, non_blocking=True)
-        out_h["mu"].copy_(mu, non_blocking=True)
-        out_h["eb"].copy_(eb, non_blocking=True)
-        out_h["rho"].copy_(rho, non_blocking=True)
-        stream.synchronize()
-        _ = float(out_h["mu"][0])
+    cs.wait_event(x0)
+    copy_in(0)
+    for i in range(k_e2e):
+        sl = i % 2
+        if i + 1 < k_e2e:
+            if i >= 1:
+                cs.wait_event(ev_used[1 - sl])  # step i-1 is done with that slot
+            copy_in(1 - sl)
+        stream.wait_event(ev_in[sl])
+        step(d_e2e[sl], before_eig=(lambda: stream.wait_event(ev_small)) if i else None,
+             before_density=(lambda: stream.wait_event(ev_rho)) if i else None)
+        ev_used[sl].record(stream)
+        copy_out()
+        if i:
+            ev_prev.synchronize()  # step i-1's results are on the host (step i is queued already)
+            _ = float(out_h["mu"][0])
+        ev_prev = torch.cuda.Event()
+        ev_prev.record(cs)
+    stream.wait_event(ev_rho)
     x1.record(stream)
+    x1.synchronize()
+    _ = float(out_h["mu"][0])
     barrier()
     e2e_ms = x0.elapsed_time(x1) / k_e2e
 
