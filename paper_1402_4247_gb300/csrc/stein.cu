@@ -184,6 +184,53 @@ __device__ int sturm64(const double* __restrict__ d, const double* __restrict__ 
   return cnt;
 }
 
+// FP64 Sturm count below x (the count of sturm64 without the derivative): the same
+// recurrence and rescaling, with the scale checked once per four steps while |T| < 2^60:
+// four steps then grow |p| by at most (2|T| + |T|^2)^4 < 2^481, so the 2^400 threshold keeps
+// every value finite (larger |T| checks every step, as sturm64 does).
+__device__ int sturm64_count(const double* __restrict__ d, const double* __restrict__ e2, int b0, int b1, double x,
+                             double tnorm) {
+  double pm1 = 1.0, p = d[b0] - x;
+  long long bits = __double_as_longlong(p);
+  int sn = (bits < 0) && ((bits << 1) != 0);
+  int cnt = sn;
+  auto step = [&](int i) {
+    const double t = d[i] - x;
+    const double pn = fma(t, p, -e2[i - 1] * pm1);
+    pm1 = p;
+    p = pn;
+    bits = __double_as_longlong(p);
+    const int ns = ((bits << 1) == 0) ? sn : (int)(bits < 0);
+    cnt += (ns != sn);
+    sn = ns;
+  };
+  auto rescale = [&]() {
+    const int ex = (int)((__double_as_longlong(p) >> 52) & 0x7ff), ex1 = (int)((__double_as_longlong(pm1) >> 52) & 0x7ff);
+    const int emax = ex > ex1 ? ex : ex1;
+    if (emax > 1023 + 400) {
+      p *= 0x1p-400;
+      pm1 *= 0x1p-400;
+    } else if (emax < 1023 - 400 && emax > 0) {
+      p *= 0x1p400;
+      pm1 *= 0x1p400;
+    }
+  };
+  int i = b0 + 1;
+  const int b4 = tnorm < 0x1p60 ? b1 : b0 + 1;  // end of the four-step part
+  for (; i + 4 <= b4; i += 4) {
+    step(i);
+    step(i + 1);
+    step(i + 2);
+    step(i + 3);
+    rescale();
+  }
+  for (; i < b1; ++i) {
+    step(i);
+    rescale();
+  }
+  return cnt;
+}
+
 __device__ __forceinline__ double hash_uniform(unsigned long long key) {
   // splitmix64 finaliser -> uniform in (-1, 1)
   key += 0x9E3779B97F4A7C15ull;
@@ -219,8 +266,8 @@ __device__ bool newton_finish(const double* __restrict__ d, const double* __rest
       // x's count fixed one side of lambda (|xn - x| <= tol); one count 2 tol beyond xn on
       // the other side closes the bracket within [xn - 2 tol, xn + 2 tol]
       lam = xn;
-      return c > idx ? sturm64(d, e2, b0, b1, xn - 2.0 * tol, false, nullptr, nullptr) <= idx
-                     : sturm64(d, e2, b0, b1, xn + 2.0 * tol, false, nullptr, nullptr) > idx;
+      return c > idx ? sturm64_count(d, e2, b0, b1, xn - 2.0 * tol, tnorm) <= idx
+                     : sturm64_count(d, e2, b0, b1, xn + 2.0 * tol, tnorm) > idx;
     }
     if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);  // outside, or not finite: bisect
     x = xn;
@@ -283,8 +330,8 @@ stebz_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__
     // the magnetite-shaped cell); 8 eps_32 |T| on each side, and the FP64 counts check it
     const double margin = 8.0 * (double)FLT_EPSILON * T.tnorm;
     double lo = fmax((double)lo32 - margin, T.gl), hi = fmin((double)hi32 + margin, T.gu);
-    const int clo = sturm64(d, e2, b0, b1, lo, false, nullptr, nullptr);
-    const int chi = sturm64(d, e2, b0, b1, hi, false, nullptr, nullptr);
+    const int clo = sturm64_count(d, e2, b0, b1, lo, T.tnorm);
+    const int chi = sturm64_count(d, e2, b0, b1, hi, T.tnorm);
     if (!(clo <= idx && idx < chi)) {
       lo = T.gl;
       hi = T.gu;
@@ -334,7 +381,7 @@ stebz_bisect_kernel(int n, const double* __restrict__ dbase, long long strideV, 
     const double mid = 0.5 * (lo + hi);
     const double tol = fmax(2.0 * eps * fmax(fabs(lo), fabs(hi)), eps * tn);
     if (hi - lo <= tol || mid <= lo || mid >= hi) break;
-    if (sturm64(d, e2, b0, b1, mid, false, nullptr, nullptr) > idx) hi = mid;
+    if (sturm64_count(d, e2, b0, b1, mid, tn) > idx) hi = mid;
     else lo = mid;
   }
   wslot[(size_t)p * n + j] = 0.5 * (lo + hi);
