@@ -68,9 +68,6 @@ __device__ __forceinline__ int oz_tile_off(int row, int k) {
   return (row >> 3) * 256 + ((k >> 3) & 1) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
-// 2^e for a compile-time e (|e| < 1000)
-__host__ __device__ constexpr double oz_pow2(int e) { return e == 0 ? 1.0 : (e > 0 ? 2.0 * oz_pow2(e - 1) : 0.5 * oz_pow2(e + 1)); }
-
 // biased exponent field of x (0 for zero / subnormal)
 __device__ __forceinline__ int exp_field(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7ff); }
 
