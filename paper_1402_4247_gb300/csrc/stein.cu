@@ -137,36 +137,34 @@ __device__ int sturm_count32(const float* __restrict__ d, const float* __restric
   return cnt;
 }
 
-// FP64 Sturm count below x, and (when want_deriv) p_n(x), p_n'(x) up to a common positive
-// power-of-two factor.
-__device__ int sturm64(const double* __restrict__ d, const double* __restrict__ e2, int b0, int b1, double x,
-                       bool want_deriv, double* pn_out, double* dpn_out) {
+// FP64 Sturm count below x, and p_n(x), p_n'(x) up to a common positive power-of-two
+// factor (for Newton's step p / p'), with the scale of p, p', and their predecessors checked
+// once per four steps while |T| < 2^60 (see sturm64_count; p' grows by the same factor plus
+// |p|), every step beyond.
+__device__ int sturm64_deriv(const double* __restrict__ d, const double* __restrict__ e2, int b0, int b1, double x,
+                             double tnorm, double* pn_out, double* dpn_out) {
   double pm1 = 1.0, p = d[b0] - x;
   double qm1 = 0.0, q = -1.0;  // derivatives
   long long bits = __double_as_longlong(p);
   int sn = (bits < 0) && ((bits << 1) != 0);
   int cnt = sn;
-  for (int i = b0 + 1; i < b1; ++i) {
+  auto step = [&](int i) {
     const double t = d[i] - x;
     const double pn = fma(t, p, -e2[i - 1] * pm1);
-    if (want_deriv) {
-      const double qn = fma(t, q, fma(-e2[i - 1], qm1, -p));
-      qm1 = q;
-      q = qn;
-    }
+    const double qn = fma(t, q, fma(-e2[i - 1], qm1, -p));
+    qm1 = q;
+    q = qn;
     pm1 = p;
     p = pn;
     bits = __double_as_longlong(p);
-    const int zero = (bits << 1) == 0;
-    const int ns = zero ? sn : (int)(bits < 0);
+    const int ns = ((bits << 1) == 0) ? sn : (int)(bits < 0);
     cnt += (ns != sn);
     sn = ns;
-    const int ex = (int)((bits >> 52) & 0x7ff), ex1 = (int)((__double_as_longlong(pm1) >> 52) & 0x7ff);
-    int emax = ex > ex1 ? ex : ex1;
-    if (want_deriv) {
-      const int eq = (int)((__double_as_longlong(q) >> 52) & 0x7ff), eq1 = (int)((__double_as_longlong(qm1) >> 52) & 0x7ff);
-      emax = max(emax, max(eq, eq1));
-    }
+  };
+  auto rescale = [&]() {
+    const int ex = (int)((__double_as_longlong(p) >> 52) & 0x7ff), ex1 = (int)((__double_as_longlong(pm1) >> 52) & 0x7ff);
+    const int eq = (int)((__double_as_longlong(q) >> 52) & 0x7ff), eq1 = (int)((__double_as_longlong(qm1) >> 52) & 0x7ff);
+    const int emax = max(max(ex, ex1), max(eq, eq1));
     if (emax > 1023 + 400) {
       p *= 0x1p-400;
       pm1 *= 0x1p-400;
@@ -178,13 +176,26 @@ __device__ int sturm64(const double* __restrict__ d, const double* __restrict__ 
       q *= 0x1p400;
       qm1 *= 0x1p400;
     }
+  };
+  int i = b0 + 1;
+  const int b4 = tnorm < 0x1p60 ? b1 : b0 + 1;
+  for (; i + 4 <= b4; i += 4) {
+    step(i);
+    step(i + 1);
+    step(i + 2);
+    step(i + 3);
+    rescale();
   }
-  if (pn_out) *pn_out = p;
-  if (dpn_out) *dpn_out = q;
+  for (; i < b1; ++i) {
+    step(i);
+    rescale();
+  }
+  *pn_out = p;
+  *dpn_out = q;
   return cnt;
 }
 
-// FP64 Sturm count below x (the count of sturm64 without the derivative): the same
+// FP64 Sturm count below x (the count of sturm64_deriv without the derivative): the same
 // recurrence and rescaling, with the scale checked once per four steps while |T| < 2^60:
 // four steps then grow |p| by at most (2|T| + |T|^2)^4 < 2^481, so the 2^400 threshold keeps
 // every value finite (larger |T| checks every step, as sturm64 does).
@@ -252,7 +263,7 @@ __device__ bool newton_finish(const double* __restrict__ d, const double* __rest
   double x = 0.5 * (lo + hi);
   for (int it = 0; it < NEWTON_MAX; ++it) {
     double pn, dpn;
-    const int c = sturm64(d, e2, b0, b1, x, true, &pn, &dpn);
+    const int c = sturm64_deriv(d, e2, b0, b1, x, tnorm, &pn, &dpn);
     if (c > idx) {
       hi = x;
       chi = c;
