@@ -100,17 +100,43 @@ __device__ __forceinline__ long long oz_f32_fixed(float x, int k) {
   return b < 0 ? -q : q;
 }
 
-// S signed base-64 digits of q (|q| < 2^{6 S}): q = sum_s d_s 2^{6(S-s)}
+// S signed base-64 digits of q (|q| < 2^{6 S}): q = sum_s d_s 2^{6(S-s)}, the lower S - 1 in
+// [-32, 31] and |d_0| <= 64; formed from the least significant digit up in int32 arithmetic
+// on the two 30-bit halves of q (the carry left by the low half is 0 or 1)
 template <int S>
 __device__ __forceinline__ void oz_digits(long long q, int* d) {
+  if (S <= 5) {
+    int x = (int)q;
 #pragma unroll
-  for (int s = 0; s < S - 1; ++s) {
-    const int sh = 6 * (S - 1 - s);
-    const long long ds = (q + (1ll << (sh - 1))) >> sh;
-    d[s] = (int)ds;
-    q -= ds * (1ll << sh);
+    for (int s = S - 1; s >= 1; --s) {
+      const int ds = ((x + 32) & 63) - 32;
+      d[s] = ds;
+      x = (x - ds) >> 6;
+    }
+    d[0] = x;
+  } else {
+    int lo = (int)(q & 0x3FFFFFFF), hi = (int)(q >> 30);  // q = hi 2^30 + lo, 0 <= lo < 2^30
+#pragma unroll
+    for (int s = S - 1; s >= S - 5; --s) {
+      const int ds = ((lo + 32) & 63) - 32;
+      d[s] = ds;
+      lo = (lo - ds) >> 6;
+    }
+    hi += lo;
+#pragma unroll
+    for (int s = S - 6; s >= 1; --s) {
+      const int ds = ((hi + 32) & 63) - 32;
+      d[s] = ds;
+      hi = (hi - ds) >> 6;
+    }
+    d[0] = hi;
   }
-  d[S - 1] = (int)q;
+}
+
+// BF16 bits of d 2^k for a digit |d| <= 64 (exact): the top half of the float d, with k
+// added to the exponent field (no conversion or multiply instructions)
+__device__ __forceinline__ uint32_t oz_bf16_bits(int d, int k) {
+  return d ? (__float_as_uint((float)d) >> 16) + (uint32_t)(k << 7) : 0u;
 }
 
 // ---------------------------------------------------------------------------- split kernels
@@ -192,25 +218,31 @@ __global__ void __launch_bounds__(256) oz_split(int nprob, GemmDims dims, GemmOp
     for (int e = 0; e < 8; ++e) {
       const int kk = c * OZ_BK + kh * 8 + e;
       double v = 0.0;
+      bool neg = false;  // negations are applied to the exact integer, not as FP64 instructions
       if (live && kk < KK) {
         if (REAL) {
           v = ((const double*)xb)[at(kk)];
         } else {
           const bool hi = kk >= K;
-          z64 z = ((const z64*)xb)[at(hi ? kk - K : kk)];
-          if (X.conj) z.y = -z.y;
-          if (!IS_B) v = hi ? z.y : z.x;              // [Re | Im]
-          else if (h == 0) v = hi ? -z.y : z.x;       // (Re b ; -Im b)
-          else v = hi ? z.x : z.y;                    // (Im b ; Re b)
+          const z64 z = ((const z64*)xb)[at(hi ? kk - K : kk)];
+          const bool cj = X.conj != 0;  // conj: Im z enters with the opposite sign
+          if (!IS_B) {                  // [Re | Im]
+            v = hi ? z.y : z.x;
+            neg = hi && cj;
+          } else if (h == 0) {          // (Re b ; -Im b)
+            v = hi ? z.y : z.x;
+            neg = hi && !cj;
+          } else {                      // (Im b ; Re b)
+            v = hi ? z.x : z.y;
+            neg = !hi && cj;
+          }
         }
       }
+      const long long q = oz_fixed<S>(v, ex);
       int d[S];
-      oz_digits<S>(oz_fixed<S>(v, ex), d);
+      oz_digits<S>(neg ? -q : q, d);
 #pragma unroll
-      for (int s = 0; s < S; ++s) {
-        const __nv_bfloat16 b = __float2bfloat16_rn(ldexpf((float)d[s], SCALE0 - 6 * s));
-        pk[s][e >> 1] |= (uint32_t)__bfloat16_as_ushort(b) << (16 * (e & 1));
-      }
+      for (int s = 0; s < S; ++s) pk[s][e >> 1] |= oz_bf16_bits(d[s], SCALE0 - 6 * s) << (16 * (e & 1));
     }
 #pragma unroll
     for (int s = 0; s < S; ++s)
