@@ -36,7 +36,8 @@
 
 namespace {
 
-constexpr int ST_THREADS = 128;   // = slots per block (eigenvectors)
+constexpr int ST_THREADS = 64;    // = slots per block (eigenvectors): the overlap phase (64 problems)
+                                  // has ~36k of them, so 64-thread blocks spread over all SMs
 constexpr int SZ_THREADS = 64;    // = slots per block (eigenvalues): ~8 blocks per SM for 128 problems
                                   // of n = 568, so the SMs' FP64 pipes finish within one block of each other
 constexpr int MAXITS = 5;         // inverse-iteration solves before giving up
@@ -399,7 +400,7 @@ stebz_bisect_kernel(int n, const double* __restrict__ dbase, long long strideV, 
 }
 
 // ---------------------------------------------------------------- kernel 2: eigenvectors
-__global__ void __launch_bounds__(ST_THREADS, 5)  // 5 blocks per SM: 640 blocks (128 problems) in one wave
+__global__ void __launch_bounds__(ST_THREADS, 8)  // up to 8 blocks per SM (shared memory allows ~9)
 stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ dbase, const double* __restrict__ ebase,
                  long long strideV, const double* __restrict__ wslot, double* __restrict__ wbase,
                  double* __restrict__ Zbase, int ldz, long long strideZ, double* __restrict__ scratch,
