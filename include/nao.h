@@ -114,7 +114,9 @@ int nao_bloch_sum(nao_ctx* ctx, int n, int nR, const int32_t* R, int nmat, const
  *   nS        number of S matrices (ignored when s_of_prob is NULL)
  *   s_cut     absolute cutoff on the eigenvalues of S (e.g. 1e-10)
  *   precision NAO_FP64: every product FP64-accurate (ten-digit tensor-core products, or
- *             FP64 CUDA cores with NAO_GEMM_FP64).
+ *             FP64 CUDA cores with NAO_GEMM_FP64); the one exception is the Newton-Schulz
+ *             correction of the tridiagonal eigenvectors, a term ~1e-9 of them, formed with
+ *             five digits (30 bits), far below the FP64 rounding of the vectors it corrects.
  *             NAO_MIXED_BF16X3: the back-transformations, X^H H X, the rank-2k updates of H'
  *             and X V use 30-bit tensor-core products (five BF16 digit planes); the reduction
  *             of S, the tridiagonal solves and s^{-1/2} stay FP64.  Then one Ritz refinement
