@@ -50,7 +50,10 @@ enum {
   NAO_GEMM_FP64 = 0,  /* FP64 FMA on the CUDA cores                                        */
   NAO_GEMM_TC = 1     /* BF16 tensor cores on exact 6-bit digit planes of the FP64 operands
                          (60-bit splitting, FP32-exact partial sums; FP64-level accuracy);
-                         contractions longer than 896 run as chunks summed in FP64         */
+                         contractions longer than 896 run as chunks summed in FP64.  With
+                         this method the Householder matrix-vector products also run on
+                         exact 8-bit digits (62 bits, int32 dot products on the integer
+                         pipe) up to the order whose digits fit a block (n ~ 3200)        */
 };
 
 /* Library / context ------------------------------------------------------------------ */
