@@ -1,5 +1,5 @@
 """Shared helpers of the GPU parity tests: run the CUDA band step through the C ABI binding
-and compare it with the oracle by the tolerances of the benchmark spec workload statement."""
+and compare it with the oracle by the parity tolerances stated for the workload."""
 import numpy as np
 
 # Tolerances (floating point): eigenvalues |d eps| <= 1e-10 * ||H'|| with ||H'|| = max |eps|
