@@ -3,7 +3,7 @@
 Readings of the paper taken here (each also listed in the design notes):
 
 * Part 1, k-dependence: M(k) = sum_R exp(+2 pi i k.R) M(R), k fractional, R integer
-  cell vectors (the spec form H(k) = sum_R e^{ik.R} H(R)).
+  cell vectors (the form H(k) = sum_R e^{ik.R} H(R) of Sec. 3 Part 1).
 * Procedure 2 ("subtract s from the i-th element"): the element is the first one below the
   diagonal and s carries the phase -x_0/|x_0|, so u_0 = x_0 + e^{i arg x_0} |x|: no
   cancellation.
