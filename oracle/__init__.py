@@ -6,7 +6,7 @@ product path (the C-ABI library and its Python binding) never does, and shares n
 table or helper with it.
 
 Every function follows the paper's Band_DFT_Col (Sec. 3, Parts 1-6) and its Eigen_HH
-steps (Householder tridiagonalization, Procedures 1-6; a LAPACK tridiagonal eigensolver;
+steps (Householder tridiagonalization, Procedures 1-6; an implicit-QL tridiagonal eigensolver;
 rearrangement of eigenvectors; normalization), written out in numpy, float64/complex128.
 
 Pins (tests/test_oracle_pins.py) tie it to things other than itself: closed-form chain

@@ -13,9 +13,10 @@ Readings of the paper taken here (each also listed in the design notes):
   which makes Procedure 6, B <- B - q u^H - u q^H, the two-sided reflector update.
 * The complex subdiagonal left by the procedures is made real by a diagonal unitary
   phase matrix before the tridiagonal solve.
-* The LAPACK step of Eigen_HH: the paper allows dstevx, dstedc or dstegr; the oracle calls
-  LAPACK's MRRR routine (dstemr, successor of dstegr) through scipy, so it reaches the
-  tridiagonal eigenpairs by a different route from the GPU's bisection + inverse iteration.
+* The LAPACK step of Eigen_HH: the paper allows dstevx, dstedc or dstegr; the oracle writes
+  out the implicit QL method with Wilkinson shifts (no library eigensolver), so it reaches
+  the tridiagonal eigenpairs by a different route from the GPU's bisection + inverse
+  iteration.
 * Part 2's "rearrange S": canonical orthogonalisation X = U_m diag(s_m^{-1/2}) over the
   eigenvalues s_j >= s_cut (absolute cutoff; negative s_j are cut as well).
 * Part 3's "S^dagger H S" is X^H H X.
@@ -26,8 +27,10 @@ Readings of the paper taken here (each also listed in the design notes):
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
-import scipy.linalg
+from scipy.linalg.blas import drot as _rot
 
 
 # --------------------------------------------------------------------------------------
@@ -90,27 +93,85 @@ def householder_tridiagonalize(A: np.ndarray):
 
 
 # --------------------------------------------------------------------------------------
-# Eigen_HH step 2: the LAPACK tridiagonal eigensolver
+# Eigen_HH step 2: the tridiagonal eigensolver (implicit QL with Wilkinson shifts)
 # --------------------------------------------------------------------------------------
 
-def tridiagonal_eigensolve(d: np.ndarray, e: np.ndarray, method: str = "mrrr"):
-    """Sec. 3, Eigen_HH step 2: all eigenpairs of the real symmetric tridiagonal
-    tridiag(e, d, e) by a LAPACK routine, eigenvalues ascending.  The paper allows dstevx,
-    dstedc or dstegr.  method "mrrr" (default): MRRR (dstemr, the successor of dstegr); when
-    MRRR reports failure (it can on spectra with hundreds of eigenvalues packed within
-    ~1e-7 |T|, as the overlap of an ill-conditioned basis has), the implicit QL/QR routine
-    (dstev) gives the same eigenpairs by another route.  method "bisection": bisection and
-    inverse iteration (dstebz + dstein, the method of dstevx)."""
-    n = d.shape[0]
-    if n == 1:
-        return d.copy(), np.ones((1, 1))
-    if method == "bisection":
-        return scipy.linalg.eigh_tridiagonal(d, e, lapack_driver="stebz")
-    try:
-        w, Z = scipy.linalg.eigh_tridiagonal(d, e, lapack_driver="stemr")
-    except np.linalg.LinAlgError:
-        w, Z = scipy.linalg.eigh_tridiagonal(d, e, lapack_driver="stev")
-    return w, Z
+_EPS = float(np.finfo(np.float64).eps)
+_TINY = float(np.finfo(np.float64).tiny)
+
+
+def tridiagonal_eigensolve(d: np.ndarray, e: np.ndarray, max_sweeps_per_value: int = 30):
+    """Sec. 3, Eigen_HH step 2: all eigenpairs of the real symmetric tridiagonal T with
+    diagonal d[0..n) and off-diagonal e[0..n-1), eigenvalues ascending.
+
+    The paper hands this step to LAPACK (dstevx, dstedc or dstegr).  The oracle takes the
+    implicit QL method with Wilkinson shifts instead, written out here, with the plane
+    rotations accumulated into Z (T = Z diag(w) Z^T), so that it reaches the eigenpairs by a
+    route of its own, different from the CUDA path's bisection + inverse iteration:
+
+    * Deflation: an off-diagonal e_i with |e_i| <= eps (|d_i| + |d_{i+1}|) is set to zero,
+      which splits T.  The eigenvalue at the top of the unreduced block [l, m] is found
+      when the block shrinks to one row (l = m); then l moves down by one.
+    * Shift: the eigenvalue of the leading 2 x 2 block [[d_l, e_l], [e_l, d_{l+1}]] that lies
+      closer to d_l (Wilkinson's choice), sigma = d_l - e_l^2 / (delta + sign(delta)
+      sqrt(delta^2 + e_l^2)) with delta = (d_{l+1} - d_l) / 2.
+    * One QL sweep on T[l..m]: the first rotation, in the plane (m-1, m), is the one that
+      annihilates entry (m-1, m) of P (T - sigma I); applied to T as T <- P T P^T it leaves a
+      bulge at (m-2, m).  Each further rotation in the plane (i, i+1), i = m-2 .. l, removes
+      the bulge at (i, i+2) and creates the next at (i-1, i+1), until it leaves the block at
+      the top.  Z <- Z P^T accumulates every rotation: columns (z_i, z_{i+1}) become
+      (c z_i + s z_{i+1}, -s z_i + c z_{i+1}).
+    The scalar recurrences run on Python floats (IEEE doubles); the columns of Z are rows of
+    a C-ordered array, and each plane rotation of a pair of them is the BLAS level-1 routine
+    drot (x, y <- c x + s y, c y - s x), a library primitive.
+    """
+    dl = [float(x) for x in np.asarray(d, dtype=np.float64)]
+    n = len(dl)
+    off = [float(x) for x in np.asarray(e, dtype=np.float64)] + [0.0]  # off[i] couples rows i, i+1
+    Zt = np.eye(n)                               # rows of Zt are the columns of Z
+    hypot = math.hypot
+    for l in range(n):
+        sweeps = 0
+        while True:
+            # end m of the unreduced block that starts at l
+            m = l
+            while m < n - 1:
+                if abs(off[m]) <= _EPS * (abs(dl[m]) + abs(dl[m + 1])) or abs(off[m]) <= _TINY:
+                    off[m] = 0.0
+                    break
+                m += 1
+            if m == l:
+                break                            # dl[l] is an eigenvalue
+            sweeps += 1
+            if sweeps > max_sweeps_per_value:
+                raise np.linalg.LinAlgError("implicit QL: no convergence")
+            # Wilkinson shift from the leading 2 x 2 block
+            delta = 0.5 * (dl[l + 1] - dl[l])
+            root = hypot(delta, off[l])
+            sigma = dl[l] - off[l] * off[l] / (delta + (root if delta >= 0.0 else -root))
+            # first rotation, plane (m-1, m): zero (m-1, m) of P (T - sigma I)
+            x, z = dl[m] - sigma, off[m - 1]
+            for i in range(m - 1, l - 1, -1):
+                r = hypot(x, z)
+                if r > 0.0:
+                    c, s = x / r, -z / r
+                else:
+                    c, s = 1.0, 0.0
+                if i < m - 1:
+                    off[i + 1] = r                # (i+1, i+2) once the bulge at (i, i+2) is gone
+                a, b, dd = dl[i], off[i], dl[i + 1]
+                cs2 = 2.0 * c * s * b
+                dl[i] = c * c * a + cs2 + s * s * dd
+                dl[i + 1] = s * s * a - cs2 + c * c * dd
+                off[i] = c * s * (dd - a) + (c * c - s * s) * b
+                if i > l:                          # new bulge at (i-1, i+1)
+                    bulge = -s * off[i - 1]
+                    off[i - 1] = c * off[i - 1]
+                    x, z = off[i], bulge           # the next rotation zeroes the bulge
+                _rot(Zt[i], Zt[i + 1], c, s, overwrite_x=1, overwrite_y=1)
+    w = np.array(dl)
+    order = np.argsort(w, kind="stable")
+    return w[order], np.ascontiguousarray(Zt[order].T)
 
 
 # --------------------------------------------------------------------------------------
@@ -131,10 +192,12 @@ def rearrange_eigenvectors(Z: np.ndarray, us, hs, delta) -> np.ndarray:
     return V
 
 
-def eigen_hh(A: np.ndarray, method: str = "mrrr"):
-    """Sec. 3 Eigen_HH: eigenvalues (ascending) and orthonormal eigenvectors of Hermitian A."""
+def eigen_hh(A: np.ndarray, tridiagonal=None):
+    """Sec. 3 Eigen_HH: eigenvalues (ascending) and orthonormal eigenvectors of Hermitian A.
+    ``tridiagonal`` replaces the step-2 solver (a function (d, e) -> (w, Z)) when a test
+    wants another route through the same steps 1, 3 and 4."""
     d, e, us, hs, delta = householder_tridiagonalize(A)
-    w, Z = tridiagonal_eigensolve(d, e, method)
+    w, Z = (tridiagonal or tridiagonal_eigensolve)(d, e)
     return w, rearrange_eigenvectors(Z, us, hs, delta)
 
 
@@ -142,14 +205,14 @@ def eigen_hh(A: np.ndarray, method: str = "mrrr"):
 # Parts 2-4: the generalized eigenproblem H C = S C eps
 # --------------------------------------------------------------------------------------
 
-def generalized_eigensolve(H: np.ndarray, S: np.ndarray, s_cut: float = 1e-10, method: str = "mrrr"):
+def generalized_eigensolve(H: np.ndarray, S: np.ndarray, s_cut: float = 1e-10, tridiagonal=None):
     """Sec. 3 Parts 2-4.
 
     Part 2: Eigen_HH(S) -> s, U; X = U_m s_m^{-1/2} over s_j >= s_cut.
     Part 3: H' = X^H H X (made exactly Hermitian from its lower triangle).
     Part 4: Eigen_HH(H') -> eps, V; C = X V.
     Returns (eps [m], C [n, m], m, s [n])."""
-    s, U = eigen_hh(S, method)
+    s, U = eigen_hh(S, tridiagonal)
     keep = s >= s_cut
     X = U[:, keep] / np.sqrt(s[keep])[None, :]
     Hp = X.conj().T @ H @ X
@@ -158,7 +221,7 @@ def generalized_eigensolve(H: np.ndarray, S: np.ndarray, s_cut: float = 1e-10, m
     m = int(keep.sum())
     if m == 0:
         return np.zeros(0), np.zeros((H.shape[0], 0), dtype=np.complex128), 0, s
-    eps, V = eigen_hh(Hp, method)
+    eps, V = eigen_hh(Hp, tridiagonal)
     return eps, X @ V, m, s
 
 

@@ -70,6 +70,83 @@ def test_tridiagonalization_preserves_spectrum_exact(n):
     assert np.all(e >= 0)
 
 
+# Eigen_HH step 2: the oracle's own tridiagonal eigensolver (implicit QL), pinned on its own
+
+def _tri(d, e):
+    return np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 100, 301])
+def test_ql_discrete_laplacian_closed_form(n):
+    """tridiag(-1, 2, -1): eigenvalues 2 - 2 cos(j pi/(n+1)), eigenvectors sin(i j pi/(n+1))
+    (distinct eigenvalues, so each column is fixed up to sign)."""
+    w, Z = oracle.tridiagonal_eigensolve(2.0 * np.ones(n), -np.ones(n - 1))
+    j = np.arange(1, n + 1)
+    exact = 2.0 - 2.0 * np.cos(j * np.pi / (n + 1))
+    assert np.abs(w - exact).max() <= 8e-15 * n
+    zs = np.sin(np.outer(np.arange(1, n + 1), j) * np.pi / (n + 1))
+    zs /= np.linalg.norm(zs, axis=0)
+    dots = np.abs(np.sum(zs * Z, axis=0))
+    assert np.abs(dots - 1.0).max() <= 1e-12
+
+
+@pytest.mark.parametrize("n", [2, 5, 8, 33])
+def test_ql_clement_matrix_integer_spectrum(n):
+    """Zero diagonal, off-diagonals sqrt(i (n - i)): the eigenvalues are exactly
+    -(n-1), -(n-3), ..., n-1 (the Clement / Kac-Sylvester matrix)."""
+    i = np.arange(1, n)
+    w, Z = oracle.tridiagonal_eigensolve(np.zeros(n), np.sqrt(i * (n - i)))
+    exact = np.arange(-(n - 1), n, 2, dtype=float)
+    assert np.abs(w - exact).max() <= 1e-13 * n
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
+def test_ql_exact_sturm_roots(n):
+    """Random tridiagonals against the exact roots of det(T - l I) (rational arithmetic),
+    with the residual and orthogonality of the eigenvectors."""
+    rng = np.random.Generator(np.random.PCG64(300 + n))
+    d = rng.standard_normal(n)
+    e = rng.standard_normal(n - 1)
+    T = _tri(d, e)
+    cre, cim = bruteforce.char_poly(T.astype(complex), np.eye(n))
+    exact = np.array(bruteforce.real_roots(cre))
+    w, Z = oracle.tridiagonal_eigensolve(d, e)
+    assert len(exact) == n
+    assert np.abs(w - exact).max() <= 1e-14 * max(1.0, np.abs(exact).max())
+    assert np.abs(Z.T @ Z - np.eye(n)).max() <= 1e-14
+    assert np.abs(T @ Z - Z * w[None, :]).max() <= 1e-14 * max(1.0, np.abs(w).max())
+
+
+def test_ql_split_blocks_clusters_and_grading():
+    """Zero off-diagonals split T (the diagonal entries are eigenvalues); a Wilkinson W21+
+    matrix has pairs of eigenvalues equal to ~1e-13 (orthogonality must survive); a graded
+    matrix spans 1e-8 .. 1e8.  Residual and orthogonality at working precision."""
+    cases = []
+    d = np.array([3.0, 1.0, -2.0, 5.0, 0.5])
+    cases.append((d, np.zeros(4), np.sort(d)))
+    d = np.array([1.0, 2.0, 3.0, 4.0, 5.0, 6.0])
+    e = np.array([0.5, 0.0, 0.25, 0.0, 1.0])
+    ex = np.sort(np.concatenate([np.linalg.eigvalsh(_tri(d[:2], e[:1])), np.linalg.eigvalsh(_tri(d[2:4], e[2:3])),
+                                 np.linalg.eigvalsh(_tri(d[4:], e[4:]))]))
+    cases.append((d, e, ex))
+    cases.append((np.abs(np.arange(-10, 11)).astype(float), np.ones(20), None))
+    g = 10.0 ** np.linspace(-8, 8, 12)
+    cases.append((g, np.sqrt(g[:-1] * g[1:]) * 0.3, None))
+    for d, e, ex in cases:
+        w, Z = oracle.tridiagonal_eigensolve(d, e)
+        T = _tri(d, e)
+        nrm = np.abs(w).max()
+        if ex is not None:
+            assert np.abs(w - ex).max() <= 1e-14 * nrm
+        assert np.all(np.diff(w) >= 0)
+        assert np.abs(Z.T @ Z - np.eye(len(d))).max() <= 1e-13
+        assert np.abs(T @ Z - Z * w[None, :]).max() <= 1e-14 * nrm * len(d)
+    # W21+: the two largest eigenvalues agree to ~1e-13 and still get orthogonal vectors
+    w, Z = oracle.tridiagonal_eigensolve(np.abs(np.arange(-10, 11)).astype(float), np.ones(20))
+    assert w[-1] - w[-2] < 1e-12
+    assert abs(Z[:, -1] @ Z[:, -2]) < 1e-13
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 6])
 def test_generalized_eigenvalues_vs_exact_char_poly(n):
     """Parts 2-4 against exact roots of det(H - l S) (Gaussian-rational arithmetic)."""
