@@ -17,6 +17,7 @@ import argparse
 import json
 import multiprocessing as mp
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -71,6 +72,24 @@ def _oracle_worker(args):
     Sk = oracle.bloch_sum(SR, R, kp[q:q + 1])[0]
     eps, C, m, _ = oracle.generalized_eigensolve(Hk, Sk)
     return time.perf_counter() - t0, int(m)
+
+
+def _cpu_model():
+    """The host CPU's model string (lscpu, else /proc/cpuinfo), for the baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
 
 
 class OracleSampler:
@@ -177,14 +196,25 @@ def _stage_flops(stage, inp, m_mean, nocc_mean):
     return None
 
 
+def _sum_sq(k):
+    """sum_{L=1}^{k-1} L^2: the trailing orders of the columns of a reduction of order k."""
+    k = float(k)
+    return (k - 1.0) * k * (2.0 * k - 1.0) / 6.0
+
+
 def _panel_bytes(inp, m_mean):
-    """Algorithmic DRAM bytes of the Householder panel kernels of one step: every column's
-    Hermitian matrix-vector product reads the trailing matrix once, as 8-bit digits of both
-    triangles (8 digits x (re, im) = 16 bytes per entry), i.e. 16 sum_L L^2 per matrix."""
-    def s2(k):  # sum_{L=1}^{k-1} L^2
-        k = float(k)
-        return (k - 1.0) * k * (2.0 * k - 1.0) / 6.0
-    return 16.0 * (inp.nk * s2(inp.n) + inp.nprob * s2(m_mean))
+    """Algorithmic DRAM bytes of the Householder reductions of one step: every column's
+    Hermitian matrix-vector product reads the trailing matrix once in half storage (the
+    lower triangle, FP64 complex: 16 B per entry, L^2 / 2 entries), i.e. 8 sum_L L^2 ~
+    (8/3) n^3 bytes per reduction (nk overlap matrices of order n, nprob H' of order m)."""
+    return 8.0 * (inp.nk * _sum_sq(inp.n) + inp.nprob * _sum_sq(m_mean))
+
+
+def _digit_stream_bytes(inp, m_mean):
+    """Bytes the digit form of the panel kernel streams by design: 8-bit digits of both
+    triangles (8 digits x (re, im) = 16 B per entry, L^2 entries), 16 sum_L L^2 per matrix:
+    twice the algorithmic bytes, the price of per-row digit scales."""
+    return 16.0 * (inp.nk * _sum_sq(inp.n) + inp.nprob * _sum_sq(m_mean))
 
 
 def _load_traffic(stage, units_per_launch):
@@ -288,6 +318,160 @@ def run_serve(local_rank, n_requests=48, seed=5):
             "mean_batch_requests_offline": float(np.mean(batch)), "peak_hbm_bytes": peak, "status_ok": ok}
 
 
+def _band_step_timed(ctx, inp, dev, steps, warmup, precision=0, density=True):
+    """Run the band step (Parts 1-6; Parts 1-4 when density is False) of one cell through the
+    public binding: ``warmup`` untimed steps, then ``steps`` steps timed by CUDA events on the
+    launching stream with the library's per-stage trace.  Returns (ms per step, stages,
+    outputs of the last step)."""
+    import torch
+    n, nk, nprob = inp.n, inp.nk, inp.nprob
+    d = {"HR": torch.from_numpy(inp.HR).to(dev), "SR": torch.from_numpy(inp.SR)[None].to(dev),
+         "R": torch.from_numpy(inp.R).to(dev), "k": torch.from_numpy(inp.kpts).to(dev),
+         "w": torch.from_numpy(inp.wk).to(dev)}
+    Hk = torch.empty((inp.nspin, nk, n, n), dtype=torch.complex128, device=dev)
+    Sk = torch.empty((1, nk, n, n), dtype=torch.complex128, device=dev)
+    eps = torch.empty((nprob, n), dtype=torch.float64, device=dev)
+    C = torch.empty((nprob, n, n), dtype=torch.complex128, device=dev)
+    m = torch.empty(nprob, dtype=torch.int32, device=dev)
+    st = torch.empty(nprob, dtype=torch.int32, device=dev)
+    smap = (torch.arange(nprob, dtype=torch.int32) % nk).to(dev)
+    dens = None
+    if density:
+        dens = (torch.empty(1, dtype=torch.float64, device=dev), torch.empty(1, dtype=torch.float64, device=dev),
+                torch.empty((nprob, n), dtype=torch.float64, device=dev),
+                torch.empty((inp.nspin, inp.nR, n, n), dtype=torch.float64, device=dev),
+                torch.empty(1, dtype=torch.int32, device=dev))
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ctx.nao_bloch_sum(d["SR"], d["R"], d["k"], out=Sk)
+        ctx.nao_bloch_sum(d["HR"], d["R"], d["k"], out=Hk)
+        ctx.nao_gen_eig(Hk.view(nprob, n, n), Sk[0], s_of_prob=smap, precision=precision, out=(eps, C, m, st))
+        if density:
+            ctx.nao_density_matrix(d["w"], d["k"], eps, C, m, inp.n_electrons, inp.kT, d["R"], inp.nspin, out=dens)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.nao_profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = ctx.nao_profile_read()
+    ctx.nao_profile_enable(False)
+    ms = e0.elapsed_time(e1) / steps
+    stages = {k_: round(v[0] / steps, 3) for k_, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    ok = int(st.abs().sum()) == 0 and (not density or int(dens[4][0]) == 0)
+    return ms, stages, {"eps": eps, "C": C, "m": m, "status_ok": ok, "Hk": Hk, "Sk": Sk}
+
+
+def _oracle_golden(path):
+    """{problem: (m, eps)} from a golden file written by a committed oracle-only script."""
+    import numpy as np
+    out = {}
+    if not os.path.exists(path):
+        return out
+    rows = np.loadtxt(path, comments="#")
+    for p in np.unique(rows[:, 0]).astype(int):
+        r = rows[rows[:, 0] == p]
+        out[int(p)] = (int(r[0, 1]), r[np.argsort(r[:, 2]), 3])
+    return out
+
+
+def run_mixed_n2000(local_rank, steps=2, warmup=1):
+    """The mixed-precision workload: n = 2000, 4x4x4 k, one spin (64 problems + mu + rho), seed 4.
+    The FP64 step and the mixed step (NAO_MIXED_BF16X3 + one Ritz sweep) are timed alike; the
+    eigenvalues of two fixed problems are compared with the oracle's (a golden file written by
+    tests/golden/make_mixed_n2000_oracle.py), for the mixed path before and after its
+    refinement sweep, with residual and S-orthonormality on the host."""
+    import numpy as np
+    import torch
+    from paper_1402_4247_gb300 import synth
+    from paper_1402_4247_gb300.nao import Context
+    dev = torch.device("cuda", local_rank)
+    inp = synth.scaled_cell(2000, seed=4, kgrid=(4, 4, 4), nspin=1, ill_conditioned=False)
+    gold = _oracle_golden(os.path.join(ROOT, "tests", "golden", "mixed_n2000_oracle_eps.txt"))
+    ctx = Context(local_rank)
+    res = {"workload": "n=2000 (80 heavy x 13 + 120 light x 8 orbitals), 125 images, 4x4x4 k, 1 spin, seed 4: "
+                       "64 generalized eigensolves + mu + rho per step", "n": inp.n, "problems_per_step": inp.nprob}
+    checks = {}
+
+    def errors(out, label):
+        eps, C, m = out["eps"].cpu().numpy(), out["C"], out["m"].cpu().numpy()
+        for p, (mo, eo) in gold.items():
+            e = checks.setdefault(p, {})
+            e[f"{label}_m_equal"] = bool(int(m[p]) == mo)
+            e[f"{label}_max_abs_deps_Ha"] = float(np.abs(eps[p][:mo] - eo).max()) if int(m[p]) == mo else None
+            H = out["Hk"].view(-1, inp.n, inp.n)[p].cpu().numpy()
+            S = out["Sk"][0, p].cpu().numpy()
+            Cp = C[p, :, :mo].cpu().numpy()
+            ep = eps[p][:mo]
+            v = np.random.default_rng(0).standard_normal(inp.n) + 0j  # ||H||_2 by power iteration
+            for _ in range(60):
+                w_ = H @ v
+                hn = np.linalg.norm(w_) / np.linalg.norm(v)
+                v = w_ / np.linalg.norm(w_)
+            e[f"{label}_residual"] = float(np.linalg.norm(H @ Cp - (S @ Cp) * ep[None, :]) / (inp.n * hn))
+            e[f"{label}_orth"] = float(np.abs(Cp.conj().T @ S @ Cp - np.eye(mo)).max())
+
+    ms64, st64, out = _band_step_timed(ctx, inp, dev, steps, warmup, precision=0)
+    res["fp64"] = {"value": inp.nprob / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64, "stages_ms": st64,
+                   "status_ok": out["status_ok"]}
+    errors(out, "fp64")
+    del out
+    ctx.nao_set_refinement(0)
+    msr, _, out = _band_step_timed(ctx, inp, dev, 1, 0, precision=2)
+    errors(out, "mixed_raw")
+    del out
+    ctx.nao_set_refinement(1)
+    msm, stm, out = _band_step_timed(ctx, inp, dev, steps, warmup, precision=2)
+    res["mixed"] = {"value": inp.nprob / (msm * 1e-3), "unit": UNIT, "ms_per_step": msm, "stages_ms": stm,
+                    "precision": "NAO_MIXED_BF16X3 + one Ritz sweep", "status_ok": out["status_ok"]}
+    errors(out, "mixed_refined")
+    del out
+    ctx.close()
+    torch.cuda.empty_cache()
+    res["mixed_over_fp64_speed"] = res["mixed"]["value"] / res["fp64"]["value"]
+    res["vs_oracle"] = {"problems": sorted(gold), "per_problem": checks,
+                        "source": "tests/golden/mixed_n2000_oracle_eps.txt (oracle/ only)"}
+    worst = [c.get("mixed_refined_max_abs_deps_Ha") for c in checks.values()]
+    res["mixed_bound_Ha"] = 1e-9
+    res["mixed_meets_bound"] = bool(worst and all(w is not None and w <= 1e-9 for w in worst))
+    return res
+
+
+def run_large_basis(local_rank, sizes=(1000, 2000, 3000), steps=2, warmup=1):
+    """The large-basis FP64 sweep: n in {1000, 2000, 3000}, 4x4x1 k, one spin, seed 3, overlap
+    condition ~1e8 plus one orbital in 50 duplicated (exact null directions; m = n - n/50).
+    Per size: solves/s of the band step (Parts 1-6) and its per-stage split; the Householder
+    panel kernel's achieved HBM rate by its algorithmic bytes."""
+    import torch
+    from paper_1402_4247_gb300 import synth
+    from paper_1402_4247_gb300.nao import Context
+    dev = torch.device("cuda", local_rank)
+    hbm, _ = _hbm_peak()
+    rows = []
+    for n in sizes:
+        inp = synth.scaled_cell(n, seed=3, kgrid=(4, 4, 1), nspin=1, ill_conditioned=True)
+        ctx = Context(local_rank)
+        ms, stages, out = _band_step_timed(ctx, inp, dev, steps, warmup)
+        m_mean = float(out["m"].double().mean())
+        ctx.close()
+        del out
+        torch.cuda.empty_cache()
+        row = {"n": n, "problems_per_step": inp.nprob, "value": inp.nprob / (ms * 1e-3), "unit": UNIT,
+               "ms_per_step": ms, "m_mean": m_mean, "stages_ms": stages}
+        if "hetrd" in stages:
+            row["panel_hbm_frac"] = _panel_bytes(inp, m_mean) / (stages["hetrd"] * 1e-3) / 1e9 / hbm
+        rows.append(row)
+    return {"workload": "large-basis cells (n/25 heavy x 13 + 3n/50 light x 8 orbitals), 125 images, 4x4x1 k, "
+                        "1 spin, eta ~ 1e-8 and one orbital in 50 duplicated (kappa(S) ~ 1e8, exact null "
+                        "directions), seed 3", "sizes": rows}
+
+
 # ------------------------------------------------------------------------------ arms
 
 def run_reference(args, rank, world):
@@ -313,6 +497,7 @@ def run_reference(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _workload_config(inp, {"sample": f"{cores} problems (one per core) per step, Parts 1-4"}),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "nproc": os.cpu_count(), "cpu_model": _cpu_model(),
                          "sample": f"{cores} of 128 (spin, k) problems per step through Parts 1-4 "
                                    f"(Bloch sum for one k + generalized eigensolve), one per process, "
                                    f"single-threaded BLAS"},
@@ -508,6 +693,8 @@ def run_ours(args, rank, world, local_rank):
               "status_ok": bool(int(st.abs().sum()) == 0 and int(rst[0]) == 0)}
 
     serve = run_serve(local_rank) if (world == 1 and not args.no_serve) else None
+    mixed_n2000 = run_mixed_n2000(local_rank) if (world == 1 and not args.quick) else None
+    large_basis = run_large_basis(local_rank) if (world == 1 and not args.quick) else None
 
     t_max = ms_total
     e2e_max = e2e_ms
@@ -526,8 +713,10 @@ def run_ours(args, rank, world, local_rank):
         cnt, wall, _ = sampler.run()
         sampler.close()
         cpu = {"value": cnt / wall, "unit": UNIT, "cores": sampler.cores, "kind": "oracle",
+               "nproc": os.cpu_count(), "cpu_model": _cpu_model(),
                "sample": f"{cnt} of 128 (spin, k) problems through Parts 1-4 (Bloch sum for one k + "
-                         f"generalized eigensolve), one per process, single-threaded BLAS, {wall:.1f} s wall"}
+                         f"generalized eigensolve), one per process on each of {sampler.cores} host cores, "
+                         f"single-threaded BLAS, {wall:.1f} s wall"}
 
     if rank == 0:
         m_mean = float(m.double().mean())
@@ -543,15 +732,18 @@ def run_ours(args, rank, world, local_rank):
         dname, (dms, dcalls, dl) = dom
         per_launch_ms = dms / max(dl, 1)
         if dname == "hetrd":
-            # the Householder panel kernel: its speed-of-light bound is the digit matrix it
-            # streams from HBM every column (the integer dot-product pipe and the FP64 pipe
-            # of its corrections would allow more; the per-resource fractions are in the notes)
+            # the Householder panel kernel against HBM: algorithmic bytes = the trailing
+            # matrix in half storage once per column, (8/3) n^3 per reduction
             hbm, hsrc = _hbm_peak()
             byts = _panel_bytes(inp, m_mean) * args.steps / max(dl, 1)
             achieved = byts / (per_launch_ms * 1e-3) / 1e9
             roof = {"kernel": "hetrd_panel_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": achieved / hbm, "traffic": _load_traffic(dname, (inp.nk + inp.nprob) / (dl / args.steps)),
-                    "peak_source": hsrc, "algorithmic_bytes_per_launch": byts}
+                    "peak_source": hsrc, "algorithmic_bytes_per_launch": byts,
+                    "algorithmic_bytes": "8 sum_L L^2 ~ (8/3) n^3 per reduction: the trailing matrix in half "
+                                         "storage (FP64 complex) once per column",
+                    "digit_stream_bytes_per_launch": _digit_stream_bytes(inp, m_mean) * args.steps / max(dl, 1),
+                    "ms_per_step": dms / args.steps}
         else:
             fl = _stage_flops(dname, inp, m_mean, nocc_mean)
             achieved = (fl * args.steps / max(dl, 1)) / (per_launch_ms * 1e-3) / 1e12 if fl else None
@@ -569,6 +761,7 @@ def run_ours(args, rank, world, local_rank):
             "e2e": {"value": nprob * world / (e2e_max * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu, "mixed": mixed, "subset": subset, "serve": serve,
+            "mixed_n2000": mixed_n2000, "large_basis": large_basis,
             "status_ok": bool(int(st.abs().sum()) == 0 and int(rst[0]) == 0),
         }
         print(json.dumps(line), flush=True)
@@ -585,7 +778,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-stream measurement")
-    ap.add_argument("--cpu-cores", type=int, default=16)
+    ap.add_argument("--quick", action="store_true",
+                    help="skip the n = 2000 mixed-precision and large-basis measurements")
+    ap.add_argument("--cpu-cores", type=int, default=os.cpu_count() or 1,
+                    help="host cores for the oracle (default: all of them)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -58,8 +58,38 @@ enum {
 
 /* Library / context ------------------------------------------------------------------ */
 
-/* Create a context bound to CUDA device `device`.  *out receives the handle.             */
-int nao_init(nao_ctx** out, int device);
+/* Run-time settings of a context (nao_config_defaults fills the defaults).              */
+typedef struct {
+  double f_min;               /* occupation at or below which a band is left out of the
+                                 density matrices and treated as empty (Part 6); default
+                                 1e-16, range [0, 1e-3]                                      */
+  int inverse_iteration_max;  /* inverse-iteration solves per eigenvector of the
+                                 tridiagonal solve (Eigen_HH step 2) before it is declared
+                                 not converged (status NAO_E_NOCONV, vector still written);
+                                 default 5, range [0, 64]; 0 makes every vector fail         */
+  long long tc_wait_cycles;   /* bound, in SM clock cycles, on each wait of a tensor-core
+                                 product's copy/MMA pipeline; when it expires the product's
+                                 block lets its copies land, skips its output, frees its
+                                 tensor memory and raises the context's timeout flag
+                                 (reported as NAO_E_TIMEOUT by the next status, below);
+                                 default 4e9 (~2 s), range [1, 1e12]; below 1024 each wait
+                                 is a single non-blocking test (to exercise that path)       */
+} nao_config;
+
+void nao_config_defaults(nao_config* cfg);
+
+/* Create a context bound to CUDA device `device`.  *out receives the handle.
+ *   hbm_budget_bytes  upper bound on the device memory the context itself holds (its
+ *                     workspace arena); a call whose workspace would exceed it fails with
+ *                     NAO_E_NOMEM before any launch.  0: no bound.  The serving scheduler
+ *                     (below) admits requests within this budget unless nao_serve_config
+ *                     sets another.
+ *   cfg               settings, or NULL for the defaults.                                  */
+int nao_init(nao_ctx** out, int device, size_t hbm_budget_bytes, const nao_config* cfg);
+/* Read / replace the settings of a context (between calls; the new ones apply to work
+ * enqueued afterwards).  NAO_E_INVALID for values outside the ranges above.                */
+int nao_get_config(const nao_ctx* ctx, nao_config* cfg);
+int nao_set_config(nao_ctx* ctx, const nao_config* cfg);
 /* Release the context and its workspace (after all its work has completed).             */
 void nao_destroy(nao_ctx* ctx);
 /* Text of the last host-side error on this context ("" if none).  Valid until the next
@@ -100,7 +130,8 @@ int nao_zgemm(nao_ctx* ctx, int method, int nprob, int M, int N, int K, double a
  * With NAO_GEMM_TC (the default) and nk >= 8 the sum is one FP64-accurate tensor-core
  * product per chunk of rows (phase matrix [cos; sin] times the element columns; the
  * context's workspace grows by up to 256 MB); otherwise FP64 FMAs.  A tensor-core wait that
- * expired shows as NAO_E_TIMEOUT in the status of the context's next nao_gen_eig.          */
+ * expired (see nao_config.tc_wait_cycles) shows as NAO_E_TIMEOUT in the status of the
+ * context's next nao_gen_eig or nao_density_matrix, which reports it once.                 */
 int nao_bloch_sum(nao_ctx* ctx, int n, int nR, const int32_t* R, int nmat, const double* MR,
                   int nk, const double* kpts, nao_c128* Mk, void* stream);
 
@@ -135,7 +166,10 @@ int nao_bloch_sum(nao_ctx* ctx, int n, int nR, const int32_t* R, int nmat, const
  *             eps[j], S-orthonormal (C^H S C = I); columns j >= m are zero
  *   m_kept    int32 [nprob] out: m, the number of kept overlap directions
  *   status    int32 [nprob] out: 0, NAO_E_NOCONV (a vector did not converge within the
- *             iteration bound; results still written) or NAO_E_ALLCUT (m = 0)          */
+ *             iteration bound nao_config.inverse_iteration_max; results still written),
+ *             NAO_E_ALLCUT (m = 0) or NAO_E_TIMEOUT (a tensor-core wait of this call, or of
+ *             an earlier call on the context not yet reported, expired: results invalid).
+ * Workspace: grows on demand (NAO_E_NOMEM past the context's hbm_budget_bytes).             */
 int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c128* S,
                 const int32_t* s_of_prob, int nS, double s_cut, int precision, int nb,
                 double* eps, nao_c128* C, int32_t* m_kept, int32_t* status, void* stream);
@@ -152,11 +186,13 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
  * The k sum runs, like Part 1's, as FP64-accurate tensor-core products (cos Re P + sin Im P)
  * with NAO_GEMM_TC and nk >= 8, else with FP64 FMAs.
  *   eps, C, m_kept as written by nao_gen_eig (C [nprob][n][nb]); bands j >= nb must be
- *     unoccupied (f <= 1e-16), else status NAO_E_INVALID is written.
+ *     unoccupied (f <= f_min), else status NAO_E_INVALID is written.
  *   mu_out, eband_out  float64 [1] out (device);  f_out float64 [nprob][n] out or NULL
  *   rhoR   float64 [nspin][nR][n][n] out (device)
  *   edmR   float64 [nspin][nR][n][n] out (device), or NULL to skip it
- *   status int32 [1] out (device): 0, NAO_E_RANGE or NAO_E_INVALID                    */
+ *   status int32 [1] out (device): 0, NAO_E_RANGE, NAO_E_INVALID or NAO_E_TIMEOUT (a
+ *          tensor-core wait expired, as in nao_gen_eig)
+ * Bands with f <= nao_config.f_min are left out of rhoR and edmR.                          */
 int nao_density_matrix(nao_ctx* ctx, int n, int nspin, int nk, const double* wk,
                        const double* kpts, const double* eps, const nao_c128* C, int nb,
                        const int32_t* m_kept, double n_electrons, double kT, int nR,
@@ -183,13 +219,15 @@ int64_t nao_launch_count(const nao_ctx* ctx);
  * and forbid allocations behind their back, and loops that cannot afford the device
  * synchronisation a cudaMalloc/cudaFree may cause.  It takes no context and never calls
  * cudaMalloc, cudaFree or an allocating library routine: its scratch (grid partial sums
- * and per-problem occupied-band counts, 296 KiB) is a static array in the library image,
- * resident on every GPU that loads the library until the process exits.
+ * and per-problem occupied-band counts, 288.5 KiB = 295,424 bytes) is a static array in the
+ * library image, resident on every GPU that loads the library until the process exits.
  *   Limits: nspin * nk <= 65536 problems (else NAO_E_INVALID); runs on the current
  *   device, on `stream`; f_out float64 [nspin*nk][n] is required.
  *   Set-up: the first call on a device looks up the scratch array's device address
  *   (cudaGetSymbolAddress, once per device, with that device current); make that first
- *   call before any stream capture.
+ *   call before any stream capture.  The address is kept for the life of the process: do
+ *   not cudaDeviceReset a device between calls (the kept address would be stale).
+ *   The band cut f_min is the default of nao_config (1e-16).
  *   Sharing: every call uses the same scratch and leaves its contents behind (the kernel
  *   resets what must start at zero).  Calls that overlap on the GPU (other streams, other
  *   host threads) race on it and must be serialised by the caller.
@@ -248,7 +286,8 @@ typedef struct {
 } nao_result;
 
 /* Scheduler settings; call before the first submit (or when nothing is queued or running).
- * Defaults: 80 % of the free device memory at the first submit, 256 problems, 2 slots.   */
+ * Defaults: the context's hbm_budget_bytes, or (when that is 0) 80 % of the free device
+ * memory at the first submit; 256 problems; 2 slots.                                        */
 int nao_serve_config(nao_ctx* ctx, size_t hbm_budget_bytes, int max_batch_problems, int slots);
 /* Hold (on = 1) or resume (on = 0) admission: while held, requests queue but none starts;
  * running batches finish.  For draining a device or assembling a batch deliberately.     */

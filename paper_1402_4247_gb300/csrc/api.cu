@@ -22,6 +22,9 @@ int nao_fail(nao_ctx* ctx, int code, const char* fmt, ...) {
 
 int nao_ws_reserve(nao_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->ws_bytes) return NAO_OK;
+  if (ctx->hbm_budget && bytes > ctx->hbm_budget)
+    return nao_fail(ctx, NAO_E_NOMEM, "workspace of %zu bytes exceeds the context's HBM budget of %zu bytes", bytes,
+                    ctx->hbm_budget);
   // Growing the arena frees the old one: wait for work that may still use it.
   NAO_CUDA_TRY(ctx, cudaDeviceSynchronize());
   if (ctx->ws) {
@@ -30,6 +33,7 @@ int nao_ws_reserve(nao_ctx* ctx, size_t bytes) {
     ctx->ws_bytes = 0;
   }
   size_t want = bytes + bytes / 8;
+  if (ctx->hbm_budget && want > ctx->hbm_budget) want = ctx->hbm_budget;
   cudaError_t e = cudaMalloc(&ctx->ws, want);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -133,8 +137,18 @@ __global__ void finish_status_kernel(int nprob, const int32_t* mP, const int32_t
   m_kept[p] = mP[p];
   int32_t s = statP[p];
   if (s == 0) s = statH[p];
-  if (s == 0 && flags[0]) s = NAO_E_TIMEOUT;
+  if (s == 0 && flags[NAO_FLAG_TIMEOUT]) s = NAO_E_TIMEOUT;
   status[p] = s;
+}
+
+// after the statuses that report it: status[0..nstatus) of a one-word status array takes
+// NAO_E_TIMEOUT if the flag is set and it is 0; the flag is cleared (reported once)
+__global__ void report_timeout_kernel(int* flags, int32_t* status, int nstatus) {
+  if (threadIdx.x != 0) return;
+  if (status && flags[NAO_FLAG_TIMEOUT])
+    for (int i = 0; i < nstatus; ++i)
+      if (status[i] == 0) status[i] = NAO_E_TIMEOUT;
+  flags[NAO_FLAG_TIMEOUT] = 0;
 }
 
 // One batched complex product of the band step, on the tensor cores (digit planes) when the
@@ -379,6 +393,24 @@ bool is_device_ptr(const void* p) {
 
 }  // namespace
 
+cudaError_t launch_report_timeout(int* flags, int32_t* status, int nstatus, cudaStream_t st) {
+  report_timeout_kernel<<<1, 32, 0, st>>>(flags, status, nstatus);
+  return cudaGetLastError();
+}
+
+static int check_config(const nao_config& c) {
+  return (c.f_min >= 0.0 && c.f_min <= 1e-3 && c.inverse_iteration_max >= 0 && c.inverse_iteration_max <= 64 &&
+          c.tc_wait_cycles >= 1 && c.tc_wait_cycles <= 1000000000000LL)
+             ? NAO_OK
+             : NAO_E_INVALID;
+}
+
+// the wait bound lives in device memory, where the tensor-core kernels read it
+static cudaError_t push_wait_bound(nao_ctx* c) {
+  const long long w = c->cfg.tc_wait_cycles;
+  return cudaMemcpy(c->dev_flags + NAO_FLAG_WAIT, &w, sizeof w, cudaMemcpyHostToDevice);
+}
+
 size_t gen_eig_ws_bytes(const nao_ctx* ctx, int n, int nprob, int nSe) {
   const bool use_tc = ctx->gemm_method == NAO_GEMM_TC && zgemm_oz_supported(GemmDims{n, n, n, nullptr, nullptr, nullptr, 0});
   return plan_gen_eig(n, nprob, nSe, use_tc).bytes;
@@ -396,9 +428,20 @@ size_t bloch_ws_bytes(const nao_ctx* ctx, int n, int nR, int nmat, int nk) {
 
 extern "C" {
 
-int nao_init(nao_ctx** out, int device) {
+void nao_config_defaults(nao_config* cfg) {
+  if (!cfg) return;
+  cfg->f_min = NAO_F_MIN_DEFAULT;
+  cfg->inverse_iteration_max = NAO_INV_ITER_DEFAULT;
+  cfg->tc_wait_cycles = NAO_TC_WAIT_DEFAULT;
+}
+
+int nao_init(nao_ctx** out, int device, size_t hbm_budget_bytes, const nao_config* cfg) {
   if (!out) return nao_fail(nullptr, NAO_E_INVALID, "nao_init: out is NULL");
   *out = nullptr;
+  nao_config conf;
+  nao_config_defaults(&conf);
+  if (cfg) conf = *cfg;
+  if (check_config(conf) != NAO_OK) return nao_fail(nullptr, NAO_E_INVALID, "nao_init: configuration out of range");
   int count = 0;
   cudaError_t e = cudaGetDeviceCount(&count);
   if (e != cudaSuccess || count == 0)
@@ -414,9 +457,13 @@ int nao_init(nao_ctx** out, int device) {
     return nao_fail(nullptr, NAO_E_CUDA, "nao_init: %s", cudaGetErrorString(e));
   }
   c->num_sms = prop.multiProcessorCount;
+  c->hbm_budget = hbm_budget_bytes;
+  c->cfg = conf;
   e = cudaMalloc(&c->dev_flags, 64 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->dev_flags, 0, 64 * sizeof(int));
+  if (e == cudaSuccess) e = push_wait_bound(c);
   if (e != cudaSuccess) {
+    if (c->dev_flags) cudaFree(c->dev_flags);
     delete c;
     return nao_fail(nullptr, NAO_E_CUDA, "nao_init: %s", cudaGetErrorString(e));
   }
@@ -435,6 +482,23 @@ void nao_destroy(nao_ctx* ctx) {
     if (ctx->dev_flags) cudaFree(ctx->dev_flags);
   }
   delete ctx;
+}
+
+int nao_get_config(const nao_ctx* ctx, nao_config* cfg) {
+  if (!ctx || !cfg) return nao_fail(nullptr, NAO_E_INVALID, "nao_get_config: NULL argument");
+  *cfg = ctx->cfg;
+  return NAO_OK;
+}
+
+int nao_set_config(nao_ctx* ctx, const nao_config* cfg) {
+  if (!ctx || !cfg) return nao_fail(nullptr, NAO_E_INVALID, "nao_set_config: NULL argument");
+  if (check_config(*cfg) != NAO_OK) return nao_fail(ctx, NAO_E_INVALID, "nao_set_config: configuration out of range");
+  DeviceGuard g(ctx->device);
+  // the bound is read by kernels at their start: make the change after the work queued so far
+  NAO_CUDA_TRY(ctx, cudaDeviceSynchronize());
+  ctx->cfg = *cfg;
+  NAO_CUDA_TRY(ctx, push_wait_bound(ctx));
+  return NAO_OK;
 }
 
 int nao_profile_enable(nao_ctx* ctx, int on) {
@@ -594,7 +658,8 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   // ---- Part 2: Eigen_HH(S) -> s, U;  X = U_m s_m^{-1/2}
   NAO_STAGE("herm_fill", 1, launch_herm_fill(n, nSe, (const z64*)S, snn, nullptr, AS, n, snn, st));
   NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nSe, nullptr, AS, dS, eS, tauS, VWp, ozws, st, NAO_OZ_DIGITS_FP64, digp, erowp));
-  NAO_STAGE("stein", 1, launch_stein(n, nSe, nullptr, dS, eS, n, wS, Z, n, snn, scr, stS, nullptr, n, st));
+  NAO_STAGE("stein", 1, launch_stein(n, nSe, nullptr, dS, eS, n, wS, Z, n, snn, scr, stS, nullptr, n,
+                                     ctx->cfg.inverse_iteration_max, st));
   NAO_STAGE("misc", 1, launch_count_kept(n, nSe, wS, n, s_cut, mS, stS, st));
   double* Zo = Z2;  // the Newton-Schulz result (Z itself on the tensor-core method)
   {  // one Newton-Schulz step: Z (3I - Z^T Z)/2 = Z - Z (Z^T Z - I)/2
@@ -633,7 +698,8 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   const bool all_vecs = mixed && ctx->refine_sweeps > 0;
   const int32_t* nvP = all_vecs ? mP : nbP;
   const int nv_max = (C || all_vecs) ? n : 0;
-  NAO_STAGE("stein", 1, launch_stein(n, nprob, mP, dH, eH, n, wH, Z, n, snn, scr, stH, nvP, nv_max, st));
+  NAO_STAGE("stein", 1, launch_stein(n, nprob, mP, dH, eH, n, wH, Z, n, snn, scr, stH, nvP, nv_max,
+                                     ctx->cfg.inverse_iteration_max, st));
   if (nv_max > 0) {
     {
       GemmDims d{n, n, n, nvP, nvP, mP, 1};
@@ -703,6 +769,7 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
     finish_status_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(nprob, mP, stP, stH, ctx->dev_flags, m_kept, status);
     NAO_CUDA_TRY(ctx, cudaGetLastError());
   }
+  NAO_STAGE("misc", 1, launch_report_timeout(ctx->dev_flags, nullptr, 0, st));  // reported: clear the flag
   return NAO_OK;
 }
 
@@ -736,8 +803,8 @@ int nao_density_matrix(nao_ctx* ctx, int n, int nspin, int nk, const double* wk,
   int32_t* st_local = (int32_t*)(ws + ost);
   z64* Cs = (z64*)(ws + oCs);
   z64* Pk = (z64*)(ws + oP);
-  NAO_STAGE("fermi", 1, launch_fermi(ctx->num_sms, n, nprob, nk, gdeg, wk, eps, m_kept, nb, n_electrons, kT, f, nocc,
-                                 mu_out, eband_out, status ? status : st_local, scr, st));
+  NAO_STAGE("fermi", 1, launch_fermi(ctx->num_sms, n, nprob, nk, gdeg, wk, eps, m_kept, nb, n_electrons, kT,
+                                     ctx->cfg.f_min, f, nocc, mu_out, eband_out, status ? status : st_local, scr, st));
   NAO_STAGE("misc", 1, launch_scale_cols_sqrt(n, nprob, nb, (const z64*)C, f, Cs, st));
   {
     // P(k) = Cs Cs^H over the occupied bands (row-major [n][n])
@@ -768,6 +835,7 @@ int nao_density_matrix(nao_ctx* ctx, int n, int nspin, int nk, const double* wk,
                                 use_tc ? (void*)(ws + oOz) : nullptr, st));
     NAO_CUDA_TRY(ctx, phase_sum(edmR));
   }
+  NAO_STAGE("misc", 1, launch_report_timeout(ctx->dev_flags, status ? status : st_local, 1, st));
   return NAO_OK;
 }
 

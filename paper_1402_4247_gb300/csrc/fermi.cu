@@ -65,8 +65,8 @@ __device__ double grid_sum(cg::grid_group& grid, double v, double* red, double* 
 
 __global__ void __launch_bounds__(FT)
 fermi_kernel(int n, int nprob, int nk, double g, const double* __restrict__ wk, const double* __restrict__ eps,
-             const int32_t* __restrict__ m, int nb, double n_electrons, double kT, double* __restrict__ f,
-             int32_t* __restrict__ nocc, double* __restrict__ mu_out, double* __restrict__ eband_out,
+             const int32_t* __restrict__ m, int nb, double n_electrons, double kT, double f_min,
+             double* __restrict__ f, int32_t* __restrict__ nocc, double* __restrict__ mu_out, double* __restrict__ eband_out,
              int32_t* __restrict__ status, double* __restrict__ scratch) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double red[32];
@@ -127,7 +127,7 @@ fermi_kernel(int n, int nprob, int nk, double g, const double* __restrict__ wk, 
     if (st == 0 && j < m[p]) {
       fj = fermi_fn((eps[idx] - mu) / kT);
       eb += g * wk[p % nk] * fj * eps[idx];
-      if (fj > NAO_F_MIN) atomicMax(&nocc[p], j + 1);
+      if (fj > f_min) atomicMax(&nocc[p], j + 1);
     }
     f[idx] = fj;
   }
@@ -155,14 +155,15 @@ fermi_kernel(int n, int nprob, int nk, double g, const double* __restrict__ wk, 
 size_t fermi_scratch_doubles(int num_sms) { return (size_t)4 * num_sms + 64; }
 
 cudaError_t launch_fermi(int num_sms, int n, int nprob, int nk, double g, const double* wk, const double* eps,
-                         const int32_t* m, int nb, double n_electrons, double kT, double* f, int32_t* nocc,
-                         double* mu, double* eband, int32_t* status, double* scratch, cudaStream_t st) {
+                         const int32_t* m, int nb, double n_electrons, double kT, double f_min, double* f,
+                         int32_t* nocc, double* mu, double* eband, int32_t* status, double* scratch, cudaStream_t st) {
   int per_sm = 0;
   cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fermi_kernel, FT, 0);
   if (err != cudaSuccess) return err;
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
   int grid = num_sms;  // one block per SM is enough: ~nprob*n/(num_sms*FT) values per thread
-  void* args[] = {&n, &nprob, &nk, &g, &wk, &eps, &m, &nb, &n_electrons, &kT, &f, &nocc, &mu, &eband, &status, &scratch};
+  void* args[] = {&n,  &nprob, &nk,   &g,  &wk,    &eps,   &m,       &nb,     &n_electrons,
+                  &kT, &f_min, &f,    &nocc, &mu,  &eband, &status, &scratch};
   return cudaLaunchCooperativeKernel((const void*)fermi_kernel, dim3(grid), dim3(FT), args, 0, st);
 }
 
@@ -187,7 +188,8 @@ constexpr size_t NOALLOC_PART_DOUBLES = 4 * (size_t)NOALLOC_MAX_BLOCKS + 64;
 constexpr size_t NOALLOC_DOUBLES = NOALLOC_PART_DOUBLES + NOALLOC_MAX_PROBLEMS / 2;  // + int32 counts
 }  // namespace
 
-// 296 KiB of device memory, held by every GPU that loads the library until the process exits.
+// 288.5 KiB (295,424 bytes) of device memory, held by every GPU that loads the library until
+// the process exits.
 static __device__ __align__(256) double nao_fermi_scratch[NOALLOC_DOUBLES];
 
 namespace {
@@ -195,8 +197,10 @@ std::mutex g_noalloc_mu;
 constexpr int NOALLOC_MAX_DEVICES = 64;
 void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 
-// Device address of nao_fermi_scratch on the current device, looked up once per device.
-// (In host code the symbol names a host-side shadow, not device memory.)
+// Device address of nao_fermi_scratch on the current device, looked up once per device and
+// kept for the life of the process (a cudaDeviceReset of the device in between would leave
+// it stale; the entry point's documentation excludes that).  In host code the symbol names
+// a host-side shadow, not device memory.
 cudaError_t noalloc_scratch(int dev, double** out) {
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
@@ -232,8 +236,8 @@ extern "C" int nao_fermi_level_noalloc(int n, int nspin, int nk, const double* w
     return nao_fail(nullptr, NAO_E_CUDA, "nao_fermi_level_noalloc: %s", cudaGetErrorString(e));
   const int grid = sms < NOALLOC_MAX_BLOCKS ? sms : NOALLOC_MAX_BLOCKS;
   int32_t* nocc = (int32_t*)(scratch + NOALLOC_PART_DOUBLES);
-  e = launch_fermi(grid, n, nspin * nk, nk, nspin == 1 ? 2.0 : 1.0, wk, eps, m_kept, nb, n_electrons, kT, f_out,
-                   nocc, mu_out, eband_out, status, scratch, (cudaStream_t)stream);
+  e = launch_fermi(grid, n, nspin * nk, nk, nspin == 1 ? 2.0 : 1.0, wk, eps, m_kept, nb, n_electrons, kT,
+                   NAO_F_MIN_DEFAULT, f_out, nocc, mu_out, eband_out, status, scratch, (cudaStream_t)stream);
   if (e != cudaSuccess)
     return nao_fail(nullptr, NAO_E_CUDA, "nao_fermi_level_noalloc: launch failed: %s", cudaGetErrorString(e));
   return NAO_OK;

@@ -80,9 +80,23 @@ struct nao_ctx {
   std::vector<cudaEvent_t> event_pool;
   int gemm_method = NAO_GEMM_TC;
   int refine_sweeps = 1;     // Ritz refinement sweeps after a mixed-precision solve (0, 1 or 2)
-  int* dev_flags = nullptr;  // [0]: a bounded wait in a tensor-core kernel expired
+  int* dev_flags = nullptr;  // NAO_FLAG_*: device words shared by the context's kernels
+  size_t hbm_budget = 0;     // bound on the workspace arena (0: none)
+  nao_config cfg{};          // run-time settings (nao_init / nao_set_config)
   struct NaoServer* server = nullptr;  // request scheduler (csrc/serve.cu), made on first use
 };
+
+// Layout of nao_ctx::dev_flags (64 ints of device memory):
+//   [NAO_FLAG_TIMEOUT]   set to 1 by a tensor-core product whose bounded wait expired;
+//                        reported (and cleared) by the next nao_gen_eig / nao_density_matrix
+//   [NAO_FLAG_WAIT .. +1] long long: the wait bound in SM cycles (nao_config.tc_wait_cycles),
+//                        read by the tensor-core kernels at their start
+constexpr int NAO_FLAG_TIMEOUT = 0;
+constexpr int NAO_FLAG_WAIT = 2;
+// Defaults of nao_config.
+constexpr double NAO_F_MIN_DEFAULT = 1e-16;
+constexpr int NAO_INV_ITER_DEFAULT = 5;
+constexpr long long NAO_TC_WAIT_DEFAULT = 4000000000LL;  // ~2 s at 2 GHz
 
 // Workspace bytes nao_gen_eig / nao_density_matrix reserve on this context (before the
 // arena's 1/8 headroom); the scheduler's admission test uses them.
@@ -163,9 +177,11 @@ cudaError_t launch_hetrd_digits(int n, int nprob, const int32_t* size, const z64
 size_t stein_scratch_doubles(int n, int nprob);
 // nvec (nullable: all) and nvec_max bound the eigenvectors computed per problem to the lowest
 // min(nvec[p], nvec_max); the eigenvalues are always all computed.
+// maxits: inverse-iteration solves per vector before NAO_E_NOCONV (nao_config).
 cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d, const double* e,
                          long long strideV, double* w, double* Z, int ld, long long strideZ,
-                         double* scratch, int32_t* status, const int32_t* nvec, int nvec_max, cudaStream_t st);
+                         double* scratch, int32_t* status, const int32_t* nvec, int nvec_max, int maxits,
+                         cudaStream_t st);
 
 // Blocked (compact WY) back-transformation helpers, see backtr.cu.
 constexpr int NAO_WY_NB = 128;
@@ -222,7 +238,8 @@ cudaError_t launch_ns_correct(int n, int nprob, const int32_t* size, const int32
 // FP64-accurate complex GEMM on the BF16 tensor cores (digit-plane splitting): C = alpha
 // op(A) op(B) + beta C with real alpha, beta.  Contractions longer than 896 (1792 real) run
 // as chunks whose FP32 group sums stay exact, accumulated in FP64.  ws: zgemm_oz_workspace
-// bytes; err: device int set to 1 if a bounded wait expired.  digits: NAO_OZ_DIGITS_FP64
+// bytes; err: the context's dev_flags (err[NAO_FLAG_TIMEOUT] set to 1 if a bounded wait
+// expired; the bound is the long long at err + NAO_FLAG_WAIT).  digits: NAO_OZ_DIGITS_FP64
 // (ten base-64 planes, FP64 accuracy) or NAO_OZ_DIGITS_MIXED (five planes: 30 bits, a little
 // above an FP32 or three-term BF16 split product; 15 tensor-core products instead of 55).
 constexpr int NAO_OZ_DIGITS_FP64 = 10;
@@ -265,11 +282,13 @@ cudaError_t launch_write_eps(int n, int nprob, const int32_t* m, const double* w
 cudaError_t launch_zero_cols(int n, int nprob, int nb, const int32_t* m, z64* C, cudaStream_t st);
 
 // Part 5: mu by bisection on the electron count, f, E_band, and per problem the number of
-// occupied bands (f > NAO_F_MIN), in one cooperative grid-wide kernel.
-constexpr double NAO_F_MIN = 1e-16;
+// occupied bands (f > f_min), in one cooperative grid-wide kernel.
 cudaError_t launch_fermi(int num_sms, int n, int nprob, int nk, double g, const double* wk, const double* eps,
-                         const int32_t* m, int nb, double n_electrons, double kT, double* f, int32_t* nocc,
-                         double* mu, double* eband, int32_t* status, double* scratch, cudaStream_t st);
+                         const int32_t* m, int nb, double n_electrons, double kT, double f_min, double* f,
+                         int32_t* nocc, double* mu, double* eband, int32_t* status, double* scratch, cudaStream_t st);
+// status[0] <- NAO_E_TIMEOUT if the context's timeout flag is set and status[0] is 0; the
+// flag is cleared (it is reported once).  status may be NULL (then the flag is only cleared).
+cudaError_t launch_report_timeout(int* flags, int32_t* status, int nstatus, cudaStream_t st);
 size_t fermi_scratch_doubles(int num_sms);
 
 // Part 6 helpers: Cs = C diag(sqrt f), Ce = Cs diag(eps) (occupied columns), and the inverse

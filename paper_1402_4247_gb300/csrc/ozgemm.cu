@@ -25,9 +25,10 @@
 //    everything converted to FP64 once and scaled by 2^{e_i + f_j - 42}; real alpha, beta.
 // Pipeline: the digit tiles of each K step (16) arrive in one of three shared-memory stages
 // by bulk asynchronous copies (TMA) issued by one producer thread; one thread issues the
-// MMAs and commits them to the stage's barrier.  Every wait is bounded (clock64); on
-// timeout the block records an error, lets its copies land, skips its epilogue and still
-// frees its tensor memory.
+// MMAs and commits them to the stage's barrier.  Every wait is bounded (clock64; the
+// pipeline's waits by the context's nao_config.tc_wait_cycles); on timeout the block records
+// an error, waits for its issued MMAs and lets its issued copies land (both with the fixed
+// long bound), skips its epilogue and still frees its tensor memory.
 #include <cuda_bf16.h>
 
 #include "nao_internal.cuh"
@@ -47,7 +48,7 @@ constexpr int OZ_STAGES = 3;
 // the other's MMAs; their B tiles are the contiguous 32-row halves of the 64-row plane tiles.
 constexpr int OZ_SHORT_KSTEPS = 16;
 constexpr int OZ_THREADS = 256;
-constexpr long long OZ_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+constexpr long long OZ_WAIT_CYCLES = NAO_TC_WAIT_DEFAULT;  // ~2 s at 2 GHz
 constexpr int OZ_MAX_K2 = 1792;      // 2K bound for exact FP32 group sums (group 8: 9 2^10 per k)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -262,14 +263,25 @@ __device__ __forceinline__ void oz_mma(uint32_t dtmem, uint64_t adesc, uint64_t 
                :: "r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ bool oz_wait(uint64_t* mbar, uint32_t parity) {
+// A bound below OZ_PROBE_CYCLES makes the wait one non-blocking test (try_wait may suspend
+// the thread for a while on its own, so a short bound would otherwise expire or not
+// depending on that suspension).
+constexpr long long OZ_PROBE_CYCLES = 1024;
+
+__device__ __forceinline__ bool oz_wait(uint64_t* mbar, uint32_t parity, long long limit = OZ_WAIT_CYCLES) {
+  if (limit < OZ_PROBE_CYCLES) {
+    uint32_t ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(smem_u32(mbar)), "r"(parity));
+    return ok != 0;
+  }
   const long long t0 = clock64();
   while (true) {
     uint32_t ok;
     asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                  : "=r"(ok) : "r"(smem_u32(mbar)), "r"(parity));
     if (ok) return true;
-    if (clock64() - t0 > OZ_WAIT_CYCLES) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -347,12 +359,17 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tbase;
 
+  // the pipeline's waits take the context's bound (nao_config.tc_wait_cycles); the wait for
+  // the issued MMAs and the drain of issued copies after a failure keep the fixed long bound,
+  // so that no copy or MMA is still in flight when the block frees its memory
+  long long wait_lim = err ? *(const volatile long long*)(err + NAO_FLAG_WAIT) : OZ_WAIT_CYCLES;
+  if (wait_lim <= 0) wait_lim = OZ_WAIT_CYCLES;
   if (warp == 0 && lane == 0) {
     // ---------------- producer
     int ks = 0;
     for (; ks < nks_p; ++ks) {
       const int st = ks % NST;
-      if (ks >= NST && !oz_wait(&empty_bar[st], ((ks / NST) - 1) & 1)) {
+      if (ks >= NST && !oz_wait(&empty_bar[st], ((ks / NST) - 1) & 1, wait_lim)) {
         s_fail = 1;
         break;
       }
@@ -375,7 +392,7 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
     int ks = 0;
     for (; ks < nks_p; ++ks) {
       const int st = ks % NST;
-      if (!oz_wait(&full_bar[st], (ks / NST) & 1)) {
+      if (!oz_wait(&full_bar[st], (ks / NST) & 1, wait_lim)) {
         s_fail = 1;
         break;
       }
@@ -423,7 +440,7 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (s_fail) {
     if (tid == 0) {
-      atomicExch(err, 1);
+      atomicExch(err + NAO_FLAG_TIMEOUT, 1);
       // let every bulk copy that was issued land before the block (and its shared memory) goes
       const int issued = s_issued;
       for (int ks = (issued > NST ? issued - NST : 0); ks < issued; ++ks)

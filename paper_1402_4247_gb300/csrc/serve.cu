@@ -401,6 +401,7 @@ NaoServerCore* get_server(nao_ctx* ctx) {
 int start_server(nao_ctx* ctx, NaoServerCore* s) {
   if (s->started) return NAO_OK;
   cudaSetDevice(s->device);
+  if (s->budget == 0) s->budget = ctx->hbm_budget;  // the context's budget, when it has one
   if (s->budget == 0) {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return nao_fail(ctx, NAO_E_CUDA, "nao_serve: cudaMemGetInfo failed");
@@ -417,7 +418,9 @@ int start_server(nao_ctx* ctx, NaoServerCore* s) {
   for (int i = 0; i < s->nslots; ++i) {
     auto slot = std::make_unique<ServeSlot>();
     slot->srv = s;
-    int rc = nao_init(&slot->sub, s->device);
+    // a slot's context takes the owner's settings; its workspace is bounded by the
+    // scheduler's admission test, not by a budget of its own
+    int rc = nao_init(&slot->sub, s->device, 0, &ctx->cfg);
     if (rc) return nao_fail(ctx, rc, "nao_serve: slot context: %s", nao_last_error(nullptr));
     nao_set_gemm_method(slot->sub, ctx->gemm_method);
     if (cudaStreamCreateWithFlags(&slot->stream, cudaStreamNonBlocking) != cudaSuccess)

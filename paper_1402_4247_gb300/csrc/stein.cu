@@ -20,10 +20,11 @@
 //        one thread per queue entry, so that its warps are full.
 // * Eigenvectors (kernel 2, same block split): inverse iteration with a partially pivoted LU
 //   of T - lambda I (tiny pivots perturbed to eps |T|), a scaled right-hand side, the growth
-//   test |x|_inf >= sqrt(0.1/blocksize) plus two extra solves, and modified Gram-Schmidt
-//   against the earlier members of a TIGHT cluster (gap < 1e-7 |T|_1), whose leader walks the
-//   cluster in order.  Wider near-degeneracies leave overlaps of order eps|T|/gap <= ~1e-9,
-//   which the caller removes with one Newton-Schulz step Z <- Z (3I - Z^T Z)/2.
+//   test |x|_inf >= sqrt(0.1/blocksize) within `maxits` solves plus two extra solves, and
+//   modified Gram-Schmidt against the earlier members of a TIGHT cluster (gap < 1e-7 |T|_1),
+//   whose leader walks the cluster in order.  Wider near-degeneracies leave overlaps of order
+//   eps|T|/gap <= ~1e-9, which the caller removes with one Newton-Schulz step
+//   Z <- Z (3I - Z^T Z)/2.
 //   A tight cluster of more than BIG members (the near-null spectrum of an ill-conditioned
 //   overlap matrix can chain hundreds) is handed to kernel 3: one block per cluster, the
 //   same iteration with the reorthogonalisation done by the whole block (classical
@@ -40,7 +41,6 @@ constexpr int ST_THREADS = 64;    // = slots per block (eigenvectors): the overl
                                   // has ~36k of them, so 64-thread blocks spread over all SMs
 constexpr int SZ_THREADS = 64;    // = slots per block (eigenvalues): ~8 blocks per SM for 128 problems
                                   // of n = 568, so the SMs' FP64 pipes finish within one block of each other
-constexpr int MAXITS = 5;         // inverse-iteration solves before giving up
 constexpr int EXTRA = 2;          // extra solves after the growth test passes
 constexpr double TIGHT = 1e-7;
 constexpr int NARR = 6;           // scratch arrays per eigenvalue: L, U0inv, U1, U2, PIV, X
@@ -405,7 +405,7 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
                  long long strideV, const double* __restrict__ wslot, double* __restrict__ wbase,
                  double* __restrict__ Zbase, int ldz, long long strideZ, double* __restrict__ scratch,
                  int32_t* __restrict__ status, int* __restrict__ biglist, int bigcap,
-                 const int32_t* __restrict__ nvec, int nvec_max) {
+                 const int32_t* __restrict__ nvec, int nvec_max, int maxits) {
   extern __shared__ double smd[];
   double* d = smd;
   double* e = smd + n;
@@ -532,7 +532,7 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
           AT(X, i) = hash_uniform(((unsigned long long)p << 40) ^ ((unsigned long long)q << 20) ^ (unsigned long long)i);
         int its = 0, nrmchk = 0;
         bool ok = false;
-        while (its < MAXITS + EXTRA) {
+        while (its < maxits + EXTRA) {
           ++its;
           double x1 = 0.0;
           for (int i = b0; i < b1; ++i) x1 += fabs(AT(X, i));
@@ -575,7 +575,7 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
             xinf = fmax(xinf, a);
           }
           if (!finite) break;
-          if (its > MAXITS && nrmchk == 0) break;
+          if (its > maxits && nrmchk == 0) break;
           if (xinf < sqrt(0.1 / bs)) continue;
           ++nrmchk;
           if (nrmchk < EXTRA + 1) continue;
@@ -639,7 +639,7 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
                      const double* __restrict__ ebase, long long strideV, const double* __restrict__ wslot,
                      double* __restrict__ Zbase, int ldz, long long strideZ, double* __restrict__ scratch,
                      int32_t* __restrict__ status, const int* __restrict__ biglist, int bigcap,
-                     const int32_t* __restrict__ nvec, int nvec_max) {
+                     const int32_t* __restrict__ nvec, int nvec_max, int maxits) {
   extern __shared__ double smc[];
   double* d = smc;
   double* e = smc + n;
@@ -737,7 +737,7 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
       __syncthreads();
       int its = 0, nrmchk = 0;
       bool ok = false;
-      while (its < MAXITS + EXTRA) {
+      while (its < maxits + EXTRA) {
         ++its;
         double a1 = 0.0;
         for (int i = b0 + tid; i < b1; i += nt) a1 += fabs(sx[i]);
@@ -793,7 +793,7 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
         }
         const double xinf = block_max1(fin ? am : INFINITY, red);
         if (!(xinf <= DBL_MAX)) break;
-        if (its > MAXITS && nrmchk == 0) break;
+        if (its > maxits && nrmchk == 0) break;
         if (xinf < sqrt(0.1 / bs)) continue;
         ++nrmchk;
         if (nrmchk < EXTRA + 1) continue;
@@ -846,7 +846,7 @@ size_t stein_scratch_doubles(int n, int nprob) {
 
 cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d, const double* e, long long strideV,
                          double* w, double* Z, int ld, long long strideZ, double* scratch, int32_t* status,
-                         const int32_t* nvec, int nvec_max, cudaStream_t st) {
+                         const int32_t* nvec, int nvec_max, int maxits, cudaStream_t st) {
   double* wslot = scratch + (size_t)NARR * n * n * nprob;
   const size_t smem1 = sizeof(double) * 3 * (size_t)n + sizeof(float) * 2 * (size_t)n + sizeof(int) * 2 * (size_t)n;
   cudaError_t err = cudaFuncSetAttribute(stebz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
@@ -881,7 +881,7 @@ cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d,
   err = cudaFuncSetAttribute(stein_vec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
   if (err != cudaSuccess) return err;
   stein_vec_kernel<<<grid, ST_THREADS, smem2, st>>>(n, size, d, e, strideV, wslot, w, Z, ld, strideZ, scratch, status,
-                                                    biglist, bigcap, nvec, nvec_max);
+                                                    biglist, bigcap, nvec, nvec_max, maxits);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   // kernel 3: a grid that stays resident; blocks without a listed cluster exit at once
@@ -892,6 +892,6 @@ cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d,
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   stein_cluster_kernel<<<sms, SC_THREADS, smem3, st>>>(n, size, d, e, strideV, wslot, Z, ld, strideZ, scratch, status,
-                                                       biglist, bigcap, nvec, nvec_max);
+                                                       biglist, bigcap, nvec, nvec_max, maxits);
   return cudaGetLastError();
 }

@@ -28,7 +28,8 @@ NAO_MIXED_TF32 = 1
 NAO_MIXED_BF16X3 = 2
 
 #: every symbol include/nao.h declares
-EXPORTS = ("nao_init", "nao_destroy", "nao_last_error", "nao_workspace_bytes", "nao_bloch_sum",
+EXPORTS = ("nao_config_defaults", "nao_init", "nao_get_config", "nao_set_config", "nao_destroy",
+           "nao_last_error", "nao_workspace_bytes", "nao_bloch_sum",
            "nao_gen_eig", "nao_density_matrix", "nao_profile_enable", "nao_profile_read", "nao_launch_count",
            "nao_fermi_level_noalloc", "nao_set_gemm_method", "nao_set_refinement", "nao_zgemm",
            "nao_gen_eig_workspace", "nao_serve_config", "nao_serve_pause", "nao_serve_submit", "nao_serve_poll",
@@ -41,6 +42,12 @@ _lib = None
 
 class NaoError(RuntimeError):
     pass
+
+
+class NaoConfig(ctypes.Structure):
+    """``nao_config`` of include/nao.h."""
+    _fields_ = [("f_min", ctypes.c_double), ("inverse_iteration_max", ctypes.c_int),
+                ("tc_wait_cycles", ctypes.c_longlong)]
 
 
 class NaoRequest(ctypes.Structure):
@@ -80,8 +87,14 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         _build.build()
     lib = ctypes.CDLL(path)
     vp, i32, f64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
-    lib.nao_init.argtypes = [ctypes.POINTER(vp), i32]
+    lib.nao_config_defaults.argtypes = [ctypes.POINTER(NaoConfig)]
+    lib.nao_config_defaults.restype = None
+    lib.nao_init.argtypes = [ctypes.POINTER(vp), i32, sz, ctypes.POINTER(NaoConfig)]
     lib.nao_init.restype = i32
+    lib.nao_get_config.argtypes = [vp, ctypes.POINTER(NaoConfig)]
+    lib.nao_get_config.restype = i32
+    lib.nao_set_config.argtypes = [vp, ctypes.POINTER(NaoConfig)]
+    lib.nao_set_config.restype = i32
     lib.nao_destroy.argtypes = [vp]
     lib.nao_destroy.restype = None
     lib.nao_last_error.argtypes = [vp]
@@ -146,16 +159,48 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-class Context:
-    """Owns an ``nao_ctx`` (device workspace) on one CUDA device."""
+def nao_config_defaults() -> dict:
+    """The default ``nao_config`` as a dict (f_min, inverse_iteration_max, tc_wait_cycles)."""
+    c = NaoConfig()
+    load_library().nao_config_defaults(ctypes.byref(c))
+    return {k: getattr(c, k) for k, _ in NaoConfig._fields_}
 
-    def __init__(self, device: int = 0):
+
+class Context:
+    """Owns an ``nao_ctx`` (device workspace) on one CUDA device.
+
+    ``hbm_budget_bytes`` bounds the context's workspace (0: no bound); ``config`` is a dict
+    with any of the ``nao_config`` fields (the others keep their defaults)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, config: dict | None = None):
         self.lib = load_library()
         self.handle = ctypes.c_void_p()
-        rc = self.lib.nao_init(ctypes.byref(self.handle), int(device))
+        cfg = None
+        if config is not None:
+            cfg = NaoConfig()
+            self.lib.nao_config_defaults(ctypes.byref(cfg))
+            for k, v in config.items():
+                setattr(cfg, k, v)
+        rc = self.lib.nao_init(ctypes.byref(self.handle), int(device), int(hbm_budget_bytes),
+                               ctypes.byref(cfg) if cfg is not None else None)
         if rc != NAO_OK:
             raise NaoError(f"nao_init failed ({rc}): {self.lib.nao_last_error(None).decode()}")
         self.device = device
+
+    def nao_get_config(self) -> dict:
+        c = NaoConfig()
+        self._check(self.lib.nao_get_config(self.handle, ctypes.byref(c)), "nao_get_config")
+        return {k: getattr(c, k) for k, _ in NaoConfig._fields_}
+
+    def nao_set_config(self, **changes):
+        """Replace some ``nao_config`` fields (synchronises the device first)."""
+        c = NaoConfig()
+        self._check(self.lib.nao_get_config(self.handle, ctypes.byref(c)), "nao_get_config")
+        for k, v in changes.items():
+            if k not in dict(NaoConfig._fields_):
+                raise ValueError(f"unknown nao_config field {k}")
+            setattr(c, k, v)
+        self._check(self.lib.nao_set_config(self.handle, ctypes.byref(c)), "nao_set_config")
 
     def close(self):
         if self.handle:
@@ -349,6 +394,23 @@ def nao_fermi_level_noalloc(wk, eps, m_kept, nb, n_electrons, kT, nspin, f_out, 
     lib = load_library()
     nprob, n = eps.shape
     nk = wk.shape[0]
+    # the kernel walks nspin * nk rows of n entries: every buffer must hold exactly that
+    if nprob != int(nspin) * nk:
+        raise ValueError(f"eps has {nprob} rows, expected nspin * nk = {int(nspin) * nk}")
+    if tuple(f_out.shape) != (nprob, n):
+        raise ValueError(f"f_out must have shape {(nprob, n)}, not {tuple(f_out.shape)}")
+    if tuple(m_kept.shape) != (nprob,):
+        raise ValueError(f"m_kept must have shape {(nprob,)}, not {tuple(m_kept.shape)}")
+    for name, t, dt, numel in (("wk", wk, torch.float64, nk), ("eps", eps, torch.float64, nprob * n),
+                               ("m_kept", m_kept, torch.int32, nprob), ("f_out", f_out, torch.float64, nprob * n),
+                               ("mu_out", mu_out, torch.float64, 1), ("eband_out", eband_out, torch.float64, 1),
+                               ("status", status, torch.int32, 1)):
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, not {t.dtype}")
+        if t.numel() < numel:
+            raise ValueError(f"{name} holds {t.numel()} elements, needs {numel}")
+        if not t.is_cuda or t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} must be on the current CUDA device (cuda:{torch.cuda.current_device()})")
     rc = lib.nao_fermi_level_noalloc(n, int(nspin), nk, _ptr(wk), _ptr(eps), _ptr(m_kept), int(nb),
                                      float(n_electrons), float(kT), _ptr(f_out), _ptr(mu_out), _ptr(eband_out),
                                      _ptr(status), _stream(stream))

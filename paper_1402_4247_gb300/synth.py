@@ -30,6 +30,8 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -156,14 +158,21 @@ def make_cell(
 
     SR = np.empty((nR, n, n))
     HR = np.empty((nspin, nR, n, n))
-    r0 = None
-    for ir in range(nR):
+    r0 = next(ir for ir in range(nR) if not R[ir].any())
+    th = -(t / HARTREE_EV)
+
+    def image(ir):  # the images are independent: threads fill their own slices
         d = dvec - L * R[ir].astype(np.float64)[None, None, :]
         g = np.exp(-np.einsum("ijx,ijx->ij", d, d) / s2)
         SR[ir] = pref * g
-        HR[0, ir] = -(t / HARTREE_EV) * g
-        if not R[ir].any():
-            r0 = ir
+        HR[0, ir] = th * g
+
+    if n >= 256:
+        with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+            list(ex.map(image, range(nR)))
+    else:
+        for ir in range(nR):
+            image(ir)
     SR[r0] += np.diag(eta)
     HR[0, r0] += np.diag(onsite / HARTREE_EV)
 

@@ -92,3 +92,75 @@ def test_mixed_precision_arguments(ctx):
         ctx.nao_set_refinement(3)
     with pytest.raises(NaoError):
         gpu_band_step(ctx, inp, torch, DEV, precision=7, density=False)
+
+
+def _host_norm2(H, iters=60):
+    """||H||_2 of a Hermitian matrix by power iteration (an estimate from below, good to a
+    few digits: enough for a residual's normalisation)."""
+    v = np.random.default_rng(0).standard_normal(H.shape[0]) + 0j
+    lam = 0.0
+    for _ in range(iters):
+        w = H @ v
+        lam = np.linalg.norm(w) / np.linalg.norm(v)
+        v = w / np.linalg.norm(w)
+    return lam
+
+
+def test_mixed_full_size_magnetite_against_oracle(ctx):
+    """The magnetite-shaped step (n = 568, 128 problems in one call, the bench's launch
+    configuration) in mixed precision: sampled problems against the oracle at the mixed-mode
+    bound |d eps| <= 1e-9 Ha; residual and S-orthonormality after the one sweep."""
+    inp = synth.magnetite_cell()
+    ctx.nao_set_refinement(1)
+    g = gpu_band_step(ctx, inp, torch, DEV, precision=NAO_MIXED_BF16X3)
+    assert (g["status"] == 0).all() and int(g["rstatus"][0]) == 0
+    sample = [3, 42, 64 + 17, 126]
+    ref = oracle.band_step(inp.HR, inp.SR, inp.R, inp.kpts, inp.wk, inp.n_electrons, inp.kT, problems=sample)
+    worst = {}
+    for p in sample:
+        sg, k = divmod(p, inp.nk)
+        H, S = ref["Hk"][sg, k], ref["Sk"][k]
+        m = int(g["m"][p])
+        assert m == ref["m"][p]
+        de = np.abs(g["eps"][p][:m] - ref["eps"][p]).max()
+        C = g["C"][p][:, :m]
+        res = np.linalg.norm(H @ C - S @ C * g["eps"][p][:m][None, :]) / (inp.n * _host_norm2(H))
+        orth = np.abs(C.conj().T @ S @ C - np.eye(m)).max()
+        worst[p] = (de, res, orth)
+        assert de <= TOL_MIXED_EPS_HA, f"p={p}: |d eps| = {de:.3e} Ha"
+        assert res <= 1e-9 and orth <= 1e-7, (p, res, orth)
+    print("\nmagnetite mixed (1 sweep): " + "; ".join(f"p={p}: |d eps| {v[0]:.2e} Ha, residual {v[1]:.2e}, "
+                                                      f"C^H S C - I {v[2]:.2e}" for p, v in worst.items()))
+
+
+def test_mixed_n2000_against_oracle_golden(ctx):
+    """Two problems of the n = 2000 mixed-precision workload (4x4x4 k, seed 4) against the
+    oracle's eigenvalues stored by tests/golden/make_mixed_n2000_oracle.py (oracle/ only):
+    the mixed path with one sweep within 1e-9 Ha, the FP64 path within 1e-10 ||H'||."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "mixed_n2000_oracle_eps.txt")
+    rows = np.loadtxt(path, comments="#")
+    inp = synth.scaled_cell(2000, seed=4, kgrid=(4, 4, 4), nspin=1, ill_conditioned=False)
+    probs = [int(p) for p in np.unique(rows[:, 0])]
+    sub = inp.kpts[probs]
+    HR = torch.from_numpy(inp.HR).to(DEV)
+    SR = torch.from_numpy(inp.SR)[None].to(DEV)
+    R = torch.from_numpy(inp.R).to(DEV)
+    k = torch.from_numpy(np.ascontiguousarray(sub)).to(DEV)
+    Hk = ctx.nao_bloch_sum(HR, R, k)[0]
+    Sk = ctx.nao_bloch_sum(SR, R, k)[0]
+    del HR, SR
+    for prec, tol in ((0, None), (NAO_MIXED_BF16X3, TOL_MIXED_EPS_HA)):
+        eps, C, m, st = ctx.nao_gen_eig(Hk, Sk, precision=prec, want_vectors=False)
+        torch.cuda.synchronize()
+        assert int(st.abs().sum()) == 0
+        e = eps.cpu().numpy()
+        for i, p in enumerate(probs):
+            r = rows[rows[:, 0] == p]
+            mo = int(r[0, 1])
+            eo = r[np.argsort(r[:, 2]), 3]
+            assert int(m[i]) == mo
+            bound = tol if tol is not None else 1e-10 * np.abs(eo).max()
+            de = np.abs(e[i][:mo] - eo).max()
+            assert de <= bound, (prec, p, de, bound)
+            print(f"\nn2000 p={p} precision={prec}: |d eps| = {de:.2e} Ha (bound {bound:.1e})")
