@@ -422,14 +422,22 @@ def run_mixed_n2000(local_rank, steps=2, warmup=1):
                    "status_ok": out["status_ok"]}
     errors(out, "fp64")
     del out
-    ctx.nao_set_refinement(0)
+    ctx.nao_set_refinement(-1)
     msr, _, out = _band_step_timed(ctx, inp, dev, 1, 0, precision=2)
     errors(out, "mixed_raw")
     del out
     ctx.nao_set_refinement(1)
+    ms1, st1, out = _band_step_timed(ctx, inp, dev, 1, 0, precision=2)
+    res["mixed_one_sweep"] = {"value": inp.nprob / (ms1 * 1e-3), "unit": UNIT, "ms_per_step": ms1,
+                              "precision": "NAO_MIXED_BF16X3 + one Ritz sweep + Rayleigh quotients"}
+    errors(out, "mixed_sweep")
+    del out
+    ctx.nao_set_refinement(0)
     msm, stm, out = _band_step_timed(ctx, inp, dev, steps, warmup, precision=2)
     res["mixed"] = {"value": inp.nprob / (msm * 1e-3), "unit": UNIT, "ms_per_step": msm, "stages_ms": stm,
-                    "precision": "NAO_MIXED_BF16X3 + one Ritz sweep", "status_ok": out["status_ok"]}
+                    "precision": "NAO_MIXED_BF16X3 (36-bit products, 46-bit H' Householder digits) + Rayleigh "
+                                 "quotients with FP64-accurate S C and H C (the default refinement)",
+                    "status_ok": out["status_ok"]}
     errors(out, "mixed_refined")
     del out
     ctx.close()
@@ -645,8 +653,8 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     e2e_ms = x0.elapsed_time(x1) / k_e2e
 
-    # the mixed-precision form of the same step: 30-bit products where the mixed mode allows
-    # them, then one Ritz refinement sweep (NAO_MIXED_BF16X3); its eigenvalues are compared
+    # the mixed-precision form of the same step: reduced-precision products where the mixed mode allows
+    # them, then the default refinement (NAO_MIXED_BF16X3); its eigenvalues are compared
     # with the FP64 step's
     eps_mx = torch.empty_like(eps)
     step(d_in, 2, eps_mx)
@@ -660,8 +668,9 @@ def run_ours(args, rank, world, local_rank):
     mixed_ms = y0.elapsed_time(y1) / args.steps
     fin = torch.isfinite(eps)
     mixed = {"value": nprob * world / (mixed_ms * 1e-3), "unit": UNIT, "ms_per_step": mixed_ms,
-             "precision": "NAO_MIXED_BF16X3: five BF16 digit planes (30 bits) for the back-transformations, "
-                          "X^H H X, the H' rank-2k updates and X V; one Ritz refinement sweep",
+             "precision": "NAO_MIXED_BF16X3: six BF16 digit planes (36 bits) for the back-transformations, "
+                          "X^H H X, the H' rank-2k updates and X V, 46-bit digits for the H' Householder "
+                          "matrix-vector products; Rayleigh quotients with FP64-accurate S C and H C",
              "max_abs_deps_vs_fp64_Ha": float((eps_mx - eps)[fin].abs().max()),
              "status_ok": bool(int(st.abs().sum()) == 0 and int(rst[0]) == 0)}
 

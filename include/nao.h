@@ -74,6 +74,9 @@ typedef struct {
                                  (reported as NAO_E_TIMEOUT by the next status, below);
                                  default 4e9 (~2 s), range [1, 1e12]; below 1024 each wait
                                  is a single non-blocking test (to exercise that path)       */
+  int mixed_planes;           /* BF16 digit planes per operand of the products that the
+                                 mixed mode (NAO_MIXED_BF16X3) computes to reduced precision:
+                                 5, 6 or 7 (30, 36 or 42 bits); default 6                    */
 } nao_config;
 
 void nao_config_defaults(nao_config* cfg);
@@ -101,9 +104,15 @@ size_t nao_workspace_bytes(const nao_ctx* ctx);
 /* Select the product method of this context's band-step calls (default NAO_GEMM_TC).    */
 int nao_set_gemm_method(nao_ctx* ctx, int method);
 
-/* Ritz refinement sweeps after a mixed-precision nao_gen_eig: 1 (default; eigenvalues to
- * the mixed-mode bound), 2 (eigenvectors to FP64 accuracy too) or 0 (none: raw mixed
- * results).  Returns NAO_E_INVALID for other values.  No effect on NAO_FP64 calls.        */
+/* Refinement after a mixed-precision nao_gen_eig (no effect on NAO_FP64 calls):
+ *   0 (default): eigenvalues = Rayleigh quotients c^H H c / c^H S c of the mixed-precision
+ *      vectors, with FP64-accurate products of the input H and S: the eigenvalue error is
+ *      second order in the vectors' (~1e-7 with 6 planes), so eigenvalues meet the mixed-mode
+ *      bound; the vectors keep their mixed-precision accuracy;
+ *   1 or 2: that many Ritz (Ogita-Aishima) sweeps first, each squaring the vector error
+ *      (2: eigenvectors to FP64 accuracy), then the Rayleigh quotients;
+ *   -1: none (raw mixed results, for measurements).
+ * Returns NAO_E_INVALID for other values.                                                  */
 int nao_set_refinement(nao_ctx* ctx, int sweeps);
 
 /* Batched complex GEMM (the products of Parts 3, 4 and 6):
@@ -152,12 +161,14 @@ int nao_bloch_sum(nao_ctx* ctx, int n, int nR, const int32_t* R, int nmat, const
  *             correction of the tridiagonal eigenvectors, a term ~1e-9 of them, formed with
  *             five digits (30 bits), far below the FP64 rounding of the vectors it corrects.
  *             NAO_MIXED_BF16X3: the back-transformations, X^H H X, the rank-2k updates of H'
- *             and X V use 30-bit tensor-core products (five BF16 digit planes); the reduction
- *             of S, the tridiagonal solves and s^{-1/2} stay FP64.  Then one Ritz refinement
- *             sweep (Ogita-Aishima in the S inner product, FP64-accurate products of the
- *             input H and S; not in the paper) restores the accuracy: eps are the Rayleigh
- *             quotients of the refined vectors, sorted.  nao_set_refinement chooses 0-2
- *             sweeps (default 1).
+ *             and X V use reduced-precision tensor-core products (nao_config.mixed_planes
+ *             BF16 digit planes, 36 bits by default), and the Householder matrix-vector
+ *             products of H' 46-bit integer digits; the reduction of S, the tridiagonal
+ *             solves and s^{-1/2} stay FP64.  Then the refinement (not in the paper) restores
+ *             the accuracy with FP64-accurate products of the input H and S: by default eps
+ *             are the Rayleigh quotients of the mixed-precision vectors, sorted; with
+ *             nao_set_refinement(1 or 2) Ritz (Ogita-Aishima) sweeps refine the vectors
+ *             first.
  *             NAO_MIXED_TF32: rejected (NAO_E_INVALID): 12-bit products leave errors that
  *             one sweep does not remove.
  *   nb        eigenvector columns wanted, 1 <= nb <= n

@@ -153,7 +153,7 @@ __global__ void report_timeout_kernel(int* flags, int32_t* status, int nstatus) 
 
 // One batched complex product of the band step, on the tensor cores (digit planes) when the
 // context asks for it and the contraction length allows, else on the FP64 CUDA cores.
-// digits: NAO_OZ_DIGITS_FP64, or NAO_OZ_DIGITS_MIXED for the products the mixed mode
+// digits: NAO_OZ_DIGITS_FP64, or nao_config.mixed_planes for the products the mixed mode
 // computes to 30 bits (the FP64 CUDA-core route ignores it).
 cudaError_t run_zgemm(nao_ctx* ctx, const char* stage, int nprob, GemmDims d, double alpha, GemmOperand A,
                       GemmOperand B, double beta, z64* C, long long Cbs, long long Crs, long long Ccs, void* ozws,
@@ -231,7 +231,7 @@ GenEigPlan plan_gen_eig(int n, int nprob, int nSe, bool use_tc) {
   W.oW2 = P.take<z64>((size_t)NAO_WY_NB * n * nmax);
   W.oVW = P.take<z64>((size_t)3 * NAO_HT_NB * n * nmax);
   // 8-bit digit planes of the Householder trailing matrix (tensor-core product method)
-  W.oDig = P.take<char>(use_tc ? hetrd_digits_bytes(n, nmax) : 16);
+  W.oDig = P.take<char>(use_tc ? hetrd_digits_bytes(n, nmax, NAO_HT_DIGITS_FP64) : 16);
   W.oErow = P.take<int>((size_t)(n > 1 ? n - 1 : 1) * nmax);
   W.bytes = P.off;
   return W;
@@ -326,25 +326,29 @@ cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t*
 
 // Eigen_HH step 1, blocked: panels of NAO_HT_NB columns reduced by the cluster kernel, each
 // followed by the deferred update A(r0:, r0:) -= V W^H + W V^H of the rest (lower triangle,
-// one rank-2 NB product).  VW: [nprob][n][3 NB] workspace.
+// one rank-2 NB product).  VW: [nprob][n][3 NB] workspace.  digits: planes of the update
+// products; panel_digits: digits of the panel's integer matrix-vector products
+// (NAO_HT_DIGITS_FP64, or NAO_HT_DIGITS_MIXED for the H' reduction of the mixed mode).
 cudaError_t hetrd_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, z64* A, double* d, double* e, z64* tau,
-                          z64* VW, void* ozws, cudaStream_t st, int digits, void* dig, int* erow) {
+                          z64* VW, void* ozws, cudaStream_t st, int digits, void* dig, int* erow,
+                          int panel_digits = NAO_HT_DIGITS_FP64) {
   // exact integer matrix-vector products with the tensor-core method; FP64 FMAs otherwise
   // (up to the order whose digit words still fit in a block's shared memory)
-  const bool use_dig = ctx->gemm_method == NAO_GEMM_TC && dig != nullptr && hetrd_digits_fit(n);
+  const bool use_dig = ctx->gemm_method == NAO_GEMM_TC && dig != nullptr && hetrd_digits_fit(n, panel_digits);
+  const int pd = use_dig ? panel_digits : 0;
   const int NB = NAO_HT_NB;
-  const int cl = hetrd_cluster_size(n, nprob, ctx->num_sms, use_dig);
+  const int cl = hetrd_cluster_size(n, nprob, ctx->num_sms, pd);
   const long long snn = (long long)n * n, svw = (long long)n * 3 * NB;
   for (int i0 = 0; i0 < n; i0 += NB) {
     cudaError_t err = cudaSuccess;
     if (use_dig) {
       NaoStage stage_(ctx, "hetrd_digits", st, 1);
-      err = launch_hetrd_digits(n, nprob, size, A, n, snn, i0, dig, erow, st);
+      err = launch_hetrd_digits(n, nprob, size, A, n, snn, i0, dig, erow, pd, st);
     }
     if (err == cudaSuccess) {
       NaoStage stage_(ctx, "hetrd", st, 1);
       err = launch_hetrd_panel(n, nprob, size, A, n, snn, d, e, tau, n, VW, svw, i0, cl, use_dig ? dig : nullptr,
-                               erow, st);
+                               erow, pd, st);
     }
     if (err != cudaSuccess) return err;
     const int r0 = i0 + NB;
@@ -374,7 +378,7 @@ double* ns_correct(nao_ctx* ctx, int n, int nprob, const int32_t* size, const in
     *err = launch_sym_minus_identity(n, nprob, ncols, G, n, snn, st);
     if (*err == cudaSuccess)
       *err = launch_dgemm_oz(nprob, d, -0.5, GemmOperand{Z, snn, 1, n, 0, nullptr}, GemmOperand{G, snn, 1, n, 0, nullptr},
-                             1.0, Z, snn, 1, n, ozws, ctx->dev_flags, st, NAO_OZ_DIGITS_MIXED);
+                             1.0, Z, snn, 1, n, ozws, ctx->dev_flags, st, NAO_OZ_DIGITS_NS);
     return Z;
   }
   NaoStage stage_(ctx, "ortho_ns", st, 1);
@@ -400,7 +404,7 @@ cudaError_t launch_report_timeout(int* flags, int32_t* status, int nstatus, cuda
 
 static int check_config(const nao_config& c) {
   return (c.f_min >= 0.0 && c.f_min <= 1e-3 && c.inverse_iteration_max >= 0 && c.inverse_iteration_max <= 64 &&
-          c.tc_wait_cycles >= 1 && c.tc_wait_cycles <= 1000000000000LL)
+          c.tc_wait_cycles >= 1 && c.tc_wait_cycles <= 1000000000000LL && c.mixed_planes >= 5 && c.mixed_planes <= 7)
              ? NAO_OK
              : NAO_E_INVALID;
 }
@@ -433,6 +437,7 @@ void nao_config_defaults(nao_config* cfg) {
   cfg->f_min = NAO_F_MIN_DEFAULT;
   cfg->inverse_iteration_max = NAO_INV_ITER_DEFAULT;
   cfg->tc_wait_cycles = NAO_TC_WAIT_DEFAULT;
+  cfg->mixed_planes = NAO_MIXED_PLANES_DEFAULT;
 }
 
 int nao_init(nao_ctx** out, int device, size_t hbm_budget_bytes, const nao_config* cfg) {
@@ -546,7 +551,8 @@ int nao_gen_eig_workspace(nao_ctx* ctx, int n, int nprob, int nS, int precision,
 
 int nao_set_refinement(nao_ctx* ctx, int sweeps) {
   if (!ctx) return nao_fail(nullptr, NAO_E_INVALID, "nao_set_refinement: ctx is NULL");
-  if (sweeps < 0 || sweeps > 2) return nao_fail(ctx, NAO_E_INVALID, "nao_set_refinement: sweeps must be 0, 1 or 2");
+  if (sweeps < -1 || sweeps > 2)
+    return nao_fail(ctx, NAO_E_INVALID, "nao_set_refinement: sweeps must be -1, 0, 1 or 2");
   ctx->refine_sweeps = sweeps;
   return NAO_OK;
 }
@@ -653,7 +659,7 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   // step) and s^{-1/2} stay FP64-accurate, and one Ritz refinement sweep with FP64-accurate
   // products follows.
   const bool mixed = precision != NAO_FP64;
-  const int dig = mixed ? NAO_OZ_DIGITS_MIXED : NAO_OZ_DIGITS_FP64;
+  const int dig = mixed ? ctx->cfg.mixed_planes : NAO_OZ_DIGITS_FP64;
 
   // ---- Part 2: Eigen_HH(S) -> s, U;  X = U_m s_m^{-1/2}
   NAO_STAGE("herm_fill", 1, launch_herm_fill(n, nSe, (const z64*)S, snn, nullptr, AS, n, snn, st));
@@ -691,11 +697,12 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   NAO_STAGE("misc", 1, launch_hermitize(n, nprob, mP, Hp, n, snn, st));
 
   // ---- Part 4: Eigen_HH(H') -> eps, V;  C = X V
-  NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nprob, mP, Hp, dH, eH, tauH, VWp, ozws, st, dig, digp, erowp));
+  NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nprob, mP, Hp, dH, eH, tauH, VWp, ozws, st, dig, digp, erowp,
+                                  mixed ? NAO_HT_DIGITS_MIXED : NAO_HT_DIGITS_FP64));
   // Eigenvectors of H' only where they are used (the paper's second pass, dstevx's index
   // range): the lowest nb per problem for C, all m for the mixed-mode refinement, none when
   // the caller asks for eigenvalues only (C = NULL).
-  const bool all_vecs = mixed && ctx->refine_sweeps > 0;
+  const bool all_vecs = mixed && ctx->refine_sweeps >= 0;
   const int32_t* nvP = all_vecs ? mP : nbP;
   const int nv_max = (C || all_vecs) ? n : 0;
   NAO_STAGE("stein", 1, launch_stein(n, nprob, mP, dH, eH, n, wH, Z, n, snn, scr, stH, nvP, nv_max,
@@ -712,11 +719,11 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
     NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nprob, mP, nvP, Hp, tauH, Zo, wH, 0, V, Vf, tauc, Gw, Tw, Ww, W2w,
                                             ozws, st, dig, 1));
   }
-  if (mixed && ctx->refine_sweeps > 0) {
+  if (mixed && ctx->refine_sweeps >= 0) {
     // C^ = X V (all m columns, column-major in Hp), then Ritz refinement sweeps with
     // FP64-accurate products (csrc/refine.cu):  R' = C^H S C^, G = C^H H C^ -> I + F,
-    // C = C^ (I + F); after the last sweep eps = Rayleigh quotients of C, columns
-    // S-normalised, sorted.
+    // C = C^ (I + F); after the last sweep (or directly on C^ when there is none) eps =
+    // Rayleigh quotients of C from FP64-accurate S C and H C, columns S-normalised, sorted.
     const long long svf = (long long)n * ncolv;
     int32_t* perm = (int32_t*)scr;
     GemmDims dc{n, n, n, nullptr, mP, mP};
@@ -747,13 +754,18 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
       NAO_CUDA_TRY(ctx, run_zgemm(ctx, "refine", nprob, du, 1.0, GemmOperand{Hp, snn, 1, n, 0, nullptr},
                                   GemmOperand{Y, snn, 1, n, 0, nullptr}, 0.0, Vf, svf, 1, n, ozws, st));
     }
+    // the vectors whose Rayleigh quotients are taken: the last sweep's C (in Vf), or C^
+    const bool swept = ctx->refine_sweeps > 0;
+    z64* Cf = swept ? Vf : Hp;
+    const long long cfs = swept ? svf : snn;
+    z64* W2 = swept ? Hp : V;  // H C (V is free once X V has been formed)
     NAO_CUDA_TRY(ctx, run_zgemm(ctx, "refine", nprob, dw, 1.0, GemmOperand{AS, snn, 1, n, 0, s_of_prob},
-                                GemmOperand{Vf, svf, 1, n, 0, nullptr}, 0.0, Y, snn, 1, n, ozws, st));
+                                GemmOperand{Cf, cfs, 1, n, 0, nullptr}, 0.0, Y, snn, 1, n, ozws, st));
     NAO_CUDA_TRY(ctx, run_zgemm(ctx, "refine", nprob, dw, 1.0, GemmOperand{Hf, snn, 1, n, 0, nullptr},
-                                GemmOperand{Vf, svf, 1, n, 0, nullptr}, 0.0, Hp, snn, 1, n, ozws, st));
-    NAO_STAGE("refine", 1, launch_oa_rq(n, nprob, mP, Vf, n, svf, Y, Hp, n, snn, wH, n, st));
+                                GemmOperand{Cf, cfs, 1, n, 0, nullptr}, 0.0, W2, snn, 1, n, ozws, st));
+    NAO_STAGE("refine", 1, launch_oa_rq(n, nprob, mP, Cf, n, cfs, Y, W2, n, snn, wH, n, st));
     NAO_STAGE("refine", 1, launch_oa_sort(n, nprob, mP, wH, n, eps, perm, st));
-    if (C) NAO_STAGE("refine", 1, launch_oa_gather(n, nprob, nb, perm, Vf, n, svf, (z64*)C, st));
+    if (C) NAO_STAGE("refine", 1, launch_oa_gather(n, nprob, nb, perm, Cf, n, cfs, (z64*)C, st));
   } else {
     if (C) {
       GemmDims d{n, nb, n, nullptr, nbP, mP};  // C = X V(:, :nb) : n x nb, row-major [n][nb]

@@ -79,20 +79,24 @@ __device__ __forceinline__ double2 block_sum2(double a, double b, double* red) {
 //  * p_r = 2^{e_r + f - 12} sum_G (RR_G + i RI_G) 2^{-8 G}, combined in integer arithmetic.
 // Digit layout: dig[p][rr][w][16 words], rr = r - (i0 + 1), word w holds columns
 // i0 + 1 + 4w .. +3 (4 int8 lanes) of plane s, part t at word index 2 s + t.
-constexpr int HD_S = 8;      // digits per value
-constexpr int HD_G = 8;      // digit orders kept (G = 0..7)
+// The digit count S is a template parameter: S = 8 (62 bits, FP64 accuracy; the orders
+// G <= 7 are kept) for every reduction of the FP64 mode and for the overlap, S = 6 (46 bits,
+// orders G <= 5, truncation below 2^-43 of |row| |v|) for the H' reduction of the mixed mode,
+// whose results the Ritz refinement corrects.  A digit row holds 2 S words per four columns.
+constexpr int HD_S = 8;      // digits per value of the FP64 form
 // words (4 columns) per digit row: rows and columns i0 + 1 .. n - 1
 __host__ __device__ inline int hd_words(int n) { return n > 1 ? (n - 1 + 3) / 4 : 1; }
 
 __device__ __forceinline__ int hd_exp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7ff); }
 
-// q = round(x 2^{62 - e}) for |x| < 2^e (integer arithmetic on the bits of x)
+// q = round(x 2^{8S - 2 - e}) for |x| < 2^e (integer arithmetic on the bits of x)
+template <int S>
 __device__ __forceinline__ long long hd_fixed(double x, int e) {
   const long long bits = __double_as_longlong(x);
   const int b = (int)((bits >> 52) & 0x7ff);
   if (b == 0) return 0;
   long long m = (bits & 0xFFFFFFFFFFFFFll) | 0x10000000000000ll;
-  const int sh = b - 1075 + 62 - e;
+  const int sh = b - 1075 + 8 * S - 2 - e;
   long long q;
   if (sh >= 0) q = m << sh;
   else if (sh <= -62) q = 0;
@@ -100,10 +104,11 @@ __device__ __forceinline__ long long hd_fixed(double x, int e) {
   return bits < 0 ? -q : q;
 }
 
-// balanced base-256 digits of q (|q| < 2^62), most significant first, as unsigned bytes
+// S balanced base-256 digits of q (|q| < 2^{8S-2}), most significant first, as unsigned bytes
+template <int S>
 __device__ __forceinline__ void hd_digits(long long q, unsigned int* d) {
 #pragma unroll
-  for (int s = HD_S - 1; s >= 1; --s) {
+  for (int s = S - 1; s >= 1; --s) {
     const int ds = (int)((q + 128) & 255) - 128;
     d[s] = (unsigned int)(ds & 255);
     q = (q - ds) >> 8;
@@ -111,38 +116,41 @@ __device__ __forceinline__ void hd_digits(long long q, unsigned int* d) {
   d[0] = (unsigned int)((int)q & 255);
 }
 
-// digit words of 4 complex values x[0..3]: out[2 s + t] = plane s of part t (t = 0 re, 1 im)
+// digit words of 4 complex values x[0..3]: out[2 s + t] = plane s of part t (t = 0 re, 1 im);
+// S / 2 uint4 per four columns
+template <int S>
 __device__ __forceinline__ void hd_pack4(const z64* x, int e, uint4* out4) {
-  unsigned int w[2 * HD_S];
+  unsigned int w[2 * S];
 #pragma unroll
-  for (int k = 0; k < 2 * HD_S; ++k) w[k] = 0u;
+  for (int k = 0; k < 2 * S; ++k) w[k] = 0u;
 #pragma unroll
   for (int l = 0; l < 4; ++l) {
-    unsigned int dr[HD_S], di[HD_S];
-    hd_digits(hd_fixed(x[l].x, e), dr);
-    hd_digits(hd_fixed(x[l].y, e), di);
+    unsigned int dr[S], di[S];
+    hd_digits<S>(hd_fixed<S>(x[l].x, e), dr);
+    hd_digits<S>(hd_fixed<S>(x[l].y, e), di);
 #pragma unroll
-    for (int s = 0; s < HD_S; ++s) {
+    for (int s = 0; s < S; ++s) {
       w[2 * s] |= dr[s] << (8 * l);
       w[2 * s + 1] |= di[s] << (8 * l);
     }
   }
 #pragma unroll
-  for (int k = 0; k < 4; ++k) out4[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+  for (int k = 0; k < S / 2; ++k) out4[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
 }
 
 // digit words of v's 4 values: out[3 t + k], k = 0: Re v, 1: Im v, 2: -Im v (plane t)
+template <int S>
 __device__ __forceinline__ void hd_pack4v(const z64* x, int e, unsigned int* out) {
 #pragma unroll
-  for (int k = 0; k < 3 * HD_S; ++k) out[k] = 0u;
+  for (int k = 0; k < 3 * S; ++k) out[k] = 0u;
 #pragma unroll
   for (int l = 0; l < 4; ++l) {
-    unsigned int dr[HD_S], di[HD_S], dn[HD_S];
-    hd_digits(hd_fixed(x[l].x, e), dr);
-    hd_digits(hd_fixed(x[l].y, e), di);
-    hd_digits(hd_fixed(-x[l].y, e), dn);
+    unsigned int dr[S], di[S], dn[S];
+    hd_digits<S>(hd_fixed<S>(x[l].x, e), dr);
+    hd_digits<S>(hd_fixed<S>(x[l].y, e), di);
+    hd_digits<S>(hd_fixed<S>(-x[l].y, e), dn);
 #pragma unroll
-    for (int t = 0; t < HD_S; ++t) {
+    for (int t = 0; t < S; ++t) {
       out[3 * t] |= dr[t] << (8 * l);
       out[3 * t + 1] |= di[t] << (8 * l);
       out[3 * t + 2] |= dn[t] << (8 * l);
@@ -150,16 +158,17 @@ __device__ __forceinline__ void hd_pack4v(const z64* x, int e, unsigned int* out
   }
 }
 
-// sum_G R[G] 2^{-8 G} 2^ex as a double, in integer arithmetic: the orders G < 4 and G >= 4
-// are combined exactly in two int64 words (|R[G]| < 2^31 gives |.| < 2^56 each), which are
-// then joined in one 63-bit integer, with a rounding of the low word far below the result's
-// last bit, and converted with one rounding
+// sum_{G < NG} R[G] 2^{-8 G} 2^ex as a double (NG <= 8), in integer arithmetic: the orders
+// G < 4 and G >= 4 are combined exactly in two int64 words (|R[G]| < 2^31 gives |.| < 2^56
+// each), which are then joined in one 63-bit integer, with a rounding of the low word far
+// below the result's last bit, and converted with one rounding
+template <int NG>
 __device__ __forceinline__ double hd_combine(const int* R, int ex) {
   long long hi = 0, lo = 0;
 #pragma unroll
-  for (int G = 0; G < 4; ++G) hi += (long long)R[G] * (1ll << (8 * (3 - G)));
+  for (int G = 0; G < 4 && G < NG; ++G) hi += (long long)R[G] * (1ll << (8 * (3 - G)));
 #pragma unroll
-  for (int G = 4; G < HD_G; ++G) lo += (long long)R[G] * (1ll << (8 * (7 - G)));
+  for (int G = 4; G < NG; ++G) lo += (long long)R[G] * (1ll << (8 * (7 - G)));
   // value = (hi 2^32 + lo) 2^{ex - 56}; shift hi up by s <= 32 so that |hi 2^s| < 2^61
   const unsigned long long ah = hi < 0 ? 0ull - (unsigned long long)hi : (unsigned long long)hi;
   const int s = min(max(__clzll((long long)ah) - 3, 0), 32);
@@ -176,6 +185,7 @@ __device__ __forceinline__ z64 herm_at(const z64* A, int ld, int r, int c) {
 
 // Digits of the trailing matrix rows/columns i0+1 .. m-1 at the start of a panel.  One warp
 // per row; lanes over words.  Lmax rows x W words per problem.
+template <int S>
 __global__ void __launch_bounds__(256)
 hetrd_digits_kernel(int n, const int32_t* __restrict__ size, const z64* __restrict__ Abase, int ld,
                     long long strideA, int i0, int Lmax, int W, uint4* __restrict__ dig, int* __restrict__ erow) {
@@ -196,7 +206,7 @@ hetrd_digits_kernel(int n, const int32_t* __restrict__ size, const z64* __restri
   for (int o = 16; o > 0; o >>= 1) bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
   const int e = bmax == 0 ? -1100 : bmax - 1022;
   if (lane == 0) erow[(size_t)p * Lmax + rr] = e;
-  uint4* row = dig + ((size_t)p * Lmax + rr) * W * 4;
+  uint4* row = dig + ((size_t)p * Lmax + rr) * W * (S / 2);
   const int Wp = (L + 3) >> 2;
   for (int w = lane; w < Wp; w += 32) {
     z64 x[4];
@@ -205,7 +215,7 @@ hetrd_digits_kernel(int n, const int32_t* __restrict__ size, const z64* __restri
       const int c = 4 * w + l;
       x[l] = c < L ? herm_at(A, ld, r, i0 + 1 + c) : zmk(0.0, 0.0);
     }
-    hd_pack4(x, e, row + (size_t)w * 4);
+    hd_pack4<S>(x, e, row + (size_t)w * (S / 2));
   }
 }
 
@@ -219,6 +229,7 @@ __device__ __forceinline__ int pair_start(int k, int npairs, int C) { return (in
 //   p = A22 v - V (W^H v) - W (V^H v)   (c, d),   w = tau p - (tau/2)(p^H tau p ...) v (e).
 // The caller applies A22 -= V W^H + W V^H to the rest of the matrix after the panel
 // (a rank-2 NB update, run as one tensor-core product).  VW holds, per row, [V | W | V].
+template <int S>
 __global__ void __launch_bounds__(HT_THREADS)
 hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Abase, int ld, long long strideA,
                    double* __restrict__ dbase, double* __restrict__ ebase, z64* __restrict__ taubase, long long strideV,
@@ -234,7 +245,7 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
   z64* w = sm + n;           // [n] w; in the digit path first the corrections of p (one-block clusters)
   z64* pown = sm + 2 * n;    // [n] p for this block's rows (read by the others)
   z64* part = sm + 3 * n;    // FP64 path: [2 * HT_THREADS] partial sums of the K threads of each pair
-  unsigned int* vd = (unsigned int*)(sm + 3 * n);  // digit path, same region: [24][W] digit words of v
+  unsigned int* vd = (unsigned int*)(sm + 3 * n);  // digit path, same region: [3 S][W] digit words of v
   __shared__ int ired[32];
   __shared__ z64 ypart[2 * NB], yfull[2 * NB];
   __shared__ double red[64];
@@ -350,10 +361,10 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
           const int c = 4 * w + l - kk0;
           x[l] = (c >= 0 && c < mt) ? v[c] : zmk(0.0, 0.0);
         }
-        unsigned int t[3 * HD_S];
-        hd_pack4v(x, f, t);
+        unsigned int t[3 * S];
+        hd_pack4v<S>(x, f, t);
 #pragma unroll
-        for (int k = 0; k < 3 * HD_S; ++k) vd[k * W + w] = t[k];
+        for (int k = 0; k < 3 * S; ++k) vd[k * W + w] = t[k];
       }
       __syncthreads();
       // rows of this block's pairs: four rows per warp, eight lanes per row
@@ -366,17 +377,17 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
           r = (qq & 1) ? mt - 1 - g : g;
           if ((qq & 1) && r == g) r = -1;
         }
-        int RR[HD_G], RI[HD_G];
+        int RR[S], RI[S];
 #pragma unroll
-        for (int G = 0; G < HD_G; ++G) RR[G] = RI[G] = 0;
+        for (int G = 0; G < S; ++G) RR[G] = RI[G] = 0;
         const int rr = r + kk0;  // digit row
         if (r >= 0) {
-          const uint4* row = dig + ((size_t)p * Lmax + rr) * W * 4;
+          const uint4* row = dig + ((size_t)p * Lmax + rr) * W * (S / 2);
           for (int w = w0 + wl; w < Wp; w += 8) {
-            unsigned int a[2 * HD_S];
-            const uint4* aw = row + (size_t)w * 4;
+            unsigned int a[2 * S];
+            const uint4* aw = row + (size_t)w * (S / 2);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < S / 2; ++k) {
               const uint4 q4 = aw[k];
               a[4 * k] = q4.x;
               a[4 * k + 1] = q4.y;
@@ -384,11 +395,11 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
               a[4 * k + 3] = q4.w;
             }
 #pragma unroll
-            for (int t2 = 0; t2 < HD_G; ++t2) {
+            for (int t2 = 0; t2 < S; ++t2) {
               const int bre = (int)vd[(3 * t2) * W + w], bim = (int)vd[(3 * t2 + 1) * W + w],
                         bni = (int)vd[(3 * t2 + 2) * W + w];
 #pragma unroll
-              for (int s2 = 0; s2 + t2 < HD_G; ++s2) {
+              for (int s2 = 0; s2 + t2 < S; ++s2) {
                 const int G = s2 + t2;
                 RR[G] = __dp4a((int)a[2 * s2], bre, RR[G]);      // Re a Re v
                 RR[G] = __dp4a((int)a[2 * s2 + 1], bni, RR[G]);  // Im a (-Im v)
@@ -401,13 +412,15 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
 #pragma unroll
         for (int o = 1; o < 8; o <<= 1)
 #pragma unroll
-          for (int G = 0; G < HD_G; ++G) {
+          for (int G = 0; G < S; ++G) {
             RR[G] += __shfl_xor_sync(0xffffffffu, RR[G], o);
             RI[G] += __shfl_xor_sync(0xffffffffu, RI[G], o);
           }
         if (r >= 0 && wl < 2) {  // lane 0 the real part, lane 1 the imaginary part
+          // a = 2^{e_r - (8S-2)} q_a, v = 2^{f - (8S-2)} q_v, q_a q_v = sum_G R_G 2^{8(2S-2-G)}:
+          // the product is 2^{e_r + f - 12} sum_G R_G 2^{-8G} for every S
           double* dst = (double*)&pown[r] + wl;
-          *dst = hd_combine(wl ? RI : RR, erow[(size_t)p * Lmax + rr] + f - 12);
+          *dst = hd_combine<S>(wl ? RI : RR, erow[(size_t)p * Lmax + rr] + f - 12);
         }
       }
     }
@@ -566,28 +579,33 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
 }  // namespace
 
 // v, w, pown, then one region shared by the FP64 path's partial sums and the digit path's
-// digit words of v
-static size_t panel_smem(int n, bool digits) {
-  const size_t region = digits ? sizeof(unsigned int) * 3 * HD_S * hd_words(n) : sizeof(z64) * 2 * HT_THREADS;
+// digit words of v (digits: 0 for the FP64 path, else the digit count S)
+static size_t panel_smem(int n, int digits) {
+  const size_t region = digits ? sizeof(unsigned int) * 3 * digits * hd_words(n) : sizeof(z64) * 2 * HT_THREADS;
   return sizeof(z64) * 3 * (size_t)n + region;
 }
 
-bool hetrd_digits_fit(int n) {
+static const void* panel_fn(int digits) {
+  return digits == 6 ? (const void*)hetrd_panel_kernel<6> : (const void*)hetrd_panel_kernel<HD_S>;
+}
+
+bool hetrd_digits_fit(int n, int digits) {
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return panel_smem(n, true) <= (size_t)optin;
+  return panel_smem(n, digits) <= (size_t)optin;
 }
 
 // Largest cluster size C (1..8, at most one block per 128 rows) for which the nprob clusters
 // of C blocks are all resident at once, as the occupancy calculator reports for this kernel.
-int hetrd_cluster_size(int n, int nprob, int num_sms, bool digits) {
+int hetrd_cluster_size(int n, int nprob, int num_sms, int digits) {
   const size_t smem = panel_smem(n, digits);
-  if (cudaFuncSetAttribute(hetrd_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-      cudaFuncSetAttribute(hetrd_panel_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 0) != cudaSuccess) {
+  const void* fn = panel_fn(digits);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 0) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
@@ -606,7 +624,7 @@ int hetrd_cluster_size(int n, int nprob, int num_sms, bool digits) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&clusters, hetrd_panel_kernel, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
@@ -617,9 +635,11 @@ int hetrd_cluster_size(int n, int nprob, int num_sms, bool digits) {
 
 cudaError_t launch_hetrd_panel(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA, double* d,
                                double* e, z64* tau, long long strideV, z64* VW, long long strideVW, int i0, int cluster,
-                               const void* dig, const int* erow, cudaStream_t st) {
-  size_t smem = panel_smem(n, dig != nullptr);
-  cudaError_t err = cudaFuncSetAttribute(hetrd_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                               const void* dig, const int* erow, int digits, cudaStream_t st) {
+  if (!dig) digits = 0;
+  if (digits != 0 && digits != 6 && digits != HD_S) return cudaErrorInvalidValue;
+  size_t smem = panel_smem(n, digits);
+  cudaError_t err = cudaFuncSetAttribute(panel_fn(digits), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nprob * cluster));
@@ -633,20 +653,28 @@ cudaError_t launch_hetrd_panel(int n, int nprob, const int32_t* size, z64* A, in
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, hetrd_panel_kernel, n, size, A, ld, strideA, d, e, tau, strideV, VW, strideVW, i0,
-                            (const uint4*)dig, erow, n > 1 ? n - 1 : 1, hd_words(n));
+  if (digits == 6)
+    return cudaLaunchKernelEx(&cfg, hetrd_panel_kernel<6>, n, size, A, ld, strideA, d, e, tau, strideV, VW, strideVW,
+                              i0, (const uint4*)dig, erow, n > 1 ? n - 1 : 1, hd_words(n));
+  return cudaLaunchKernelEx(&cfg, hetrd_panel_kernel<HD_S>, n, size, A, ld, strideA, d, e, tau, strideV, VW, strideVW,
+                            i0, (const uint4*)dig, erow, n > 1 ? n - 1 : 1, hd_words(n));
 }
 
-size_t hetrd_digits_bytes(int n, int nprob) {
+size_t hetrd_digits_bytes(int n, int nprob, int digits) {
   const size_t L = n > 1 ? n - 1 : 1;
-  return L * hd_words(n) * 64 * (size_t)nprob;
+  return L * hd_words(n) * 8 * (size_t)digits * (size_t)nprob;
 }
 
 cudaError_t launch_hetrd_digits(int n, int nprob, const int32_t* size, const z64* A, int ld, long long strideA, int i0,
-                                void* dig, int* erow, cudaStream_t st) {
+                                void* dig, int* erow, int digits, cudaStream_t st) {
   const int Lmax = n > 1 ? n - 1 : 1, L = n - i0 - 1;
   if (L <= 0) return cudaSuccess;
   dim3 grid((L + 7) / 8, nprob);
-  hetrd_digits_kernel<<<grid, 256, 0, st>>>(n, size, A, ld, strideA, i0, Lmax, hd_words(n), (uint4*)dig, erow);
+  if (digits == 6)
+    hetrd_digits_kernel<6><<<grid, 256, 0, st>>>(n, size, A, ld, strideA, i0, Lmax, hd_words(n), (uint4*)dig, erow);
+  else if (digits == HD_S)
+    hetrd_digits_kernel<HD_S><<<grid, 256, 0, st>>>(n, size, A, ld, strideA, i0, Lmax, hd_words(n), (uint4*)dig, erow);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

@@ -79,7 +79,7 @@ struct nao_ctx {
   std::vector<NaoPending> pending;
   std::vector<cudaEvent_t> event_pool;
   int gemm_method = NAO_GEMM_TC;
-  int refine_sweeps = 1;     // Ritz refinement sweeps after a mixed-precision solve (0, 1 or 2)
+  int refine_sweeps = 0;     // mixed mode: -1 none, 0 Rayleigh quotients, 1-2 Ritz sweeps + quotients
   int* dev_flags = nullptr;  // NAO_FLAG_*: device words shared by the context's kernels
   size_t hbm_budget = 0;     // bound on the workspace arena (0: none)
   nao_config cfg{};          // run-time settings (nao_init / nao_set_config)
@@ -97,6 +97,7 @@ constexpr int NAO_FLAG_WAIT = 2;
 constexpr double NAO_F_MIN_DEFAULT = 1e-16;
 constexpr int NAO_INV_ITER_DEFAULT = 5;
 constexpr long long NAO_TC_WAIT_DEFAULT = 4000000000LL;  // ~2 s at 2 GHz
+constexpr int NAO_MIXED_PLANES_DEFAULT = 6;
 
 // Workspace bytes nao_gen_eig / nao_density_matrix reserve on this context (before the
 // arena's 1/8 headroom); the scheduler's admission test uses them.
@@ -160,17 +161,22 @@ cudaError_t launch_herm_fill(int n, int nprob, const z64* src, long long src_str
 // per row [V | W | V]) receives the panel's reflectors and update vectors, and the caller
 // applies A(i0+NB:, i0+NB:) -= V W^H + W V^H before the next panel.
 constexpr int NAO_HT_NB = 32;
-int hetrd_cluster_size(int n, int nprob, int num_sms, bool digits);
-bool hetrd_digits_fit(int n);  // the digit path's shared memory fits a block at order n
+// Digit counts of the panel's integer matrix-vector products: 8 (62 bits, FP64 accuracy) or
+// 6 (46 bits: the H' reduction of the mixed mode); 0 selects the FP64 FMA path.
+constexpr int NAO_HT_DIGITS_FP64 = 8;
+constexpr int NAO_HT_DIGITS_MIXED = 6;
+int hetrd_cluster_size(int n, int nprob, int num_sms, int digits);
+bool hetrd_digits_fit(int n, int digits);  // the digit path's shared memory fits a block at order n
 // dig / erow (nullable): 8-bit digit planes of the trailing matrix made by launch_hetrd_digits
-// for this panel; with them the panel forms its Hermitian matrix-vector products exactly with
-// integer dot products (DP4A) instead of FP64 FMAs.
+// for this panel (with the same digit count); with them the panel forms its Hermitian
+// matrix-vector products exactly with integer dot products (DP4A) instead of FP64 FMAs.
 cudaError_t launch_hetrd_panel(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA, double* d,
                                double* e, z64* tau, long long strideV, z64* VW, long long strideVW, int i0, int cluster,
-                               const void* dig, const int* erow, cudaStream_t st);
-size_t hetrd_digits_bytes(int n, int nprob);  // digit planes (row exponents: (n - 1) nprob ints)
+                               const void* dig, const int* erow, int digits, cudaStream_t st);
+// digit planes (row exponents: (n - 1) nprob ints)
+size_t hetrd_digits_bytes(int n, int nprob, int digits);
 cudaError_t launch_hetrd_digits(int n, int nprob, const int32_t* size, const z64* A, int ld, long long strideA, int i0,
-                                void* dig, int* erow, cudaStream_t st);
+                                void* dig, int* erow, int digits, cudaStream_t st);
 
 // Eigen_HH step 2: eigenvalues w (ascending) and orthonormal eigenvectors Z (column-major,
 // ld) of tridiag(e, d, e) by bisection + inverse iteration.  scratch: see stein_scratch_doubles.
@@ -239,11 +245,12 @@ cudaError_t launch_ns_correct(int n, int nprob, const int32_t* size, const int32
 // op(A) op(B) + beta C with real alpha, beta.  Contractions longer than 896 (1792 real) run
 // as chunks whose FP32 group sums stay exact, accumulated in FP64.  ws: zgemm_oz_workspace
 // bytes; err: the context's dev_flags (err[NAO_FLAG_TIMEOUT] set to 1 if a bounded wait
-// expired; the bound is the long long at err + NAO_FLAG_WAIT).  digits: NAO_OZ_DIGITS_FP64
-// (ten base-64 planes, FP64 accuracy) or NAO_OZ_DIGITS_MIXED (five planes: 30 bits, a little
-// above an FP32 or three-term BF16 split product; 15 tensor-core products instead of 55).
+// expired; the bound is the long long at err + NAO_FLAG_WAIT).  digits: base-64 planes per
+// operand: NAO_OZ_DIGITS_FP64 (ten planes, 60 bits: FP64 accuracy, 55 tensor-core products),
+// or 5, 6, 7 (30, 36, 42 bits: 15, 21, 28 products) for terms that tolerate less.
 constexpr int NAO_OZ_DIGITS_FP64 = 10;
-constexpr int NAO_OZ_DIGITS_MIXED = 5;
+constexpr int NAO_OZ_DIGITS_NS = 5;   // the Newton-Schulz correction term (~1e-9 of Z)
+// the mixed mode's products take nao_config.mixed_planes (5, 6 or 7) planes
 bool zgemm_oz_supported(GemmDims dims);
 size_t zgemm_oz_workspace(int nprob, GemmDims dims);
 cudaError_t launch_zgemm_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta, z64* C,

@@ -605,10 +605,13 @@ cudaError_t launch_oz_chunked(int nprob, GemmDims dims, double alpha, GemmOperan
     b.ptr = (const char*)B.ptr + (long long)k0 * B.rs * (long long)esz;  // op(B)(k, j) at k rs + j cs
     const double bt = k0 == 0 ? beta : 1.0;
     cudaError_t e;
-    if (digits == NAO_OZ_DIGITS_MIXED)
-      e = launch_oz<REAL, NAO_OZ_DIGITS_MIXED>(nprob, d, alpha, a, b, bt, C, Cbs, Crs, Ccs, ws, err, st);
-    else
-      e = launch_oz<REAL, OZ_S>(nprob, d, alpha, a, b, bt, C, Cbs, Crs, Ccs, ws, err, st);
+    switch (digits) {
+      case 5: e = launch_oz<REAL, 5>(nprob, d, alpha, a, b, bt, C, Cbs, Crs, Ccs, ws, err, st); break;
+      case 6: e = launch_oz<REAL, 6>(nprob, d, alpha, a, b, bt, C, Cbs, Crs, Ccs, ws, err, st); break;
+      case 7: e = launch_oz<REAL, 7>(nprob, d, alpha, a, b, bt, C, Cbs, Crs, Ccs, ws, err, st); break;
+      case OZ_S: e = launch_oz<REAL, OZ_S>(nprob, d, alpha, a, b, bt, C, Cbs, Crs, Ccs, ws, err, st); break;
+      default: return cudaErrorInvalidValue;
+    }
     if (e != cudaSuccess) return e;
     if (dims.K <= chunk) break;
   }

@@ -262,7 +262,7 @@ void NaoServerCore::launch(ServeSlot* slot, std::vector<ServeReq*> rs) {
                          (const double*)r->dk.p, Hk + (size_t)r->prob_off * n * n, st);
   }
   if (!rc) {  // Parts 2-4 of the whole batch in one launch sequence
-    nao_set_refinement(slot->sub, 1);
+    nao_set_refinement(slot->sub, slot->srv->owner->refine_sweeps);  // the owner's refinement
     rc = nao_gen_eig(slot->sub, n, P, Hk, Sk, (const int32_t*)b->smap.p, NS, q0.s_cut, q0.precision, nb,
                      (double*)b->eps.p, (nao_c128*)b->C.p, (int32_t*)b->m.p, (int32_t*)b->st.p, st);
   }

@@ -47,7 +47,7 @@ class NaoError(RuntimeError):
 class NaoConfig(ctypes.Structure):
     """``nao_config`` of include/nao.h."""
     _fields_ = [("f_min", ctypes.c_double), ("inverse_iteration_max", ctypes.c_int),
-                ("tc_wait_cycles", ctypes.c_longlong)]
+                ("tc_wait_cycles", ctypes.c_longlong), ("mixed_planes", ctypes.c_int)]
 
 
 class NaoRequest(ctypes.Structure):
@@ -224,7 +224,8 @@ class Context:
         self._check(self.lib.nao_set_gemm_method(self.handle, int(method)), "nao_set_gemm_method")
 
     def nao_set_refinement(self, sweeps: int):
-        """Ritz refinement sweeps after a mixed-precision nao_gen_eig (0, 1 or 2)."""
+        """Refinement after a mixed-precision nao_gen_eig: 0 Rayleigh quotients only (default),
+        1 or 2 Ritz sweeps first, -1 none."""
         self._check(self.lib.nao_set_refinement(self.handle, int(sweeps)), "nao_set_refinement")
 
     def nao_zgemm(self, A, B, C=None, alpha=1.0, beta=0.0, transA=0, transB=0, method=NAO_GEMM_TC, stream=None):
