@@ -229,7 +229,7 @@ GenEigPlan plan_gen_eig(int n, int nprob, int nSe, bool use_tc) {
   W.oT2 = P.take<z64>((size_t)NAO_WY_NB * NAO_WY_NB * nmax * nblk);
   W.oW = P.take<z64>((size_t)NAO_WY_NB * n * nmax);
   W.oW2 = P.take<z64>((size_t)NAO_WY_NB * n * nmax);
-  W.oVW = P.take<z64>((size_t)3 * NAO_HT_NB * n * nmax);
+  W.oVW = P.take<z64>((size_t)2 * 3 * NAO_HT_NB * n * nmax);  // column-major + row-major copies
   // 8-bit digit planes of the Householder trailing matrix (tensor-core product method)
   W.oDig = P.take<char>(use_tc ? hetrd_digits_bytes(n, nmax, NAO_HT_DIGITS_FP64) : 16);
   W.oErow = P.take<int>((size_t)(n > 1 ? n - 1 : 1) * nmax);
@@ -326,7 +326,7 @@ cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t*
 
 // Eigen_HH step 1, blocked: panels of NAO_HT_NB columns reduced by the cluster kernel, each
 // followed by the deferred update A(r0:, r0:) -= V W^H + W V^H of the rest (lower triangle,
-// one rank-2 NB product).  VW: [nprob][n][3 NB] workspace.  digits: planes of the update
+// one rank-2 NB product).  VW: [nprob][3 NB][n] workspace (the panel's [V | W | V] columns).  digits: planes of the update
 // products; panel_digits: digits of the panel's integer matrix-vector products
 // (NAO_HT_DIGITS_FP64, or NAO_HT_DIGITS_MIXED for the H' reduction of the mixed mode).
 cudaError_t hetrd_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, z64* A, double* d, double* e, z64* tau,
@@ -348,15 +348,17 @@ cudaError_t hetrd_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, z
     if (err == cudaSuccess) {
       NaoStage stage_(ctx, "hetrd", st, 1);
       err = launch_hetrd_panel(n, nprob, size, A, n, snn, d, e, tau, n, VW, svw, i0, cl, use_dig ? dig : nullptr,
-                               erow, pd, st);
+                               erow, pd, VW + (size_t)nprob * svw, st);
     }
     if (err != cudaSuccess) return err;
     const int r0 = i0 + NB;
     if (r0 >= n) break;
     const int rows = n - r0;
     GemmDims dd{rows, rows, 2 * NB, nullptr, nullptr, nullptr, 1};
-    err = run_zgemm(ctx, "hetrd_update", nprob, dd, -1.0, GemmOperand{VW + (size_t)r0 * 3 * NB, svw, 3 * NB, 1, 0, nullptr},
-                    GemmOperand{VW + (size_t)r0 * 3 * NB + NB, svw, 1, 3 * NB, 1, nullptr}, 1.0,
+    // [V | W] (rows r0..) times [W | V]^H; VW holds the panel's columns column-major
+    z64* VWr = VW + (size_t)nprob * svw;
+    err = run_zgemm(ctx, "hetrd_update", nprob, dd, -1.0, GemmOperand{VWr + (size_t)r0 * 3 * NB, svw, 3 * NB, 1, 0, nullptr},
+                    GemmOperand{VWr + (size_t)r0 * 3 * NB + NB, svw, 1, 3 * NB, 1, nullptr}, 1.0,
                     A + r0 + (size_t)r0 * n, snn, 1, n, ozws, st, digits);
     if (err != cudaSuccess) return err;
   }

@@ -21,8 +21,9 @@
 //  * each pair's work (its full Hermitian row: row part + column part, and its share of the
 //    rank-2 update) is split over K threads so that ~1000 threads per block keep the FP64
 //    pipe fed; the K partial sums meet in shared memory in a fixed order;
-//  * two cluster barriers per column (release/acquire at cluster scope, so rows written by
-//    another block in the previous column are visible to ordinary loads afterwards).
+//  * four barriers per column: cluster barriers (release/acquire at cluster scope, so rows
+//    written by another block in the previous column are visible to ordinary loads
+//    afterwards) when C > 1, block barriers when one block holds the matrix.
 // Output: d[0..m), e[0..m-1) (e[m-1] = 0), tau[0..m) (tau[m-1] = 0), v_i in A(i+2:m, i).
 #include <cooperative_groups.h>
 
@@ -42,23 +43,32 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Sum of (a, b) over the block, returned to every thread.  red: >= 64 doubles of shared memory.
-__device__ __forceinline__ double2 block_sum2(double a, double b, double* red) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  a = warp_sum(a);
-  b = warp_sum(b);
-  __syncthreads();  // red may still be read from the previous call
-  if (lane == 0) {
-    red[wid] = a;
-    red[32 + wid] = b;
+// Sum of (a, b) over the first HT_RED_WARPS warps (the threads that hold data; the others pass
+// nothing), returned to every thread of the block.  On this GPU an FP64 warp instruction
+// holds the FP64 pipe for 16 cycles of the SM, so a reduction tree in all 32 warps of a block
+// costs ~10 us per column; in four warps it costs a tenth of that.  red: >= 8 doubles.
+constexpr int HT_RED_WARPS = 4;
+__device__ __forceinline__ double2 red_sum2(double a, double b, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (wid < HT_RED_WARPS) {
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane == 0) {
+      red[wid] = a;
+      red[HT_RED_WARPS + wid] = b;
+    }
   }
   __syncthreads();
-  a = (lane < nw) ? red[lane] : 0.0;
-  b = (lane < nw) ? red[32 + lane] : 0.0;
-  a = warp_sum(a);
-  b = warp_sum(b);
-  return make_double2(a, b);
+  double2 r = make_double2(0.0, 0.0);
+#pragma unroll
+  for (int k = 0; k < HT_RED_WARPS; ++k) {
+    r.x += red[k];
+    r.y += red[HT_RED_WARPS + k];
+  }
+  __syncthreads();  // red may be reused at once
+  return r;
 }
+
 
 
 // ---------------------------------------------------------------------------------------
@@ -136,6 +146,20 @@ __device__ __forceinline__ void hd_pack4(const z64* x, int e, uint4* out4) {
   }
 #pragma unroll
   for (int k = 0; k < S / 2; ++k) out4[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+}
+
+// digit words of 4 real values x[0..3]: out[t] = plane t
+template <int S>
+__device__ __forceinline__ void hd_pack4p(const double* x, int e, unsigned int* out) {
+#pragma unroll
+  for (int t = 0; t < S; ++t) out[t] = 0u;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    unsigned int dg[S];
+    hd_digits<S>(hd_fixed<S>(x[l], e), dg);
+#pragma unroll
+    for (int t = 0; t < S; ++t) out[t] |= dg[t] << (8 * l);
+  }
 }
 
 // digit words of v's 4 values: out[3 t + k], k = 0: Re v, 1: Im v, 2: -Im v (plane t)
@@ -228,20 +252,29 @@ __device__ __forceinline__ int pair_start(int k, int npairs, int C) { return (in
 // matrix as it stood at the panel start is corrected by the panel's V and W columns:
 //   p = A22 v - V (W^H v) - W (V^H v)   (c, d),   w = tau p - (tau/2)(p^H tau p ...) v (e).
 // The caller applies A22 -= V W^H + W V^H to the rest of the matrix after the panel
-// (a rank-2 NB update, run as one tensor-core product).  VW holds, per row, [V | W | V].
+// (a rank-2 NB product on the tensor cores).  VW holds the panel's columns [V | W | V]
+// column-major: VW(r, c) at VW[c n + r] (c < 3 NB), so that the FP64 warps, which walk
+// rows, read them coalesced.
+//
+// Digit path: the 24 digit-product warps take groups of four rows dynamically (a counter in
+// shared memory), eight lanes per row.  (Streaming the digit rows through per-warp rings of
+// shared memory with asynchronous copies was measured slower: 96 vs 90 ms per step on the
+// magnetite-shaped cell; the rows then pass the shared-memory pipe twice.)  With one block
+// per matrix (C = 1) the barriers are block barriers; clusters use cluster barriers
+// (release/acquire at cluster scope).
 template <int S>
 __global__ void __launch_bounds__(HT_THREADS)
 hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Abase, int ld, long long strideA,
                    double* __restrict__ dbase, double* __restrict__ ebase, z64* __restrict__ taubase, long long strideV,
                    z64* __restrict__ VWbase, long long strideVW, int i0, const uint4* __restrict__ dig,
-                   const int* __restrict__ erow, int Lmax, int W) {
+                   const int* __restrict__ erow, int Lmax, int W, z64* __restrict__ VWrbase) {
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
   constexpr int NB = NAO_HT_NB;
-  constexpr int LDVW = 3 * NB;
+  constexpr int QW = S / 2;  // uint4 per four columns of a digit row
   extern __shared__ z64 sm[];
-  z64* v = sm;               // [n] reflector (trailing coordinates)
+  z64* v = sm;               // [n] reflector (trailing coordinates); first x itself
   z64* w = sm + n;           // [n] w; in the digit path first the corrections of p (one-block clusters)
   z64* pown = sm + 2 * n;    // [n] p for this block's rows (read by the others)
   z64* part = sm + 3 * n;    // FP64 path: [2 * HT_THREADS] partial sums of the K threads of each pair
@@ -251,6 +284,7 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
   __shared__ double red[64];
   __shared__ z64 s_tau, s_scale;
   __shared__ double s_beta;
+  __shared__ int s_next;
 
   const int p = blockIdx.x / C;
   const int m = size ? size[p] : n;
@@ -259,6 +293,8 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
   double* e = ebase + (size_t)p * strideV;
   z64* tau = taubase + (size_t)p * strideV;
   z64* VW = VWbase + (size_t)p * strideVW;
+#define VWAT(r, c) VW[(size_t)(c) * n + (r)]
+  z64* VWr = VWrbase + (size_t)p * strideVW;  // row-major copy: VWr[r * 3 NB + c]
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   const int iend = min(i0 + NB, m);  // uniform over the cluster (one problem per cluster)
   // Digit path: warps [0, NWD) form the digit products while the last HT_FP64_WARPS warps
@@ -267,6 +303,10 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
   // integer and FP64 pipes work at the same time.
   const bool dp = dig != nullptr;
   const int NWD = dp ? nw - HT_FP64_WARPS : nw;
+  auto csync = [&]() {
+    if (C == 1) __syncthreads();
+    else cluster.sync();
+  };
 
   for (int i = i0; i < iend; ++i) {
     const int j = i - i0;
@@ -276,17 +316,15 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
       const int jj0 = dp ? j - 1 : 0;
       for (int r = i + rank * nt + tid; r < m; r += C * nt) {
         z64 acc = A[(size_t)i * ld + r];
-        const z64* Vr = VW + (size_t)r * LDVW;
-        const z64* Vi = VW + (size_t)i * LDVW;
         for (int jj = jj0; jj < j; ++jj) {
-          acc = zfmsc(Vr[jj], Vi[NB + jj], acc);  // - V(r,jj) conj(W(i,jj))
-          acc = zfmsc(Vr[NB + jj], Vi[jj], acc);  // - W(r,jj) conj(V(i,jj))
+          acc = zfmsc(VWAT(r, jj), VWAT(i, NB + jj), acc);  // - V(r,jj) conj(W(i,jj))
+          acc = zfmsc(VWAT(r, NB + jj), VWAT(i, jj), acc);  // - W(r,jj) conj(V(i,jj))
         }
         if (r == i) acc.y = 0.0;
         A[(size_t)i * ld + r] = acc;
       }
     }
-    cluster.sync();  // S1: column i is final everywhere
+    csync();  // S1: column i is final everywhere
     if (i == m - 1) {  // last diagonal element, no reflector
       if (rank == 0 && tid == 0) {
         d[m - 1] = A[(size_t)(m - 1) * ld + (m - 1)].x;
@@ -297,12 +335,18 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
     }
     const int mt = m - i - 1;
     const z64* col = A + (size_t)i * ld;
-    // (b) Procedures 1-2 (every block, redundantly): the reflector of x = A(i+1:m, i)
+    // (b) Procedures 1-2 (every block, redundantly): x = A(i+1:m, i) read once into v, the
+    // norm of x(1:) summed on the way; then the reflector, and v = x / (alpha - beta)
     double s = 0.0;
-    for (int r = i + 2 + tid; r < m; r += nt) s += zabs2(col[r]);
-    s = block_sum2(s, 0.0, red).x;
+    if (tid < 32 * HT_RED_WARPS)
+      for (int r = tid; r < mt; r += 32 * HT_RED_WARPS) {
+        const z64 x = col[i + 1 + r];
+        v[r] = x;
+        if (r > 0) s += zabs2(x);
+      }
+    s = red_sum2(s, 0.0, red).x;  // (its barriers also publish v)
     if (tid == 0) {
-      const z64 alpha = col[i + 1];
+      const z64 alpha = v[0];
       const double xnorm = sqrt(s);
       z64 t, scale;
       double beta;
@@ -329,7 +373,7 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
     __syncthreads();
     const z64 t = s_tau;
     const z64 scale = s_scale;
-    for (int r = tid; r < mt; r += nt) v[r] = (r == 0) ? zmk(1.0, 0.0) : zmul(col[i + 1 + r], scale);
+    for (int r = tid; r < mt; r += nt) v[r] = (r == 0) ? zmk(1.0, 0.0) : zmul(v[r], scale);
     __syncthreads();
     const bool active = !(t.x == 0.0 && t.y == 0.0);  // H_i = I otherwise (uniform)
 
@@ -354,23 +398,31 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
       const int f = bm == 0 ? -1100 : bm - 1022;
       const int kk0 = i - i0;  // column i + 1 relative to i0 + 1
       const int w0 = kk0 >> 2, Wp = (m - i0 - 1 + 3) >> 2;
-      for (int w = w0 + tid; w < Wp; w += nt) {
-        z64 x[4];
+      for (int idx = tid; idx < 3 * (Wp - w0); idx += nt) {  // one (word, part) per thread
+        const int w = w0 + idx / 3, part = idx % 3;
+        double x[4];
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
           const int c = 4 * w + l - kk0;
-          x[l] = (c >= 0 && c < mt) ? v[c] : zmk(0.0, 0.0);
+          const z64 vc = (c >= 0 && c < mt) ? v[c] : zmk(0.0, 0.0);
+          x[l] = part == 0 ? vc.x : (part == 1 ? vc.y : -vc.y);
         }
-        unsigned int t[3 * S];
-        hd_pack4v<S>(x, f, t);
+        unsigned int t[S];
+        hd_pack4p<S>(x, f, t);
 #pragma unroll
-        for (int k = 0; k < 3 * S; ++k) vd[k * W + w] = t[k];
+        for (int k = 0; k < S; ++k) vd[(3 * k + part) * W + w] = t[k];
       }
+      if (tid == 0) s_next = 0;
       __syncthreads();
-      // rows of this block's pairs: four rows per warp, eight lanes per row
-      const int nrows = 2 * P, rslot = lane >> 3, wl = lane & 7;
-      for (int q0 = wid * 4; wid < NWD && q0 < nrows; q0 += NWD * 4) {
-        const int qq = q0 + rslot;
+      // rows of this block's pairs, in groups of two taken dynamically: sixteen lanes per row
+      const int nrows = 2 * P, rslot = lane >> 4, wl = lane & 15;
+      const int ngroups = (nrows + 1) >> 1;
+      while (wid < NWD) {
+        int grp = 0;
+        if (lane == 0) grp = atomicAdd(&s_next, 1);
+        grp = __shfl_sync(0xffffffffu, grp, 0);
+        if (grp >= ngroups) break;
+        const int qq = grp * 2 + rslot;
         int r = -1;
         if (qq < nrows) {
           const int g = g0 + (qq >> 1);
@@ -382,22 +434,24 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
         for (int G = 0; G < S; ++G) RR[G] = RI[G] = 0;
         const int rr = r + kk0;  // digit row
         if (r >= 0) {
-          const uint4* row = dig + ((size_t)p * Lmax + rr) * W * (S / 2);
-          for (int w = w0 + wl; w < Wp; w += 8) {
+          const uint4* row = dig + ((size_t)p * Lmax + rr) * W * QW;
+          for (int ww = w0 + wl; ww < Wp; ww += 16) {
             unsigned int a[2 * S];
-            const uint4* aw = row + (size_t)w * (S / 2);
+            const uint4* aw = row + (size_t)ww * QW;
+            // the lane's word two iterations on, into L2 (the row stream comes from DRAM)
+            if (ww + 32 < Wp) asm volatile("prefetch.global.L2 [%0];" :: "l"(row + (size_t)(ww + 32) * QW));
 #pragma unroll
-            for (int k = 0; k < S / 2; ++k) {
-              const uint4 q4 = aw[k];
-              a[4 * k] = q4.x;
-              a[4 * k + 1] = q4.y;
-              a[4 * k + 2] = q4.z;
-              a[4 * k + 3] = q4.w;
+            for (int q = 0; q < QW; ++q) {
+              const uint4 q4 = __ldcs(aw + q);
+              a[4 * q] = q4.x;
+              a[4 * q + 1] = q4.y;
+              a[4 * q + 2] = q4.z;
+              a[4 * q + 3] = q4.w;
             }
 #pragma unroll
             for (int t2 = 0; t2 < S; ++t2) {
-              const int bre = (int)vd[(3 * t2) * W + w], bim = (int)vd[(3 * t2 + 1) * W + w],
-                        bni = (int)vd[(3 * t2 + 2) * W + w];
+              const int bre = (int)vd[(3 * t2) * W + ww], bim = (int)vd[(3 * t2 + 1) * W + ww],
+                        bni = (int)vd[(3 * t2 + 2) * W + ww];
 #pragma unroll
               for (int s2 = 0; s2 + t2 < S; ++s2) {
                 const int G = s2 + t2;
@@ -410,7 +464,7 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
           }
         }
 #pragma unroll
-        for (int o = 1; o < 8; o <<= 1)
+        for (int o = 1; o < 16; o <<= 1)
 #pragma unroll
           for (int G = 0; G < S; ++G) {
             RR[G] += __shfl_xor_sync(0xffffffffu, RR[G], o);
@@ -449,8 +503,8 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
         z64 acc = zmk(0.0, 0.0);
         for (int g = g0 + lane; g < g1; g += 32) {
           const int ra = g, rb = mt - 1 - g;
-          acc = zcfma(VW[(size_t)(i + 1 + ra) * LDVW + cidx], v[ra], acc);
-          if (rb != ra) acc = zcfma(VW[(size_t)(i + 1 + rb) * LDVW + cidx], v[rb], acc);
+          acc = zcfma(VWAT(i + 1 + ra, cidx), v[ra], acc);
+          if (rb != ra) acc = zcfma(VWAT(i + 1 + rb, cidx), v[rb], acc);
         }
         const double sre = warp_sum(acc.x), sim = warp_sum(acc.y);
         if (lane == 0) ypart[jj] = zmk(sre, sim);
@@ -475,8 +529,8 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
           z64 acc = zmk(0.0, 0.0);
           for (int g = g0 + lane; g < g1; g += 32) {
             const int ra = g, rb = mt - 1 - g;
-            acc = zcfma(VW[(size_t)(i + 1 + ra) * LDVW + cidx], v[ra], acc);
-            if (rb != ra) acc = zcfma(VW[(size_t)(i + 1 + rb) * LDVW + cidx], v[rb], acc);
+            acc = zcfma(VWAT(i + 1 + ra, cidx), v[ra], acc);
+            if (rb != ra) acc = zcfma(VWAT(i + 1 + rb, cidx), v[rb], acc);
           }
           const double sre = warp_sum(acc.x), sim = warp_sum(acc.y);
           if (lane == 0) ypart[jj] = zmk(sre, sim);
@@ -486,11 +540,10 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
           // are formed here too, into w (subtracted from p in (e))
           asm volatile("bar.sync 1, %0;" :: "r"(nft) : "memory");
           for (int r = ft; r < mt; r += nft) {
-            const z64* row = VW + (size_t)(i + 1 + r) * LDVW;
             z64 acc = zmk(0.0, 0.0);
             for (int jj = 0; jj < j; ++jj) {
-              acc = zfma(row[jj], ypart[jj], acc);           // V(r,jj) (W^H v)_jj
-              acc = zfma(row[NB + jj], ypart[j + jj], acc);  // W(r,jj) (V^H v)_jj
+              acc = zfma(VWAT(i + 1 + r, jj), ypart[jj], acc);           // V(r,jj) (W^H v)_jj
+              acc = zfma(VWAT(i + 1 + r, NB + jj), ypart[j + jj], acc);  // W(r,jj) (V^H v)_jj
             }
             w[r] = acc;
           }
@@ -500,26 +553,26 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
       // column j follows in its (a)
       if (j > 0 && j + 1 < NB && i + 1 < iend) {
         const int i1 = i + 1;
-        const z64* Vi = VW + (size_t)i1 * LDVW;
         for (int r = i1 + rank * nft + ft; r < m; r += C * nft) {
           z64 acc = A[(size_t)i1 * ld + r];
-          const z64* Vr = VW + (size_t)r * LDVW;
           for (int jj = 0; jj < j; ++jj) {
-            acc = zfmsc(Vr[jj], Vi[NB + jj], acc);
-            acc = zfmsc(Vr[NB + jj], Vi[jj], acc);
+            acc = zfmsc(VWAT(r, jj), VWAT(i1, NB + jj), acc);
+            acc = zfmsc(VWAT(r, NB + jj), VWAT(i1, jj), acc);
           }
           A[(size_t)i1 * ld + r] = acc;
         }
       }
     }
-    cluster.sync();  // S2: partial results ready; every block is done reading column i
+    csync();  // S2: partial results ready; every block is done reading column i
     if (rank == 0) {  // Procedure 3: keep v below the subdiagonal of column i, and in V
       z64* colw = A + (size_t)i * ld;
       for (int r = tid; r < mt; r += nt) {
         colw[i + 1 + r] = (r == 0) ? zmk(s_beta, 0.0) : v[r];
-        z64* row = VW + (size_t)(i + 1 + r) * LDVW;
-        row[j] = active ? v[r] : zmk(0.0, 0.0);
-        row[2 * NB + j] = row[j];
+        const z64 vr = active ? v[r] : zmk(0.0, 0.0);
+        VWAT(i + 1 + r, j) = vr;
+        VWAT(i + 1 + r, 2 * NB + j) = vr;
+        VWr[(size_t)(i + 1 + r) * 3 * NB + j] = vr;
+        VWr[(size_t)(i + 1 + r) * 3 * NB + 2 * NB + j] = vr;
       }
     }
     if (active && (!dp || C > 1)) {
@@ -536,25 +589,24 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
           const int gl = tt >> 1, h = tt & 1, g = g0 + gl;
           const int r = h ? mt - 1 - g : g;
           if (h && r == g) continue;
-          const z64* row = VW + (size_t)(i + 1 + r) * LDVW;
           z64 acc = pown[r];
           for (int jj = 0; jj < j; ++jj) {
-            acc = zfms(row[jj], yfull[jj], acc);           // - V(r,jj) (W^H v)_jj
-            acc = zfms(row[NB + jj], yfull[j + jj], acc);  // - W(r,jj) (V^H v)_jj
+            acc = zfms(VWAT(i + 1 + r, jj), yfull[jj], acc);           // - V(r,jj) (W^H v)_jj
+            acc = zfms(VWAT(i + 1 + r, NB + jj), yfull[j + jj], acc);  // - W(r,jj) (V^H v)_jj
           }
           pown[r] = acc;
         }
     }
-    cluster.sync();  // S3: corrected pieces of p ready
+    csync();  // S3: corrected pieces of p ready
     if (active) {
       // (e) Procedure 5: w = tau p - (tau/2) ((tau p)^H v) v on the full vector (in the digit
       // path with a one-block cluster, p = pown - w: the corrections formed beside (c))
       const bool dpc = dp && C == 1 && j > 0;
       z64 dacc = zmk(0.0, 0.0);
-      for (int g = tid; g < npairs; g += nt) {
+      for (int g = tid; tid < 32 * HT_RED_WARPS && g < npairs; g += 32 * HT_RED_WARPS) {
         int k = 0;
         while (k + 1 < C && pair_start(k + 1, npairs, C) <= g) ++k;
-        const z64* src = cluster.map_shared_rank(pown, k);
+        const z64* src = C == 1 ? pown : cluster.map_shared_rank(pown, k);
         const int ra = g, rb = mt - 1 - g;
         const z64 pa = zmul(t, dpc ? zsub(src[ra], w[ra]) : src[ra]);
         w[ra] = pa;
@@ -565,17 +617,26 @@ hetrd_panel_kernel(int n, const int32_t* __restrict__ size, z64* __restrict__ Ab
           dacc = zcfma(pb, v[rb], dacc);
         }
       }
-      const double2 dot = block_sum2(dacc.x, dacc.y, red);
+      const double2 dot = red_sum2(dacc.x, dacc.y, red);  // (its barriers also publish w)
       const z64 alpha2 = zscale(zmul(t, zmk(dot.x, dot.y)), -0.5);
-      for (int r = tid; r < mt; r += nt) w[r] = zfma(alpha2, v[r], w[r]);
-      __syncthreads();
+      for (int r = tid; r < mt; r += nt) {
+        const z64 wr = zfma(alpha2, v[r], w[r]);
+        w[r] = wr;
+        if (rank == 0) {
+          VWAT(i + 1 + r, NB + j) = wr;
+          VWr[(size_t)(i + 1 + r) * 3 * NB + NB + j] = wr;
+        }
+      }
+    } else if (rank == 0) {
+      for (int r = tid; r < mt; r += nt) {
+        VWAT(i + 1 + r, NB + j) = zmk(0.0, 0.0);
+        VWr[(size_t)(i + 1 + r) * 3 * NB + NB + j] = zmk(0.0, 0.0);
+      }
     }
-    if (rank == 0)
-      for (int r = tid; r < mt; r += nt) VW[(size_t)(i + 1 + r) * LDVW + NB + j] = active ? w[r] : zmk(0.0, 0.0);
-    cluster.sync();  // S4: V and W column j visible to the whole cluster
+    csync();  // S4: V and W column j visible to the whole cluster
   }
+#undef VWAT
 }
-
 }  // namespace
 
 // v, w, pown, then one region shared by the FP64 path's partial sums and the digit path's
@@ -585,19 +646,21 @@ static size_t panel_smem(int n, int digits) {
   return sizeof(z64) * 3 * (size_t)n + region;
 }
 
-static const void* panel_fn(int digits) {
-  return digits == 6 ? (const void*)hetrd_panel_kernel<6> : (const void*)hetrd_panel_kernel<HD_S>;
-}
-
-bool hetrd_digits_fit(int n, int digits) {
+static int smem_optin() {
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return 0;
   }
-  return panel_smem(n, digits) <= (size_t)optin;
+  return optin;
 }
+
+static const void* panel_fn(int digits) {
+  return digits == 6 ? (const void*)hetrd_panel_kernel<6> : (const void*)hetrd_panel_kernel<HD_S>;
+}
+
+bool hetrd_digits_fit(int n, int digits) { return panel_smem(n, digits) <= (size_t)smem_optin(); }
 
 // Largest cluster size C (1..8, at most one block per 128 rows) for which the nprob clusters
 // of C blocks are all resident at once, as the occupancy calculator reports for this kernel.
@@ -635,7 +698,7 @@ int hetrd_cluster_size(int n, int nprob, int num_sms, int digits) {
 
 cudaError_t launch_hetrd_panel(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA, double* d,
                                double* e, z64* tau, long long strideV, z64* VW, long long strideVW, int i0, int cluster,
-                               const void* dig, const int* erow, int digits, cudaStream_t st) {
+                               const void* dig, const int* erow, int digits, z64* VWr, cudaStream_t st) {
   if (!dig) digits = 0;
   if (digits != 0 && digits != 6 && digits != HD_S) return cudaErrorInvalidValue;
   size_t smem = panel_smem(n, digits);
@@ -655,9 +718,9 @@ cudaError_t launch_hetrd_panel(int n, int nprob, const int32_t* size, z64* A, in
   cfg.numAttrs = 1;
   if (digits == 6)
     return cudaLaunchKernelEx(&cfg, hetrd_panel_kernel<6>, n, size, A, ld, strideA, d, e, tau, strideV, VW, strideVW,
-                              i0, (const uint4*)dig, erow, n > 1 ? n - 1 : 1, hd_words(n));
+                              i0, (const uint4*)dig, erow, n > 1 ? n - 1 : 1, hd_words(n), VWr);
   return cudaLaunchKernelEx(&cfg, hetrd_panel_kernel<HD_S>, n, size, A, ld, strideA, d, e, tau, strideV, VW, strideVW,
-                            i0, (const uint4*)dig, erow, n > 1 ? n - 1 : 1, hd_words(n));
+                            i0, (const uint4*)dig, erow, n > 1 ? n - 1 : 1, hd_words(n), VWr);
 }
 
 size_t hetrd_digits_bytes(int n, int nprob, int digits) {

@@ -157,8 +157,8 @@ cudaError_t launch_herm_fill(int n, int nprob, const z64* src, long long src_str
 // full Hermitian column-major matrix A (ld).  size[p] (or n when size == null) is the order.
 // Only the lower triangle of A is read and updated.  `cluster` blocks (1..8, a thread-block
 // cluster) share each matrix; hetrd_cluster_size picks it from the problem count.
-// One launch reduces the panel of columns i0 .. i0+NAO_HT_NB-1; VW ([nprob][n][3 NB],
-// per row [V | W | V]) receives the panel's reflectors and update vectors, and the caller
+// One launch reduces the panel of columns i0 .. i0+NAO_HT_NB-1; VW ([nprob][3 NB][n], the
+// columns [V | W | V]) receives the panel's reflectors and update vectors, and the caller
 // applies A(i0+NB:, i0+NB:) -= V W^H + W V^H before the next panel.
 constexpr int NAO_HT_NB = 32;
 // Digit counts of the panel's integer matrix-vector products: 8 (62 bits, FP64 accuracy) or
@@ -172,7 +172,7 @@ bool hetrd_digits_fit(int n, int digits);  // the digit path's shared memory fit
 // matrix-vector products exactly with integer dot products (DP4A) instead of FP64 FMAs.
 cudaError_t launch_hetrd_panel(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA, double* d,
                                double* e, z64* tau, long long strideV, z64* VW, long long strideVW, int i0, int cluster,
-                               const void* dig, const int* erow, int digits, cudaStream_t st);
+                               const void* dig, const int* erow, int digits, z64* VWr, cudaStream_t st);
 // digit planes (row exponents: (n - 1) nprob ints)
 size_t hetrd_digits_bytes(int n, int nprob, int digits);
 cudaError_t launch_hetrd_digits(int n, int nprob, const int32_t* size, const z64* A, int ld, long long strideA, int i0,
