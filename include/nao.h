@@ -77,6 +77,12 @@ typedef struct {
   int mixed_planes;           /* BF16 digit planes per operand of the products that the
                                  mixed mode (NAO_MIXED_BF16X3) computes to reduced precision:
                                  5, 6 or 7 (30, 36 or 42 bits); default 6                    */
+  int overlap_mrrr;           /* eigenvectors of the overlap's tridiagonal (Eigen_HH step 2
+                                 of Part 2): 1 (default) from a relatively robust
+                                 representation L D L^T of T - sigma I (dstegr's method, which
+                                 the paper names) wherever an eigenvalue's relative gap is at
+                                 least 1e-3, inverse iteration for the rest; 0: inverse
+                                 iteration (dstevx's method) for all                         */
 } nao_config;
 
 void nao_config_defaults(nao_config* cfg);

@@ -98,6 +98,7 @@ constexpr double NAO_F_MIN_DEFAULT = 1e-16;
 constexpr int NAO_INV_ITER_DEFAULT = 5;
 constexpr long long NAO_TC_WAIT_DEFAULT = 4000000000LL;  // ~2 s at 2 GHz
 constexpr int NAO_MIXED_PLANES_DEFAULT = 6;
+constexpr int NAO_OVERLAP_MRRR_DEFAULT = 1;
 
 // Workspace bytes nao_gen_eig / nao_density_matrix reserve on this context (before the
 // arena's 1/8 headroom); the scheduler's admission test uses them.
@@ -183,11 +184,14 @@ cudaError_t launch_hetrd_digits(int n, int nprob, const int32_t* size, const z64
 size_t stein_scratch_doubles(int n, int nprob);
 // nvec (nullable: all) and nvec_max bound the eigenvectors computed per problem to the lowest
 // min(nvec[p], nvec_max); the eigenvalues are always all computed.
-// maxits: inverse-iteration solves per vector before NAO_E_NOCONV (nao_config).
+// maxits: inverse-iteration solves per vector before NAO_E_NOCONV (nao_config).  mrrr: first
+// compute the vectors of relatively well separated eigenvalues from a relatively robust
+// representation (positive semidefinite T only: the overlap's tridiagonal); inverse iteration
+// takes the rest.
 cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d, const double* e,
                          long long strideV, double* w, double* Z, int ld, long long strideZ,
                          double* scratch, int32_t* status, const int32_t* nvec, int nvec_max, int maxits,
-                         cudaStream_t st);
+                         int mrrr, cudaStream_t st);
 
 // Blocked (compact WY) back-transformation helpers, see backtr.cu.
 constexpr int NAO_WY_NB = 128;

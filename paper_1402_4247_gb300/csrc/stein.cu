@@ -405,7 +405,7 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
                  long long strideV, const double* __restrict__ wslot, double* __restrict__ wbase,
                  double* __restrict__ Zbase, int ldz, long long strideZ, double* __restrict__ scratch,
                  int32_t* __restrict__ status, int* __restrict__ biglist, int bigcap,
-                 const int32_t* __restrict__ nvec, int nvec_max, int maxits) {
+                 const int32_t* __restrict__ nvec, int nvec_max, int maxits, const int* __restrict__ mdone) {
   extern __shared__ double smd[];
   double* d = smd;
   double* e = smd + n;
@@ -478,6 +478,11 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
           rq += (wt < wq) || (wt == wq && t < q);
         }
         if (rq >= nv) break;  // members ascend: the rest of the cluster is not wanted either
+        const int* dn = mdone ? mdone + (size_t)p * n : nullptr;
+        if (dn && dn[q]) {  // an MRRR vector (kernel 0) is already in Z
+          lamprev = wq;
+          continue;
+        }
         double* zc = Z + (size_t)rq * ldz;
         if (bs == 1) {
           for (int i = 0; i < m; ++i) zc[i] = (i == b0) ? 1.0 : 0.0;
@@ -558,7 +563,8 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
             x2 = x1v;
             x1v = xv;
           }
-          for (int t = j; t < q; ++t) {  // reorthogonalise against earlier tight-cluster members
+          for (int t = j; t < jend; ++t) {  // reorthogonalise against the cluster's finished members
+            if (t == q || (t > q && !(dn && dn[t]))) continue;
             const double wt = w[t];
             int rt = 0;
             for (int u = 0; u < m; ++u) rt += (w[u] < wt) || (w[u] == wt && u < t);
@@ -639,7 +645,7 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
                      const double* __restrict__ ebase, long long strideV, const double* __restrict__ wslot,
                      double* __restrict__ Zbase, int ldz, long long strideZ, double* __restrict__ scratch,
                      int32_t* __restrict__ status, const int* __restrict__ biglist, int bigcap,
-                     const int32_t* __restrict__ nvec, int nvec_max, int maxits) {
+                     const int32_t* __restrict__ nvec, int nvec_max, int maxits, const int* __restrict__ mdone) {
   extern __shared__ double smc[];
   double* d = smc;
   double* e = smc + n;
@@ -650,8 +656,9 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
   int* bst = (int*)(smc + 5 * n);
   int* ben = bst + n;
   int* rnk = ben + n;
+  int* fin = rnk + n;  // the finished members a member is re-orthogonalised against
   __shared__ double red[96];
-  __shared__ int s_go, s_ok;
+  __shared__ int s_go, s_ok, s_nf;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   const int count = min(biglist[0], bigcap);
   for (int ent = blockIdx.x; ent < count; ent += gridDim.x) {
@@ -683,8 +690,19 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
     double lamprev = 0.0, ulast = 0.0;
     bool fail = false;
     const int nv = min(nvec ? nvec[p] : m, nvec_max);
+    const int* dn = mdone ? mdone + (size_t)p * n : nullptr;
     for (int q = j; q < jend; ++q) {
       if (rnk[q - j] >= nv) break;  // uniform: ranks ascend with q
+      if (dn && dn[q]) {  // an MRRR vector (kernel 0) is already in Z
+        lamprev = w[q];
+        continue;
+      }
+      if (tid == 0) {  // finished members: the earlier ones and the later MRRR vectors
+        int c = 0;
+        for (int t = 0; t < jend - j; ++t)
+          if (t < q - j || (t > q - j && dn && dn[j + t])) fin[c++] = t;
+        s_nf = c;
+      }
       const int sl = q;
 #define AT(arr, i) arr[(size_t)(i) * n + sl]
       if (tid == 0) {  // LU with partial pivoting of T[b0:b1) - lam I (as kernel 2)
@@ -766,20 +784,20 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
           }
         }
         __syncthreads();
-        const int np = q - j;  // earlier members
-        for (int pass = 0; pass < 2 && np > 0; ++pass) {
-          for (int t = wid; t < np; t += nw) {
-            const double* zt = Z + (size_t)rnk[t] * ldz;
+        const int nf = s_nf;  // (published by the barriers above)
+        for (int pass = 0; pass < 2 && nf > 0; ++pass) {
+          for (int u = wid; u < nf; u += nw) {
+            const double* zt = Z + (size_t)rnk[fin[u]] * ldz;
             double dt = 0.0;
             for (int i = b0 + lane; i < b1; i += 32) dt = fma(sx[i], zt[i], dt);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) dt += __shfl_xor_sync(0xffffffffu, dt, o);
-            if (lane == 0) dots[t] = dt;
+            if (lane == 0) dots[u] = dt;
           }
           __syncthreads();
           for (int i = b0 + tid; i < b1; i += nt) {
             double v = sx[i];
-            for (int t = 0; t < np; ++t) v = fma(-dots[t], Z[(size_t)rnk[t] * ldz + i], v);
+            for (int u = 0; u < nf; ++u) v = fma(-dots[u], Z[(size_t)rnk[fin[u]] * ldz + i], v);
             sx[i] = v;
           }
           __syncthreads();
@@ -832,6 +850,264 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
   }
 }
 
+
+// ---------------------------------------------------------------- kernel 0: MRRR vectors
+// Eigenvectors from a relatively robust representation (the method of LAPACK's dstegr /
+// dstemr, which the paper names beside dstevx; one root representation, not the whole
+// representation tree): for every unreduced block of a positive semidefinite tridiagonal (the
+// overlap's), shift to just below its smallest eigenvalue, T - sigma I = L D L^T with D > 0.
+// A definite L D L^T determines its eigenvalues to high relative accuracy, so the near-null
+// spectrum of an ill-conditioned overlap, hundreds of eigenvalues within 1e-7 |T| of each
+// other but relatively far apart, becomes well separated.
+//   A member of a big tight cluster (gaps < 1e-7 |T|_1, more than BIG members: the ones
+// inverse iteration would re-orthogonalise at O(k^2 n)) whose shifted eigenvalue
+// mu = lambda - sigma has a relative gap of at least MR_MINRGP to both neighbours is refined
+// by bisection on negative-pivot counts of L D L^T - x I (the stationary qd transform) to
+// relative accuracy, and its eigenvector comes from one twisted factorization of
+// L D L^T - mu I: the forward (stationary) and backward (progressive) transforms give
+// gamma_k = s_k + p_k + mu, and with r = argmin |gamma_k|, z_r = 1, z_k = -L+_k z_{k+1} above
+// r, z_{k+1} = -U-_k z_k below it.
+//   Vectors of one representation are orthogonal to O(n eps / relgap) without any
+// Gram-Schmidt (LAPACK asks relgap >= 1e-3 for 1e-13 orthogonality; here the Newton-Schulz
+// step that follows removes overlaps up to ~1e-6, so relgap >= 1e-5 suffices: overlaps
+// <= n eps / 1e-5 ~ 3e-8 at n = 3000).  Slots with smaller relative gaps are left
+// (mdone = 0) to inverse iteration, which re-orthogonalises them against the finished members.
+constexpr double MR_MINRGP = 1e-5;
+constexpr int MR_THREADS = 64;
+
+// negative pivots of L D L^T - x I over [b0, b1) (stationary qd; tiny pivots set to -pivmin)
+__device__ int mr_negcount(const double* __restrict__ D, const double* __restrict__ L, int b0, int b1, double x,
+                           double pivmin) {
+  double s = -x;
+  int cnt = 0;
+  for (int k = b0; k < b1 - 1; ++k) {
+    double dp = D[k] + s;
+    if (fabs(dp) < pivmin) dp = -pivmin;
+    cnt += dp < 0.0;
+    s = (L[k] * L[k] * D[k]) * s / dp - x;
+  }
+  double dp = D[b1 - 1] + s;
+  if (fabs(dp) < pivmin) dp = -pivmin;
+  return cnt + (dp < 0.0);
+}
+
+__global__ void __launch_bounds__(MR_THREADS)
+mrrr_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ dbase,
+                const double* __restrict__ ebase, long long strideV, const double* __restrict__ wslot,
+                double* __restrict__ Zbase, int ldz, long long strideZ, double* __restrict__ scratch,
+                int* __restrict__ mdone, const int32_t* __restrict__ nvec, int nvec_max) {
+  extern __shared__ double smr[];
+  double* w = smr;           // [n] eigenvalues (slot order)
+  double* D = smr + n;       // [n] root representation of each unreduced block
+  double* L = smr + 2 * n;   // [n]
+  double* sig = smr + 3 * n; // [n] the block's shift, per row
+  int* bst = (int*)(smr + 4 * n);
+  int* ben = bst + n;
+  __shared__ double s_tn;
+  const int p = blockIdx.y;
+  const int m = size ? size[p] : n;
+  if (m <= 0 || (int)(blockIdx.x * blockDim.x) >= m) return;  // uniform per block
+  const double* din = dbase + (size_t)p * strideV;
+  const double* ein = ebase + (size_t)p * strideV;
+  const double* ws = wslot + (size_t)p * n;
+  const double eps = DBL_EPSILON * 0.5;
+  {
+    // nothing to do for a block of slots none of which lies in a tight cluster (a
+    // conservative test on the neighbouring slots, the tridiagonal's 1-norm bounded by
+    // 3 max(|d|, |e|) from a block-wide maximum)
+    const int jj = blockIdx.x * blockDim.x + threadIdx.x;
+    if (jj < m) mdone[(size_t)p * n + jj] = 0;  // kernel 2 reads every slot's flag
+    double am = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) am = fmax(am, fmax(fabs(din[i]), i < m - 1 ? fabs(ein[i]) : 0.0));
+    __shared__ double s_am;
+    if (threadIdx.x == 0) s_am = 0.0;
+    __syncthreads();
+    atomicMax((unsigned long long*)&s_am, (unsigned long long)__double_as_longlong(am));  // am >= 0
+    __syncthreads();
+    const double tb = TIGHT * 3.0 * s_am;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) w[i] = ws[i];
+    __syncthreads();
+    // only the members of big tight clusters (more than BIG members, the ones kernel 3 would
+    // re-orthogonalise at O(k^2 n)); smaller clusters are cheap by inverse iteration
+    bool big = false;
+    if (jj < m) {
+      int c = 1;
+      for (int t = jj; t > 0 && c <= BIG && fabs(w[t] - w[t - 1]) < tb; --t) ++c;
+      for (int t = jj; t < m - 1 && c <= BIG && fabs(w[t + 1] - w[t]) < tb; ++t) ++c;
+      big = c > BIG;
+    }
+    if (!__syncthreads_or(big)) return;
+  }
+  if (threadIdx.x == 0) {
+    // split (as kernel 1), max |T| for the shift margins
+    double tn = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double r = (i > 0 ? fabs(ein[i - 1]) : 0.0) + (i < m - 1 ? fabs(ein[i]) : 0.0);
+      tn = fmax(tn, fabs(din[i]) + r);
+    }
+    tn = fmax(tn, DBL_MIN);
+    s_tn = tn;
+    int b0 = 0;
+    for (int i = 0; i < m; ++i) {
+      bst[i] = b0;
+      bool cut = i == m - 1;
+      if (!cut) {
+        const double ei = ein[i];
+        cut = ei * ei <= eps * eps * fabs(din[i] * din[i + 1]) + DBL_MIN;
+      }
+      if (cut) {
+        for (int k = b0; k <= i; ++k) ben[k] = i + 1;
+        b0 = i + 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // root representation per block: sigma just below the block's smallest eigenvalue (slot
+    // b0 holds it), D > 0 checked, the margin doubled until it holds
+    const double tn = s_tn;
+    for (int b0 = 0; b0 < m; b0 = ben[b0]) {
+      const int b1 = ben[b0];
+      double off = 32.0 * eps * tn;
+      bool ok = false;
+      double sg = 0.0;
+      for (int tr = 0; tr < 40 && !ok; ++tr, off *= 2.0) {
+        sg = w[b0] - off;
+        ok = true;
+        double dk = din[b0] - sg;
+        for (int k = b0; k < b1 - 1 && ok; ++k) {
+          if (!(dk > 0.0)) ok = false;
+          const double ek = ein[k];
+          const double lk = ek / dk;
+          D[k] = dk;
+          L[k] = lk;
+          dk = (din[k + 1] - sg) - lk * ek;
+        }
+        if (!(dk > 0.0)) ok = false;
+        D[b1 - 1] = dk;
+        L[b1 - 1] = 0.0;
+      }
+      for (int k = b0; k < b1; ++k) sig[k] = ok ? sg : NAN;  // NaN: no representation, inverse iteration
+    }
+  }
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const int nv = min(nvec ? nvec[p] : m, nvec_max);
+  const double wj = w[j];
+  int rk = 0;  // rank of slot j in the global ascending order (ties by slot), as kernel 2
+  for (int t = 0; t < m; ++t) {
+    const double wt = w[t];
+    rk += (wt < wj) || (wt == wj && t < j);
+  }
+  int* done = mdone + (size_t)p * n;
+  done[j] = 0;
+  if (rk >= nv) return;
+  const int b0 = bst[j], b1 = ben[j], bs = b1 - b0;
+  const double sg = sig[j];
+  if (bs == 1 || !(sg == sg)) return;  // singletons and blocks without a representation: kernel 2
+  const double mu0 = wj - sg;
+  const double gl = j > b0 ? wj - w[j - 1] : INFINITY, gr = j < b1 - 1 ? w[j + 1] - wj : INFINITY;
+  const double tn = s_tn;
+  // only members of big tight clusters (as above, now within the split block)
+  {
+    int c = 1;
+    for (int t = j; t > b0 && c <= BIG && w[t] - w[t - 1] < TIGHT * tn; --t) ++c;
+    for (int t = j; t < b1 - 1 && c <= BIG && w[t + 1] - w[t] < TIGHT * tn; ++t) ++c;
+    if (c <= BIG) return;
+  }
+  if (!(fmin(gl, gr) >= MR_MINRGP * mu0)) return;  // a relative cluster: kernel 2
+  const double pivmin = DBL_MIN * fmax(1.0, tn * tn);
+  // relative bisection of eigenvalue idx of the block, from the absolute bracket of kernel 1
+  const int idx = j - b0;
+  double lo = fmax(mu0 - 8.0 * eps * tn, 0.0), hi = mu0 + 8.0 * eps * tn;
+  if (!(mr_negcount(D, L, b0, b1, lo, pivmin) <= idx && mr_negcount(D, L, b0, b1, hi, pivmin) > idx)) {
+    lo = 0.0;
+    hi = 2.0 * tn + fabs(sg) + 4.0 * eps * tn;
+  }
+  for (int it = 0; it < 160; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (hi - lo <= 4.0 * eps * hi || mid <= lo || mid >= hi) break;
+    if (mr_negcount(D, L, b0, b1, mid, pivmin) > idx) hi = mid;
+    else lo = mid;
+  }
+  const double mu = 0.5 * (lo + hi);
+  // twisted factorization at mu: forward (stationary) multipliers Lp and s, backward
+  // (progressive) multipliers Um with gamma_k = s_k + p_k + mu on the way
+  double* scr = scratch + (size_t)p * NARR * n * n;
+  const size_t nn = (size_t)n * n;
+  double* Lp = scr + 0 * nn;
+  double* Sa = scr + 1 * nn;
+  double* Um = scr + 2 * nn;
+  double* Xz = scr + 3 * nn;
+#define AT(arr, i) arr[(size_t)(i) * n + j]
+  double sv = -mu;
+  for (int k = b0; k < b1 - 1; ++k) {
+    AT(Sa, k) = sv;
+    double dp = D[k] + sv;
+    if (fabs(dp) < pivmin) dp = -pivmin;
+    const double lp = L[k] * D[k] / dp;
+    AT(Lp, k) = lp;
+    sv = lp * L[k] * sv - mu;
+  }
+  AT(Sa, b1 - 1) = sv;
+  double pv = D[b1 - 1] - mu;
+  double gbest = sv + pv + mu;
+  int r = b1 - 1;
+  for (int k = b1 - 2; k >= b0; --k) {
+    double dm = L[k] * L[k] * D[k] + pv;
+    if (fabs(dm) < pivmin) dm = -pivmin;
+    const double t = D[k] / dm;
+    AT(Um, k) = L[k] * t;
+    pv = pv * t - mu;
+    const double g = AT(Sa, k) + pv + mu;
+    if (fabs(g) < fabs(gbest)) {
+      gbest = g;
+      r = k;
+    }
+  }
+  // z from the twist index outwards; the running magnitude is kept finite by rescaling
+  AT(Xz, r) = 1.0;
+  double zk = 1.0;
+  for (int k = r - 1; k >= b0; --k) {
+    zk = -AT(Lp, k) * zk;
+    if (fabs(zk) > 0x1p500) {
+      for (int q = k + 1; q <= r; ++q) AT(Xz, q) *= 0x1p-500;
+      zk *= 0x1p-500;
+    }
+    AT(Xz, k) = zk;
+  }
+  double scale_up = 1.0;  // factor applied to [b0, r] by rescales of the lower part
+  zk = 1.0;
+  for (int k = r; k < b1 - 1; ++k) {
+    zk = -AT(Um, k) * zk;
+    if (fabs(zk) > 0x1p500) {
+      for (int q = r + 1; q <= k; ++q) AT(Xz, q) *= 0x1p-500;
+      scale_up *= 0x1p-500;
+      zk *= 0x1p-500;
+    }
+    AT(Xz, k + 1) = zk;
+  }
+  if (scale_up != 1.0)
+    for (int q = b0; q <= r; ++q) AT(Xz, q) *= scale_up;
+  double nrm2 = 0.0, big = 0.0;
+  int jmax = b0;
+  for (int i = b0; i < b1; ++i) {
+    const double a = AT(Xz, i);
+    nrm2 = fma(a, a, nrm2);
+    if (fabs(a) > big) {
+      big = fabs(a);
+      jmax = i;
+    }
+  }
+  if (!(nrm2 > 0.0 && nrm2 <= DBL_MAX)) return;  // no usable vector: kernel 2
+  double sc = 1.0 / sqrt(nrm2);
+  if (AT(Xz, jmax) < 0.0) sc = -sc;
+  double* zc = Zbase + (size_t)p * strideZ + (size_t)rk * ldz;
+  for (int i = 0; i < m; ++i) zc[i] = (i >= b0 && i < b1) ? AT(Xz, i) * sc : 0.0;
+#undef AT
+  done[j] = 1;
+}
 }  // namespace
 
 // scratch: NARR n^2 doubles per problem, the eigenvalue slots (n per problem), and the
@@ -841,12 +1117,13 @@ static int big_capacity(int n, int nprob) { return nprob * (n / (BIG + 1) + 1); 
 size_t stein_scratch_doubles(int n, int nprob) {
   // the bisection queue (5 n + 1 doubles per problem, + 1) fits in the first NARR n^2 per
   // problem for n >= 2; the pad covers n = 1
-  return (size_t)NARR * n * n * nprob + (size_t)n * nprob + (3 * (size_t)big_capacity(n, nprob) + 2) / 2 + 1 + nprob + 2;
+  return (size_t)NARR * n * n * nprob + (size_t)n * nprob + (3 * (size_t)big_capacity(n, nprob) + 2) / 2 + 1 +
+         ((size_t)n * nprob + 1) / 2 + 1 + nprob + 2;
 }
 
 cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d, const double* e, long long strideV,
                          double* w, double* Z, int ld, long long strideZ, double* scratch, int32_t* status,
-                         const int32_t* nvec, int nvec_max, int maxits, cudaStream_t st) {
+                         const int32_t* nvec, int nvec_max, int maxits, int mrrr, cudaStream_t st) {
   double* wslot = scratch + (size_t)NARR * n * n * nprob;
   const size_t smem1 = sizeof(double) * 3 * (size_t)n + sizeof(float) * 2 * (size_t)n + sizeof(int) * 2 * (size_t)n;
   cudaError_t err = cudaFuncSetAttribute(stebz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
@@ -877,21 +1154,34 @@ cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d,
   const int bigcap = big_capacity(n, nprob);
   err = cudaMemsetAsync(biglist, 0, sizeof(int), st);
   if (err != cudaSuccess) return err;
+  // kernel 0 (MRRR vectors where the representation separates the eigenvalues), when asked
+  int* mdone = nullptr;
+  if (mrrr) {
+    mdone = biglist + 1 + 3 * (size_t)bigcap + 1;  // n ints per problem after the cluster list
+    const size_t smem0 = sizeof(double) * 4 * (size_t)n + sizeof(int) * 2 * (size_t)n;
+    err = cudaFuncSetAttribute(mrrr_vec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem0);
+    if (err != cudaSuccess) return err;
+    dim3 grid0((n + MR_THREADS - 1) / MR_THREADS, nprob);
+    mrrr_vec_kernel<<<grid0, MR_THREADS, smem0, st>>>(n, size, d, e, strideV, wslot, Z, ld, strideZ, scratch, mdone,
+                                                       nvec, nvec_max);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
   const size_t smem2 = sizeof(double) * 4 * (size_t)n + sizeof(int) * 2 * (size_t)n;
   err = cudaFuncSetAttribute(stein_vec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
   if (err != cudaSuccess) return err;
   stein_vec_kernel<<<grid, ST_THREADS, smem2, st>>>(n, size, d, e, strideV, wslot, w, Z, ld, strideZ, scratch, status,
-                                                    biglist, bigcap, nvec, nvec_max, maxits);
+                                                    biglist, bigcap, nvec, nvec_max, maxits, mdone);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   // kernel 3: a grid that stays resident; blocks without a listed cluster exit at once
-  const size_t smem3 = sizeof(double) * 5 * (size_t)n + sizeof(int) * 3 * (size_t)n;
+  const size_t smem3 = sizeof(double) * 5 * (size_t)n + sizeof(int) * 4 * (size_t)n;
   err = cudaFuncSetAttribute(stein_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3);
   if (err != cudaSuccess) return err;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   stein_cluster_kernel<<<sms, SC_THREADS, smem3, st>>>(n, size, d, e, strideV, wslot, Z, ld, strideZ, scratch, status,
-                                                       biglist, bigcap, nvec, nvec_max, maxits);
+                                                       biglist, bigcap, nvec, nvec_max, maxits, mdone);
   return cudaGetLastError();
 }

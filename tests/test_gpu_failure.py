@@ -139,12 +139,12 @@ def test_config_range_checks():
     from paper_1402_4247_gb300.nao import NaoError, nao_config_defaults
     d = nao_config_defaults()
     assert d["inverse_iteration_max"] == 5 and d["f_min"] == 1e-16 and d["tc_wait_cycles"] == 4_000_000_000
-    assert d["mixed_planes"] == 6
+    assert d["mixed_planes"] == 6 and d["overlap_mrrr"] == 1
     with pytest.raises(NaoError):
         _ctx(config={"inverse_iteration_max": -1})
     ctx = _ctx()
     for bad in ({"f_min": 0.5}, {"tc_wait_cycles": 0}, {"inverse_iteration_max": 65}, {"mixed_planes": 4},
-                {"mixed_planes": 10}):
+                {"mixed_planes": 10}, {"overlap_mrrr": 2}):
         with pytest.raises(NaoError):
             ctx.nao_set_config(**bad)
     assert ctx.nao_get_config() == d

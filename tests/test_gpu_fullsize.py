@@ -193,6 +193,34 @@ def test_large_basis_n1000(ctx, ill):
     assert be.max() <= 10 * be_x.max(), (be.max(), be_x.max())
 
 
+def test_ill_conditioned_overlap_mrrr_and_inverse_iteration_agree():
+    """The big near-null cluster of the ill-conditioned overlap (n = 1000, ~670 eigenvalues
+    within 1e-7 |T| of each other) through both eigenvector routes of the overlap's tridiagonal
+    (Eigen_HH step 2 of Part 2): the relatively robust representation (default) and inverse
+    iteration with Gram-Schmidt (dstevx's method).  Both must reproduce the oracle's cut count
+    and eigenvalues within 10x the oracle's own distance from a third route, and agree with
+    each other to that bound."""
+    from paper_1402_4247_gb300.nao import Context
+    inp = synth.scaled_cell(1000, kgrid=(1, 1, 1), nspin=1, ill_conditioned=True)
+    ref = oracle.band_step(inp.HR, inp.SR, inp.R, inp.kpts, inp.wk, inp.n_electrons, inp.kT, problems=[0])
+    H, S = ref["Hk"][0, 0], ref["Sk"][0]
+    ws, U = np.linalg.eigh(S)
+    keep = ws >= 1e-10
+    X = U[:, keep] / np.sqrt(ws[keep])
+    e_lib = np.linalg.eigvalsh(X.conj().T @ H @ X)
+    bound = max(1e-10 * np.abs(e_lib).max(), 10 * np.abs(ref["eps"][0] - e_lib).max())
+    got = {}
+    for mr in (1, 0):
+        c = Context(0, config={"overlap_mrrr": mr})
+        g = gpu_band_step(c, inp, torch, DEV, density=False)
+        c.close()
+        assert int(g["status"][0]) == 0
+        assert int(g["m"][0]) == ref["m"][0] == int(keep.sum())
+        got[mr] = g["eps"][0][: ref["m"][0]]
+        assert np.abs(got[mr] - ref["eps"][0]).max() <= bound, (mr, np.abs(got[mr] - ref["eps"][0]).max(), bound)
+    assert np.abs(got[1] - got[0]).max() <= bound
+
+
 @pytest.mark.parametrize("n", [2900, 3300], ids=["n2900-digit-panel", "n3300-fp64-panel"])
 def test_large_order_launch_limits(ctx, n):
     """Orders near the shared-memory limits of the Householder panel: n = 2900 keeps the
