@@ -237,7 +237,17 @@ def _load_traffic(stage, units_per_launch):
         return None
 
 
-def run_serve(local_rank, n_requests=48, seed=5):
+def run_serve_stated(local_rank, n_requests=12, seed=5, ncells=4):
+    """The serving workload at its stated distribution, on a bounded sample: n log-uniform in
+    [200, 4000] (four seeded cells of the same generator, n rounded to a multiple of 50, 27
+    images so that a request's real-space inputs stay a few GB), 1-32 mirrored random
+    k-points, 1 or 2 spins, FP64 or mixed; offline capacity first, then Poisson arrivals at
+    0.7x that rate; latencies from submit to finished on the GPU."""
+    return run_serve(local_rank, n_requests=n_requests, seed=seed, ncells=ncells, n_range=(200, 4000), nk_max=32,
+                     stated=True)
+
+
+def run_serve(local_rank, n_requests=48, seed=5, ncells=6, n_range=(128, 768), nk_max=8, stated=False):
     """Serving stream (a scaled-down form of the serving workload: fewer requests, n up to 768):
     cells with n log-uniform in [128, 768], 1-8 random k-points mirrored to +-k (Gamma added
     when odd), 1 or 2 spins, FP64 or mixed precision.  First the offline capacity (all
@@ -250,14 +260,18 @@ def run_serve(local_rank, n_requests=48, seed=5):
 
     rng = np.random.default_rng(seed)
     cells = []
-    for i in range(6):
-        nt = float(np.exp(rng.uniform(np.log(128), np.log(768))))
-        h, l = max(1, round(nt / 25)), max(1, round(3 * nt / 50))
-        cells.append(synth.small_cell(500 + i, h, l, kgrid=(1, 1, 1), nspin=2))
+    for i in range(ncells):
+        nt = float(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1]))))
+        if stated:
+            cells.append(synth.scaled_cell(max(50, int(round(nt / 50.0)) * 50), seed=600 + i, kgrid=(1, 1, 1), nspin=2,
+                                           ill_conditioned=False, image_radius=1))
+        else:
+            h, l = max(1, round(nt / 25)), max(1, round(3 * nt / 50))
+            cells.append(synth.small_cell(500 + i, h, l, kgrid=(1, 1, 1), nspin=2))
     reqs = []
     for _ in range(n_requests):
         c = cells[int(rng.integers(len(cells)))]
-        nk = int(rng.integers(1, 9))
+        nk = int(rng.integers(1, nk_max + 1))
         half = rng.uniform(-0.5, 0.5, size=(nk // 2, 3))
         k = np.concatenate([half, -half] + ([np.zeros((1, 3))] if nk % 2 else []))
         nspin = int(rng.integers(1, 3))
@@ -309,9 +323,9 @@ def run_serve(local_rank, n_requests=48, seed=5):
         ctx.nao_serve_release(t)
     _, peak, _, _ = ctx.nao_serve_stats()
     ctx.close()
-    return {"workload": f"{n_requests} requests: n log-uniform in [128, 768] over 6 cells (n = "
-                        + ", ".join(str(c.n) for c in cells) + "), 1-8 mirrored random k-points, 1-2 spins, "
-                        "FP64 or mixed 50/50, Parts 1-6 each; 2 slots, batches up to 256 problems",
+    return {"workload": f"{n_requests} requests: n log-uniform in [{n_range[0]}, {n_range[1]}] over {ncells} cells (n = "
+                        + ", ".join(str(c.n) for c in cells) + f", {cells[0].nR} images), 1-{nk_max} mirrored random "
+                        "k-points, 1-2 spins, FP64 or mixed 50/50, Parts 1-6 each; 2 slots, batches up to 256 problems",
             "requests": n_requests, "capacity_req_per_s": cap,
             "solves_per_s_offline": sum(q["nprob"] for q in reqs) / t_off,
             "rate_req_per_s": rate, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
@@ -702,6 +716,7 @@ def run_ours(args, rank, world, local_rank):
               "status_ok": bool(int(st.abs().sum()) == 0 and int(rst[0]) == 0)}
 
     serve = run_serve(local_rank) if (world == 1 and not args.no_serve) else None
+    serve_stated = run_serve_stated(local_rank) if (world == 1 and not args.no_serve and not args.quick) else None
     mixed_n2000 = run_mixed_n2000(local_rank) if (world == 1 and not args.quick) else None
     large_basis = run_large_basis(local_rank) if (world == 1 and not args.quick) else None
 
@@ -770,7 +785,7 @@ def run_ours(args, rank, world, local_rank):
             "e2e": {"value": nprob * world / (e2e_max * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu, "mixed": mixed, "subset": subset, "serve": serve,
-            "mixed_n2000": mixed_n2000, "large_basis": large_basis,
+            "mixed_n2000": mixed_n2000, "large_basis": large_basis, "serve_stated": serve_stated,
             "status_ok": bool(int(st.abs().sum()) == 0 and int(rst[0]) == 0),
         }
         print(json.dumps(line), flush=True)
