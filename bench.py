@@ -465,7 +465,7 @@ def run_mixed_n2000(local_rank, steps=2, warmup=1):
     return res
 
 
-def run_large_basis(local_rank, sizes=(1000, 2000, 3000), steps=2, warmup=1):
+def run_large_basis(local_rank, sizes=(1000, 2000, 3000), steps=1, warmup=0):
     """The large-basis FP64 sweep: n in {1000, 2000, 3000}, 4x4x1 k, one spin, seed 3, overlap
     condition ~1e8 plus one orbital in 50 duplicated (exact null directions; m = n - n/50).
     Per size: solves/s of the band step (Parts 1-6) and its per-stage split; the Householder
