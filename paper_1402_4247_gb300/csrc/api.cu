@@ -228,7 +228,7 @@ GenEigPlan plan_gen_eig(int n, int nprob, int nSe, bool use_tc) {
   W.oG2 = P.take<z64>((size_t)NAO_WY_NB * NAO_WY_NB * nmax * nblk);
   W.oT2 = P.take<z64>((size_t)NAO_WY_NB * NAO_WY_NB * nmax * nblk);
   W.oW = P.take<z64>((size_t)NAO_WY_NB * n * nmax);
-  W.oW2 = P.take<z64>((size_t)NAO_WY_NB * n * nmax);
+  W.oW2 = P.take<z64>((size_t)n * ncolv * nmax);  // V_j T_j of all blocks
   W.oVW = P.take<z64>((size_t)2 * 3 * NAO_HT_NB * n * nmax);  // column-major + row-major copies
   // 8-bit digit planes of the Householder trailing matrix (tensor-core product method)
   W.oDig = P.take<char>(use_tc ? hetrd_digits_bytes(n, nmax, NAO_HT_DIGITS_FP64) : 16);
@@ -269,12 +269,14 @@ DensityPlan plan_density(int n, int nspin, int nk, int nR, int nb, int num_sms, 
 // Eigen_HH steps 3-4 in blocked form: U(:, c) = Q Z(:, m - nc + c) for c < nc (nc = ncols[p];
 // Z(:, c) when lowest),
 // normalised (times 1/sqrt(w) when use_rsqrt), with Q = prod_j (I - V_j T_j V_j^H) applied from
-// the last block of NAO_WY_NB reflectors to the first; every block costs three products
-// (W = V^H U, W = T W, U -= V W).  The Gram matrices V_j^H V_j of all blocks come first and
-// all T_j are built in one launch (they do not depend on U), so that launch fills the GPU.
+// the last block of NAO_WY_NB reflectors to the first.  Nothing about V_j and T_j depends on
+// U, so the Gram matrices V_j^H V_j of all blocks come first, then all T_j in one launch,
+// then the products VT_j = V_j T_j; each block then costs two products on the chain through
+// U: W = V_j^H U and U -= VT_j W.  VT: [nprob][ncolv][n] (column-major like Vf, block j in
+// columns j nb ..).
 cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, const int32_t* ncols, const z64* A,
                                   const z64* tau, const double* Z, const double* w, int use_rsqrt, z64* U, z64* Vf,
-                                  z64* tauc, z64* G, z64* T, z64* W, z64* W2, void* ozws, cudaStream_t st,
+                                  z64* tauc, z64* G, z64* T, z64* W, z64* VT, void* ozws, cudaStream_t st,
                                   int digits, int lowest) {
   const int nb = NAO_WY_NB;
   const int ncolv = (n + nb - 1) / nb * nb;
@@ -302,22 +304,26 @@ cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t*
     e = launch_build_t(nb, nprob, nblk, G, tauc, ncolv, T, st);
     if (e != cudaSuccess) return e;
   }
+  for (int j = 0; j < nblk; ++j) {  // VT_j = V_j T_j (rows x nb; T_j upper triangular, row-major)
+    const int R0 = j * nb + 1, rows = n - R0;
+    GemmDims dv{rows, nb, nb, nullptr, nullptr, nullptr, 0};
+    e = run_zgemm(ctx, "backtransform", nprob, dv, 1.0, GemmOperand{Vf + R0 + (size_t)j * nb * n, svf, 1, n, 0, nullptr},
+                  GemmOperand{T + (size_t)j * nprob * snb2, snb2, nb, 1, 0, nullptr}, 0.0,
+                  VT + R0 + (size_t)j * nb * n, svf, 1, n, ozws, st, digits);
+    if (e != cudaSuccess) return e;
+  }
   for (int j = nblk - 1; j >= 0; --j) {
     const int R0 = j * nb + 1, rows = n - R0;
     if (rows <= 0) continue;
     const z64* Vj = Vf + R0 + (size_t)j * nb * n;
-    const z64* Tj = T + (size_t)j * nprob * snb2;
+    const z64* VTj = VT + R0 + (size_t)j * nb * n;
     GemmDims dw{nb, n, rows, nullptr, ncols, nullptr, 0};
     e = run_zgemm(ctx, "backtransform", nprob, dw, 1.0, GemmOperand{Vj, svf, n, 1, 1, nullptr},
                   GemmOperand{U + R0, snn, 1, n, 0, nullptr}, 0.0, W, snbn, n, 1, ozws, st, digits);
     if (e != cudaSuccess) return e;
-    GemmDims dt{nb, n, nb, nullptr, ncols, nullptr, 0};
-    e = run_zgemm(ctx, "backtransform", nprob, dt, 1.0, GemmOperand{Tj, snb2, nb, 1, 0, nullptr},
-                  GemmOperand{W, snbn, n, 1, 0, nullptr}, 0.0, W2, snbn, n, 1, ozws, st, digits);
-    if (e != cudaSuccess) return e;
     GemmDims du{rows, n, nb, nullptr, ncols, nullptr, 0};
-    e = run_zgemm(ctx, "backtransform", nprob, du, -1.0, GemmOperand{Vj, svf, 1, n, 0, nullptr},
-                  GemmOperand{W2, snbn, n, 1, 0, nullptr}, 1.0, U + R0, snn, 1, n, ozws, st, digits);
+    e = run_zgemm(ctx, "backtransform", nprob, du, -1.0, GemmOperand{VTj, svf, 1, n, 0, nullptr},
+                  GemmOperand{W, snbn, n, 1, 0, nullptr}, 1.0, U + R0, snn, 1, n, ozws, st, digits);
     if (e != cudaSuccess) return e;
   }
   NaoStage stage_(ctx, "backtransform", st, 1);
@@ -654,7 +660,7 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
           *stH = (int32_t*)(ws + W.ostH);
   void* ozws = use_tc ? (void*)(ws + W.oOz) : nullptr;
   z64 *Vf = (z64*)(ws + W.oVf), *tauc = (z64*)(ws + W.oTc), *Gw = (z64*)(ws + W.oG2), *Tw = (z64*)(ws + W.oT2),
-      *Ww = (z64*)(ws + W.oW), *W2w = (z64*)(ws + W.oW2), *VWp = (z64*)(ws + W.oVW);
+      *Ww = (z64*)(ws + W.oW), *VTw = (z64*)(ws + W.oW2), *VWp = (z64*)(ws + W.oVW);
   void* digp = use_tc ? (void*)(ws + W.oDig) : nullptr;
   int* erowp = (int*)(ws + W.oErow);
   const long long snn = (long long)nn;
@@ -681,7 +687,7 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
     Zo = ns_correct(ctx, n, nSe, nullptr, nullptr, Z, G, Z2, ozws, st, &e);
     NAO_CUDA_TRY(ctx, e);
   }
-  NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nSe, nullptr, mS, AS, tauS, Zo, wS, 1, X, Vf, tauc, Gw, Tw, Ww, W2w,
+  NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nSe, nullptr, mS, AS, tauS, Zo, wS, 1, X, Vf, tauc, Gw, Tw, Ww, VTw,
                                           ozws, st, dig, 0));
   {
     NaoStage stage_(ctx, "misc", st, 1);
@@ -721,7 +727,7 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
       Zo = ns_correct(ctx, n, nprob, mP, nvP, Z, G, Z2, ozws, st, &e);
       NAO_CUDA_TRY(ctx, e);
     }
-    NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nprob, mP, nvP, Hp, tauH, Zo, wH, 0, V, Vf, tauc, Gw, Tw, Ww, W2w,
+    NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nprob, mP, nvP, Hp, tauH, Zo, wH, 0, V, Vf, tauc, Gw, Tw, Ww, VTw,
                                             ozws, st, dig, 1));
   }
   if (mixed && ctx->refine_sweeps >= 0) {

@@ -1,7 +1,7 @@
 // Eigen_HH steps 3-4 (Sec. 3: "rearrangement of eigenvectors" and "normalization") and the
 // small element-wise steps around them.  The eigenvectors of A are U = Q Z with
 // Q = H_0 H_1 ... H_{m-2} from the tridiagonalization; Q is applied in compact WY blocks
-// (Q_j = I - V_j T_j V_j^H, three tensor-core products per block issued by the caller), then
+// (Q_j = I - V_j T_j V_j^H: W = V_j^H U, then U -= (V_j T_j) W, products issued by the caller), then
 // the columns are scaled to unit 2-norm.  For the overlap matrix the normalization also
 // applies Part 2's canonical orthogonalization X = U_m diag(s_m^{-1/2}).
 #include "nao_internal.cuh"
@@ -119,8 +119,8 @@ cudaError_t launch_scale_cols_sqrt(int n, int nprob, int nb, const z64* C, const
 
 // ---------------------------------------------------------------------------------------
 // Blocked form of steps 3-4 (compact WY): Q = Q_0 Q_1 ... with Q_j = H_{j nb} ... H_{j nb+nb-1}
-// = I - V_j T_j V_j^H, applied as three matrix products per block (run on the tensor
-// cores by the caller).  The kernels below prepare the operands.
+// = I - V_j T_j V_j^H, applied as two matrix products per block with V_j T_j formed once (run
+// on the tensor cores by the caller).  The kernels below prepare the operands.
 // ---------------------------------------------------------------------------------------
 namespace {
 

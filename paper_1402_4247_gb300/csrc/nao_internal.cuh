@@ -251,8 +251,11 @@ cudaError_t launch_ns_correct(int n, int nprob, const int32_t* size, const int32
 // bytes; err: the context's dev_flags (err[NAO_FLAG_TIMEOUT] set to 1 if a bounded wait
 // expired; the bound is the long long at err + NAO_FLAG_WAIT).  digits: base-64 planes per
 // operand: NAO_OZ_DIGITS_FP64 (ten planes, 60 bits: FP64 accuracy, 55 tensor-core products),
-// or 5, 6, 7 (30, 36, 42 bits: 15, 21, 28 products) for terms that tolerate less.
+// or 5, 6, 7 (30, 36, 42 bits: 15, 21, 28 products) for terms that tolerate less, or
+// NAO_OZ_DIGITS_B128: nine base-128 planes (63 bits, 45 products in 17 MMAs per K step
+// instead of 27-31), FP64 accuracy for short contractions (chunks of 256, 512 real).
 constexpr int NAO_OZ_DIGITS_FP64 = 10;
+constexpr int NAO_OZ_DIGITS_B128 = 9;
 constexpr int NAO_OZ_DIGITS_NS = 5;   // the Newton-Schulz correction term (~1e-9 of Z)
 // the mixed mode's products take nao_config.mixed_planes (5, 6 or 7) planes
 bool zgemm_oz_supported(GemmDims dims);

@@ -72,14 +72,14 @@ __device__ __forceinline__ int oz_tile_off(int row, int k) {
 // biased exponent field of x (0 for zero / subnormal)
 __device__ __forceinline__ int exp_field(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7ff); }
 
-// q = round(x * 2^{6 S - e}) for |x| < 2^e, by integer arithmetic on the bits of x
-template <int S>
+// q = round(x * 2^{DB S - e}) for |x| < 2^e (|q| < 2^63), by integer arithmetic on the bits of x
+template <int S, int DB>
 __device__ __forceinline__ long long oz_fixed(double x, int e) {
   const long long bits = __double_as_longlong(x);
   const int b = (int)((bits >> 52) & 0x7ff);
   if (b == 0) return 0;  // zero (subnormals are far below any row scale used here)
   long long m = (bits & 0xFFFFFFFFFFFFFll) | 0x10000000000000ll;  // 53-bit integer mantissa
-  const int sh = b - 1075 + 6 * S - e;                              // x 2^{6S-e} = m 2^{sh}
+  const int sh = b - 1075 + DB * S - e;                             // x 2^{DB S - e} = m 2^{sh}
   long long q;
   if (sh >= 0) q = m << sh;
   else if (sh <= -62) q = 0;
@@ -101,12 +101,38 @@ __device__ __forceinline__ long long oz_f32_fixed(float x, int k) {
   return b < 0 ? -q : q;
 }
 
-// S signed base-64 digits of q (|q| < 2^{6 S}): q = sum_s d_s 2^{6(S-s)}, the lower S - 1 in
-// [-32, 31] and |d_0| <= 64; formed from the least significant digit up in int32 arithmetic
-// on the two 30-bit halves of q (the carry left by the low half is 0 or 1)
-template <int S>
+// S signed base-2^DB digits of q (|q| < 2^{DB S}): q = sum_s d_s 2^{DB(S-1-s)}.
+// DB = 6: the lower S - 1 in [-32, 31] and |d_0| <= 64, formed from the least significant
+// digit up in int32 arithmetic on the two 30-bit halves of q (the carry left by the low half
+// is 0 or 1).  DB = 7 (S = 9, 63 bits): the lower eight in [-64, 63] and |d_0| <= 128, from
+// three 21-bit parts of q, each leaving a carry of 0 or 1 for the next.
+template <int S, int DB>
 __device__ __forceinline__ void oz_digits(long long q, int* d) {
-  if (S <= 5) {
+  if (DB == 7) {
+    static_assert(DB != 7 || S == 9, "base-128 digits come in nines");
+    int x = (int)(q & 0x1FFFFF), y = (int)((q >> 21) & 0x1FFFFF), z = (int)(q >> 42);
+#pragma unroll
+    for (int s = S - 1; s >= S - 3; --s) {
+      const int ds = ((x + 64) & 127) - 64;
+      d[s] = ds;
+      x = (x - ds) >> 7;
+    }
+    y += x;
+#pragma unroll
+    for (int s = S - 4; s >= S - 6; --s) {
+      const int ds = ((y + 64) & 127) - 64;
+      d[s] = ds;
+      y = (y - ds) >> 7;
+    }
+    z += y;
+#pragma unroll
+    for (int s = S - 7; s >= 1; --s) {
+      const int ds = ((z + 64) & 127) - 64;
+      d[s] = ds;
+      z = (z - ds) >> 7;
+    }
+    d[0] = z;
+  } else if (S <= 5) {
     int x = (int)q;
 #pragma unroll
     for (int s = S - 1; s >= 1; --s) {
@@ -147,17 +173,23 @@ __device__ __forceinline__ uint32_t oz_bf16_bits(int d, int k) {
 //                     complex: row 2j = (Re b_j ; -Im b_j), row 2j+1 = (Im b_j ; Re b_j)).
 // Plane layout (K-major tiles of TR = 128 (A) or 64 (B) rows x 16 K, bf16):
 //   planes[prob][s][row / TR][k' / 16][oz_tile_off(row % TR, k' % 16)].
+// Complex operands: K' = 2 Kh with Kh = round_up(K, 8); entries 0..K-1 hold the first
+// part (Re op(A); Re b or Im b), entries Kh..Kh+K-1 the second, the rest are zero, so that
+// both halves start on an 8-entry (16-byte) boundary.
 // A block of 256 threads owns 16 consecutive rows and walks all of K'.  Lane l of a warp
 // holds row (l & 7) + 8 (l >> 4) and the 8-element half (l >> 3) & 1 of a 16-wide K step, so
 // each of its 16-byte plane chunks is contiguous and a warp stores 512 contiguous bytes per
 // plane.  Pass 1 takes the row's largest exponent (the power-of-two row scale), pass 2 writes
-// the digits.  Complex rows 2j and 2j+1 of B see the same set of values, hence one scale.
-template <bool IS_B, bool REAL, int S>
+// the digits.  Complex rows 2j and 2j+1 of B see the same set of values, hence one scale;
+// their second halves repeat the first halves' values (Re b', and -Im b' = -(Im b')), so each
+// lane forms the digits of its own first half only and also stores them, negated where the
+// value is, as its partner row's second half.
+template <bool IS_B, bool REAL, int S, int DB>
 __global__ void __launch_bounds__(256) oz_split(int nprob, GemmDims dims, GemmOperand X, int Rp, int K2p,
                                                  __nv_bfloat16* __restrict__ planes, int* __restrict__ xexp) {
   constexpr int TR = IS_B ? OZ_BN : OZ_BM;            // rows per plane tile
   constexpr int TB = TR * OZ_BK * 2;                  // bytes per plane tile
-  constexpr int SCALE0 = IS_B ? 30 : 0;               // plane s holds d_s 2^{SCALE0 - 6 s}
+  constexpr int SCALE0 = IS_B ? 30 : 0;               // plane s holds d_s 2^{SCALE0 - DB s}
   const int p = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lr = (lane & 7) + 8 * (lane >> 4);
@@ -206,11 +238,52 @@ __global__ void __launch_bounds__(256) oz_split(int nprob, GemmDims dims, GemmOp
     }
   }
   // pass 2: digits of 8 consecutive K' entries per thread, one 16-byte store per plane
-  const int KK = REAL ? K : 2 * K;
+  const int Kh = REAL ? K2p : K2p / 2;  // start of the second half of K' (complex)
   const int nks = K2p / OZ_BK;
   const size_t plane_bytes = (size_t)(Rp / TR) * nks * TB;
-  unsigned char* base = (unsigned char*)planes + (size_t)p * S * plane_bytes +
-                        (size_t)(row / TR) * nks * TB + oz_tile_off(row % TR, kh * 8);
+  unsigned char* pl0 = (unsigned char*)planes + (size_t)p * S * plane_bytes;
+  if (IS_B && !REAL) {
+    // 8-groups g of the first half: own row at K' = 8 g, the partner row (same complex
+    // column, other part) at K' = Kh + 8 g; both rows lie in the same plane tile
+    const int ng = Kh / 8;
+    const int prow = row ^ 1;
+    unsigned char* rb0 = pl0 + (size_t)(row / TR) * nks * TB;
+    const bool cj = X.conj != 0;
+    // lane h = 0: Re b' = Re b to both rows; h = 1: Im b' = (cj ? -1 : 1) Im b to its own row
+    // and its negation to the partner's second half
+    const bool neg = h == 1 && cj;
+    const uint32_t pflip = h == 1 ? 0x80008000u : 0u;  // bf16 sign bits (a zero becomes -0)
+    for (int g = 2 * warp + kh; g < ng; g += 16) {
+      uint32_t pk[S][4];
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2) pk[s2][0] = pk[s2][1] = pk[s2][2] = pk[s2][3] = 0u;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = 8 * g + e;
+        double v = 0.0;
+        if (live && k < K) {
+          const z64 z = ((const z64*)xb)[at(k)];
+          v = h ? z.y : z.x;
+        }
+        const long long q = oz_fixed<S, DB>(v, ex);
+        int d[S];
+        oz_digits<S, DB>(neg ? -q : q, d);
+#pragma unroll
+        for (int s2 = 0; s2 < S; ++s2) pk[s2][e >> 1] |= oz_bf16_bits(d[s2], SCALE0 - DB * s2) << (16 * (e & 1));
+      }
+      const int g2 = ng + g;
+      unsigned char* own = rb0 + (size_t)(g >> 1) * TB + oz_tile_off(row % TR, (g & 1) * 8);
+      unsigned char* par = rb0 + (size_t)(g2 >> 1) * TB + oz_tile_off(prow % TR, (g2 & 1) * 8);
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2) {
+        *(uint4*)(own + (size_t)s2 * plane_bytes) = make_uint4(pk[s2][0], pk[s2][1], pk[s2][2], pk[s2][3]);
+        *(uint4*)(par + (size_t)s2 * plane_bytes) =
+            make_uint4(pk[s2][0] ^ pflip, pk[s2][1] ^ pflip, pk[s2][2] ^ pflip, pk[s2][3] ^ pflip);
+      }
+    }
+    return;
+  }
+  unsigned char* base = pl0 + (size_t)(row / TR) * nks * TB + oz_tile_off(row % TR, kh * 8);
   for (int c = warp; c < nks; c += 8) {
     uint32_t pk[S][4];
 #pragma unroll
@@ -220,30 +293,22 @@ __global__ void __launch_bounds__(256) oz_split(int nprob, GemmDims dims, GemmOp
       const int kk = c * OZ_BK + kh * 8 + e;
       double v = 0.0;
       bool neg = false;  // negations are applied to the exact integer, not as FP64 instructions
-      if (live && kk < KK) {
-        if (REAL) {
-          v = ((const double*)xb)[at(kk)];
-        } else {
-          const bool hi = kk >= K;
-          const z64 z = ((const z64*)xb)[at(hi ? kk - K : kk)];
-          const bool cj = X.conj != 0;  // conj: Im z enters with the opposite sign
-          if (!IS_B) {                  // [Re | Im]
-            v = hi ? z.y : z.x;
-            neg = hi && cj;
-          } else if (h == 0) {          // (Re b ; -Im b)
-            v = hi ? z.y : z.x;
-            neg = hi && !cj;
-          } else {                      // (Im b ; Re b)
-            v = hi ? z.x : z.y;
-            neg = !hi && cj;
-          }
+      if (REAL) {
+        if (live && kk < K) v = ((const double*)xb)[at(kk)];
+      } else {  // A' = [Re op(A) | Im op(A)], the second half from K' = Kh on
+        const bool hi = kk >= Kh;
+        const int k = hi ? kk - Kh : kk;
+        if (live && k < K) {
+          const z64 z = ((const z64*)xb)[at(k)];
+          v = hi ? z.y : z.x;
+          neg = hi && X.conj != 0;  // conj: Im z enters with the opposite sign
         }
       }
-      const long long q = oz_fixed<S>(v, ex);
+      const long long q = oz_fixed<S, DB>(v, ex);
       int d[S];
-      oz_digits<S>(neg ? -q : q, d);
+      oz_digits<S, DB>(neg ? -q : q, d);
 #pragma unroll
-      for (int s = 0; s < S; ++s) pk[s][e >> 1] |= oz_bf16_bits(d[s], SCALE0 - 6 * s) << (16 * (e & 1));
+      for (int s = 0; s < S; ++s) pk[s][e >> 1] |= oz_bf16_bits(d[s], SCALE0 - DB * s) << (16 * (e & 1));
     }
 #pragma unroll
     for (int s = 0; s < S; ++s)
@@ -298,22 +363,27 @@ __device__ __forceinline__ void oz_bulk_copy(void* dst_smem, const void* src_gme
 //   warp 0 / lane 0 (producer): waits until a stage is free (its "empty" barrier, arrived
 //     by the MMA commit), then loads it with 20 bulk copies (cp.async.bulk, the 1-D TMA)
 //     that complete on the stage's "full" barrier;
-//   warp 1 / lane 0 (MMA issuer): waits for a full stage, issues the 37 MMAs (55 digit products), commits them
+//   warp 1 / lane 0 (MMA issuer): waits for a full stage, issues the MMAs of its digit products, commits them
 //     to the stage's empty barrier, and after the last stage to the "done" barrier;
 //   all 8 warps: wait for "done", then run the epilogue from TMEM.
-template <bool REAL, int S, int BN, int NST>
+template <bool REAL, int S, int DB, int BN, int NST>
 __global__ void __launch_bounds__(OZ_THREADS, BN == OZ_BN ? 1 : 2)
 oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_bfloat16* __restrict__ Ap,
                const __nv_bfloat16* __restrict__ Bp, const int* __restrict__ rexp, const int* __restrict__ cexp, int Mp,
                int N2p, int K2p, void* __restrict__ Cv, long long Cbs, long long Crs, long long Ccs, int* __restrict__ err) {
-  // exact FP32 groups g = 2 .. NEX+1, one TMEM accumulator each; groups above 8 share one
-  constexpr int NEX = (S + 1 <= 8) ? S : 7;
-  constexpr bool MERGED = S + 1 > 8;
-  constexpr int NACC = NEX + (MERGED ? 1 : 0);
+  // Accumulator a holds the digit group s + t = a (0-based; G_a = n_a 2^{30 - DB a}), the last
+  // one also every group beyond it (MERGED).  The first NEX accumulators are combined exactly
+  // (their FP32 sums are exact integers: DB = 6 while 2K' <= 1792, DB = 7 while K' <= 512);
+  // the rest lie at least 2^-35 below the first group and enter rounded.
+  constexpr int NACC = S < 8 ? S : 8;
+  constexpr bool MERGED = S > NACC;
+  constexpr int NEX = DB == 7 ? 6 : (MERGED ? NACC - 1 : NACC);
   constexpr int TMEM_COLS = NACC * BN <= 128 ? 128 : (NACC * BN <= 256 ? 256 : 512);
   constexpr int TILE_B = BN * OZ_BK * 2;              // bytes of one B tile in shared memory
   constexpr int STAGE = S * (OZ_TILE_A + TILE_B);     // bytes per pipeline stage
-  constexpr int kUnitExp = 36 - 6 * NEX;              // one unit of the last exact group is 2^kUnitExp
+  constexpr int kUnitExp = DB * (NEX - 1) - 30;       // an accumulator's value in units of the last exact
+                                                      // group: v 2^kUnitExp
+  constexpr int kExp = -DB * (NEX + 1);               // the output is t 2^{e_i + f_j + kExp}
   extern __shared__ __align__(1024) unsigned char oz_smem[];
   __shared__ uint64_t full_bar[NST], empty_bar[NST], done_bar;
   __shared__ uint32_t tbase;
@@ -330,9 +400,17 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
   if (dims.lower && cb * CPT > rb * OZ_BM + OZ_BM - 1) return;
   unsigned char* stage0 = (unsigned char*)(((uintptr_t)oz_smem + 1023) & ~(uintptr_t)1023);
   const int nks = K2p / OZ_BK;  // plane layout (all problems)
-  // this problem's digit planes are zero beyond column 2 K_p (K_p when real): stop the K loop there
+  // this problem's digit planes hold data in the K steps [0, s1) and (complex) [s2a, s2b), the
+  // second half K2p / 2 .. K2p / 2 + K_p; the loop runs over those steps only (one range when
+  // they meet, as for K_p = K)
   const int Kprob = gemm_k(dims, p);
-  const int nks_p = max(1, min(nks, ((REAL ? 1 : 2) * Kprob + OZ_BK - 1) / OZ_BK));
+  int s1 = min(nks, (Kprob + OZ_BK - 1) / OZ_BK), s2a = s1, s2b = s1;
+  if (!REAL) {
+    s2a = (K2p / 2) / OZ_BK;
+    s2b = min(nks, (K2p / 2 + Kprob + OZ_BK - 1) / OZ_BK);
+    if (s2a <= s1) s1 = s2a = s2b;
+  }
+  const int nks_p = max(1, s1 + (s2b - s2a));
   const size_t aplane = (size_t)(Mp / OZ_BM) * nks * (OZ_TILE_A / 2);
   const size_t bplane = (size_t)(N2p / OZ_BN) * nks * (OZ_TILE_B / 2);
   const unsigned char* Abase = (const unsigned char*)(Ap + (size_t)p * S * aplane) + (size_t)rb * nks * OZ_TILE_A;
@@ -374,15 +452,16 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
         break;
       }
       if (s_fail) break;
+      const int kst = ks < s1 ? ks : s2a + (ks - s1);  // K step of the planes
       unsigned char* sdst = stage0 + st * STAGE;
       oz_expect_tx(&full_bar[st], STAGE);
 #pragma unroll
       for (int s = 0; s < S; ++s)
-        oz_bulk_copy(sdst + s * OZ_TILE_A, Abase + (size_t)s * aplane * 2 + (size_t)ks * OZ_TILE_A, OZ_TILE_A,
+        oz_bulk_copy(sdst + s * OZ_TILE_A, Abase + (size_t)s * aplane * 2 + (size_t)kst * OZ_TILE_A, OZ_TILE_A,
                      &full_bar[st]);
 #pragma unroll
       for (int t = 0; t < S; ++t)
-        oz_bulk_copy(sdst + S * OZ_TILE_A + t * TILE_B, Bbase + (size_t)t * bplane * 2 + (size_t)ks * OZ_TILE_B,
+        oz_bulk_copy(sdst + S * OZ_TILE_A + t * TILE_B, Bbase + (size_t)t * bplane * 2 + (size_t)kst * OZ_TILE_B,
                      TILE_B, &full_bar[st]);
     }
     s_issued = ks;
@@ -400,29 +479,31 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
       asm volatile("tcgen05.fence::after_thread_sync;");
       unsigned char* ssrc = stage0 + st * STAGE;
       const uint32_t sa = smem_u32(ssrc), sb = smem_u32(ssrc + S * OZ_TILE_A);
-      // Digit products A_s B_t (0-based; group s + t + 2).  The exact groups have adjacent
-      // accumulators and the B planes adjacent tiles, so for each s the planes t0..t0+w-1
-      // stack into one operand of 64 w rows: one MMA with N = 64 w (w <= 4) feeds w
-      // accumulators and reads A_s from shared memory once instead of w times.  The merged
-      // groups (one accumulator) take one N = 64 MMA each.  A window's accumulators are all
-      // fresh or all written, so one accumulate flag serves it.
+      // Digit products A_s B_t (0-based, s + t <= S - 1) into accumulator min(s + t, NACC - 1).
+      // The accumulators are adjacent and so are the B planes, so for each s the planes
+      // t = 0 .. NACC - 1 - s stack into one operand of BN w rows: one MMA with N = BN w
+      // (<= 256) feeds w accumulators (the last one the merged groups' first product) and
+      // reads A_s from shared memory once instead of w times.  The merged groups' other
+      // products take one N = BN MMA each.  A window's accumulators are all fresh or all
+      // written (s = 0 writes all of them first), so one accumulate flag serves it.
+      constexpr int WMAX = 256 / BN;
 #pragma unroll
       for (int s = 0; s < S; ++s) {
         const uint64_t ad = oz_desc(sa + s * OZ_TILE_A);
+        const int tlast = min(NACC - 1 - s, S - 1 - s);  // last t of the window (< 0: none)
 #pragma unroll
-        for (int t0 = 0; t0 < NEX - s && t0 < S; t0 += 4) {
-          const int tend = min(min(NEX - s, S), t0 + 4);
-          const int w = tend - t0, acc0 = s + t0;
+        for (int t0 = 0; t0 <= tlast; t0 += WMAX) {
+          const int w = min(WMAX, tlast - t0 + 1), acc0 = s + t0;
           const uint32_t on = (init_mask >> acc0) & 1u;
           oz_mma(tmem + acc0 * BN, ad, oz_desc(sb + t0 * TILE_B), oz_idesc(w * BN), on);
           init_mask |= ((1u << w) - 1u) << acc0;
         }
         if (MERGED) {
 #pragma unroll
-          for (int t = (NEX - s > 0 ? NEX - s : 0); t < S && s + t + 2 <= S + 1; ++t) {
-            const uint32_t on = (init_mask >> NEX) & 1u;
-            oz_mma(tmem + NEX * BN, ad, oz_desc(sb + t * TILE_B), oz_idesc(BN), on);
-            init_mask |= 1u << NEX;
+          for (int t = (tlast + 1 > 0 ? tlast + 1 : 0); t < S && s + t <= S - 1; ++t) {
+            const uint32_t on = (init_mask >> (NACC - 1)) & 1u;
+            oz_mma(tmem + (NACC - 1) * BN, ad, oz_desc(sb + t * TILE_B), oz_idesc(BN), on);
+            init_mask |= 1u << (NACC - 1);
           }
         }
       }
@@ -472,27 +553,30 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
       }
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       if (gi >= M) continue;
-      // every output as one exact fixed-point integer t (value t 2^{kUnitExp - sh}), turned
+      // every output as one fixed-point integer t (value t 2^{e_i + f_j + kExp - sh}), turned
       // into a double by integer operations: no FP64 instruction unless beta != 0
       long long t[8];
       int sh[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
-        // exact groups g = 2..NEX+1 (accumulator g-2): G_g = n_g 2^{42-6g} with integer n_g;
-        // hi = sum_g n_g 2^{6(NEX+1-g)} counts in units of the last exact group, 2^{36-6 NEX}
+        // exact groups a < NEX: G_a = n_a 2^{30 - DB a} with integer n_a;
+        // hi = sum_a n_a 2^{DB (NEX - 1 - a)} counts in units of the last exact group
         long long hi = 0;
 #pragma unroll
         for (int a = 0; a < NEX; ++a) {
           const float gv = __uint_as_float(v[a][c]);
-          const long long ng = (long long)__float2int_rn(ldexpf(gv, -6 * (5 - a)));
-          hi += ng * (1ll << (6 * (NEX - 1 - a)));
+          const long long ng = (long long)__float2int_rn(ldexpf(gv, DB * a - 30));
+          hi += ng * (1ll << (DB * (NEX - 1 - a)));
         }
-        if (MERGED) {
-          // |hi| < 2^59 (2K' <= 1792); shift it up to just below 2^60 and add the merged
-          // groups (|.| < 2^13 in units of 1) rounded to the new unit, which stays below 2^62
+        if (NEX < NACC) {
+          // |hi| < 2^59; shift it up to just below 2^60 and add the other accumulators
+          // (|.| < 2^18 in units of 1) rounded to the new unit, which stays below 2^62
           const unsigned long long ah = hi < 0 ? 0ull - (unsigned long long)hi : (unsigned long long)hi;
           const int s = min(max(__clzll((long long)ah) - 4, 0), 40);
-          t[c] = (long long)((unsigned long long)hi << s) + oz_f32_fixed(__uint_as_float(v[NEX][c]), s - kUnitExp);
+          long long tt = (long long)((unsigned long long)hi << s);
+#pragma unroll
+          for (int a = NEX; a < NACC; ++a) tt += oz_f32_fixed(__uint_as_float(v[a][c]), s + kUnitExp);
+          t[c] = tt;
           sh[c] = s;
         } else {
           t[c] = hi;
@@ -505,7 +589,7 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
         for (int c = 0; c < 8; ++c) {
           const int gj = cb * BN + col0 + c;
           if (gj >= N) continue;
-          const int ex = erow + cexp[(size_t)p * N2p + gj] - 42 + kUnitExp + ae;
+          const int ex = erow + cexp[(size_t)p * N2p + gj] + kExp + ae;
           double* cp = Cp + (long long)gi * Crs + (long long)gj * Ccs;
           double r = fix_to_double(t[c], ex - sh[c], aneg);
           if (amul) r *= alpha;
@@ -518,7 +602,7 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
         for (int q = 0; q < 4; ++q) {
           const int gj = cb * (BN / 2) + half * (BN / 4) + cc + q;  // complex column
           if (gj >= N) continue;
-          const int ex = erow + cexp[(size_t)p * (N2p / 2) + gj] - 42 + kUnitExp + ae;
+          const int ex = erow + cexp[(size_t)p * (N2p / 2) + gj] + kExp + ae;
           z64* cp = Cp + (long long)gi * Crs + (long long)gj * Ccs;
           z64 r = zmk(fix_to_double(t[2 * q], ex - sh[2 * q], aneg),
                       fix_to_double(t[2 * q + 1], ex - sh[2 * q + 1], aneg));
@@ -544,9 +628,10 @@ oz_gemm_kernel(int nprob, GemmDims dims, double alpha, double beta, const __nv_b
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-// Split both operands into S digit planes and run the tensor kernel.  The plane buffers are
-// laid out for OZ_S planes (the workspace size), whatever S is used.
-template <bool REAL, int S>
+// Split both operands into S digit planes of DB bits and run the tensor kernel.  The plane
+// buffers are laid out for OZ_S planes (the workspace size), whatever S is used.  Base-128
+// digits (DB = 7) always take the 32-column tiles: their contractions are at most 32 K steps.
+template <bool REAL, int S, int DB>
 cudaError_t launch_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta, void* C,
                       long long Cbs, long long Crs, long long Ccs, void* ws, int* err, cudaStream_t st) {
   if (nprob <= 0 || dims.M <= 0 || dims.N <= 0) return cudaSuccess;
@@ -559,42 +644,52 @@ cudaError_t launch_oz(int nprob, GemmDims dims, double alpha, GemmOperand A, Gem
   w += (size_t)nprob * OZ_S * N2p * K2p * 2;
   int* rexp = (int*)w;
   int* cexp = rexp + (size_t)nprob * Mp;
-  oz_split<false, REAL, S><<<dim3(Mp / 16, nprob), 256, 0, st>>>(nprob, dims, A, Mp, K2p, Apl, rexp);
+  oz_split<false, REAL, S, DB><<<dim3(Mp / 16, nprob), 256, 0, st>>>(nprob, dims, A, Mp, K2p, Apl, rexp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  oz_split<true, REAL, S><<<dim3(N2p / 16, nprob), 256, 0, st>>>(nprob, dims, B, N2p, K2p, Bpl, cexp);
+  oz_split<true, REAL, S, DB><<<dim3(N2p / 16, nprob), 256, 0, st>>>(nprob, dims, B, N2p, K2p, Bpl, cexp);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (K2p / OZ_BK <= OZ_SHORT_KSTEPS) {
+  if (DB == 7 || K2p / OZ_BK <= OZ_SHORT_KSTEPS) {
     constexpr int BN = OZ_BN / 2, NST = 2;
     const size_t smem = NST * (size_t)S * (OZ_TILE_A + BN * OZ_BK * 2) + 1024;
-    e = cudaFuncSetAttribute(oz_gemm_kernel<REAL, S, BN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(oz_gemm_kernel<REAL, S, DB, BN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(N2p / BN, Mp / OZ_BM, nprob);
-    oz_gemm_kernel<REAL, S, BN, NST><<<grid, OZ_THREADS, smem, st>>>(nprob, dims, alpha, beta, Apl, Bpl, rexp, cexp, Mp,
-                                                                     N2p, K2p, C, Cbs, Crs, Ccs, err);
+    oz_gemm_kernel<REAL, S, DB, BN, NST><<<grid, OZ_THREADS, smem, st>>>(nprob, dims, alpha, beta, Apl, Bpl, rexp,
+                                                                         cexp, Mp, N2p, K2p, C, Cbs, Crs, Ccs, err);
     return cudaGetLastError();
   }
-  const size_t smem = OZ_STAGES * (size_t)S * (OZ_TILE_A + OZ_TILE_B) + 1024;
-  e = cudaFuncSetAttribute(oz_gemm_kernel<REAL, S, OZ_BN, OZ_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
-  if (e != cudaSuccess) return e;
-  dim3 grid(N2p / OZ_BN, Mp / OZ_BM, nprob);
-  oz_gemm_kernel<REAL, S, OZ_BN, OZ_STAGES><<<grid, OZ_THREADS, smem, st>>>(nprob, dims, alpha, beta, Apl, Bpl, rexp,
-                                                                           cexp, Mp, N2p, K2p, C, Cbs, Crs, Ccs, err);
+  if constexpr (DB == 6) {
+    const size_t smem = OZ_STAGES * (size_t)S * (OZ_TILE_A + OZ_TILE_B) + 1024;
+    e = cudaFuncSetAttribute(oz_gemm_kernel<REAL, S, DB, OZ_BN, OZ_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(N2p / OZ_BN, Mp / OZ_BM, nprob);
+    oz_gemm_kernel<REAL, S, DB, OZ_BN, OZ_STAGES><<<grid, OZ_THREADS, smem, st>>>(
+        nprob, dims, alpha, beta, Apl, Bpl, rexp, cexp, Mp, N2p, K2p, C, Cbs, Crs, Ccs, err);
+  }
   return cudaGetLastError();
 }
 
-// Longest contraction of one exact chunk: 2K' <= OZ_MAX_K2 (complex) or K' <= OZ_MAX_K2 (real).
+// Longest contraction of one exact chunk: base-64 digits 2K' <= OZ_MAX_K2 (complex) or
+// K' <= OZ_MAX_K2 (real); base-128 digits K' <= 512.
 constexpr int OZ_CHUNK_C = OZ_MAX_K2 / 2, OZ_CHUNK_R = OZ_MAX_K2;
+constexpr int OZ7_CHUNK_C = 256, OZ7_CHUNK_R = 512;
 
 // Products longer than one chunk: C = alpha sum_c op(A)(:, c) op(B)(c, :) + beta C, every
-// chunk FP64-accurate, the sum accumulated in FP64 through beta = 1.
+// chunk FP64-accurate, the sum accumulated in FP64 through beta = 1.  digits: 5, 6, 7 or 10
+// base-64 planes, or NAO_OZ_DIGITS_B128 (nine base-128 planes, 63 bits).
 template <bool REAL>
 cudaError_t launch_oz_chunked(int nprob, GemmDims dims, double alpha, GemmOperand A, GemmOperand B, double beta,
                               void* C, long long Cbs, long long Crs, long long Ccs, void* ws, int* err,
                               cudaStream_t st, int digits) {
-  const int chunk = REAL ? OZ_CHUNK_R : OZ_CHUNK_C;
+  // FP64-accurate contractions that fit one base-128 chunk take the nine base-128 planes: as
+  // accurate (63 bits) and fewer, wider MMAs
+  if (digits == NAO_OZ_DIGITS_FP64 && dims.K <= (REAL ? OZ7_CHUNK_R : OZ7_CHUNK_C)) digits = NAO_OZ_DIGITS_B128;
+  const bool b128 = digits == NAO_OZ_DIGITS_B128;
+  const int chunk = b128 ? (REAL ? OZ7_CHUNK_R : OZ7_CHUNK_C) : (REAL ? OZ_CHUNK_R : OZ_CHUNK_C);
   const size_t esz = REAL ? sizeof(double) : sizeof(z64);
   for (int k0 = 0; k0 < dims.K || k0 == 0; k0 += chunk) {
     GemmDims d = dims;
@@ -606,10 +701,11 @@ cudaError_t launch_oz_chunked(int nprob, GemmDims dims, double alpha, GemmOperan
     const double bt = k0 == 0 ? beta : 1.0;
     cudaError_t e;
     switch (digits) {
-      case 5: e = launch_oz<REAL, 5>(nprob, d, alpha, a, b, bt, C, Cbs, Crs, Ccs, ws, err, st); break;
-      case 6: e = launch_oz<REAL, 6>(nprob, d, alpha, a, b, bt, C, Cbs, Crs, Ccs, ws, err, st); break;
-      case 7: e = launch_oz<REAL, 7>(nprob, d, alpha, a, b, bt, C, Cbs, Crs, Ccs, ws, err, st); break;
-      case OZ_S: e = launch_oz<REAL, OZ_S>(nprob, d, alpha, a, b, bt, C, Cbs, Crs, Ccs, ws, err, st); break;
+      case 5: e = launch_oz<REAL, 5, 6>(nprob, d, alpha, a, b, bt, C, Cbs, Crs, Ccs, ws, err, st); break;
+      case 6: e = launch_oz<REAL, 6, 6>(nprob, d, alpha, a, b, bt, C, Cbs, Crs, Ccs, ws, err, st); break;
+      case 7: e = launch_oz<REAL, 7, 6>(nprob, d, alpha, a, b, bt, C, Cbs, Crs, Ccs, ws, err, st); break;
+      case OZ_S: e = launch_oz<REAL, OZ_S, 6>(nprob, d, alpha, a, b, bt, C, Cbs, Crs, Ccs, ws, err, st); break;
+      case NAO_OZ_DIGITS_B128: e = launch_oz<REAL, 9, 7>(nprob, d, alpha, a, b, bt, C, Cbs, Crs, Ccs, ws, err, st); break;
       default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;

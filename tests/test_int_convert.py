@@ -90,6 +90,74 @@ def driver(tmp_path_factory):
     return str(exe)
 
 
+DIGITS_DRIVER = r"""
+#include <cstdio>
+#include <cstring>
+#include <cstdint>
+#include <cmath>
+#include <random>
+#define __device__
+#define __forceinline__ inline
+static long long __double_as_longlong(double x) { long long b; memcpy(&b, &x, 8); return b; }
+%(fixed)s
+%(digits)s
+template <int S, int DB> static long check(std::mt19937_64& g, int bits) {
+  long bad = 0;
+  const int half = 1 << (DB - 1);
+  for (int it = 0; it < 400000; ++it) {
+    const int nb = 1 + (int)(g() %% bits);
+    long long q = (long long)(g() >> (64 - nb));
+    if (g() & 1) q = -q;
+    int d[S];
+    oz_digits<S, DB>(q, d);
+    __int128 r = 0;
+    for (int s = 0; s < S; ++s) r = r * ((__int128)1 << DB) + d[s];
+    if (r != (__int128)q) ++bad;
+    if (d[0] < -2 * half || d[0] > 2 * half) ++bad;
+    for (int s = 1; s < S; ++s) if (d[s] < -half || d[s] >= half) ++bad;
+  }
+  // q = round(x 2^{DB S - e}) for |x| < 2^e, rounded half away from zero
+  for (int it = 0; it < 400000; ++it) {
+    const int e = (int)(g() %% 80) - 40;
+    double x = ldexp((double)(g() >> 11) / 9007199254740992.0, e);  // [0, 2^e)
+    x = ldexp(x, -(int)(g() %% 70));
+    if (g() & 1) x = -x;
+    const long long q = oz_fixed<S, DB>(x, e);
+    const long double y = ldexpl((long double)x, DB * S - e);
+    const long long ref = (long long)(y < 0 ? -floorl(-y + 0.5L) : floorl(y + 0.5L));
+    if (q != ref) ++bad;
+  }
+  return bad;
+}
+int main() {
+  std::mt19937_64 g(7);
+  printf("%%ld %%ld\n", check<10, 6>(g, 60), check<9, 7>(g, 63));
+  return 0;
+}
+"""
+
+
+def test_digit_splits():
+    """The digit-plane split of the FP64-accurate tensor-core products: q = round(x 2^{DB S - e})
+    and its S balanced digits, for ten base-64 digits (60 bits) and nine base-128 digits (63
+    bits): exact reconstruction and the digit ranges that the exactness bounds of the FP32
+    group sums assume (lower digits in [-2^{DB-1}, 2^{DB-1}), the leading one within 2^DB)."""
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("no host C++ compiler")
+    src = os.path.join(CSRC, "ozgemm.cu")
+    fixed = _extract(src, "template <int S, int DB>\n__device__ __forceinline__ long long oz_fixed(", "\n}\n") + "\n}\n"
+    digits = _extract(src, "template <int S, int DB>\n__device__ __forceinline__ void oz_digits(", "\n}\n") + "\n}\n"
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "dig.cpp")
+        open(c, "w").write(DIGITS_DRIVER % {"fixed": fixed, "digits": digits})
+        exe = os.path.join(d, "dig")
+        subprocess.run([cxx, "-O2", "-std=c++17", "-o", exe, c], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    assert out == ["0", "0"], out
+
+
 def test_fixed_point_conversions(driver):
     out = subprocess.run([driver], check=True, capture_output=True, text=True).stdout.split()
     bad_fix, bad_comb = int(out[0]), int(out[1])
