@@ -565,16 +565,17 @@ def run_ours(args, rank, world, local_rank):
     smap = (torch.arange(nprob, dtype=torch.int32) % nk).to(dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(src, precision=0, eps_out=eps, before_eig=None, before_density=None):
-        ctx.nao_bloch_sum(src["SR"], src["R"], src["k"], out=Sk)
-        ctx.nao_bloch_sum(src["HR"], src["R"], src["k"], out=Hk)
+    def step(src, precision=0, eps_out=eps, before_eig=None, before_density=None, c=None):
+        c = c or ctx
+        c.nao_bloch_sum(src["SR"], src["R"], src["k"], out=Sk)
+        c.nao_bloch_sum(src["HR"], src["R"], src["k"], out=Hk)
         if before_eig:
             before_eig()
-        ctx.nao_gen_eig(Hk.view(nprob, n, n), Sk[0], s_of_prob=smap, precision=precision, out=(eps_out, C, m, st))
+        c.nao_gen_eig(Hk.view(nprob, n, n), Sk[0], s_of_prob=smap, precision=precision, out=(eps_out, C, m, st))
         if before_density:
             before_density()
-        ctx.nao_density_matrix(src["w"], src["k"], eps_out, C, m, inp.n_electrons, inp.kT, src["R"], nspin,
-                               out=(mu, eb, f, rho, rst))
+        c.nao_density_matrix(src["w"], src["k"], eps_out, C, m, inp.n_electrons, inp.kT, src["R"], nspin,
+                             out=(mu, eb, f, rho, rst))
 
     def barrier():
         torch.cuda.synchronize()
@@ -715,6 +716,32 @@ def run_ours(args, rank, world, local_rank):
                       "eigenvalues all; the density-matrix status confirms no occupied band lies beyond nb",
               "status_ok": bool(int(st.abs().sum()) == 0 and int(rst[0]) == 0)}
 
+    # the two-stage Householder reduction (dense -> band -> tridiagonal, then the second
+    # back-transformation) on the same FP64 step, at both band widths, against the one-stage
+    # step above
+    two_stage = {}
+    for bw in (32, 16):
+        c2 = Context(local_rank, config={"band_width": bw})
+        eps_ts = torch.empty_like(eps)
+        step(d_in, 0, eps_ts, c=c2)
+        barrier()
+        c2.nao_profile_enable(True)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step(d_in, 0, eps_ts, c=c2)
+        t1.record(stream)
+        barrier()
+        ts_ms = t0.elapsed_time(t1) / args.steps
+        tprof = c2.nao_profile_read()
+        c2.close()
+        two_stage[f"band_width_{bw}"] = {
+            "value": nprob * world / (ts_ms * 1e-3), "unit": UNIT, "ms_per_step": ts_ms,
+            "over_one_stage_speed": ms_total / args.steps / ts_ms,
+            "stages_ms": {k_: round(v[0] / args.steps, 3) for k_, v in sorted(tprof.items(), key=lambda kv: -kv[1][0])},
+            "max_abs_deps_vs_one_stage_Ha": float((eps_ts - eps)[fin].abs().max()),
+            "status_ok": bool(int(st.abs().sum()) == 0 and int(rst[0]) == 0)}
+
     serve = run_serve(local_rank) if (world == 1 and not args.no_serve) else None
     serve_stated = run_serve_stated(local_rank) if (world == 1 and not args.no_serve and not args.quick) else None
     mixed_n2000 = run_mixed_n2000(local_rank) if (world == 1 and not args.quick) else None
@@ -786,6 +813,7 @@ def run_ours(args, rank, world, local_rank):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu, "mixed": mixed, "subset": subset, "serve": serve,
             "mixed_n2000": mixed_n2000, "large_basis": large_basis, "serve_stated": serve_stated,
+            "two_stage": two_stage,
             "status_ok": bool(int(st.abs().sum()) == 0 and int(rst[0]) == 0),
         }
         print(json.dumps(line), flush=True)

@@ -83,6 +83,13 @@ typedef struct {
                                  the paper names) wherever an eigenvalue's relative gap is at
                                  least 1e-3, inverse iteration for the rest; 0: inverse
                                  iteration (dstevx's method) for all                         */
+  int band_width;             /* Householder reduction of Eigen_HH step 1 (Sec. 3; the
+                                 paper's conclusion calls for a change of this algorithm):
+                                 0 (default) one stage, blocked Householder straight to
+                                 tridiagonal form; 16 or 32: two stages, dense -> band of that
+                                 lower bandwidth (panel QR and tensor-core updates), then
+                                 band -> tridiagonal by bulge chasing, with a second
+                                 back-transformation of the eigenvectors                      */
 } nao_config;
 
 void nao_config_defaults(nao_config* cfg);

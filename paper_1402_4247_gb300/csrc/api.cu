@@ -181,10 +181,12 @@ cudaError_t run_dgemm(nao_ctx* ctx, const char* stage, int nprob, GemmDims d, do
 // Workspace layout of nao_gen_eig (byte offsets into the context's arena) and its size.
 struct GenEigPlan {
   size_t oAS, oTauS, odS, oeS, owS, oZ, oZ2, oG, oScr, omS, ostS, oX, oHf, oY, oHp, oV, oTauH, odH, oeH, owH, omP, onbP, ostP, ostH, oOz, oVf, oTc, oG2, oT2, oW, oW2, oVW, oDig, oErow;
+  // two-stage reduction (band width B2 > 0): V T, the panel's small matrices, band, stage-2 reflectors
+  size_t oSVT, oSG, oST, oSM, oSN, oSTc, oSAB, oSV2, oSTau2;
   size_t bytes;
 };
 
-GenEigPlan plan_gen_eig(int n, int nprob, int nSe, bool use_tc) {
+GenEigPlan plan_gen_eig(int n, int nprob, int nSe, bool use_tc, int B2) {
   GenEigPlan W;
   WsPlan P;
   const size_t nn = (size_t)n * n;
@@ -233,6 +235,17 @@ GenEigPlan plan_gen_eig(int n, int nprob, int nSe, bool use_tc) {
   // 8-bit digit planes of the Householder trailing matrix (tensor-core product method)
   W.oDig = P.take<char>(use_tc ? hetrd_digits_bytes(n, nmax, NAO_HT_DIGITS_FP64) : 16);
   W.oErow = P.take<int>((size_t)(n > 1 ? n - 1 : 1) * nmax);
+  const size_t b2 = B2 > 0 ? (size_t)B2 : 0;
+  const size_t sq = B2 > 0 ? (size_t)sbr_q2_count(n, B2) : 0;
+  W.oSVT = P.take<z64>(b2 * n * nmax + 1);
+  W.oSG = P.take<z64>(b2 * b2 * nmax + 1);
+  W.oST = P.take<z64>(b2 * b2 * nmax + 1);
+  W.oSM = P.take<z64>(b2 * b2 * nmax + 1);
+  W.oSN = P.take<z64>(b2 * b2 * nmax + 1);
+  W.oSTc = P.take<z64>(b2 * nmax + 1);
+  W.oSAB = P.take<z64>(2 * b2 * n * nmax + 1);
+  W.oSV2 = P.take<z64>(sq * b2 * nmax + 1);
+  W.oSTau2 = P.take<z64>(sq * nmax + 1);
   W.bytes = P.off;
   return W;
 }
@@ -274,10 +287,18 @@ DensityPlan plan_density(int n, int nspin, int nk, int nR, int nb, int num_sms, 
 // then the products VT_j = V_j T_j; each block then costs two products on the chain through
 // U: W = V_j^H U and U -= VT_j W.  VT: [nprob][ncolv][n] (column-major like Vf, block j in
 // columns j nb ..).
+// The second reduction stage of the two-stage form: its reflectors (csrc/sbr.cu).
+struct Q2Ref {
+  int B;
+  const z64* V2;
+  const z64* tau2;
+  long long sq;
+};
+
 cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, const int32_t* ncols, const z64* A,
                                   const z64* tau, const double* Z, const double* w, int use_rsqrt, z64* U, z64* Vf,
                                   z64* tauc, z64* G, z64* T, z64* W, z64* VT, void* ozws, cudaStream_t st,
-                                  int digits, int lowest) {
+                                  int digits, int lowest, int off = 1, const Q2Ref* q2 = nullptr) {
   const int nb = NAO_WY_NB;
   const int ncolv = (n + nb - 1) / nb * nb;
   const long long snn = (long long)n * n, svf = (long long)n * ncolv, snb2 = (long long)nb * nb,
@@ -285,13 +306,18 @@ cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t*
   cudaError_t e;
   {
     NaoStage stage_(ctx, "backtransform", st, 2);
-    e = launch_extract_v(n, nprob, size, A, n, snn, tau, n, ncolv, Vf, n, svf, tauc, st);
+    e = launch_extract_v(n, nprob, size, A, n, snn, tau, n, ncolv, Vf, n, svf, tauc, off, st);
     if (e == cudaSuccess) e = launch_init_u(n, nprob, size, ncols, Z, n, snn, U, n, snn, lowest, st);
     if (e != cudaSuccess) return e;
   }
-  const int nblk = (n - 1 + nb - 1) / nb;
+  if (q2) {  // U = Q2 Z first (stage 2's reflectors), then stage 1's blocks below
+    NaoStage stage_(ctx, "sbr_q2", st, 1);
+    e = launch_sbr_q2(q2->B, n, nprob, size, ncols, q2->V2, q2->tau2, q2->sq, U, n, snn, st);
+    if (e != cudaSuccess) return e;
+  }
+  const int nblk = n > off ? (n - off + nb - 1) / nb : 0;
   for (int j = 0; j < nblk; ++j) {  // Gram matrices of all blocks
-    const int R0 = j * nb + 1, rows = n - R0;
+    const int R0 = j * nb + off, rows = n - R0;
     const z64* Vj = Vf + R0 + (size_t)j * nb * n;  // V_j(r, c) at Vj[r + c n]
     GemmDims dg{nb, nb, rows, nullptr, nullptr, nullptr, 0};
     e = run_zgemm(ctx, "backtransform", nprob, dg, 1.0, GemmOperand{Vj, svf, n, 1, 1, nullptr},
@@ -305,7 +331,7 @@ cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t*
     if (e != cudaSuccess) return e;
   }
   for (int j = 0; j < nblk; ++j) {  // VT_j = V_j T_j (rows x nb; T_j upper triangular, row-major)
-    const int R0 = j * nb + 1, rows = n - R0;
+    const int R0 = j * nb + off, rows = n - R0;
     GemmDims dv{rows, nb, nb, nullptr, nullptr, nullptr, 0};
     e = run_zgemm(ctx, "backtransform", nprob, dv, 1.0, GemmOperand{Vf + R0 + (size_t)j * nb * n, svf, 1, n, 0, nullptr},
                   GemmOperand{T + (size_t)j * nprob * snb2, snb2, nb, 1, 0, nullptr}, 0.0,
@@ -313,7 +339,7 @@ cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t*
     if (e != cudaSuccess) return e;
   }
   for (int j = nblk - 1; j >= 0; --j) {
-    const int R0 = j * nb + 1, rows = n - R0;
+    const int R0 = j * nb + off, rows = n - R0;
     if (rows <= 0) continue;
     const z64* Vj = Vf + R0 + (size_t)j * nb * n;
     const z64* VTj = VT + R0 + (size_t)j * nb * n;
@@ -371,6 +397,75 @@ cudaError_t hetrd_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, z
   return cudaSuccess;
 }
 
+// Eigen_HH step 1 in two stages (csrc/sbr.cu): dense -> band of lower bandwidth B, one
+// panel of B columns at a time (panel QR, then A22 <- Q^H A22 Q as the tensor-core products
+// G = V^H V -> T, X = A22 (V T), M = V^H X, N = T^H M, W = X - V N / 2 and the full rank-2B
+// update A22 -= V W^H + W V^H), then band -> tridiagonal by bulge chasing.  Stage 1's
+// reflectors stay in A below the band (head of reflector c at row c + B, tau[c]); stage 2's
+// go to V2 / tau2.  A must hold the full Hermitian matrix.
+struct SbrWork {
+  z64 *VW, *VT, *G, *T, *M, *N, *tauc, *AB, *V2, *tau2;
+  long long sq;
+};
+
+cudaError_t hetrd_two_stage(nao_ctx* ctx, int n, int nprob, const int32_t* size, z64* A, double* d, double* e, z64* tau,
+                            const SbrWork& S, int B, void* ozws, cudaStream_t st, int digits) {
+  const long long snn = (long long)n * n, svw = (long long)n * 3 * B, svt = (long long)n * B, sbb = (long long)B * B;
+  cudaError_t err = cudaSuccess;
+  if (size) {  // the products read all n rows and columns
+    NaoStage stage_(ctx, "sbr_qr", st, 1);
+    err = launch_zero_outside(n, nprob, size, A, snn, st);
+    if (err != cudaSuccess) return err;
+  }
+  for (int c0 = 0; c0 + B < n; c0 += B) {
+    const int r0 = c0 + B, rows = n - r0;
+    {
+      NaoStage stage_(ctx, "sbr_qr", st, 1);
+      err = launch_sbr_qr(B, n, nprob, size, A, snn, c0, S.tauc, tau, n, S.VW, svw, st);
+      if (err != cudaSuccess) return err;
+    }
+    const z64* Vp = S.VW + (size_t)r0 * 3 * B;  // V: rows x B, row-major (ld 3B)
+    z64* Xp = S.VW + (size_t)r0 * 3 * B + B;    // X, then W, beside it
+    z64* A22 = A + r0 + (size_t)r0 * n;
+    const GemmOperand opV{Vp, svw, 3 * B, 1, 0, nullptr}, opVh{Vp, svw, 1, 3 * B, 1, nullptr};
+    err = run_zgemm(ctx, "sbr_update", nprob, GemmDims{B, B, rows, nullptr, nullptr, nullptr, 0}, 1.0, opVh, opV, 0.0,
+                    S.G, sbb, B, 1, ozws, st, digits);  // G = V^H V
+    if (err != cudaSuccess) return err;
+    {
+      NaoStage stage_(ctx, "sbr_update", st, 1);
+      err = launch_build_t(B, nprob, 1, S.G, S.tauc, B, S.T, st);
+      if (err != cudaSuccess) return err;
+    }
+    err = run_zgemm(ctx, "sbr_update", nprob, GemmDims{rows, B, B, nullptr, nullptr, nullptr, 0}, 1.0, opV,
+                    GemmOperand{S.T, sbb, B, 1, 0, nullptr}, 0.0, S.VT + (size_t)r0 * B, svt, B, 1, ozws, st,
+                    digits);  // V T
+    if (err == cudaSuccess)
+      err = run_zgemm(ctx, "sbr_update", nprob, GemmDims{rows, B, rows, nullptr, nullptr, nullptr, 0}, 1.0,
+                      GemmOperand{A22, snn, 1, n, 0, nullptr}, GemmOperand{S.VT + (size_t)r0 * B, svt, B, 1, 0, nullptr},
+                      0.0, Xp, svw, 3 * B, 1, ozws, st, digits);  // X = A22 V T
+    if (err == cudaSuccess)
+      err = run_zgemm(ctx, "sbr_update", nprob, GemmDims{B, B, rows, nullptr, nullptr, nullptr, 0}, 1.0, opVh,
+                      GemmOperand{Xp, svw, 3 * B, 1, 0, nullptr}, 0.0, S.M, sbb, B, 1, ozws, st, digits);  // V^H X
+    if (err == cudaSuccess)
+      err = run_zgemm(ctx, "sbr_update", nprob, GemmDims{B, B, B, nullptr, nullptr, nullptr, 0}, 1.0,
+                      GemmOperand{S.T, sbb, 1, B, 1, nullptr}, GemmOperand{S.M, sbb, B, 1, 0, nullptr}, 0.0, S.N, sbb,
+                      B, 1, ozws, st, digits);  // T^H M
+    if (err == cudaSuccess)
+      err = run_zgemm(ctx, "sbr_update", nprob, GemmDims{rows, B, B, nullptr, nullptr, nullptr, 0}, -0.5, opV,
+                      GemmOperand{S.N, sbb, B, 1, 0, nullptr}, 1.0, Xp, svw, 3 * B, 1, ozws, st, digits);  // W
+    if (err == cudaSuccess)  // A22 -= [V | W] [W | V]^H, both triangles
+      err = run_zgemm(ctx, "sbr_update", nprob, GemmDims{rows, rows, 2 * B, nullptr, nullptr, nullptr, 0}, -1.0,
+                      GemmOperand{Vp, svw, 3 * B, 1, 0, nullptr}, GemmOperand{Xp, svw, 1, 3 * B, 1, nullptr}, 1.0, A22,
+                      snn, 1, n, ozws, st, digits);
+    if (err != cudaSuccess) return err;
+  }
+  NaoStage stage_(ctx, "sbr_chase", st, 2);
+  const long long sab = (long long)n * 2 * B;
+  err = launch_sbr_band(B, n, nprob, size, A, snn, S.AB, sab, st);
+  if (err == cudaSuccess) err = launch_sbr_chase(B, n, nprob, size, S.AB, sab, d, e, n, S.V2, S.tau2, S.sq, st);
+  return err;
+}
+
 // The second half of the Newton-Schulz step, Z - Z (G - I)/2 with G = Z^T Z given by its
 // lower triangle (Z: rows size[p], columns ncols[p]).  Tensor-core method: G - I made full,
 // then one five-plane (30-bit) product with alpha = -1/2 and beta = 1 in place on Z (the
@@ -413,7 +508,7 @@ cudaError_t launch_report_timeout(int* flags, int32_t* status, int nstatus, cuda
 static int check_config(const nao_config& c) {
   return (c.f_min >= 0.0 && c.f_min <= 1e-3 && c.inverse_iteration_max >= 0 && c.inverse_iteration_max <= 64 &&
           c.tc_wait_cycles >= 1 && c.tc_wait_cycles <= 1000000000000LL && c.mixed_planes >= 5 && c.mixed_planes <= 7 &&
-          (c.overlap_mrrr == 0 || c.overlap_mrrr == 1))
+          (c.overlap_mrrr == 0 || c.overlap_mrrr == 1) && (c.band_width == 0 || c.band_width == 16 || c.band_width == 32))
              ? NAO_OK
              : NAO_E_INVALID;
 }
@@ -426,7 +521,7 @@ static cudaError_t push_wait_bound(nao_ctx* c) {
 
 size_t gen_eig_ws_bytes(const nao_ctx* ctx, int n, int nprob, int nSe) {
   const bool use_tc = ctx->gemm_method == NAO_GEMM_TC && zgemm_oz_supported(GemmDims{n, n, n, nullptr, nullptr, nullptr, 0});
-  return plan_gen_eig(n, nprob, nSe, use_tc).bytes;
+  return plan_gen_eig(n, nprob, nSe, use_tc, ctx->cfg.band_width).bytes;
 }
 
 size_t density_ws_bytes(const nao_ctx* ctx, int n, int nspin, int nk, int nR, int nb) {
@@ -448,6 +543,7 @@ void nao_config_defaults(nao_config* cfg) {
   cfg->tc_wait_cycles = NAO_TC_WAIT_DEFAULT;
   cfg->mixed_planes = NAO_MIXED_PLANES_DEFAULT;
   cfg->overlap_mrrr = NAO_OVERLAP_MRRR_DEFAULT;
+  cfg->band_width = NAO_BAND_WIDTH_DEFAULT;
 }
 
 int nao_init(nao_ctx** out, int device, size_t hbm_budget_bytes, const nao_config* cfg) {
@@ -642,7 +738,8 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   const int nmax = nSe > nprob ? nSe : nprob;
 
   const bool use_tc = ctx->gemm_method == NAO_GEMM_TC && zgemm_oz_supported(GemmDims{n, n, n, nullptr, nullptr, nullptr, 0});
-  const GenEigPlan W = plan_gen_eig(n, nprob, nSe, use_tc);
+  const int B2 = ctx->cfg.band_width;  // 0: one-stage reduction
+  const GenEigPlan W = plan_gen_eig(n, nprob, nSe, use_tc, B2);
   const int ncolv = (n + NAO_WY_NB - 1) / NAO_WY_NB * NAO_WY_NB;
   int rc = nao_ws_reserve(ctx, W.bytes);
   if (rc) return rc;
@@ -663,6 +760,12 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
       *Ww = (z64*)(ws + W.oW), *VTw = (z64*)(ws + W.oW2), *VWp = (z64*)(ws + W.oVW);
   void* digp = use_tc ? (void*)(ws + W.oDig) : nullptr;
   int* erowp = (int*)(ws + W.oErow);
+  const SbrWork sbr{VWp, (z64*)(ws + W.oSVT), (z64*)(ws + W.oSG), (z64*)(ws + W.oST), (z64*)(ws + W.oSM),
+                    (z64*)(ws + W.oSN), (z64*)(ws + W.oSTc), (z64*)(ws + W.oSAB), (z64*)(ws + W.oSV2),
+                    (z64*)(ws + W.oSTau2), B2 > 0 ? sbr_q2_count(n, B2) : 0};
+  const Q2Ref q2ref{B2, sbr.V2, sbr.tau2, sbr.sq};
+  const Q2Ref* q2 = B2 > 0 ? &q2ref : nullptr;
+  const int hoff = B2 > 0 ? B2 : 1;  // head row offset of the reduction's (first-stage) reflectors
   const long long snn = (long long)nn;
   // Mixed mode: the back-transformations, X^H H X, the rank-2k updates of H' and X V run with
   // 30-bit products; the reduction of S, the tridiagonal solves (with their Newton-Schulz
@@ -673,7 +776,10 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
 
   // ---- Part 2: Eigen_HH(S) -> s, U;  X = U_m s_m^{-1/2}
   NAO_STAGE("herm_fill", 1, launch_herm_fill(n, nSe, (const z64*)S, snn, nullptr, AS, n, snn, st));
-  NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nSe, nullptr, AS, dS, eS, tauS, VWp, ozws, st, NAO_OZ_DIGITS_FP64, digp, erowp));
+  if (B2 > 0)
+    NAO_CUDA_TRY(ctx, hetrd_two_stage(ctx, n, nSe, nullptr, AS, dS, eS, tauS, sbr, B2, ozws, st, NAO_OZ_DIGITS_FP64));
+  else
+    NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nSe, nullptr, AS, dS, eS, tauS, VWp, ozws, st, NAO_OZ_DIGITS_FP64, digp, erowp));
   NAO_STAGE("stein", ctx->cfg.overlap_mrrr ? 5 : 4,
             launch_stein(n, nSe, nullptr, dS, eS, n, wS, Z, n, snn, scr, stS, nullptr, n,
                          ctx->cfg.inverse_iteration_max, ctx->cfg.overlap_mrrr, st));
@@ -688,7 +794,7 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
     NAO_CUDA_TRY(ctx, e);
   }
   NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nSe, nullptr, mS, AS, tauS, Zo, wS, 1, X, Vf, tauc, Gw, Tw, Ww, VTw,
-                                          ozws, st, dig, 0));
+                                          ozws, st, dig, 0, hoff, q2));
   {
     NaoStage stage_(ctx, "misc", st, 1);
     gather_m_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(nprob, s_of_prob, mS, stS, nb, mP, nbP, stP);
@@ -708,8 +814,11 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   NAO_STAGE("misc", 1, launch_hermitize(n, nprob, mP, Hp, n, snn, st));
 
   // ---- Part 4: Eigen_HH(H') -> eps, V;  C = X V
-  NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nprob, mP, Hp, dH, eH, tauH, VWp, ozws, st, dig, digp, erowp,
-                                  mixed ? NAO_HT_DIGITS_MIXED : NAO_HT_DIGITS_FP64));
+  if (B2 > 0)
+    NAO_CUDA_TRY(ctx, hetrd_two_stage(ctx, n, nprob, mP, Hp, dH, eH, tauH, sbr, B2, ozws, st, dig));
+  else
+    NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nprob, mP, Hp, dH, eH, tauH, VWp, ozws, st, dig, digp, erowp,
+                                    mixed ? NAO_HT_DIGITS_MIXED : NAO_HT_DIGITS_FP64));
   // Eigenvectors of H' only where they are used (the paper's second pass, dstevx's index
   // range): the lowest nb per problem for C, all m for the mixed-mode refinement, none when
   // the caller asks for eigenvalues only (C = NULL).
@@ -728,7 +837,7 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
       NAO_CUDA_TRY(ctx, e);
     }
     NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nprob, mP, nvP, Hp, tauH, Zo, wH, 0, V, Vf, tauc, Gw, Tw, Ww, VTw,
-                                            ozws, st, dig, 1));
+                                            ozws, st, dig, 1, hoff, q2));
   }
   if (mixed && ctx->refine_sweeps >= 0) {
     // C^ = X V (all m columns, column-major in Hp), then Ritz refinement sweeps with

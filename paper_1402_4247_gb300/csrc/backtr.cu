@@ -124,11 +124,12 @@ cudaError_t launch_scale_cols_sqrt(int n, int nprob, int nb, const z64* C, const
 // ---------------------------------------------------------------------------------------
 namespace {
 
-// Vfull(:, i) = explicit reflector i (1 at row i+1, A(r, i) below, 0 elsewhere) for
-// i < m-1, zero columns otherwise (ncolv >= n columns); tauc[i] = tau[i] or 0.
+// Vfull(:, i) = explicit reflector i (1 at row i + off, A(r, i) below, 0 elsewhere) for
+// i < m - off, zero columns otherwise (ncolv >= n columns); tauc[i] = tau[i] or 0.
 __global__ void extract_v_kernel(int n, const int32_t* __restrict__ size, const z64* __restrict__ Abase, int lda,
                                  long long strideA, const z64* __restrict__ taubase, long long strideV, int ncolv,
-                                 z64* __restrict__ Vbase, int ldv, long long strideVf, z64* __restrict__ taucbase) {
+                                 z64* __restrict__ Vbase, int ldv, long long strideVf, z64* __restrict__ taucbase,
+                                 int off) {
   const int p = blockIdx.z;
   const int m = size ? size[p] : n;
   const int i = blockIdx.y;  // column
@@ -136,12 +137,12 @@ __global__ void extract_v_kernel(int n, const int32_t* __restrict__ size, const 
   if (r >= n || i >= ncolv) return;
   const z64* A = Abase + (size_t)p * strideA;
   z64 val = zmk(0.0, 0.0);
-  if (i < m - 1) {
-    if (r == i + 1) val = zmk(1.0, 0.0);
-    else if (r > i + 1 && r < m) val = A[(size_t)i * lda + r];
+  if (i < m - off) {
+    if (r == i + off) val = zmk(1.0, 0.0);
+    else if (r > i + off && r < m) val = A[(size_t)i * lda + r];
   }
   Vbase[(size_t)p * strideVf + (size_t)i * ldv + r] = val;
-  if (r == 0) taucbase[(size_t)p * ncolv + i] = (i < m - 1) ? taubase[(size_t)p * strideV + i] : zmk(0.0, 0.0);
+  if (r == 0) taucbase[(size_t)p * ncolv + i] = (i < m - off) ? taubase[(size_t)p * strideV + i] : zmk(0.0, 0.0);
 }
 
 // U(:, c) = Z(:, m - nc + c) (or Z(:, c) when lowest) as complex for c < nc, rows < m; zero
@@ -213,9 +214,9 @@ __global__ void normalize_cols_kernel(int n, const int32_t* __restrict__ size, c
 
 cudaError_t launch_extract_v(int n, int nprob, const int32_t* size, const z64* A, int lda, long long strideA,
                              const z64* tau, long long strideV, int ncolv, z64* V, int ldv, long long strideVf,
-                             z64* tauc, cudaStream_t st) {
+                             z64* tauc, int off, cudaStream_t st) {
   dim3 grid((n + 127) / 128, ncolv, nprob);
-  extract_v_kernel<<<grid, 128, 0, st>>>(n, size, A, lda, strideA, tau, strideV, ncolv, V, ldv, strideVf, tauc);
+  extract_v_kernel<<<grid, 128, 0, st>>>(n, size, A, lda, strideA, tau, strideV, ncolv, V, ldv, strideVf, tauc, off);
   return cudaGetLastError();
 }
 

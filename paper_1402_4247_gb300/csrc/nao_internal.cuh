@@ -99,6 +99,7 @@ constexpr int NAO_INV_ITER_DEFAULT = 5;
 constexpr long long NAO_TC_WAIT_DEFAULT = 4000000000LL;  // ~2 s at 2 GHz
 constexpr int NAO_MIXED_PLANES_DEFAULT = 6;
 constexpr int NAO_OVERLAP_MRRR_DEFAULT = 1;
+constexpr int NAO_BAND_WIDTH_DEFAULT = 0;  // one-stage tridiagonalization
 
 // Workspace bytes nao_gen_eig / nao_density_matrix reserve on this context (before the
 // arena's 1/8 headroom); the scheduler's admission test uses them.
@@ -179,6 +180,26 @@ size_t hetrd_digits_bytes(int n, int nprob, int digits);
 cudaError_t launch_hetrd_digits(int n, int nprob, const int32_t* size, const z64* A, int ld, long long strideA, int i0,
                                 void* dig, int* erow, int digits, cudaStream_t st);
 
+// Two-stage form of Eigen_HH step 1 (csrc/sbr.cu), lower bandwidth B (16 or 32).
+// Stage 1 panel QR of columns c0 .. c0+B-1 below row c0 + B (in place in the column-major A,
+// ld n): tau of the panel into tauc[p][B] and tau[p stau + c0 + i], explicit reflectors into
+// columns 0..B-1 and 2B..3B-1 of VW ([n][3B] row-major, rows c0+B .. n-1).
+cudaError_t launch_sbr_qr(int B, int n, int nprob, const int32_t* size, z64* A, long long sA, int c0, z64* tauc,
+                          z64* tau, long long stau, z64* VW, long long sVW, cudaStream_t st);
+// Rows and columns >= size[p] of A set to zero.
+cudaError_t launch_zero_outside(int n, int nprob, const int32_t* size, z64* A, long long sA, cudaStream_t st);
+// The band of the reduced A into AB ([n][2B] per problem: element (r, c) at c 2B + r - c).
+cudaError_t launch_sbr_band(int B, int n, int nprob, const int32_t* size, const z64* A, long long sA, z64* AB,
+                            long long sAB, cudaStream_t st);
+// Stage 2: band -> real tridiagonal (d, e) by bulge chasing; reflectors into V2 ([sq][B] per
+// problem) and tau2 ([sq]), sq = sbr_q2_count(n, B).
+long long sbr_q2_count(int n, int B);
+cudaError_t launch_sbr_chase(int B, int n, int nprob, const int32_t* size, z64* AB, long long sAB, double* d, double* e,
+                             long long sv, z64* V2, z64* tau2, long long sq, cudaStream_t st);
+// U(:, c) <- Q2 U(:, c) for c < ncols[p] (column-major U, ld ldu).
+cudaError_t launch_sbr_q2(int B, int n, int nprob, const int32_t* size, const int32_t* ncols, const z64* V2,
+                          const z64* tau2, long long sq, z64* U, int ldu, long long sU, cudaStream_t st);
+
 // Eigen_HH step 2: eigenvalues w (ascending) and orthonormal eigenvectors Z (column-major,
 // ld) of tridiag(e, d, e) by bisection + inverse iteration.  scratch: see stein_scratch_doubles.
 size_t stein_scratch_doubles(int n, int nprob);
@@ -195,9 +216,10 @@ cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d,
 
 // Blocked (compact WY) back-transformation helpers, see backtr.cu.
 constexpr int NAO_WY_NB = 128;
+// off: row of reflector i's head is i + off (1: one-stage; B: stage 1 of the two-stage form)
 cudaError_t launch_extract_v(int n, int nprob, const int32_t* size, const z64* A, int lda, long long strideA,
                              const z64* tau, long long strideV, int ncolv, z64* V, int ldv, long long strideVf,
-                             z64* tauc, cudaStream_t st);
+                             z64* tauc, int off, cudaStream_t st);
 // init_u: column c of U takes Z's column m - nc + c (the top nc) or, when lowest, column c.
 cudaError_t launch_init_u(int n, int nprob, const int32_t* size, const int32_t* ncols, const double* Z, int ldz,
                           long long strideZ, z64* U, int ldu, long long strideU, int lowest, cudaStream_t st);

@@ -2,9 +2,10 @@
 
 A small driver for tracing and profiling one configuration through the public binding:
 
-    python -m paper_1402_4247_gb300.run_case --kgrid 4 2 2 --nspin 2 --repeat 1
+    python -m paper_1402_4247_gb300.run_case --kgrid 4 2 2 --nspin 2 --repeat 1 [--band-width 32]
 
-prints the per-stage times recorded by the library's CUDA-event tracing.
+prints the per-stage times recorded by the library's CUDA-event tracing (after --warmup
+untraced steps).  --band-width selects the two-stage Householder reduction (nao_config).
 """
 from __future__ import annotations
 
@@ -23,10 +24,12 @@ def main():
     ap.add_argument("--nspin", type=int, default=2)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=0)
+    ap.add_argument("--band-width", type=int, default=0, choices=[0, 16, 32])
     args = ap.parse_args()
     inp = synth.magnetite_cell(seed=args.seed, kgrid=tuple(args.kgrid), nspin=args.nspin)
     dev = torch.device("cuda:0")
-    ctx = Context(0)
+    ctx = Context(0, config={"band_width": args.band_width})
     n, nk, nprob = inp.n, inp.nk, inp.nprob
     HR = torch.from_numpy(inp.HR).to(dev)
     SR = torch.from_numpy(inp.SR)[None].to(dev)
@@ -34,8 +37,10 @@ def main():
     k = torch.from_numpy(inp.kpts).to(dev)
     w = torch.from_numpy(inp.wk).to(dev)
     smap = (torch.arange(nprob, dtype=torch.int32) % nk).to(dev)
-    ctx.nao_profile_enable(True)
-    for _ in range(args.repeat):
+    for it in range(args.warmup + args.repeat):
+        if it == args.warmup:
+            torch.cuda.synchronize()
+            ctx.nao_profile_enable(True)
         Sk = ctx.nao_bloch_sum(SR, R, k)[0]
         Hk = ctx.nao_bloch_sum(HR, R, k).reshape(nprob, n, n)
         eps, C, m, st = ctx.nao_gen_eig(Hk, Sk, s_of_prob=smap)
@@ -43,7 +48,7 @@ def main():
     torch.cuda.synchronize()
     prof = ctx.nao_profile_read()
     ok = int(st.abs().sum()) == 0 and int(rst[0]) == 0
-    print(json.dumps({"n": n, "problems": nprob, "status_ok": ok, "mu": float(mu[0]),
+    print(json.dumps({"n": n, "problems": nprob, "band_width": args.band_width, "status_ok": ok, "mu": float(mu[0]),
                       "stages_ms": {k_: round(v[0] / args.repeat, 3) for k_, v in prof.items()}}))
     ctx.close()
     if not ok:
