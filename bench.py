@@ -465,11 +465,12 @@ def run_mixed_n2000(local_rank, steps=2, warmup=1):
     return res
 
 
-def run_large_basis(local_rank, sizes=(1000, 2000, 3000), steps=1, warmup=0):
+def run_large_basis(local_rank, sizes=(1000, 2000, 3000), steps=1, warmup=0, two_stage_sizes=(1000,)):
     """The large-basis FP64 sweep: n in {1000, 2000, 3000}, 4x4x1 k, one spin, seed 3, overlap
     condition ~1e8 plus one orbital in 50 duplicated (exact null directions; m = n - n/50).
     Per size: solves/s of the band step (Parts 1-6) and its per-stage split; the Householder
-    panel kernel's achieved HBM rate by its algorithmic bytes."""
+    panel kernel's achieved HBM rate by its algorithmic bytes; at two_stage_sizes, the same
+    step with the two-stage reduction."""
     import torch
     from paper_1402_4247_gb300 import synth
     from paper_1402_4247_gb300.nao import Context
@@ -488,6 +489,14 @@ def run_large_basis(local_rank, sizes=(1000, 2000, 3000), steps=1, warmup=0):
                "ms_per_step": ms, "m_mean": m_mean, "stages_ms": stages}
         if "hetrd" in stages:
             row["panel_hbm_frac"] = _panel_bytes(inp, m_mean) / (stages["hetrd"] * 1e-3) / 1e9 / hbm
+        if n in two_stage_sizes:  # the same step with the two-stage reduction (band width 32)
+            ctx = Context(local_rank, config={"band_width": 32})
+            ms2, stages2, out = _band_step_timed(ctx, inp, dev, steps, warmup)
+            ctx.close()
+            del out
+            torch.cuda.empty_cache()
+            row["two_stage_b32"] = {"value": inp.nprob / (ms2 * 1e-3), "unit": UNIT, "ms_per_step": ms2,
+                                    "stages_ms": stages2}
         rows.append(row)
     return {"workload": "large-basis cells (n/25 heavy x 13 + 3n/50 light x 8 orbitals), 125 images, 4x4x1 k, "
                         "1 spin, eta ~ 1e-8 and one orbital in 50 duplicated (kappa(S) ~ 1e8, exact null "

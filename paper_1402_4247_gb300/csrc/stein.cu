@@ -21,14 +21,17 @@
 // * Eigenvectors (kernel 2, same block split): inverse iteration with a partially pivoted LU
 //   of T - lambda I (tiny pivots perturbed to eps |T|), a scaled right-hand side, the growth
 //   test |x|_inf >= sqrt(0.1/blocksize) within `maxits` solves plus two extra solves, and
-//   modified Gram-Schmidt against the earlier members of a TIGHT cluster (gap < 1e-7 |T|_1),
+//   modified Gram-Schmidt against the earlier members of a TIGHT cluster (gap < 1e-9 |T|_1),
 //   whose leader walks the cluster in order.  Wider near-degeneracies leave overlaps of order
-//   eps|T|/gap <= ~1e-9, which the caller removes with one Newton-Schulz step
-//   Z <- Z (3I - Z^T Z)/2.
+//   eps|T|/gap <= ~1e-7, which the caller removes with one Newton-Schulz step
+//   Z <- Z (3I - Z^T Z)/2 (it squares them: ~1e-14).
 //   A tight cluster of more than BIG members (the near-null spectrum of an ill-conditioned
 //   overlap matrix can chain hundreds) is handed to kernel 3: one block per cluster, the
 //   same iteration with the reorthogonalisation done by the whole block (classical
-//   Gram-Schmidt applied twice) while one thread runs the tridiagonal solves.
+//   Gram-Schmidt applied twice) while one thread runs the tridiagonal solves.  A chain can
+//   span far more than the tight band; a member is re-orthogonalised only against the
+//   finished members within the band of its own eigenvalue (the others overlap it by at
+//   most eps|T|/(1e-9 |T|_1), which the Newton-Schulz step removes).
 // * Output: eigenvalues ascending (across blocks), eigenvectors in matching columns,
 //   unit 2-norm, largest component positive.  All loops are bounded.
 #include <cfloat>
@@ -42,7 +45,7 @@ constexpr int ST_THREADS = 64;    // = slots per block (eigenvectors): the overl
 constexpr int SZ_THREADS = 64;    // = slots per block (eigenvalues): ~8 blocks per SM for 128 problems
                                   // of n = 568, so the SMs' FP64 pipes finish within one block of each other
 constexpr int EXTRA = 2;          // extra solves after the growth test passes
-constexpr double TIGHT = 1e-7;
+constexpr double TIGHT = 1e-9;
 constexpr int NARR = 6;           // scratch arrays per eigenvalue: L, U0inv, U1, U2, PIV, X
 constexpr int BIG = 32;           // tight clusters with more members go to stein_cluster_kernel
 constexpr int NEWTON_MAX = 6;     // Newton steps on an isolated eigenvalue before it is queued
@@ -697,10 +700,12 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
         lamprev = w[q];
         continue;
       }
-      if (tid == 0) {  // finished members: the earlier ones and the later MRRR vectors
+      if (tid == 0) {  // finished members within the tight band of w[q]: the earlier ones and
+                       // the later MRRR vectors
+        const double tband = TIGHT * T.onenrm, wq = w[q];
         int c = 0;
         for (int t = 0; t < jend - j; ++t)
-          if (t < q - j || (t > q - j && dn && dn[j + t])) fin[c++] = t;
+          if ((t < q - j || (t > q - j && dn && dn[j + t])) && fabs(w[j + t] - wq) < tband) fin[c++] = t;
         s_nf = c;
       }
       const int sl = q;
@@ -857,9 +862,9 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
 // representation tree): for every unreduced block of a positive semidefinite tridiagonal (the
 // overlap's), shift to just below its smallest eigenvalue, T - sigma I = L D L^T with D > 0.
 // A definite L D L^T determines its eigenvalues to high relative accuracy, so the near-null
-// spectrum of an ill-conditioned overlap, hundreds of eigenvalues within 1e-7 |T| of each
+// spectrum of an ill-conditioned overlap, hundreds of eigenvalues within 1e-9 |T| of each
 // other but relatively far apart, becomes well separated.
-//   A member of a big tight cluster (gaps < 1e-7 |T|_1, more than BIG members: the ones
+//   A member of a big tight cluster (gaps < 1e-9 |T|_1, more than BIG members: the ones
 // inverse iteration would re-orthogonalise at O(k^2 n)) whose shifted eigenvalue
 // mu = lambda - sigma has a relative gap of at least MR_MINRGP to both neighbours is refined
 // by bisection on negative-pivot counts of L D L^T - x I (the stationary qd transform) to
