@@ -463,12 +463,12 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
       }
     } else if (leader) {
       const int bs = b1 - b0;
-      double* Lr = scr + 0 * nn;
-      double* U0i = scr + 1 * nn;
-      double* U1 = scr + 2 * nn;
-      double* U2 = scr + 3 * nn;
-      double* PV = scr + 4 * nn;
-      double* X = scr + 5 * nn;
+      double* __restrict__ Lr = scr + 0 * nn;
+      double* __restrict__ U0i = scr + 1 * nn;
+      double* __restrict__ U1 = scr + 2 * nn;
+      double* __restrict__ U2 = scr + 3 * nn;
+      double* __restrict__ PV = scr + 4 * nn;
+      double* __restrict__ X = scr + 5 * nn;
       const int sl = j;  // scratch column of this leader
 #define AT(arr, i) arr[(size_t)(i) * n + sl]
       double lamprev = 0.0;
@@ -536,16 +536,22 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
         if (fabs(al) < pivtol) al = copysign(pivtol, al);
         const double ulast = al;
         AT(U0i, b1 - 1) = 1.0 / al;
-        for (int i = b0; i < b1; ++i)
-          AT(X, i) = hash_uniform(((unsigned long long)p << 40) ^ ((unsigned long long)q << 20) ^ (unsigned long long)i);
+        // x1 = |X|_1 of the next right-hand side, summed in row order as it is written (the
+        // start vector) or read by the previous iteration's norm pass
+        double x1 = 0.0;
+        for (int i = b0; i < b1; ++i) {
+          const double xi =
+              hash_uniform(((unsigned long long)p << 40) ^ ((unsigned long long)q << 20) ^ (unsigned long long)i);
+          AT(X, i) = xi;
+          x1 += fabs(xi);
+        }
         int its = 0, nrmchk = 0;
         bool ok = false;
         while (its < maxits + EXTRA) {
           ++its;
-          double x1 = 0.0;
-          for (int i = b0; i < b1; ++i) x1 += fabs(AT(X, i));
           const double scl = (double)bs * T.onenrm * fmax(eps, fabs(ulast)) / fmax(x1, DBL_MIN);
           double r = AT(X, b0) * scl;
+#pragma unroll 4
           for (int k = b0; k < b1 - 1; ++k) {
             const double xn = AT(X, k + 1) * scl;
             const double l = AT(Lr, k);
@@ -560,6 +566,7 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
           AT(X, b1 - 1) = r;
           double x2 = 0.0, x1v = AT(X, b1 - 1) * AT(U0i, b1 - 1);
           AT(X, b1 - 1) = x1v;
+#pragma unroll 4
           for (int k = b1 - 2; k >= b0; --k) {
             const double xv = (AT(X, k) - AT(U1, k) * x1v - AT(U2, k) * x2) * AT(U0i, k);
             AT(X, k) = xv;
@@ -578,10 +585,12 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
           }
           double xinf = 0.0;
           bool finite = true;
+          x1 = 0.0;
           for (int i = b0; i < b1; ++i) {
             const double a = fabs(AT(X, i));
             finite = finite && (a <= DBL_MAX);
             xinf = fmax(xinf, a);
+            x1 += a;
           }
           if (!finite) break;
           if (its > maxits && nrmchk == 0) break;
@@ -643,7 +652,7 @@ __device__ __forceinline__ double block_max1(double v, double* red) {
 
 constexpr int SC_THREADS = 256;
 
-__global__ void __launch_bounds__(SC_THREADS)
+__global__ void __launch_bounds__(SC_THREADS, 1)
 stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ dbase,
                      const double* __restrict__ ebase, long long strideV, const double* __restrict__ wslot,
                      double* __restrict__ Zbase, int ldz, long long strideZ, double* __restrict__ scratch,
@@ -685,11 +694,13 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
     const double pivtol = eps * T.tnorm;
     const size_t nn = (size_t)n * n;
     const int b0 = bst[j], b1 = ben[j], bs = b1 - b0;
-    double* Lr = scr + 0 * nn;
-    double* U0i = scr + 1 * nn;
-    double* U1 = scr + 2 * nn;
-    double* U2 = scr + 3 * nn;
-    double* PV = scr + 4 * nn;
+    // the solves below run in one thread: their factor loads are independent of the
+    // recurrence, so the loops are unrolled for the loads of several rows to be in flight
+    double* __restrict__ Lr = scr + 0 * nn;
+    double* __restrict__ U0i = scr + 1 * nn;
+    double* __restrict__ U1 = scr + 2 * nn;
+    double* __restrict__ U2 = scr + 3 * nn;
+    double* __restrict__ PV = scr + 4 * nn;
     double lamprev = 0.0, ulast = 0.0;
     bool fail = false;
     const int nv = min(nvec ? nvec[p] : m, nvec_max);
@@ -768,6 +779,7 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
         if (tid == 0) {  // scaled right-hand side, forward and back substitution
           const double scl = (double)bs * T.onenrm * fmax(eps, fabs(ulast)) / fmax(x1, DBL_MIN);
           double r = sx[b0] * scl;
+          #pragma unroll 8
           for (int k = b0; k < b1 - 1; ++k) {
             const double xn = sx[k + 1] * scl;
             const double l = AT(Lr, k);
@@ -781,6 +793,7 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
           }
           double x2 = 0.0, x1v = r * AT(U0i, b1 - 1);
           sx[b1 - 1] = x1v;
+          #pragma unroll 8
           for (int k = b1 - 2; k >= b0; --k) {
             const double xv = (sx[k] - AT(U1, k) * x1v - AT(U2, k) * x2) * AT(U0i, k);
             sx[k] = xv;

@@ -3,9 +3,12 @@
 A small driver for tracing and profiling one configuration through the public binding:
 
     python -m paper_1402_4247_gb300.run_case --kgrid 4 2 2 --nspin 2 --repeat 1 [--band-width 32]
+    python -m paper_1402_4247_gb300.run_case --large-basis 1000 --kgrid 1 1 1 --nspin 1
 
 prints the per-stage times recorded by the library's CUDA-event tracing (after --warmup
-untraced steps).  --band-width selects the two-stage Householder reduction (nao_config).
+untraced steps).  --band-width selects the two-stage Householder reduction (nao_config);
+--large-basis n takes the large-basis cell of order n (overlap condition ~1e8, one orbital
+in 50 duplicated) instead of the magnetite-shaped one.
 """
 from __future__ import annotations
 
@@ -26,8 +29,13 @@ def main():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=0)
     ap.add_argument("--band-width", type=int, default=0, choices=[0, 16, 32])
+    ap.add_argument("--large-basis", type=int, default=0, metavar="N")
     args = ap.parse_args()
-    inp = synth.magnetite_cell(seed=args.seed, kgrid=tuple(args.kgrid), nspin=args.nspin)
+    if args.large_basis:
+        inp = synth.scaled_cell(args.large_basis, seed=3, kgrid=tuple(args.kgrid), nspin=args.nspin,
+                                ill_conditioned=True)
+    else:
+        inp = synth.magnetite_cell(seed=args.seed, kgrid=tuple(args.kgrid), nspin=args.nspin)
     dev = torch.device("cuda:0")
     ctx = Context(0, config={"band_width": args.band_width})
     n, nk, nprob = inp.n, inp.nk, inp.nprob
