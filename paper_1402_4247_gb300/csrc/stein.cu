@@ -49,6 +49,7 @@ constexpr double TIGHT = 1e-9;
 constexpr int NARR = 6;           // scratch arrays per eigenvalue: L, U0inv, U1, U2, PIV, X
 constexpr int BIG = 32;           // tight clusters with more members go to stein_cluster_kernel
 constexpr int NEWTON_MAX = 6;     // Newton steps on an isolated eigenvalue before it is queued
+constexpr int BQ_LANES = 4;       // lanes per queued eigenvalue in the FP64 bisection (multisection)
 
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
@@ -383,8 +384,14 @@ __global__ void __launch_bounds__(SZ_THREADS)
 stebz_bisect_kernel(int n, const double* __restrict__ dbase, long long strideV, const double* __restrict__ e2g,
                     const double* __restrict__ tng, double* __restrict__ wslot, const int* __restrict__ qcount,
                     const int4* __restrict__ qent, const double* __restrict__ qlo, const double* __restrict__ qhi) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= *qcount) return;
+  // BQ_LANES lanes per entry: each step counts at BQ_LANES interior points of the bracket,
+  // one per lane, and keeps the sub-interval that holds the eigenvalue (log2(BQ_LANES + 1)
+  // bits per step instead of one): the dependent chain of steps, which sets this kernel's
+  // time, is ~2.3x shorter
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = gt / BQ_LANES, sub = gt % BQ_LANES;
+  if (q >= *qcount) return;  // uniform over the entry's lanes
+  const unsigned gmask = ((1u << BQ_LANES) - 1u) << ((threadIdx.x & 31) & ~(BQ_LANES - 1));
   const int4 en = qent[q];
   const int p = en.x, j = en.y, b0 = en.z, b1 = en.w, idx = j - b0;
   const double* d = dbase + (size_t)p * strideV;
@@ -396,10 +403,18 @@ stebz_bisect_kernel(int n, const double* __restrict__ dbase, long long strideV, 
     const double mid = 0.5 * (lo + hi);
     const double tol = fmax(2.0 * eps * fmax(fabs(lo), fabs(hi)), eps * tn);
     if (hi - lo <= tol || mid <= lo || mid >= hi) break;
-    if (sturm64_count(d, e2, b0, b1, mid, tn) > idx) hi = mid;
-    else lo = mid;
+    const double h = (hi - lo) / (BQ_LANES + 1);
+    const double x = lo + h * (sub + 1);
+    const bool above = (x > lo && x < hi) ? sturm64_count(d, e2, b0, b1, x, tn) > idx : x >= hi;
+    // the lowest point with more than idx eigenvalues below it bounds the eigenvalue from
+    // above, the point before it from below (every lane forms the same bracket)
+    const unsigned ab = __ballot_sync(gmask, above) & gmask;
+    const int k = ab ? __ffs(ab) - 1 - ((threadIdx.x & 31) & ~(BQ_LANES - 1)) : BQ_LANES;
+    const double xk = lo + h * (k + 1), xk1 = lo + h * k;
+    if (k < BQ_LANES) hi = xk;
+    if (k > 0) lo = xk1;
   }
-  wslot[(size_t)p * n + j] = 0.5 * (lo + hi);
+  if (sub == 0) wslot[(size_t)p * n + j] = 0.5 * (lo + hi);
 }
 
 // ---------------------------------------------------------------- kernel 2: eigenvectors
@@ -1162,7 +1177,7 @@ cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d,
                                                  tng);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  stebz_bisect_kernel<<<(unsigned)((cap + SZ_THREADS - 1) / SZ_THREADS), SZ_THREADS, 0, st>>>(n, d, strideV, e2g, tng,
+  stebz_bisect_kernel<<<(unsigned)((cap * BQ_LANES + SZ_THREADS - 1) / SZ_THREADS), SZ_THREADS, 0, st>>>(n, d, strideV, e2g, tng,
                                                                                              wslot, qcount, qent, qlo,
                                                                                              qhi);
   dim3 grid((n + ST_THREADS - 1) / ST_THREADS, nprob);
