@@ -90,6 +90,12 @@ typedef struct {
                                  lower bandwidth (panel QR and tensor-core updates), then
                                  band -> tridiagonal by bulge chasing, with a second
                                  back-transformation of the eigenvectors                      */
+  int mrrr_all;               /* 1: eigenvectors of both tridiagonals (Eigen_HH step 2 of
+                                 Parts 2 and 4) from the relatively robust representation of
+                                 each unreduced block shifted below its smallest eigenvalue
+                                 (dstegr's method) for every eigenvalue whose relative gap is
+                                 at least 1e-5, inverse iteration for the rest; 0 (default):
+                                 as overlap_mrrr says                                        */
 } nao_config;
 
 void nao_config_defaults(nao_config* cfg);

@@ -508,7 +508,8 @@ cudaError_t launch_report_timeout(int* flags, int32_t* status, int nstatus, cuda
 static int check_config(const nao_config& c) {
   return (c.f_min >= 0.0 && c.f_min <= 1e-3 && c.inverse_iteration_max >= 0 && c.inverse_iteration_max <= 64 &&
           c.tc_wait_cycles >= 1 && c.tc_wait_cycles <= 1000000000000LL && c.mixed_planes >= 5 && c.mixed_planes <= 7 &&
-          (c.overlap_mrrr == 0 || c.overlap_mrrr == 1) && (c.band_width == 0 || c.band_width == 16 || c.band_width == 32))
+          (c.overlap_mrrr == 0 || c.overlap_mrrr == 1) && (c.band_width == 0 || c.band_width == 16 || c.band_width == 32) &&
+          (c.mrrr_all == 0 || c.mrrr_all == 1))
              ? NAO_OK
              : NAO_E_INVALID;
 }
@@ -544,6 +545,7 @@ void nao_config_defaults(nao_config* cfg) {
   cfg->mixed_planes = NAO_MIXED_PLANES_DEFAULT;
   cfg->overlap_mrrr = NAO_OVERLAP_MRRR_DEFAULT;
   cfg->band_width = NAO_BAND_WIDTH_DEFAULT;
+  cfg->mrrr_all = NAO_MRRR_ALL_DEFAULT;
 }
 
 int nao_init(nao_ctx** out, int device, size_t hbm_budget_bytes, const nao_config* cfg) {
@@ -780,9 +782,10 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
     NAO_CUDA_TRY(ctx, hetrd_two_stage(ctx, n, nSe, nullptr, AS, dS, eS, tauS, sbr, B2, ozws, st, NAO_OZ_DIGITS_FP64));
   else
     NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nSe, nullptr, AS, dS, eS, tauS, VWp, ozws, st, NAO_OZ_DIGITS_FP64, digp, erowp));
-  NAO_STAGE("stein", ctx->cfg.overlap_mrrr ? 5 : 4,
+  const int mrrr_s = ctx->cfg.mrrr_all ? 2 : ctx->cfg.overlap_mrrr, mrrr_h = ctx->cfg.mrrr_all ? 2 : 0;
+  NAO_STAGE("stein", mrrr_s ? 5 : 4,
             launch_stein(n, nSe, nullptr, dS, eS, n, wS, Z, n, snn, scr, stS, nullptr, n,
-                         ctx->cfg.inverse_iteration_max, ctx->cfg.overlap_mrrr, st));
+                         ctx->cfg.inverse_iteration_max, mrrr_s, st));
   NAO_STAGE("misc", 1, launch_count_kept(n, nSe, wS, n, s_cut, mS, stS, st));
   double* Zo = Z2;  // the Newton-Schulz result (Z itself on the tensor-core method)
   {  // one Newton-Schulz step: Z (3I - Z^T Z)/2 = Z - Z (Z^T Z - I)/2
@@ -825,8 +828,8 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
   const bool all_vecs = mixed && ctx->refine_sweeps >= 0;
   const int32_t* nvP = all_vecs ? mP : nbP;
   const int nv_max = (C || all_vecs) ? n : 0;
-  NAO_STAGE("stein", 4, launch_stein(n, nprob, mP, dH, eH, n, wH, Z, n, snn, scr, stH, nvP, nv_max,
-                                     ctx->cfg.inverse_iteration_max, 0, st));
+  NAO_STAGE("stein", mrrr_h ? 5 : 4, launch_stein(n, nprob, mP, dH, eH, n, wH, Z, n, snn, scr, stH, nvP, nv_max,
+                                                 ctx->cfg.inverse_iteration_max, mrrr_h, st));
   if (nv_max > 0) {
     {
       GemmDims d{n, n, n, nvP, nvP, mP, 1};

@@ -100,6 +100,7 @@ constexpr long long NAO_TC_WAIT_DEFAULT = 4000000000LL;  // ~2 s at 2 GHz
 constexpr int NAO_MIXED_PLANES_DEFAULT = 6;
 constexpr int NAO_OVERLAP_MRRR_DEFAULT = 1;
 constexpr int NAO_BAND_WIDTH_DEFAULT = 0;  // one-stage tridiagonalization
+constexpr int NAO_MRRR_ALL_DEFAULT = 0;    // MRRR vectors only for the overlap's big clusters
 
 // Workspace bytes nao_gen_eig / nao_density_matrix reserve on this context (before the
 // arena's 1/8 headroom); the scheduler's admission test uses them.
@@ -206,9 +207,10 @@ size_t stein_scratch_doubles(int n, int nprob);
 // nvec (nullable: all) and nvec_max bound the eigenvectors computed per problem to the lowest
 // min(nvec[p], nvec_max); the eigenvalues are always all computed.
 // maxits: inverse-iteration solves per vector before NAO_E_NOCONV (nao_config).  mrrr: first
-// compute the vectors of relatively well separated eigenvalues from a relatively robust
-// representation (positive semidefinite T only: the overlap's tridiagonal); inverse iteration
-// takes the rest.
+// compute vectors from a relatively robust representation L D L^T of T - sigma I (sigma just
+// below each unreduced block's smallest eigenvalue) for the members of big tight clusters
+// whose relative gap allows (1), or for every eigenvalue whose relative gap allows (2);
+// inverse iteration takes the rest (and everything at 0).
 cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d, const double* e,
                          long long strideV, double* w, double* Z, int ld, long long strideZ,
                          double* scratch, int32_t* status, const int32_t* nvec, int nvec_max, int maxits,

@@ -928,7 +928,7 @@ __global__ void __launch_bounds__(MR_THREADS)
 mrrr_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ dbase,
                 const double* __restrict__ ebase, long long strideV, const double* __restrict__ wslot,
                 double* __restrict__ Zbase, int ldz, long long strideZ, double* __restrict__ scratch,
-                int* __restrict__ mdone, const int32_t* __restrict__ nvec, int nvec_max) {
+                int* __restrict__ mdone, const int32_t* __restrict__ nvec, int nvec_max, int all) {
   extern __shared__ double smr[];
   double* w = smr;           // [n] eigenvalues (slot order)
   double* D = smr + n;       // [n] root representation of each unreduced block
@@ -962,8 +962,8 @@ mrrr_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restric
     __syncthreads();
     // only the members of big tight clusters (more than BIG members, the ones kernel 3 would
     // re-orthogonalise at O(k^2 n)); smaller clusters are cheap by inverse iteration
-    bool big = false;
-    if (jj < m) {
+    bool big = all != 0;  // all: every slot whose relative gap allows, not only big clusters
+    if (jj < m && !big) {
       int c = 1;
       for (int t = jj; t > 0 && c <= BIG && fabs(w[t] - w[t - 1]) < tb; --t) ++c;
       for (int t = jj; t < m - 1 && c <= BIG && fabs(w[t + 1] - w[t]) < tb; ++t) ++c;
@@ -1042,8 +1042,8 @@ mrrr_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restric
   const double mu0 = wj - sg;
   const double gl = j > b0 ? wj - w[j - 1] : INFINITY, gr = j < b1 - 1 ? w[j + 1] - wj : INFINITY;
   const double tn = s_tn;
-  // only members of big tight clusters (as above, now within the split block)
-  {
+  // only members of big tight clusters (as above, now within the split block), unless all
+  if (!all) {
     int c = 1;
     for (int t = j; t > b0 && c <= BIG && w[t] - w[t - 1] < TIGHT * tn; --t) ++c;
     for (int t = j; t < b1 - 1 && c <= BIG && w[t + 1] - w[t] < TIGHT * tn; ++t) ++c;
@@ -1196,7 +1196,7 @@ cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d,
     if (err != cudaSuccess) return err;
     dim3 grid0((n + MR_THREADS - 1) / MR_THREADS, nprob);
     mrrr_vec_kernel<<<grid0, MR_THREADS, smem0, st>>>(n, size, d, e, strideV, wslot, Z, ld, strideZ, scratch, mdone,
-                                                       nvec, nvec_max);
+                                                       nvec, nvec_max, mrrr == 2);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }

@@ -6,7 +6,8 @@ A small driver for tracing and profiling one configuration through the public bi
     python -m paper_1402_4247_gb300.run_case --large-basis 1000 --kgrid 1 1 1 --nspin 1
 
 prints the per-stage times recorded by the library's CUDA-event tracing (after --warmup
-untraced steps).  --band-width selects the two-stage Householder reduction (nao_config);
+untraced steps).  --band-width selects the two-stage Householder reduction and --mrrr-all the
+relatively robust representations for the eigenvectors of both tridiagonals (nao_config);
 --large-basis n takes the large-basis cell of order n (overlap condition ~1e8, one orbital
 in 50 duplicated) instead of the magnetite-shaped one.
 """
@@ -30,6 +31,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=0)
     ap.add_argument("--band-width", type=int, default=0, choices=[0, 16, 32])
     ap.add_argument("--large-basis", type=int, default=0, metavar="N")
+    ap.add_argument("--mrrr-all", action="store_true",
+                    help="eigenvectors of both tridiagonals from relatively robust representations")
     args = ap.parse_args()
     if args.large_basis:
         inp = synth.scaled_cell(args.large_basis, seed=3, kgrid=tuple(args.kgrid), nspin=args.nspin,
@@ -37,7 +40,7 @@ def main():
     else:
         inp = synth.magnetite_cell(seed=args.seed, kgrid=tuple(args.kgrid), nspin=args.nspin)
     dev = torch.device("cuda:0")
-    ctx = Context(0, config={"band_width": args.band_width})
+    ctx = Context(0, config={"band_width": args.band_width, "mrrr_all": int(args.mrrr_all)})
     n, nk, nprob = inp.n, inp.nk, inp.nprob
     HR = torch.from_numpy(inp.HR).to(dev)
     SR = torch.from_numpy(inp.SR)[None].to(dev)

@@ -218,3 +218,55 @@ def test_gap_band_spectrum_without_cluster_rule():
         worst = max(worst, a_gpu / (10.0 * a_ref + 1e-10))
         assert a_gpu <= 10.0 * a_ref + 1e-10, (j, a_gpu, a_ref)
     print(f"\ngap band n={n}: residual {res:.2e}, C^H S C - I {orth:.2e}, worst vector angle / bound {worst:.2f}")
+
+
+@pytest.fixture(scope="module")
+def ctx_mrrr():
+    """Eigenvectors of both tridiagonals from relatively robust representations wherever the
+    relative gap allows (nao_config.mrrr_all), inverse iteration for the rest."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_4247_gb300.nao import Context
+    c = Context(0, config={"mrrr_all": 1})
+    assert c.nao_get_config()["mrrr_all"] == 1
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: synth.tiny_cell(),
+    lambda: synth.small_cell(31, 1, 2, kgrid=(2, 1, 1), nspin=2),       # n = 29
+    lambda: synth.small_cell(32, 3, 5, kgrid=(2, 2, 1), nspin=1),       # n = 79
+    lambda: synth.small_cell(33, 5, 8, kgrid=(1, 2, 1), nspin=2),       # n = 129
+], ids=["tiny64", "n29", "n79", "n129"])
+def test_band_step_mrrr_vectors_match_oracle(ctx_mrrr, maker):
+    inp = maker()
+    g = gpu_band_step(ctx_mrrr, inp, torch, DEV)
+    ref = _oracle(inp)
+    _compare_all(inp, g, ref)
+    drho = np.abs(g["rho"] - ref["rho"]).max()
+    assert drho <= TOL_RHO * max(1.0, np.abs(ref["rho"]).max()), f"rho differs by {drho:.3e}"
+
+
+@pytest.mark.parametrize("N,alpha,beta,s,k", [(64, 0.0, -1.0, 0.45, 0.0), (97, 0.05, -0.7, 0.2, 0.21)])
+def test_mrrr_vectors_chain_closed_form(ctx_mrrr, N, alpha, beta, s, k):
+    # k = 0: the degenerate pairs j, N - j (relative gap 0) fall back to inverse iteration
+    inp = synth.chain_1orb(N, alpha, beta, s, np.array([[k, 0.0, 0.0]]))
+    g = gpu_band_step(ctx_mrrr, inp, torch, DEV, density=False)
+    t = 2 * np.pi * (k + np.arange(N)) / N
+    exact = np.sort((alpha + 2 * beta * np.cos(t)) / (1 + 2 * s * np.cos(t)))
+    assert int(g["m"][0]) == N
+    assert np.abs(g["eps"][0] - exact).max() <= 1e-10 * np.abs(exact).max()
+    ref = _oracle(inp, problems=[0])
+    check_problem(ref["Hk"][0, 0], ref["Sk"][0], g["eps"][0], g["C"][0], int(g["m"][0]), ref["eps"][0], ref["C"][0],
+                  ref["m"][0], label=f"chain N={N}")
+
+
+@pytest.mark.parametrize("n", [2, 33, 130])
+def test_mrrr_vectors_random_pencils(ctx_mrrr, n):
+    rng = np.random.Generator(np.random.PCG64(900 + n))
+    H, S = synth.random_hermitian_pair(rng, n, cond=100.0)
+    e, C, m, st = _gen_eig_direct(ctx_mrrr, H, S)
+    eo, Co, mo, _ = oracle.generalized_eigensolve(H, S)
+    assert st == 0
+    check_problem(H, S, e, C, m, eo, Co, mo, label=f"random n={n}")
