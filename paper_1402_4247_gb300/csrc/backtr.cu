@@ -164,30 +164,55 @@ __global__ void init_u_kernel(int n, const int32_t* __restrict__ size, const int
 // T (nb x nb, row-major, upper triangular) of block j from G = V^H V (row-major, Hermitian):
 // T_ii = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) G(0:i, i).  One block of nb threads per
 // (block j, problem p); thread r owns row r of T, which it writes and reads back itself (in
-// global memory, cached), so only G's current column is shared (2 KB of shared memory: many
-// blocks per SM).  G and T of block j of problem p at (j nprob + p) nb^2.
+// global memory, cached).  Columns are formed BT_B at a time: the part of each dot product
+// over the finished columns is accumulated for all BT_B new columns from one read of the row
+// (the reads of T fall BT_B-fold), then the new columns follow one by one from registers;
+// the terms are added in the same order as one column at a time.  G's columns of the batch
+// sit in shared memory (row stride BT_B + 1: no bank conflicts).  G and T of block j of
+// problem p at (j nprob + p) nb^2.
+constexpr int BT_B = 8;
 __global__ void build_t_kernel(int nb, int nprob, const z64* __restrict__ Gbase, const z64* __restrict__ taucbase,
                                int ncolv, z64* __restrict__ Tbase) {
-  extern __shared__ z64 gcol[];  // nb
+  extern __shared__ z64 gs[];  // G(c, i0 + k) at gs[c (BT_B + 1) + k]
   const int p = blockIdx.x % nprob, j = blockIdx.x / nprob;
   const int r = threadIdx.x;
   const z64* G = Gbase + (size_t)blockIdx.x * nb * nb;
   const z64* tau = taucbase + (size_t)p * ncolv + (size_t)j * nb;
   z64* Tr = Tbase + (size_t)blockIdx.x * nb * nb + (size_t)r * nb;  // row r
   for (int c = 0; c < r; ++c) Tr[c] = zmk(0.0, 0.0);
-  for (int i = 0; i < nb; ++i) {
-    // G(0:i, i) = conj(G(i, 0:i)) (G is Hermitian): one coalesced load of row i
-    if (r < i) gcol[r] = zconj(G[(size_t)i * nb + r]);
-    __syncthreads();
-    if (r < i) {
-      z64 acc = zmk(0.0, 0.0);
-      for (int c = r; c < i; ++c) acc = zfma(Tr[c], gcol[c], acc);
-      const z64 ti = tau[i];
-      Tr[i] = zmul(zmk(-ti.x, -ti.y), acc);
-    } else if (r == i) {
-      Tr[i] = tau[i];
+  for (int i0 = 0; i0 < nb; i0 += BT_B) {
+    const int nbat = nb - i0 < BT_B ? nb - i0 : BT_B, L = i0 + nbat;
+    __syncthreads();  // the previous batch's reads of gs are done
+    // G(c, i) = conj(G(i, c)) (G is Hermitian): coalesced loads of rows i0 .. i0 + nbat - 1
+    for (int idx = r; idx < L * nbat; idx += nb) {
+      const int k = idx / L, c = idx - k * L;
+      gs[c * (BT_B + 1) + k] = zconj(G[(size_t)(i0 + k) * nb + c]);
     }
     __syncthreads();
+    z64 acc[BT_B], tb[BT_B];
+#pragma unroll
+    for (int k = 0; k < BT_B; ++k) acc[k] = zmk(0.0, 0.0);
+    for (int c = r; c < i0; ++c) {  // finished columns
+      const z64 t = Tr[c];
+#pragma unroll
+      for (int k = 0; k < BT_B; ++k) acc[k] = zfma(t, gs[c * (BT_B + 1) + k], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < BT_B; ++k) {
+      if (k < nbat) {
+        const int i = i0 + k;
+        z64 a = acc[k];
+#pragma unroll
+        for (int c2 = 0; c2 < k; ++c2)  // the batch's earlier columns c = i0 + c2 >= r
+          if (i0 + c2 >= r) a = zfma(tb[c2], gs[(i0 + c2) * (BT_B + 1) + k], a);
+        const z64 ti = tau[i];
+        z64 tv = zmk(0.0, 0.0);
+        if (r < i) tv = zmul(zmk(-ti.x, -ti.y), a);
+        else if (r == i) tv = ti;
+        tb[k] = tv;
+        if (r <= i) Tr[i] = tv;
+      }
+    }
   }
 }
 
@@ -229,7 +254,7 @@ cudaError_t launch_init_u(int n, int nprob, const int32_t* size, const int32_t* 
 
 cudaError_t launch_build_t(int nb, int nprob, int nblk, const z64* G, const z64* tauc, int ncolv, z64* T,
                            cudaStream_t st) {
-  const size_t smem = (size_t)nb * sizeof(z64);
+  const size_t smem = (size_t)nb * (BT_B + 1) * sizeof(z64);
   build_t_kernel<<<nprob * nblk, nb, smem, st>>>(nb, nprob, G, tauc, ncolv, T);
   return cudaGetLastError();
 }

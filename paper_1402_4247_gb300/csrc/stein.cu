@@ -44,7 +44,11 @@ constexpr int ST_THREADS = 64;    // = slots per block (eigenvectors): the overl
                                   // has ~36k of them, so 64-thread blocks spread over all SMs
 constexpr int SZ_THREADS = 64;    // = slots per block (eigenvalues): ~8 blocks per SM for 128 problems
                                   // of n = 568, so the SMs' FP64 pipes finish within one block of each other
-constexpr int EXTRA = 2;          // extra solves after the growth test passes
+constexpr int EXTRA = 2;          // extra solves after the growth test passes (members of tight clusters)
+constexpr int EXTRA_ISOLATED = 1; // the same for an eigenvalue outside any tight cluster: its gap is at
+                                  // least 1e-9 |T|_1, so each solve shrinks the other eigenvectors'
+                                  // components by eps |T| / gap < 1.2e-7, and one solve past the growth
+                                  // test leaves them below ~1e-14
 constexpr double TIGHT = 1e-9;
 constexpr int NARR = 6;           // scratch arrays per eigenvalue: L, U0inv, U1, U2, PIV, X
 constexpr int BIG = 32;           // tight clusters with more members go to stein_cluster_kernel
@@ -611,7 +615,7 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
           if (its > maxits && nrmchk == 0) break;
           if (xinf < sqrt(0.1 / bs)) continue;
           ++nrmchk;
-          if (nrmchk < EXTRA + 1) continue;
+          if (nrmchk < (jend - j > 1 ? EXTRA : EXTRA_ISOLATED) + 1) continue;
           ok = true;
           break;
         }
