@@ -753,6 +753,8 @@ def run_ours(args, rank, world, local_rank):
     # relatively robust representations (dstegr's method) wherever the relative gap allows
     two_stage = {f"band_width_{bw}": alternative({"band_width": bw}) for bw in (32, 16)}
     mrrr_vectors = alternative({"mrrr_all": 1})
+    # Parts 3-4 as two staggered halves of the problems on two streams
+    split_hprime = alternative({"split_hprime": 2})
 
     serve = run_serve(local_rank) if (world == 1 and not args.no_serve) else None
     serve_stated = run_serve_stated(local_rank) if (world == 1 and not args.no_serve and not args.quick) else None
@@ -825,7 +827,7 @@ def run_ours(args, rank, world, local_rank):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu, "mixed": mixed, "subset": subset, "serve": serve,
             "mixed_n2000": mixed_n2000, "large_basis": large_basis, "serve_stated": serve_stated,
-            "two_stage": two_stage, "mrrr_vectors": mrrr_vectors,
+            "two_stage": two_stage, "mrrr_vectors": mrrr_vectors, "split_hprime": split_hprime,
             "status_ok": bool(int(st.abs().sum()) == 0 and int(rst[0]) == 0),
         }
         print(json.dumps(line), flush=True)

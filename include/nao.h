@@ -96,6 +96,13 @@ typedef struct {
                                  (dstegr's method) for every eigenvalue whose relative gap is
                                  at least 1e-5, inverse iteration for the rest; 0 (default):
                                  as overlap_mrrr says                                        */
+  int split_hprime;           /* Parts 3-4 of an FP64 one-stage nao_gen_eig call as two halves
+                                 of the problems on two streams of the context, the second
+                                 starting once the first half's Part 3 products are done, so
+                                 that its products run beside the first half's Householder
+                                 panels; the results are ordered on the caller's stream as
+                                 before.  0 (default): one pass; 1: split whenever there are
+                                 at least 2 problems; 2: split from 32 problems on           */
 } nao_config;
 
 void nao_config_defaults(nao_config* cfg);

@@ -183,10 +183,12 @@ struct GenEigPlan {
   size_t oAS, oTauS, odS, oeS, owS, oZ, oZ2, oG, oScr, omS, ostS, oX, oHf, oY, oHp, oV, oTauH, odH, oeH, owH, omP, onbP, ostP, ostH, oOz, oVf, oTc, oG2, oT2, oW, oW2, oVW, oDig, oErow;
   // two-stage reduction (band width B2 > 0): V T, the panel's small matrices, band, stage-2 reflectors
   size_t oSVT, oSG, oST, oSM, oSN, oSTc, oSAB, oSV2, oSTau2;
+  // split Parts 3-4: the second half's inverse-iteration scratch and product workspace
+  size_t oScr2, oOz2;
   size_t bytes;
 };
 
-GenEigPlan plan_gen_eig(int n, int nprob, int nSe, bool use_tc, int B2) {
+GenEigPlan plan_gen_eig(int n, int nprob, int nSe, bool use_tc, int B2, bool split = false) {
   GenEigPlan W;
   WsPlan P;
   const size_t nn = (size_t)n * n;
@@ -246,6 +248,9 @@ GenEigPlan plan_gen_eig(int n, int nprob, int nSe, bool use_tc, int B2) {
   W.oSAB = P.take<z64>(2 * b2 * n * nmax + 1);
   W.oSV2 = P.take<z64>(sq * b2 * nmax + 1);
   W.oSTau2 = P.take<z64>(sq * nmax + 1);
+  const int np2 = nprob - nprob / 2;
+  W.oScr2 = P.take<double>(split ? stein_scratch_doubles(n, np2) : 1);
+  W.oOz2 = P.take<char>(split && use_tc ? zgemm_oz_workspace(np2, dmax) : 1);
   W.bytes = P.off;
   return W;
 }
@@ -363,13 +368,15 @@ cudaError_t backtransform_blocked(nao_ctx* ctx, int n, int nprob, const int32_t*
 // (NAO_HT_DIGITS_FP64, or NAO_HT_DIGITS_MIXED for the H' reduction of the mixed mode).
 cudaError_t hetrd_blocked(nao_ctx* ctx, int n, int nprob, const int32_t* size, z64* A, double* d, double* e, z64* tau,
                           z64* VW, void* ozws, cudaStream_t st, int digits, void* dig, int* erow,
-                          int panel_digits = NAO_HT_DIGITS_FP64) {
+                          int panel_digits = NAO_HT_DIGITS_FP64, int cluster_nprob = 0) {
   // exact integer matrix-vector products with the tensor-core method; FP64 FMAs otherwise
   // (up to the order whose digit words still fit in a block's shared memory)
   const bool use_dig = ctx->gemm_method == NAO_GEMM_TC && dig != nullptr && hetrd_digits_fit(n, panel_digits);
   const int pd = use_dig ? panel_digits : 0;
   const int NB = NAO_HT_NB;
-  const int cl = hetrd_cluster_size(n, nprob, ctx->num_sms, pd);
+  // cluster size from the number of matrices that share the GPU (cluster_nprob: a concurrent
+  // launch's matrices included)
+  const int cl = hetrd_cluster_size(n, cluster_nprob > 0 ? cluster_nprob : nprob, ctx->num_sms, pd);
   const long long snn = (long long)n * n, svw = (long long)n * 3 * NB;
   for (int i0 = 0; i0 < n; i0 += NB) {
     cudaError_t err = cudaSuccess;
@@ -509,7 +516,7 @@ static int check_config(const nao_config& c) {
   return (c.f_min >= 0.0 && c.f_min <= 1e-3 && c.inverse_iteration_max >= 0 && c.inverse_iteration_max <= 64 &&
           c.tc_wait_cycles >= 1 && c.tc_wait_cycles <= 1000000000000LL && c.mixed_planes >= 5 && c.mixed_planes <= 7 &&
           (c.overlap_mrrr == 0 || c.overlap_mrrr == 1) && (c.band_width == 0 || c.band_width == 16 || c.band_width == 32) &&
-          (c.mrrr_all == 0 || c.mrrr_all == 1))
+          (c.mrrr_all == 0 || c.mrrr_all == 1) && (c.split_hprime >= 0 && c.split_hprime <= 2))
              ? NAO_OK
              : NAO_E_INVALID;
 }
@@ -522,7 +529,10 @@ static cudaError_t push_wait_bound(nao_ctx* c) {
 
 size_t gen_eig_ws_bytes(const nao_ctx* ctx, int n, int nprob, int nSe) {
   const bool use_tc = ctx->gemm_method == NAO_GEMM_TC && zgemm_oz_supported(GemmDims{n, n, n, nullptr, nullptr, nullptr, 0});
-  return plan_gen_eig(n, nprob, nSe, use_tc, ctx->cfg.band_width).bytes;
+  return plan_gen_eig(n, nprob, nSe, use_tc, ctx->cfg.band_width,
+                      ctx->cfg.band_width == 0 && nprob >= 2 &&
+                          (ctx->cfg.split_hprime == 1 ||
+                           (ctx->cfg.split_hprime == 2 && nprob >= NAO_SPLIT_MIN_PROBLEMS))).bytes;
 }
 
 size_t density_ws_bytes(const nao_ctx* ctx, int n, int nspin, int nk, int nR, int nb) {
@@ -546,6 +556,7 @@ void nao_config_defaults(nao_config* cfg) {
   cfg->overlap_mrrr = NAO_OVERLAP_MRRR_DEFAULT;
   cfg->band_width = NAO_BAND_WIDTH_DEFAULT;
   cfg->mrrr_all = NAO_MRRR_ALL_DEFAULT;
+  cfg->split_hprime = NAO_SPLIT_HPRIME_DEFAULT;
 }
 
 int nao_init(nao_ctx** out, int device, size_t hbm_budget_bytes, const nao_config* cfg) {
@@ -593,6 +604,9 @@ void nao_destroy(nao_ctx* ctx) {
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->dev_flags) cudaFree(ctx->dev_flags);
+    if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+    if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
   }
   delete ctx;
 }
@@ -741,7 +755,10 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
 
   const bool use_tc = ctx->gemm_method == NAO_GEMM_TC && zgemm_oz_supported(GemmDims{n, n, n, nullptr, nullptr, nullptr, 0});
   const int B2 = ctx->cfg.band_width;  // 0: one-stage reduction
-  const GenEigPlan W = plan_gen_eig(n, nprob, nSe, use_tc, B2);
+  // Parts 3-4 in two halves on two streams (FP64, one-stage only)
+  const bool split = B2 == 0 && precision == NAO_FP64 && nprob >= 2 &&
+                     (ctx->cfg.split_hprime == 1 || (ctx->cfg.split_hprime == 2 && nprob >= NAO_SPLIT_MIN_PROBLEMS));
+  const GenEigPlan W = plan_gen_eig(n, nprob, nSe, use_tc, B2, split);
   const int ncolv = (n + NAO_WY_NB - 1) / NAO_WY_NB * NAO_WY_NB;
   int rc = nao_ws_reserve(ctx, W.bytes);
   if (rc) return rc;
@@ -804,6 +821,113 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
     NAO_CUDA_TRY(ctx, cudaGetLastError());
   }
 
+  if (split) {
+    // Parts 3-4 for problems [p0, p0 + np) on stream st, with the workspace slices of that half:
+    // per-problem arrays at the half's offset, the arrays laid out by the half's own problem
+    // count (the panel's [V | W | V], the WY blocks' G and T, the digit planes) after the first
+    // half's, the inverse-iteration scratch and the product workspace in regions of their own
+    struct HpHalf {
+      const z64* H;
+      const z64* X;
+      const int32_t* xmap;
+      z64 *Hf, *Y, *Hp, *V, *tauH, *Vf, *tauc, *Gw, *Tw, *Ww, *VTw, *VWp, *C;
+      double *dH, *eH, *wH, *Z, *Z2, *G, *scr, *eps;
+      int32_t *mP, *nbP, *stH;
+      void *ozws, *digp;
+      int* erowp;
+    };
+    auto hp_half = [&](int np, cudaStream_t st, const HpHalf& h, cudaEvent_t part3_done) -> int {
+      NAO_STAGE("herm_fill", 1, launch_herm_fill(n, np, h.H, snn, nullptr, h.Hf, n, snn, st));
+      {
+        GemmDims d{n, n, n, nullptr, h.mP, nullptr};  // Y = Hf X : n x m
+        NAO_CUDA_TRY(ctx, run_zgemm(ctx, "zgemm_HX", np, d, 1.0, GemmOperand{h.Hf, snn, 1, n, 0, nullptr},
+                                    GemmOperand{h.X, snn, 1, n, 0, h.xmap}, 0.0, h.Y, snn, 1, n, h.ozws, st, dig));
+        GemmDims d2{n, n, n, h.mP, h.mP, nullptr, 1};  // Hp = X^H Y : m x m, lower triangle
+        NAO_CUDA_TRY(ctx, run_zgemm(ctx, "zgemm_XHY", np, d2, 1.0, GemmOperand{h.X, snn, n, 1, 1, h.xmap},
+                                    GemmOperand{h.Y, snn, 1, n, 0, nullptr}, 0.0, h.Hp, snn, 1, n, h.ozws, st, dig));
+      }
+      NAO_STAGE("misc", 1, launch_hermitize(n, np, h.mP, h.Hp, n, snn, st));
+      if (part3_done) NAO_CUDA_TRY(ctx, cudaEventRecord(part3_done, st));
+      NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, np, h.mP, h.Hp, h.dH, h.eH, h.tauH, h.VWp, h.ozws, st, dig, h.digp,
+                                      h.erowp, NAO_HT_DIGITS_FP64, nprob));
+      const int nv_max = C ? n : 0;
+      NAO_STAGE("stein", mrrr_h ? 5 : 4, launch_stein(n, np, h.mP, h.dH, h.eH, n, h.wH, h.Z, n, snn, h.scr, h.stH,
+                                                     h.nbP, nv_max, ctx->cfg.inverse_iteration_max, mrrr_h, st));
+      if (nv_max > 0) {
+        GemmDims d{n, n, n, h.nbP, h.nbP, h.mP, 1};
+        NAO_CUDA_TRY(ctx, run_dgemm(ctx, "ortho_ns", np, d, 1.0, GemmOperand{h.Z, snn, n, 1, 0, nullptr},
+                                    GemmOperand{h.Z, snn, 1, n, 0, nullptr}, 0.0, h.G, snn, 1, n, h.ozws, st));
+        cudaError_t e = cudaSuccess;
+        double* Zh = ns_correct(ctx, n, np, h.mP, h.nbP, h.Z, h.G, h.Z2, h.ozws, st, &e);
+        NAO_CUDA_TRY(ctx, e);
+        NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, np, h.mP, h.nbP, h.Hp, h.tauH, Zh, h.wH, 0, h.V, h.Vf, h.tauc,
+                                                h.Gw, h.Tw, h.Ww, h.VTw, h.ozws, st, dig, 1));
+        GemmDims dc{n, nb, n, nullptr, h.nbP, h.mP};  // C = X V(:, :nb) : n x nb, row-major [n][nb]
+        NAO_CUDA_TRY(ctx, run_zgemm(ctx, "zgemm_XV", np, dc, 1.0, GemmOperand{h.X, snn, 1, n, 0, h.xmap},
+                                    GemmOperand{h.V, snn, 1, n, 0, nullptr}, 0.0, h.C, (long long)n * nb, nb, 1,
+                                    h.ozws, st, dig));
+        NAO_STAGE("misc", 1, launch_zero_cols(n, np, nb, h.mP, h.C, st));
+      }
+      NAO_STAGE("misc", 1, launch_write_eps(n, np, h.mP, h.wH, n, h.eps, st));
+      return NAO_OK;
+    };
+    if (!ctx->aux_stream) {
+      NAO_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
+      NAO_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
+      NAO_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming));
+    }
+    const int np1 = nprob / 2, np2 = nprob - np1;
+    const int nblkw = n > 1 ? (n - 1 + NAO_WY_NB - 1) / NAO_WY_NB : 1;
+    const long long svf = (long long)n * ncolv, svw = (long long)n * 3 * NAO_HT_NB;
+    auto half = [&](int p0, int np, double* scr_h, void* oz_h, char* dig_h) {
+      HpHalf h;
+      h.H = (const z64*)H + (size_t)p0 * nn;
+      h.X = s_of_prob ? X : X + (size_t)p0 * nn;
+      h.xmap = s_of_prob ? s_of_prob + p0 : nullptr;
+      h.Hf = Hf + (size_t)p0 * nn;
+      h.Y = Y + (size_t)p0 * nn;
+      h.Hp = Hp + (size_t)p0 * nn;
+      h.V = V + (size_t)p0 * nn;
+      h.tauH = tauH + (size_t)p0 * n;
+      h.Vf = Vf + (size_t)p0 * svf;
+      h.tauc = tauc + (size_t)p0 * ncolv;
+      h.Gw = Gw + (size_t)nblkw * p0 * NAO_WY_NB * NAO_WY_NB;
+      h.Tw = Tw + (size_t)nblkw * p0 * NAO_WY_NB * NAO_WY_NB;
+      h.Ww = Ww + (size_t)p0 * NAO_WY_NB * n;
+      h.VTw = VTw + (size_t)p0 * svf;
+      h.VWp = VWp + (size_t)2 * p0 * svw;
+      h.C = C ? (z64*)C + (size_t)p0 * n * nb : nullptr;
+      h.dH = dH + (size_t)p0 * n;
+      h.eH = eH + (size_t)p0 * n;
+      h.wH = wH + (size_t)p0 * n;
+      h.Z = Z + (size_t)p0 * nn;
+      h.Z2 = use_tc ? Z2 : Z2 + (size_t)p0 * nn;
+      h.G = G + (size_t)p0 * nn;
+      h.scr = scr_h;
+      h.eps = eps + (size_t)p0 * n;
+      h.mP = mP + p0;
+      h.nbP = nbP + p0;
+      h.stH = stH + p0;
+      h.ozws = oz_h;
+      h.digp = dig_h;
+      h.erowp = erowp + (size_t)p0 * (n > 1 ? n - 1 : 1);
+      (void)np;
+      return h;
+    };
+    const HpHalf h1 = half(0, np1, scr, ozws, (char*)digp);
+    const HpHalf h2 = half(np1, np2, (double*)(ws + W.oScr2), use_tc ? (void*)(ws + W.oOz2) : nullptr,
+                           digp ? (char*)digp + hetrd_digits_bytes(n, np1, NAO_HT_DIGITS_FP64) : nullptr);
+    // the second half starts when the first half's Part 3 products are done, so that its
+    // products (tensor cores) run beside the first half's Householder panels (integer and
+    // FP64 pipes) instead of competing with the same kind of work
+    rc = hp_half(np1, st, h1, ctx->fork_ev);
+    if (rc) return rc;
+    NAO_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->aux_stream, ctx->fork_ev, 0));
+    rc = hp_half(np2, ctx->aux_stream, h2, nullptr);
+    if (rc) return rc;
+    NAO_CUDA_TRY(ctx, cudaEventRecord(ctx->join_ev, ctx->aux_stream));
+    NAO_CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->join_ev, 0));
+  } else {
   // ---- Part 3: H' = X^H H X
   NAO_STAGE("herm_fill", 1, launch_herm_fill(n, nprob, (const z64*)H, snn, nullptr, Hf, n, snn, st));
   {
@@ -899,6 +1023,7 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
     }
     NAO_STAGE("misc", 1, launch_write_eps(n, nprob, mP, wH, n, eps, st));
   }
+  }  // one pass of Parts 3-4
   {
     NaoStage stage_(ctx, "misc", st, 1);
     finish_status_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(nprob, mP, stP, stH, ctx->dev_flags, m_kept, status);

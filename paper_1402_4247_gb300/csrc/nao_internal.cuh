@@ -84,6 +84,8 @@ struct nao_ctx {
   size_t hbm_budget = 0;     // bound on the workspace arena (0: none)
   nao_config cfg{};          // run-time settings (nao_init / nao_set_config)
   struct NaoServer* server = nullptr;  // request scheduler (csrc/serve.cu), made on first use
+  cudaStream_t aux_stream = nullptr;   // second stream of split Parts 3-4 (made on first use)
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 };
 
 // Layout of nao_ctx::dev_flags (64 ints of device memory):
@@ -101,6 +103,8 @@ constexpr int NAO_MIXED_PLANES_DEFAULT = 6;
 constexpr int NAO_OVERLAP_MRRR_DEFAULT = 1;
 constexpr int NAO_BAND_WIDTH_DEFAULT = 0;  // one-stage tridiagonalization
 constexpr int NAO_MRRR_ALL_DEFAULT = 0;    // MRRR vectors only for the overlap's big clusters
+constexpr int NAO_SPLIT_HPRIME_DEFAULT = 0;  // one pass of Parts 3-4 (2: split from NAO_SPLIT_MIN_PROBLEMS on)
+constexpr int NAO_SPLIT_MIN_PROBLEMS = 32;
 
 // Workspace bytes nao_gen_eig / nao_density_matrix reserve on this context (before the
 // arena's 1/8 headroom); the scheduler's admission test uses them.

@@ -48,7 +48,8 @@ class NaoConfig(ctypes.Structure):
     """``nao_config`` of include/nao.h."""
     _fields_ = [("f_min", ctypes.c_double), ("inverse_iteration_max", ctypes.c_int),
                 ("tc_wait_cycles", ctypes.c_longlong), ("mixed_planes", ctypes.c_int),
-                ("overlap_mrrr", ctypes.c_int), ("band_width", ctypes.c_int), ("mrrr_all", ctypes.c_int)]
+                ("overlap_mrrr", ctypes.c_int), ("band_width", ctypes.c_int), ("mrrr_all", ctypes.c_int),
+                ("split_hprime", ctypes.c_int)]
 
 
 class NaoRequest(ctypes.Structure):

@@ -270,3 +270,49 @@ def test_mrrr_vectors_random_pencils(ctx_mrrr, n):
     eo, Co, mo, _ = oracle.generalized_eigensolve(H, S)
     assert st == 0
     check_problem(H, S, e, C, m, eo, Co, mo, label=f"random n={n}")
+
+
+@pytest.fixture(scope="module")
+def ctx_split():
+    """Parts 3-4 as two halves of the problems on two streams (nao_config.split_hprime)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_4247_gb300.nao import Context
+    c = Context(0, config={"split_hprime": 1})
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: synth.small_cell(31, 1, 2, kgrid=(2, 1, 1), nspin=2),       # n = 29, 4 problems
+    lambda: synth.small_cell(32, 3, 5, kgrid=(3, 1, 1), nspin=1),       # n = 79, 3 problems: halves of 1 and 2
+    lambda: synth.small_cell(33, 5, 8, kgrid=(1, 2, 1), nspin=2),       # n = 129
+    lambda: synth.small_cell(37, 2, 4, kgrid=(3, 3, 1), nspin=2),       # nk = 9, 18 problems
+], ids=["n29", "n79-odd", "n129", "nk9"])
+def test_band_step_split_halves_match_oracle(ctx_split, maker):
+    inp = maker()
+    g = gpu_band_step(ctx_split, inp, torch, DEV)
+    ref = _oracle(inp)
+    _compare_all(inp, g, ref)
+    assert int(g["rstatus"][0]) == 0
+    drho = np.abs(g["rho"] - ref["rho"]).max()
+    assert drho <= TOL_RHO * max(1.0, np.abs(ref["rho"]).max()), f"rho differs by {drho:.3e}"
+
+
+def test_split_halves_subset_and_no_vectors(ctx_split):
+    inp = synth.small_cell(34, 2, 2, kgrid=(2, 1, 1), nspin=1)  # n = 42, 2 problems
+    g = gpu_band_step(ctx_split, inp, torch, DEV, nb=17, density=False)
+    ref = _oracle(inp, problems=list(range(inp.nprob)))
+    for p in range(inp.nprob):
+        check_problem(ref["Hk"][0, p], ref["Sk"][p], g["eps"][p], g["C"][p], int(g["m"][p]), ref["eps"][p],
+                      ref["C"][p], ref["m"][p], label=f"split nb17 p={p}")
+    t = {k: torch.from_numpy(v).to(DEV) for k, v in (("HR", inp.HR), ("SR", inp.SR[None]), ("R", inp.R),
+                                                     ("k", inp.kpts))}
+    Hk = ctx_split.nao_bloch_sum(t["HR"], t["R"], t["k"]).reshape(-1, inp.n, inp.n)
+    Sk = ctx_split.nao_bloch_sum(t["SR"], t["R"], t["k"])[0]
+    eps, C, m, st = ctx_split.nao_gen_eig(Hk, Sk, want_vectors=False)
+    torch.cuda.synchronize()
+    e = eps.cpu().numpy()
+    for p in range(inp.nprob):
+        hn = np.abs(ref["eps"][p]).max()
+        assert np.abs(e[p][:ref["m"][p]] - ref["eps"][p]).max() <= 1e-10 * hn
