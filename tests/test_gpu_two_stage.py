@@ -104,3 +104,22 @@ def test_two_stage_equals_one_stage_magnetite_sample():
         sg, k = divmod(p, inp.nk)
         check_problem(ref["Hk"][sg, k], ref["Sk"][k], g2["eps"][p], g2["C"][p], int(g2["m"][p]), ref["eps"][p],
                       ref["C"][p], ref["m"][p], label=f"magnetite two-stage p={p}")
+
+
+@pytest.mark.parametrize("bw", [32, 16])
+def test_two_stage_mixed_precision_meets_mixed_bound(bw):
+    """The mixed mode on the two-stage reduction (its stage-1 products of H' with the mixed
+    planes, then the default Rayleigh-quotient refinement): eigenvalues within the mixed-mode
+    bound of 1e-9 Ha of the oracle's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_4247_gb300.nao import Context
+    inp = synth.small_cell(33, 5, 8, kgrid=(1, 2, 1), nspin=2)  # n = 129
+    ref = oracle.band_step(inp.HR, inp.SR, inp.R, inp.kpts, inp.wk, inp.n_electrons, inp.kT)
+    c = Context(0, config={"band_width": bw})
+    g = gpu_band_step(c, inp, torch, DEV, precision=2, density=False)
+    c.close()
+    for p in range(inp.nprob):
+        m = int(g["m"][p])
+        assert m == ref["m"][p] and int(g["status"][p]) == 0
+        assert np.abs(g["eps"][p][:m] - ref["eps"][p]).max() <= 1e-9
