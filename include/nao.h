@@ -211,6 +211,18 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
                 const int32_t* s_of_prob, int nS, double s_cut, int precision, int nb,
                 double* eps, nao_c128* C, int32_t* m_kept, int32_t* status, void* stream);
 
+/* Parts 2-4 for problems of different basis sizes in one call (the same method as
+ * nao_gen_eig): s_size int32 [nS] (device) gives the order n_s <= n of each overlap matrix,
+ * and every problem takes the order of its S.  Each matrix of H and S is stored n x n with
+ * its own n_s x n_s matrix in the leading block and zeros in the rest (the caller pads);
+ * the results follow the same layout: eps[p][j] for j < m_p (m_p <= n_s) and +inf beyond,
+ * rows n_s .. n-1 of C[p] zero.  s_size NULL is nao_gen_eig.  Orders outside [1, n] are the
+ * caller's error (not checked: the array is device memory).                                */
+int nao_gen_eig_sized(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c128* S,
+                      const int32_t* s_of_prob, int nS, const int32_t* s_size, double s_cut,
+                      int precision, int nb, double* eps, nao_c128* C, int32_t* m_kept,
+                      int32_t* status, void* stream);
+
 /* Parts 5-6: chemical potential, occupations, band energy, density matrix ------------ *
  * Problem p = sigma * nk + q (spin-major), as produced by nao_gen_eig on H(k) from
  * nao_bloch_sum.  g = 2 when nspin = 1, else 1.  Fermi-Dirac occupations

@@ -734,6 +734,13 @@ int nao_bloch_sum(nao_ctx* ctx, int n, int nR, const int32_t* R, int nmat, const
 int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c128* S, const int32_t* s_of_prob,
                 int nS, double s_cut, int precision, int nb, double* eps, nao_c128* C, int32_t* m_kept,
                 int32_t* status, void* stream) {
+  return nao_gen_eig_sized(ctx, n, nprob, H, S, s_of_prob, nS, nullptr, s_cut, precision, nb, eps, C, m_kept, status,
+                           stream);
+}
+
+int nao_gen_eig_sized(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c128* S, const int32_t* s_of_prob,
+                      int nS, const int32_t* s_size, double s_cut, int precision, int nb, double* eps, nao_c128* C,
+                      int32_t* m_kept, int32_t* status, void* stream) {
   if (!ctx) return nao_fail(nullptr, NAO_E_INVALID, "nao_gen_eig: ctx is NULL");
   if (n < 1 || nprob < 1) return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig: n and nprob must be >= 1");
   if (n > 4096) return nao_fail(ctx, NAO_E_INVALID, "nao_gen_eig: n = %d above the supported 4096", n);
@@ -795,25 +802,27 @@ int nao_gen_eig(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const nao_c12
 
   // ---- Part 2: Eigen_HH(S) -> s, U;  X = U_m s_m^{-1/2}
   NAO_STAGE("herm_fill", 1, launch_herm_fill(n, nSe, (const z64*)S, snn, nullptr, AS, n, snn, st));
+  // s_size (nullable): the order of each overlap matrix; the leading s_size x s_size block
+  // holds it, the rest of the n x n array is zero, and the chain keeps to the block
   if (B2 > 0)
-    NAO_CUDA_TRY(ctx, hetrd_two_stage(ctx, n, nSe, nullptr, AS, dS, eS, tauS, sbr, B2, ozws, st, NAO_OZ_DIGITS_FP64));
+    NAO_CUDA_TRY(ctx, hetrd_two_stage(ctx, n, nSe, s_size, AS, dS, eS, tauS, sbr, B2, ozws, st, NAO_OZ_DIGITS_FP64));
   else
-    NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nSe, nullptr, AS, dS, eS, tauS, VWp, ozws, st, NAO_OZ_DIGITS_FP64, digp, erowp));
+    NAO_CUDA_TRY(ctx, hetrd_blocked(ctx, n, nSe, s_size, AS, dS, eS, tauS, VWp, ozws, st, NAO_OZ_DIGITS_FP64, digp, erowp));
   const int mrrr_s = ctx->cfg.mrrr_all ? 2 : ctx->cfg.overlap_mrrr, mrrr_h = ctx->cfg.mrrr_all ? 2 : 0;
   NAO_STAGE("stein", mrrr_s ? 5 : 4,
-            launch_stein(n, nSe, nullptr, dS, eS, n, wS, Z, n, snn, scr, stS, nullptr, n,
+            launch_stein(n, nSe, s_size, dS, eS, n, wS, Z, n, snn, scr, stS, nullptr, n,
                          ctx->cfg.inverse_iteration_max, mrrr_s, st));
-  NAO_STAGE("misc", 1, launch_count_kept(n, nSe, wS, n, s_cut, mS, stS, st));
+  NAO_STAGE("misc", 1, launch_count_kept(n, nSe, s_size, wS, n, s_cut, mS, stS, st));
   double* Zo = Z2;  // the Newton-Schulz result (Z itself on the tensor-core method)
   {  // one Newton-Schulz step: Z (3I - Z^T Z)/2 = Z - Z (Z^T Z - I)/2
-    GemmDims d{n, n, n, nullptr, nullptr, nullptr, 1};
+    GemmDims d{n, n, n, s_size, s_size, s_size, 1};
     NAO_CUDA_TRY(ctx, run_dgemm(ctx, "ortho_ns", nSe, d, 1.0, GemmOperand{Z, snn, n, 1, 0, nullptr},
                                 GemmOperand{Z, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, ozws, st));
     cudaError_t e = cudaSuccess;
-    Zo = ns_correct(ctx, n, nSe, nullptr, nullptr, Z, G, Z2, ozws, st, &e);
+    Zo = ns_correct(ctx, n, nSe, s_size, s_size, Z, G, Z2, ozws, st, &e);
     NAO_CUDA_TRY(ctx, e);
   }
-  NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nSe, nullptr, mS, AS, tauS, Zo, wS, 1, X, Vf, tauc, Gw, Tw, Ww, VTw,
+  NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nSe, s_size, mS, AS, tauS, Zo, wS, 1, X, Vf, tauc, Gw, Tw, Ww, VTw,
                                           ozws, st, dig, 0, hoff, q2));
   {
     NaoStage stage_(ctx, "misc", st, 1);

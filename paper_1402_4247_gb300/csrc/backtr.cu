@@ -14,13 +14,15 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-__global__ void count_kept_kernel(int n, int nprob, const double* __restrict__ w, long long strideV, double s_cut,
-                                  int32_t* __restrict__ m, int32_t* __restrict__ status) {
+__global__ void count_kept_kernel(int n, int nprob, const int32_t* __restrict__ size, const double* __restrict__ w,
+                                  long long strideV, double s_cut, int32_t* __restrict__ m,
+                                  int32_t* __restrict__ status) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nprob) return;
   const double* wp = w + (size_t)p * strideV;
+  const int np = size ? size[p] : n;  // the problem's order: eigenvalues 0 .. np-1
   int k = 0;
-  for (int j = 0; j < n; ++j) k += (wp[j] >= s_cut);
+  for (int j = 0; j < np; ++j) k += (wp[j] >= s_cut);
   m[p] = k;
   if (k == 0 && status[p] == 0) status[p] = NAO_E_ALLCUT;
 }
@@ -79,9 +81,9 @@ __global__ void scale_cols_eps_kernel(int n, int nprob, int nb, const z64* __res
 
 }  // namespace
 
-cudaError_t launch_count_kept(int n, int nprob, const double* w, long long strideV, double s_cut, int32_t* m,
-                              int32_t* status, cudaStream_t st) {
-  count_kept_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(n, nprob, w, strideV, s_cut, m, status);
+cudaError_t launch_count_kept(int n, int nprob, const int32_t* size, const double* w, long long strideV, double s_cut,
+                              int32_t* m, int32_t* status, cudaStream_t st) {
+  count_kept_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(n, nprob, size, w, strideV, s_cut, m, status);
   return cudaGetLastError();
 }
 

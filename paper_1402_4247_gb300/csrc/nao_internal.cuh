@@ -315,7 +315,8 @@ cudaError_t launch_oa_gather(int n, int nprob, int nb, const int32_t* perm, cons
                              z64* C, cudaStream_t st);
 
 // Small helpers of the gen-eig chain.
-cudaError_t launch_count_kept(int n, int nprob, const double* w, long long strideV, double s_cut,
+// size (nullable): each problem's order (eigenvalues 0 .. size[p]-1 are counted)
+cudaError_t launch_count_kept(int n, int nprob, const int32_t* size, const double* w, long long strideV, double s_cut,
                               int32_t* m, int32_t* status, cudaStream_t st);
 cudaError_t launch_hermitize(int n, int nprob, const int32_t* size, z64* A, int ld, long long strideA,
                              cudaStream_t st);

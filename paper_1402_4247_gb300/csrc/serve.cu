@@ -1,9 +1,11 @@
 // Serving: continuous batching of band steps (not in the paper; the paper runs one fixed
 // magnetite job).  Requests (H(R), S(R), images, k-points) of mixed basis size arrive at any
-// time; a scheduler thread groups queued requests of equal (n, precision, nb, s_cut) into
-// one nao_gen_eig launch, runs each batch on a free slot (a CUDA stream plus a context of its
-// own, so its workspace is private and batches overlap on the GPU), and admits a batch only
-// when its device bytes fit next to everything the scheduler already holds.
+// time; a scheduler thread groups queued requests of equal (precision, s_cut) and either
+// equal (n, nb) or, when they want all eigenvectors, basis sizes within a factor 1.25 of each
+// other, into one nao_gen_eig launch (smaller problems padded to the batch's largest n, each
+// overlap matrix with its own order), runs each batch on a free slot (a CUDA stream plus a
+// context of its own, so its workspace is private and batches overlap on the GPU), and admits
+// a batch only when its device bytes fit next to everything the scheduler already holds.
 //
 // Life of a request:
 //   submit  (caller thread)   inputs copied to host memory the library owns; QUEUED
@@ -54,8 +56,9 @@ struct ServeReq {
   int nb = 0, nprob = 0;
   std::vector<double> HR, SR, kp, wk;
   std::vector<int32_t> R;
-  // device memory owned by the request: inputs and the Parts 5-6 outputs
-  DevBuf dHR, dSR, dR, dk, dw, df, drho, dmu, deb, drst;
+  // device memory owned by the request: inputs and the Parts 5-6 outputs; deps / dC: its
+  // eigenvalues and eigenvectors compacted to its own order when the batch padded it
+  DevBuf dHR, dSR, dR, dk, dw, df, drho, dmu, deb, drst, deps, dC;
   std::shared_ptr<ServeBatch> batch;
   int prob_off = 0, s_off = 0;  // slices of the batch arrays
   int state = Q_QUEUED;
@@ -69,7 +72,9 @@ struct NaoServerCore;
 // Device memory of one nao_gen_eig launch, shared by its requests' results.
 struct ServeBatch {
   NaoServerCore* srv = nullptr;
+  int n = 0, nb = 0;       // the launch's (largest) basis size and eigenvector columns
   DevBuf Hk, Sk, smap;     // inputs of the launch: freed when it finishes
+  DevBuf ssize, tmp;       // per-S orders and a padded request's Bloch sums (uneven batches)
   DevBuf eps, C, m, st;    // results: freed with the last request of the batch
   ~ServeBatch();
 };
@@ -121,6 +126,25 @@ struct NaoServerCore : NaoServer {
   void loop();
   void launch(ServeSlot* slot, std::vector<ServeReq*> batch_reqs);
   size_t batch_bytes(const std::vector<ServeReq*>& rs, size_t* req_bytes, size_t* ws_need) const;
+  // a batch's launch order n (its largest request's) and eigenvector columns nb
+  static void batch_shape(const std::vector<ServeReq*>& rs, int* n, int* nb) {
+    int nmax = 0;
+    bool uneven = false;
+    for (ServeReq* r : rs) {
+      if (r->rq.n != rs[0]->rq.n) uneven = true;
+      if (r->rq.n > nmax) nmax = r->rq.n;
+    }
+    *n = nmax;
+    *nb = uneven ? nmax : rs[0]->nb;  // uneven batches hold requests that want all vectors
+  }
+  // whether r may join a batch whose orders span [nlo, nhi] and whose first request is head
+  static bool joins(const ServeReq* head, const ServeReq* r, int nlo, int nhi) {
+    if (r->rq.precision != head->rq.precision || r->rq.s_cut != head->rq.s_cut) return false;
+    if (r->rq.n == head->rq.n && r->nb == head->nb && nlo == nhi) return true;
+    if (r->nb != r->rq.n || head->nb != head->rq.n) return false;  // padding needs all vectors
+    const int lo = r->rq.n < nlo ? r->rq.n : nlo, hi = r->rq.n > nhi ? r->rq.n : nhi;
+    return (long long)hi * 4 <= (long long)lo * 5;  // orders within a factor 1.25
+  }
 };
 
 size_t elems_bytes(size_t count, size_t size) { return ((count * size + 255) / 256) * 256; }
@@ -136,7 +160,7 @@ void NaoServerCore::free_buf(DevBuf& b) {
 
 ServeBatch::~ServeBatch() {
   if (!srv) return;
-  for (DevBuf* b : {&Hk, &Sk, &smap, &eps, &C, &m, &st}) srv->free_buf(*b);
+  for (DevBuf* b : {&Hk, &Sk, &smap, &ssize, &tmp, &eps, &C, &m, &st}) srv->free_buf(*b);
 }
 
 void CUDART_CB slot_done_cb(void* arg) {
@@ -153,26 +177,34 @@ void CUDART_CB slot_done_cb(void* arg) {
 // Device bytes a batch adds: the requests' own buffers, the batch arrays, and the growth of
 // the slot workspace (gen_eig of the whole batch, then Parts 5-6 per request).
 size_t NaoServerCore::batch_bytes(const std::vector<ServeReq*>& rs, size_t* req_bytes, size_t* ws_need) const {
-  const int n = rs[0]->rq.n, nb = rs[0]->nb;
-  size_t rb = 0;
+  int n = 0, nb = 0;
+  batch_shape(rs, &n, &nb);
+  size_t rb = 0, tmp = 0;
   int P = 0, NS = 0;
   for (ServeReq* r : rs) {
     const nao_request& q = r->rq;
-    size_t b = elems_bytes((size_t)q.nspin * q.nR * n * n, 8) + elems_bytes((size_t)q.nR * n * n, 8) +
+    const size_t nr = (size_t)q.n;
+    size_t b = elems_bytes((size_t)q.nspin * q.nR * nr * nr, 8) + elems_bytes((size_t)q.nR * nr * nr, 8) +
                elems_bytes((size_t)q.nR * 3, 4) + elems_bytes((size_t)q.nk * 3, 8) + elems_bytes(q.nk, 8);
     if (q.want_rho)
-      b += elems_bytes((size_t)r->nprob * n, 8) + elems_bytes((size_t)q.nspin * q.nR * n * n, 8) + 3 * 256;
+      b += elems_bytes((size_t)r->nprob * nr, 8) + elems_bytes((size_t)q.nspin * q.nR * nr * nr, 8) + 3 * 256;
+    if (q.n < n) {  // compacted results and the padding copy of its Bloch sums
+      b += elems_bytes((size_t)r->nprob * nr, 8) + elems_bytes((size_t)r->nprob * nr * nr, 16);
+      const size_t t = elems_bytes((size_t)(r->nprob > q.nk ? r->nprob : q.nk) * nr * nr, 16);
+      if (t > tmp) tmp = t;
+    }
     rb += b;
     P += r->nprob;
     NS += q.nk;
   }
   size_t bb = elems_bytes((size_t)P * n * n, 16) + elems_bytes((size_t)NS * n * n, 16) + elems_bytes(P, 4) +
-              elems_bytes((size_t)P * n, 8) + elems_bytes((size_t)P * n * nb, 16) + 2 * elems_bytes(P, 4);
+              elems_bytes((size_t)P * n, 8) + elems_bytes((size_t)P * n * nb, 16) + 2 * elems_bytes(P, 4) +
+              elems_bytes(NS, 4) + tmp;
   size_t ws = gen_eig_ws_bytes(owner, n, P, NS);
   for (ServeReq* r : rs) {  // Parts 1 and 5-6 run per request in the same workspace
     const nao_request& q = r->rq;
-    const size_t wd = density_ws_bytes(owner, n, q.nspin, q.nk, q.nR, nb);
-    const size_t wb = bloch_ws_bytes(owner, n, q.nR, q.nspin, q.nk);
+    const size_t wd = density_ws_bytes(owner, q.n, q.nspin, q.nk, q.nR, q.n < n ? q.n : nb);
+    const size_t wb = bloch_ws_bytes(owner, q.n, q.nR, q.nspin, q.nk);
     if (wd > ws) ws = wd;
     if (wb > ws) ws = wb;
   }
@@ -196,15 +228,25 @@ void NaoServerCore::launch(ServeSlot* slot, std::vector<ServeReq*> rs) {
   cudaSetDevice(device);
   cudaStream_t st = slot->stream;
   const nao_request& q0 = rs[0]->rq;
-  const int n = q0.n, nb = rs[0]->nb;
+  int n = 0, nb = 0;
+  batch_shape(rs, &n, &nb);
   auto b = std::make_shared<ServeBatch>();
   b->srv = this;
+  b->n = n;
+  b->nb = nb;
   int P = 0, NS = 0;
+  bool uneven = false;
+  size_t ntmp = 0;  // elements of the padding buffer: the largest padded request's Bloch sums
   for (ServeReq* r : rs) {
     r->prob_off = P;
     r->s_off = NS;
     P += r->nprob;
     NS += r->rq.nk;
+    if (r->rq.n < n) {
+      uneven = true;
+      const size_t t = (size_t)(r->nprob > r->rq.nk ? r->nprob : r->rq.nk) * r->rq.n * r->rq.n;
+      if (t > ntmp) ntmp = t;
+    }
   }
   int rc = NAO_OK;
   cudaError_t e = cudaSuccess;
@@ -218,19 +260,29 @@ void NaoServerCore::launch(ServeSlot* slot, std::vector<ServeReq*> rs) {
   ck(dalloc<nao_c128>(b->C, (size_t)P * n * nb, st));
   ck(dalloc<int32_t>(b->m, P, st));
   ck(dalloc<int32_t>(b->st, P, st));
-  std::vector<int32_t> smap(P);
+  if (uneven) {
+    ck(dalloc<int32_t>(b->ssize, NS, st));
+    ck(dalloc<nao_c128>(b->tmp, ntmp, st));
+  }
+  std::vector<int32_t> smap(P), ssize(NS);
   for (ServeReq* r : rs) {
     const nao_request& q = r->rq;
+    const int nr = q.n;
     for (int s = 0; s < q.nspin; ++s)
       for (int k = 0; k < q.nk; ++k) smap[r->prob_off + s * q.nk + k] = r->s_off + k;
+    for (int k = 0; k < q.nk; ++k) ssize[r->s_off + k] = nr;
     ck(dalloc<double>(r->dHR, r->HR.size(), st));
     ck(dalloc<double>(r->dSR, r->SR.size(), st));
     ck(dalloc<int32_t>(r->dR, r->R.size(), st));
     ck(dalloc<double>(r->dk, r->kp.size(), st));
     ck(dalloc<double>(r->dw, r->wk.size(), st));
+    if (nr < n) {
+      ck(dalloc<double>(r->deps, (size_t)r->nprob * nr, st));
+      ck(dalloc<nao_c128>(r->dC, (size_t)r->nprob * nr * nr, st));
+    }
     if (q.want_rho) {
-      ck(dalloc<double>(r->df, (size_t)r->nprob * n, st));
-      ck(dalloc<double>(r->drho, (size_t)q.nspin * q.nR * n * n, st));
+      ck(dalloc<double>(r->df, (size_t)r->nprob * nr, st));
+      ck(dalloc<double>(r->drho, (size_t)q.nspin * q.nR * nr * nr, st));
       ck(dalloc<double>(r->dmu, 1, st));
       ck(dalloc<double>(r->deb, 1, st));
       ck(dalloc<int32_t>(r->drst, 1, st));
@@ -238,6 +290,11 @@ void NaoServerCore::launch(ServeSlot* slot, std::vector<ServeReq*> rs) {
   }
   if (e == cudaSuccess) {
     ck(cudaMemcpyAsync(b->smap.p, smap.data(), smap.size() * 4, cudaMemcpyHostToDevice, st));
+    if (uneven) {  // the padded blocks of H(k) and S(k) stay zero
+      ck(cudaMemcpyAsync(b->ssize.p, ssize.data(), ssize.size() * 4, cudaMemcpyHostToDevice, st));
+      ck(cudaMemsetAsync(b->Hk.p, 0, b->Hk.bytes, st));
+      ck(cudaMemsetAsync(b->Sk.p, 0, b->Sk.bytes, st));
+    }
     for (ServeReq* r : rs) {
       ck(cudaMemcpyAsync(r->dHR.p, r->HR.data(), r->dHR.bytes, cudaMemcpyHostToDevice, st));
       ck(cudaMemcpyAsync(r->dSR.p, r->SR.data(), r->dSR.bytes, cudaMemcpyHostToDevice, st));
@@ -252,28 +309,65 @@ void NaoServerCore::launch(ServeSlot* slot, std::vector<ServeReq*> rs) {
   }
   nao_c128* Hk = (nao_c128*)b->Hk.p;
   nao_c128* Sk = (nao_c128*)b->Sk.p;
+  // the n_r x n_r matrices at src (dense) into the leading blocks of n x n slots at dst
+  auto pad_copy = [&](nao_c128* dst, const nao_c128* src, int count, int nr) {
+    for (int a = 0; a < count && e == cudaSuccess; ++a)
+      ck(cudaMemcpy2DAsync(dst + (size_t)a * n * n, (size_t)n * sizeof(nao_c128), src + (size_t)a * nr * nr,
+                           (size_t)nr * sizeof(nao_c128), (size_t)nr * sizeof(nao_c128), nr, cudaMemcpyDeviceToDevice,
+                           st));
+  };
   for (ServeReq* r : rs) {  // Part 1 of every request into its slice of the batch
     if (rc) break;
     const nao_request& q = r->rq;
-    rc = nao_bloch_sum(slot->sub, n, q.nR, (const int32_t*)r->dR.p, 1, (const double*)r->dSR.p, q.nk,
-                       (const double*)r->dk.p, Sk + (size_t)r->s_off * n * n, st);
-    if (!rc)
-      rc = nao_bloch_sum(slot->sub, n, q.nR, (const int32_t*)r->dR.p, q.nspin, (const double*)r->dHR.p, q.nk,
-                         (const double*)r->dk.p, Hk + (size_t)r->prob_off * n * n, st);
+    const int nr = q.n;
+    if (nr == n) {
+      rc = nao_bloch_sum(slot->sub, n, q.nR, (const int32_t*)r->dR.p, 1, (const double*)r->dSR.p, q.nk,
+                         (const double*)r->dk.p, Sk + (size_t)r->s_off * n * n, st);
+      if (!rc)
+        rc = nao_bloch_sum(slot->sub, n, q.nR, (const int32_t*)r->dR.p, q.nspin, (const double*)r->dHR.p, q.nk,
+                           (const double*)r->dk.p, Hk + (size_t)r->prob_off * n * n, st);
+    } else {  // at its own order, then padded into the batch's slots
+      nao_c128* t = (nao_c128*)b->tmp.p;
+      rc = nao_bloch_sum(slot->sub, nr, q.nR, (const int32_t*)r->dR.p, 1, (const double*)r->dSR.p, q.nk,
+                         (const double*)r->dk.p, t, st);
+      if (!rc) pad_copy(Sk + (size_t)r->s_off * n * n, t, q.nk, nr);
+      if (!rc)
+        rc = nao_bloch_sum(slot->sub, nr, q.nR, (const int32_t*)r->dR.p, q.nspin, (const double*)r->dHR.p, q.nk,
+                           (const double*)r->dk.p, t, st);
+      if (!rc) pad_copy(Hk + (size_t)r->prob_off * n * n, t, r->nprob, nr);
+      if (!rc && e != cudaSuccess) rc = NAO_E_CUDA;
+    }
   }
   if (!rc) {  // Parts 2-4 of the whole batch in one launch sequence
     nao_set_refinement(slot->sub, slot->srv->owner->refine_sweeps);  // the owner's refinement
-    rc = nao_gen_eig(slot->sub, n, P, Hk, Sk, (const int32_t*)b->smap.p, NS, q0.s_cut, q0.precision, nb,
-                     (double*)b->eps.p, (nao_c128*)b->C.p, (int32_t*)b->m.p, (int32_t*)b->st.p, st);
+    rc = nao_gen_eig_sized(slot->sub, n, P, Hk, Sk, (const int32_t*)b->smap.p, NS,
+                           uneven ? (const int32_t*)b->ssize.p : nullptr, q0.s_cut, q0.precision, nb,
+                           (double*)b->eps.p, (nao_c128*)b->C.p, (int32_t*)b->m.p, (int32_t*)b->st.p, st);
+  }
+  for (ServeReq* r : rs) {  // padded requests: eigenvalues and vectors at their own order
+    if (rc) break;
+    const int nr = r->rq.n;
+    if (nr == n) continue;
+    ck(cudaMemcpy2DAsync(r->deps.p, (size_t)nr * sizeof(double), (const double*)b->eps.p + (size_t)r->prob_off * n,
+                         (size_t)n * sizeof(double), (size_t)nr * sizeof(double), r->nprob, cudaMemcpyDeviceToDevice,
+                         st));
+    for (int p = 0; p < r->nprob && e == cudaSuccess; ++p)
+      ck(cudaMemcpy2DAsync((nao_c128*)r->dC.p + (size_t)p * nr * nr, (size_t)nr * sizeof(nao_c128),
+                           (const nao_c128*)b->C.p + (size_t)(r->prob_off + p) * n * nb, (size_t)nb * sizeof(nao_c128),
+                           (size_t)nr * sizeof(nao_c128), nr, cudaMemcpyDeviceToDevice, st));
+    if (e != cudaSuccess) rc = NAO_E_CUDA;
   }
   for (ServeReq* r : rs) {  // Parts 5-6 per request (its own electrons, weights, images)
     if (rc) break;
     const nao_request& q = r->rq;
     if (!q.want_rho) continue;
-    rc = nao_density_matrix(slot->sub, n, q.nspin, q.nk, (const double*)r->dw.p, (const double*)r->dk.p,
-                            (const double*)b->eps.p + (size_t)r->prob_off * n,
-                            (const nao_c128*)b->C.p + (size_t)r->prob_off * n * nb, nb,
-                            (const int32_t*)b->m.p + r->prob_off, q.n_electrons, q.kT, q.nR,
+    const int nr = q.n;
+    const bool own = nr < n;  // compacted results
+    const int nbr = own ? nr : nb;
+    rc = nao_density_matrix(slot->sub, nr, q.nspin, q.nk, (const double*)r->dw.p, (const double*)r->dk.p,
+                            own ? (const double*)r->deps.p : (const double*)b->eps.p + (size_t)r->prob_off * n,
+                            own ? (const nao_c128*)r->dC.p : (const nao_c128*)b->C.p + (size_t)r->prob_off * n * nb,
+                            nbr, (const int32_t*)b->m.p + r->prob_off, q.n_electrons, q.kT, q.nR,
                             (const int32_t*)r->dR.p, (double*)r->dmu.p, (double*)r->deb.p, (double*)r->df.p,
                             (double*)r->drho.p, nullptr, (int32_t*)r->drst.p, st);
   }
@@ -315,7 +409,8 @@ void NaoServerCore::loop() {
         r->state = Q_DONE;
         r->t_done = s->t_done;
         if (r->batch)
-          for (DevBuf* b : {&r->batch->Hk, &r->batch->Sk, &r->batch->smap}) free_buf(*b);
+          for (DevBuf* b : {&r->batch->Hk, &r->batch->Sk, &r->batch->smap, &r->batch->ssize, &r->batch->tmp})
+            free_buf(*b);
         // the inputs are no longer needed either
         for (DevBuf* b : {&r->dHR, &r->dSR, &r->dR, &r->dk, &r->dw}) free_buf(*b);
       }
@@ -337,15 +432,15 @@ void NaoServerCore::loop() {
     if (!stop && !paused && slot && !queue.empty()) {
       ServeReq* head = reqs[queue.front()].get();
       std::vector<ServeReq*> batch{head};
-      int probs = head->nprob;
+      int probs = head->nprob, nlo = head->rq.n, nhi = head->rq.n;
       for (size_t i = 1; i < queue.size(); ++i) {
         ServeReq* r = reqs[queue[i]].get();
-        if (r->rq.n != head->rq.n || r->rq.precision != head->rq.precision || r->nb != head->nb ||
-            r->rq.s_cut != head->rq.s_cut)
-          continue;
+        if (!joins(head, r, nlo, nhi)) continue;
         if (probs + r->nprob > max_batch) break;
         batch.push_back(r);
         probs += r->nprob;
+        if (r->rq.n < nlo) nlo = r->rq.n;
+        if (r->rq.n > nhi) nhi = r->rq.n;
       }
       size_t rb = 0, wsn = 0;
       size_t need = batch_bytes(batch, &rb, &wsn);
@@ -433,7 +528,8 @@ int start_server(nao_ctx* ctx, NaoServerCore* s) {
 }
 
 void release_request(NaoServerCore* s, ServeReq* r) {  // lock held; r is DONE
-  for (DevBuf* b : {&r->dHR, &r->dSR, &r->dR, &r->dk, &r->dw, &r->df, &r->drho, &r->dmu, &r->deb, &r->drst})
+  for (DevBuf* b : {&r->dHR, &r->dSR, &r->dR, &r->dk, &r->dw, &r->df, &r->drho, &r->dmu, &r->deb, &r->drst,
+                    &r->deps, &r->dC})
     s->free_buf(*b);
   r->batch.reset();  // the last holder frees the batch's result arrays
 }
@@ -574,10 +670,14 @@ int nao_serve_poll(nao_ctx* ctx, uint64_t ticket, int timeout_us, nao_result* ou
   out->latency_ms = ms_between(r->t_submit, r->t_done);
   out->batch_requests = r->batch_requests;
   if (r->batch && r->status == NAO_OK) {
-    const int n = r->rq.n;
     ServeBatch* b = r->batch.get();
-    out->eps = (const double*)b->eps.p + (size_t)r->prob_off * n;
-    out->C = (const nao_c128*)b->C.p + (size_t)r->prob_off * n * r->nb;
+    if (r->deps.p) {  // padded in its batch: the compacted copies
+      out->eps = (const double*)r->deps.p;
+      out->C = (const nao_c128*)r->dC.p;
+    } else {
+      out->eps = (const double*)b->eps.p + (size_t)r->prob_off * b->n;
+      out->C = (const nao_c128*)b->C.p + (size_t)r->prob_off * b->n * b->nb;
+    }
     out->m_kept = (const int32_t*)b->m.p + r->prob_off;
     out->prob_status = (const int32_t*)b->st.p + r->prob_off;
     if (r->rq.want_rho) {

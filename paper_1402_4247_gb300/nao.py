@@ -30,7 +30,8 @@ NAO_MIXED_BF16X3 = 2
 #: every symbol include/nao.h declares
 EXPORTS = ("nao_config_defaults", "nao_init", "nao_get_config", "nao_set_config", "nao_destroy",
            "nao_last_error", "nao_workspace_bytes", "nao_bloch_sum",
-           "nao_gen_eig", "nao_density_matrix", "nao_profile_enable", "nao_profile_read", "nao_launch_count",
+           "nao_gen_eig", "nao_gen_eig_sized", "nao_density_matrix", "nao_profile_enable", "nao_profile_read",
+           "nao_launch_count",
            "nao_fermi_level_noalloc", "nao_set_gemm_method", "nao_set_refinement", "nao_zgemm",
            "nao_gen_eig_workspace", "nao_serve_config", "nao_serve_pause", "nao_serve_submit", "nao_serve_poll",
            "nao_serve_release", "nao_serve_stats")
@@ -107,6 +108,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.nao_bloch_sum.restype = i32
     lib.nao_gen_eig.argtypes = [vp, i32, i32, vp, vp, vp, i32, f64, i32, i32, vp, vp, vp, vp, vp]
     lib.nao_gen_eig.restype = i32
+    lib.nao_gen_eig_sized.argtypes = [vp, i32, i32, vp, vp, vp, i32, vp, f64, i32, i32, vp, vp, vp, vp, vp]
+    lib.nao_gen_eig_sized.restype = i32
     lib.nao_density_matrix.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, i32, vp, f64, f64, i32, vp, vp, vp,
                                        vp, vp, vp, vp, vp]
     lib.nao_density_matrix.restype = i32
@@ -277,8 +280,10 @@ class Context:
 
     # ------------------------------------------------------------------ Parts 2-4
     def nao_gen_eig(self, H, S, s_of_prob=None, s_cut=1e-10, nb=None, precision=NAO_FP64, want_vectors=True,
-                    out=None, stream=None):
-        """H complex128 [nprob][n][n], S complex128 [nS][n][n] -> (eps, C, m_kept, status)."""
+                    out=None, stream=None, s_size=None):
+        """H complex128 [nprob][n][n], S complex128 [nS][n][n] -> (eps, C, m_kept, status).
+        s_size (int32 [nS] on the device, optional): each S matrix's order when the matrices
+        are padded to n (nao_gen_eig_sized)."""
         nprob, n, _ = H.shape
         nS = S.shape[0]
         nb = n if nb is None else int(nb)
@@ -292,8 +297,12 @@ class Context:
             eps, C, m, st = out
         if s_of_prob is None and nS != nprob:
             raise ValueError("S must have one matrix per problem unless s_of_prob is given")
-        rc = self.lib.nao_gen_eig(self.handle, n, nprob, _ptr(H), _ptr(S), _ptr(s_of_prob), nS, float(s_cut),
-                                  int(precision), nb, _ptr(eps), _ptr(C), _ptr(m), _ptr(st), _stream(stream))
+        if s_size is not None:
+            if s_size.dtype != torch.int32 or tuple(s_size.shape) != (nS,) or s_size.device != dev:
+                raise ValueError(f"s_size must be int32 [{nS}] on {dev}")
+        rc = self.lib.nao_gen_eig_sized(self.handle, n, nprob, _ptr(H), _ptr(S), _ptr(s_of_prob), nS, _ptr(s_size),
+                                        float(s_cut), int(precision), nb, _ptr(eps), _ptr(C), _ptr(m), _ptr(st),
+                                        _stream(stream))
         self._check(rc, "nao_gen_eig")
         return eps, C, m, st
 

@@ -316,3 +316,30 @@ def test_split_halves_subset_and_no_vectors(ctx_split):
     for p in range(inp.nprob):
         hn = np.abs(ref["eps"][p]).max()
         assert np.abs(e[p][:ref["m"][p]] - ref["eps"][p]).max() <= 1e-10 * hn
+
+
+def test_sized_problems_in_one_call(ctx):
+    """nao_gen_eig_sized: pencils of orders 40, 33 and 1 padded to n = 40 in one call, each
+    against the oracle at its own order; rows past a problem's order come back zero."""
+    rng = np.random.Generator(np.random.PCG64(4321))
+    orders = [40, 33, 1]
+    n = max(orders)
+    Hs, Ss = [], []
+    H = np.zeros((len(orders), n, n), complex)
+    S = np.zeros((len(orders), n, n), complex)
+    for i, o in enumerate(orders):
+        Hi, Si = synth.random_hermitian_pair(rng, o, cond=100.0)
+        Hs.append(Hi)
+        Ss.append(Si)
+        H[i, :o, :o] = Hi
+        S[i, :o, :o] = Si
+    size = torch.tensor(orders, dtype=torch.int32, device=DEV)
+    eps, C, m, st = ctx.nao_gen_eig(torch.from_numpy(H).to(DEV), torch.from_numpy(S).to(DEV), s_size=size)
+    torch.cuda.synchronize()
+    e, Cg, mg, sg = eps.cpu().numpy(), C.cpu().numpy(), m.cpu().numpy(), st.cpu().numpy()
+    for i, o in enumerate(orders):
+        eo, Co, mo, _ = oracle.generalized_eigensolve(Hs[i], Ss[i])
+        assert sg[i] == 0 and mg[i] == mo
+        assert np.all(np.isinf(e[i][mo:]))
+        assert np.all(Cg[i][o:, :] == 0)
+        check_problem(Hs[i], Ss[i], e[i][:o], Cg[i][:o, :o], int(mg[i]), eo, Co, mo, label=f"sized order {o}")

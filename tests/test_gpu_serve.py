@@ -1,7 +1,8 @@
 """Serving through nao_serve_* (GPU only): continuous batching of band steps of mixed basis
-size.  Each result must be the same alone and in a mix (where requests of equal n share one
-eigensolve launch and batches overlap on two slots), within the parity tolerances; admission
-follows the HBM budget; inputs may live on the host or the device."""
+size.  Each result must be the same alone and in a mix (where requests whose basis sizes lie
+within a factor 1.25 share one eigensolve launch, the smaller ones padded, and batches overlap
+on two slots), within the parity tolerances; admission follows the HBM budget; inputs may live
+on the host or the device."""
 import numpy as np
 import pytest
 
@@ -71,8 +72,8 @@ def test_alone_and_in_the_mix():
         alone = {k: _collect(ctx, _submit(ctx, inp)) for k, inp in cells.items()}
         for k, r in alone.items():
             assert r["batch_requests"] == 1, k
-        # the mix: queued together while admission is held, B79 and C79 (equal n) share one
-        # launch, and so do the two copies of A64
+        # the mix: queued together while admission is held, B79, C79 and both copies of A64
+        # (n = 64 padded to 79) share one launch; D129 is too large to join them
         order = ["D129", "B79", "A64", "C79", "A64"]
         ctx.nao_serve_pause(True)
         tickets = [(k, _submit(ctx, cells[k], on_device=(i % 2 == 0))) for i, k in enumerate(order)]
@@ -83,16 +84,18 @@ def test_alone_and_in_the_mix():
     for k, r in mixed:
         _same(r, alone[k], f"{k} in the mix")
     shared = {k: r["batch_requests"] for k, r in mixed}
-    assert shared["B79"] == 2 and shared["C79"] == 2 and shared["A64"] == 2 and shared["D129"] == 1, shared
-    # and one of them against the oracle
-    inp = cells["B79"]
-    ref = oracle.band_step(inp.HR, inp.SR, inp.R, inp.kpts, inp.wk, inp.n_electrons, inp.kT)
-    r = dict(mixed)["B79"]
-    for p in range(inp.nprob):
-        sg, k = divmod(p, inp.nk)
-        check_problem(ref["Hk"][sg, k], ref["Sk"][k], r["eps"][p], r["C"][p], int(r["m"][p]), ref["eps"][p],
-                      ref["C"][p], ref["m"][p], label=f"served B79 p={p}")
-    assert np.abs(r["rho"] - ref["rho"]).max() <= TOL_RHO * max(1.0, np.abs(ref["rho"]).max())
+    assert shared["B79"] == 4 and shared["C79"] == 4 and shared["A64"] == 4 and shared["D129"] == 1, shared
+    # and two of them (one at the launch's order, one padded into it) against the oracle
+    for name in ("B79", "A64"):
+        inp = cells[name]
+        ref = oracle.band_step(inp.HR, inp.SR, inp.R, inp.kpts, inp.wk, inp.n_electrons, inp.kT)
+        r = dict(mixed)[name]
+        assert r["eps"].shape == (inp.nprob, inp.n) and r["C"].shape == (inp.nprob, inp.n, inp.n)
+        for p in range(inp.nprob):
+            sg, k = divmod(p, inp.nk)
+            check_problem(ref["Hk"][sg, k], ref["Sk"][k], r["eps"][p], r["C"][p], int(r["m"][p]), ref["eps"][p],
+                          ref["C"][p], ref["m"][p], label=f"served {name} p={p}")
+        assert np.abs(r["rho"] - ref["rho"]).max() <= TOL_RHO * max(1.0, np.abs(ref["rho"]).max())
 
 
 def test_two_slots_match():
