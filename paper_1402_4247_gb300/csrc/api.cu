@@ -185,6 +185,8 @@ struct GenEigPlan {
   size_t oSVT, oSG, oST, oSM, oSN, oSTc, oSAB, oSV2, oSTau2;
   // split Parts 3-4: the second half's inverse-iteration scratch and product workspace
   size_t oScr2, oOz2;
+  // per problem: the second Newton-Schulz step's flag and column count
+  size_t oNs2, oNc2;
   size_t bytes;
 };
 
@@ -251,6 +253,8 @@ GenEigPlan plan_gen_eig(int n, int nprob, int nSe, bool use_tc, int B2, bool spl
   const int np2 = nprob - nprob / 2;
   W.oScr2 = P.take<double>(split ? stein_scratch_doubles(n, np2) : 1);
   W.oOz2 = P.take<char>(split && use_tc ? zgemm_oz_workspace(np2, dmax) : 1);
+  W.oNs2 = P.take<int>(nmax);
+  W.oNc2 = P.take<int32_t>(nmax);
   W.bytes = P.off;
   return W;
 }
@@ -494,6 +498,36 @@ double* ns_correct(nao_ctx* ctx, int n, int nprob, const int32_t* size, const in
   NaoStage stage_(ctx, "ortho_ns", st, 1);
   *err = launch_ns_correct(n, nprob, size, ncols, Z, G, n, snn, Z2, st);
   return Z2;
+}
+
+__global__ void ns2_cols_kernel(int nprob, const int* __restrict__ flag, const int32_t* __restrict__ ncols, int n,
+                                int32_t* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nprob) out[p] = flag[p] ? (ncols ? ncols[p] : n) : 0;
+}
+
+// The second Newton-Schulz step, for the problems the tridiagonal solve flagged (ns2) because
+// a gap in [1e-11, 1e-9) |T|_1 left overlaps up to ~1e-5 that one step reduces only to ~1e-10.
+// Tensor-core method: in place, the other problems' columns counted as zero; FP64 CUDA cores:
+// all problems, into the other array.  Returns the array that holds the result.
+double* ns_second(nao_ctx* ctx, int n, int nprob, const int32_t* size, const int32_t* ncols, const int* ns2,
+                  int32_t* ncols2, double* Zo, double* Z, double* Z2, double* G, void* ozws, cudaStream_t st,
+                  cudaError_t* err) {
+  const long long snn = (long long)n * n;
+  const bool tc = ctx->gemm_method == NAO_GEMM_TC && ozws;
+  const int32_t* nc = ncols;
+  if (tc) {
+    NaoStage stage_(ctx, "ortho_ns", st, 1);
+    ns2_cols_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(nprob, ns2, ncols, n, ncols2);
+    *err = cudaGetLastError();
+    if (*err != cudaSuccess) return Zo;
+    nc = ncols2;
+  }
+  const GemmDims d{n, n, n, nc, nc, size, 1};
+  *err = run_dgemm(ctx, "ortho_ns", nprob, d, 1.0, GemmOperand{Zo, snn, n, 1, 0, nullptr},
+                   GemmOperand{Zo, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, ozws, st);
+  if (*err != cudaSuccess) return Zo;
+  return ns_correct(ctx, n, nprob, size, nc, Zo, G, Zo == Z ? Z2 : Z, ozws, st, err);
 }
 
 bool is_device_ptr(const void* p) {
@@ -790,6 +824,8 @@ int nao_gen_eig_sized(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const n
                     (z64*)(ws + W.oSN), (z64*)(ws + W.oSTc), (z64*)(ws + W.oSAB), (z64*)(ws + W.oSV2),
                     (z64*)(ws + W.oSTau2), B2 > 0 ? sbr_q2_count(n, B2) : 0};
   const Q2Ref q2ref{B2, sbr.V2, sbr.tau2, sbr.sq};
+  int* ns2f = (int*)(ws + W.oNs2);
+  int32_t* nc2 = (int32_t*)(ws + W.oNc2);
   const Q2Ref* q2 = B2 > 0 ? &q2ref : nullptr;
   const int hoff = B2 > 0 ? B2 : 1;  // head row offset of the reduction's (first-stage) reflectors
   const long long snn = (long long)nn;
@@ -811,7 +847,7 @@ int nao_gen_eig_sized(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const n
   const int mrrr_s = ctx->cfg.mrrr_all ? 2 : ctx->cfg.overlap_mrrr, mrrr_h = ctx->cfg.mrrr_all ? 2 : 0;
   NAO_STAGE("stein", mrrr_s ? 5 : 4,
             launch_stein(n, nSe, s_size, dS, eS, n, wS, Z, n, snn, scr, stS, nullptr, n,
-                         ctx->cfg.inverse_iteration_max, mrrr_s, st));
+                         ctx->cfg.inverse_iteration_max, mrrr_s, st, ns2f));
   NAO_STAGE("misc", 1, launch_count_kept(n, nSe, s_size, wS, n, s_cut, mS, stS, st));
   double* Zo = Z2;  // the Newton-Schulz result (Z itself on the tensor-core method)
   {  // one Newton-Schulz step: Z (3I - Z^T Z)/2 = Z - Z (Z^T Z - I)/2
@@ -820,6 +856,8 @@ int nao_gen_eig_sized(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const n
                                 GemmOperand{Z, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, ozws, st));
     cudaError_t e = cudaSuccess;
     Zo = ns_correct(ctx, n, nSe, s_size, s_size, Z, G, Z2, ozws, st, &e);
+    NAO_CUDA_TRY(ctx, e);
+    Zo = ns_second(ctx, n, nSe, s_size, s_size, ns2f, nc2, Zo, Z, Z2, G, ozws, st, &e);
     NAO_CUDA_TRY(ctx, e);
   }
   NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nSe, s_size, mS, AS, tauS, Zo, wS, 1, X, Vf, tauc, Gw, Tw, Ww, VTw,
@@ -841,9 +879,9 @@ int nao_gen_eig_sized(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const n
       const int32_t* xmap;
       z64 *Hf, *Y, *Hp, *V, *tauH, *Vf, *tauc, *Gw, *Tw, *Ww, *VTw, *VWp, *C;
       double *dH, *eH, *wH, *Z, *Z2, *G, *scr, *eps;
-      int32_t *mP, *nbP, *stH;
+      int32_t *mP, *nbP, *stH, *nc2;
       void *ozws, *digp;
-      int* erowp;
+      int *erowp, *ns2;
     };
     auto hp_half = [&](int np, cudaStream_t st, const HpHalf& h, cudaEvent_t part3_done) -> int {
       NAO_STAGE("herm_fill", 1, launch_herm_fill(n, np, h.H, snn, nullptr, h.Hf, n, snn, st));
@@ -861,13 +899,16 @@ int nao_gen_eig_sized(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const n
                                       h.erowp, NAO_HT_DIGITS_FP64, nprob));
       const int nv_max = C ? n : 0;
       NAO_STAGE("stein", mrrr_h ? 5 : 4, launch_stein(n, np, h.mP, h.dH, h.eH, n, h.wH, h.Z, n, snn, h.scr, h.stH,
-                                                     h.nbP, nv_max, ctx->cfg.inverse_iteration_max, mrrr_h, st));
+                                                     h.nbP, nv_max, ctx->cfg.inverse_iteration_max, mrrr_h, st,
+                                                     h.ns2));
       if (nv_max > 0) {
         GemmDims d{n, n, n, h.nbP, h.nbP, h.mP, 1};
         NAO_CUDA_TRY(ctx, run_dgemm(ctx, "ortho_ns", np, d, 1.0, GemmOperand{h.Z, snn, n, 1, 0, nullptr},
                                     GemmOperand{h.Z, snn, 1, n, 0, nullptr}, 0.0, h.G, snn, 1, n, h.ozws, st));
         cudaError_t e = cudaSuccess;
         double* Zh = ns_correct(ctx, n, np, h.mP, h.nbP, h.Z, h.G, h.Z2, h.ozws, st, &e);
+        NAO_CUDA_TRY(ctx, e);
+        Zh = ns_second(ctx, n, np, h.mP, h.nbP, h.ns2, h.nc2, Zh, h.Z, h.Z2, h.G, h.ozws, st, &e);
         NAO_CUDA_TRY(ctx, e);
         NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, np, h.mP, h.nbP, h.Hp, h.tauH, Zh, h.wH, 0, h.V, h.Vf, h.tauc,
                                                 h.Gw, h.Tw, h.Ww, h.VTw, h.ozws, st, dig, 1));
@@ -920,6 +961,8 @@ int nao_gen_eig_sized(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const n
       h.ozws = oz_h;
       h.digp = dig_h;
       h.erowp = erowp + (size_t)p0 * (n > 1 ? n - 1 : 1);
+      h.ns2 = ns2f + p0;
+      h.nc2 = nc2 + p0;
       (void)np;
       return h;
     };
@@ -962,7 +1005,7 @@ int nao_gen_eig_sized(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const n
   const int32_t* nvP = all_vecs ? mP : nbP;
   const int nv_max = (C || all_vecs) ? n : 0;
   NAO_STAGE("stein", mrrr_h ? 5 : 4, launch_stein(n, nprob, mP, dH, eH, n, wH, Z, n, snn, scr, stH, nvP, nv_max,
-                                                 ctx->cfg.inverse_iteration_max, mrrr_h, st));
+                                                 ctx->cfg.inverse_iteration_max, mrrr_h, st, ns2f));
   if (nv_max > 0) {
     {
       GemmDims d{n, n, n, nvP, nvP, mP, 1};
@@ -970,6 +1013,8 @@ int nao_gen_eig_sized(nao_ctx* ctx, int n, int nprob, const nao_c128* H, const n
                                   GemmOperand{Z, snn, 1, n, 0, nullptr}, 0.0, G, snn, 1, n, ozws, st));
       cudaError_t e = cudaSuccess;
       Zo = ns_correct(ctx, n, nprob, mP, nvP, Z, G, Z2, ozws, st, &e);
+      NAO_CUDA_TRY(ctx, e);
+      Zo = ns_second(ctx, n, nprob, mP, nvP, ns2f, nc2, Zo, Z, Z2, G, ozws, st, &e);
       NAO_CUDA_TRY(ctx, e);
     }
     NAO_CUDA_TRY(ctx, backtransform_blocked(ctx, n, nprob, mP, nvP, Hp, tauH, Zo, wH, 0, V, Vf, tauc, Gw, Tw, Ww, VTw,

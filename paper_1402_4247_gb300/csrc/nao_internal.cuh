@@ -218,7 +218,9 @@ size_t stein_scratch_doubles(int n, int nprob);
 cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d, const double* e,
                          long long strideV, double* w, double* Z, int ld, long long strideZ,
                          double* scratch, int32_t* status, const int32_t* nvec, int nvec_max, int maxits,
-                         int mrrr, cudaStream_t st);
+                         int mrrr, cudaStream_t st, int* ns2 = nullptr);
+// ns2 (nullable, [nprob]): set to 1 for a problem whose vectors need a second Newton-Schulz
+// step (a gap in [1e-11, 1e-9) |T|_1, where inverse iteration leaves overlaps up to ~1e-5)
 
 // Blocked (compact WY) back-transformation helpers, see backtr.cu.
 constexpr int NAO_WY_NB = 128;

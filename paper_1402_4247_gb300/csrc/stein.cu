@@ -21,17 +21,19 @@
 // * Eigenvectors (kernel 2, same block split): inverse iteration with a partially pivoted LU
 //   of T - lambda I (tiny pivots perturbed to eps |T|), a scaled right-hand side, the growth
 //   test |x|_inf >= sqrt(0.1/blocksize) within `maxits` solves plus two extra solves, and
-//   modified Gram-Schmidt against the earlier members of a TIGHT cluster (gap < 1e-9 |T|_1),
+//   modified Gram-Schmidt against the earlier members of a TIGHT cluster (gap < 1e-11 |T|_1),
 //   whose leader walks the cluster in order.  Wider near-degeneracies leave overlaps of order
-//   eps|T|/gap <= ~1e-7, which the caller removes with one Newton-Schulz step
-//   Z <- Z (3I - Z^T Z)/2 (it squares them: ~1e-14).
+//   eps|T|/gap, which the caller removes with Newton-Schulz steps Z <- Z (3I - Z^T Z)/2
+//   (each squares them): one step for gaps >= 1e-9 |T|_1 (overlaps <= ~1e-7), a second one
+//   for the problems flagged in ns2[] because a gap lies in [1e-11, 1e-9) |T|_1 (overlaps
+//   <= ~1e-5).
 //   A tight cluster of more than BIG members (the near-null spectrum of an ill-conditioned
 //   overlap matrix can chain hundreds) is handed to kernel 3: one block per cluster, the
 //   same iteration with the reorthogonalisation done by the whole block (classical
 //   Gram-Schmidt applied twice) while one thread runs the tridiagonal solves.  A chain can
 //   span far more than the tight band; a member is re-orthogonalised only against the
 //   finished members within the band of its own eigenvalue (the others overlap it by at
-//   most eps|T|/(1e-9 |T|_1), which the Newton-Schulz step removes).
+//   most eps|T|/(1e-11 |T|_1), which the Newton-Schulz steps remove).
 // * Output: eigenvalues ascending (across blocks), eigenvectors in matching columns,
 //   unit 2-norm, largest component positive.  All loops are bounded.
 #include <cfloat>
@@ -49,7 +51,8 @@ constexpr int EXTRA_ISOLATED = 1; // the same for an eigenvalue outside any tigh
                                   // least 1e-9 |T|_1, so each solve shrinks the other eigenvectors'
                                   // components by eps |T| / gap < 1.2e-7, and one solve past the growth
                                   // test leaves them below ~1e-14
-constexpr double TIGHT = 1e-9;
+constexpr double TIGHT = 1e-9;      // gaps below it need more than one Newton-Schulz step...
+constexpr double TIGHT_GS = 1e-11;  // ...and below this, Gram-Schmidt
 constexpr int NARR = 6;           // scratch arrays per eigenvalue: L, U0inv, U1, U2, PIV, X
 constexpr int BIG = 32;           // tight clusters with more members go to stein_cluster_kernel
 constexpr int NEWTON_MAX = 6;     // Newton steps on an isolated eigenvalue before it is queued
@@ -427,7 +430,8 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
                  long long strideV, const double* __restrict__ wslot, double* __restrict__ wbase,
                  double* __restrict__ Zbase, int ldz, long long strideZ, double* __restrict__ scratch,
                  int32_t* __restrict__ status, int* __restrict__ biglist, int bigcap,
-                 const int32_t* __restrict__ nvec, int nvec_max, int maxits, const int* __restrict__ mdone) {
+                 const int32_t* __restrict__ nvec, int nvec_max, int maxits, const int* __restrict__ mdone,
+                 int* __restrict__ ns2) {
   extern __shared__ double smd[];
   double* d = smd;
   double* e = smd + n;
@@ -451,9 +455,13 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
   double* Z = Zbase + (size_t)p * strideZ;
   double* scr = scratch + (size_t)p * NARR * n * n;
   const double eps = DBL_EPSILON * 0.5;
-  const double tight = TIGHT * T.onenrm;
+  const double tight = TIGHT_GS * T.onenrm, tight1 = TIGHT * T.onenrm;
   const double pivtol = eps * T.tnorm;
   const size_t nn = (size_t)n * n;
+  if (j < m && ns2 && j > bst[j]) {  // a gap that one Newton-Schulz step does not cover
+    const double gap = w[j] - w[j - 1];
+    if (gap < tight1 && !(gap < tight)) ns2[p] = 1;
+  }
   if (j < m) {
     // global ascending order (ties broken by slot)
     const double wj = w[j];
@@ -732,7 +740,7 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
       }
       if (tid == 0) {  // finished members within the tight band of w[q]: the earlier ones and
                        // the later MRRR vectors
-        const double tband = TIGHT * T.onenrm, wq = w[q];
+        const double tband = TIGHT_GS * T.onenrm, wq = w[q];
         int c = 0;
         for (int t = 0; t < jend - j; ++t)
           if ((t < q - j || (t > q - j && dn && dn[j + t])) && fabs(w[j + t] - wq) < tband) fin[c++] = t;
@@ -961,7 +969,7 @@ mrrr_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restric
     __syncthreads();
     atomicMax((unsigned long long*)&s_am, (unsigned long long)__double_as_longlong(am));  // am >= 0
     __syncthreads();
-    const double tb = TIGHT * 3.0 * s_am;
+    const double tb = TIGHT_GS * 3.0 * s_am;
     for (int i = threadIdx.x; i < m; i += blockDim.x) w[i] = ws[i];
     __syncthreads();
     // only the members of big tight clusters (more than BIG members, the ones kernel 3 would
@@ -1049,8 +1057,8 @@ mrrr_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restric
   // only members of big tight clusters (as above, now within the split block), unless all
   if (!all) {
     int c = 1;
-    for (int t = j; t > b0 && c <= BIG && w[t] - w[t - 1] < TIGHT * tn; --t) ++c;
-    for (int t = j; t < b1 - 1 && c <= BIG && w[t + 1] - w[t] < TIGHT * tn; ++t) ++c;
+    for (int t = j; t > b0 && c <= BIG && w[t] - w[t - 1] < TIGHT_GS * tn; --t) ++c;
+    for (int t = j; t < b1 - 1 && c <= BIG && w[t + 1] - w[t] < TIGHT_GS * tn; ++t) ++c;
     if (c <= BIG) return;
   }
   if (!(fmin(gl, gr) >= MR_MINRGP * mu0)) return;  // a relative cluster: kernel 2
@@ -1160,7 +1168,7 @@ size_t stein_scratch_doubles(int n, int nprob) {
 
 cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d, const double* e, long long strideV,
                          double* w, double* Z, int ld, long long strideZ, double* scratch, int32_t* status,
-                         const int32_t* nvec, int nvec_max, int maxits, int mrrr, cudaStream_t st) {
+                         const int32_t* nvec, int nvec_max, int maxits, int mrrr, cudaStream_t st, int* ns2) {
   double* wslot = scratch + (size_t)NARR * n * n * nprob;
   const size_t smem1 = sizeof(double) * 3 * (size_t)n + sizeof(float) * 2 * (size_t)n + sizeof(int) * 2 * (size_t)n;
   cudaError_t err = cudaFuncSetAttribute(stebz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
@@ -1207,8 +1215,12 @@ cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d,
   const size_t smem2 = sizeof(double) * 4 * (size_t)n + sizeof(int) * 2 * (size_t)n;
   err = cudaFuncSetAttribute(stein_vec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
   if (err != cudaSuccess) return err;
+  if (ns2) {
+    err = cudaMemsetAsync(ns2, 0, sizeof(int) * (size_t)nprob, st);
+    if (err != cudaSuccess) return err;
+  }
   stein_vec_kernel<<<grid, ST_THREADS, smem2, st>>>(n, size, d, e, strideV, wslot, w, Z, ld, strideZ, scratch, status,
-                                                    biglist, bigcap, nvec, nvec_max, maxits, mdone);
+                                                    biglist, bigcap, nvec, nvec_max, maxits, mdone, ns2);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   // kernel 3: a grid that stays resident; blocks without a listed cluster exit at once
