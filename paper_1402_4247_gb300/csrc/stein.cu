@@ -48,9 +48,9 @@ constexpr int SZ_THREADS = 64;    // = slots per block (eigenvalues): ~8 blocks 
                                   // of n = 568, so the SMs' FP64 pipes finish within one block of each other
 constexpr int EXTRA = 2;          // extra solves after the growth test passes (members of tight clusters)
 constexpr int EXTRA_ISOLATED = 1; // the same for an eigenvalue outside any tight cluster: its gap is at
-                                  // least 1e-9 |T|_1, so each solve shrinks the other eigenvectors'
-                                  // components by eps |T| / gap < 1.2e-7, and one solve past the growth
-                                  // test leaves them below ~1e-14
+                                  // least 1e-11 |T|_1, so the other eigenvectors' components fall to
+                                  // their rounding floor eps |T| / gap < 2.2e-5 within one solve past
+                                  // the growth test; the Newton-Schulz steps remove that floor
 constexpr double TIGHT = 1e-9;      // gaps below it need more than one Newton-Schulz step...
 constexpr double TIGHT_GS = 1e-11;  // ...and below this, Gram-Schmidt
 constexpr int NARR = 6;           // scratch arrays per eigenvalue: L, U0inv, U1, U2, PIV, X
@@ -902,9 +902,9 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
 // representation tree): for every unreduced block of a positive semidefinite tridiagonal (the
 // overlap's), shift to just below its smallest eigenvalue, T - sigma I = L D L^T with D > 0.
 // A definite L D L^T determines its eigenvalues to high relative accuracy, so the near-null
-// spectrum of an ill-conditioned overlap, hundreds of eigenvalues within 1e-9 |T| of each
+// spectrum of an ill-conditioned overlap, hundreds of eigenvalues within 1e-11 |T| of each
 // other but relatively far apart, becomes well separated.
-//   A member of a big tight cluster (gaps < 1e-9 |T|_1, more than BIG members: the ones
+//   A member of a big tight cluster (gaps < 1e-11 |T|_1, more than BIG members: the ones
 // inverse iteration would re-orthogonalise at O(k^2 n)) whose shifted eigenvalue
 // mu = lambda - sigma has a relative gap of at least MR_MINRGP to both neighbours is refined
 // by bisection on negative-pivot counts of L D L^T - x I (the stationary qd transform) to

@@ -175,8 +175,8 @@ def _vec_angle(a, b):
 def test_gap_band_spectrum_without_cluster_rule():
     """n = 600 pencil whose eigenvalues come in clusters of ten with gaps 10^-u ||T||,
     u ~ U[3, 9]: every gap lies in the band that LAPACK's dstein re-orthogonalises (gap <
-    1e-3 ||T||_1) but the CUDA path does not (it re-orthogonalises only gaps < 1e-9 ||T||_1 and
-    applies one Newton-Schulz step to all vectors).  Eigenvalues, residual and S-orthonormality
+    1e-3 ||T||_1) but the CUDA path does not (it re-orthogonalises only gaps < 1e-11 ||T||_1
+    and applies Newton-Schulz steps to all vectors: two where a gap is below 1e-9 ||T||_1).  Eigenvalues, residual and S-orthonormality
     at the workload's bounds; each eigenvector within 10x the angle by which two FP64 routes
     (the oracle's implicit QL and LAPACK's generalized solver) differ, plus 1e-10."""
     scipy_linalg = pytest.importorskip("scipy.linalg")
