@@ -21,19 +21,19 @@
 // * Eigenvectors (kernel 2, same block split): inverse iteration with a partially pivoted LU
 //   of T - lambda I (tiny pivots perturbed to eps |T|), a scaled right-hand side, the growth
 //   test |x|_inf >= sqrt(0.1/blocksize) within `maxits` solves plus two extra solves, and
-//   modified Gram-Schmidt against the earlier members of a TIGHT cluster (gap < 1e-11 |T|_1),
-//   whose leader walks the cluster in order.  Wider near-degeneracies leave overlaps of order
-//   eps|T|/gap, which the caller removes with Newton-Schulz steps Z <- Z (3I - Z^T Z)/2
-//   (each squares them): one step for gaps >= 1e-9 |T|_1 (overlaps <= ~1e-7), a second one
-//   for the problems flagged in ns2[] because a gap lies in [1e-11, 1e-9) |T|_1 (overlaps
-//   <= ~1e-5).
+//   modified Gram-Schmidt against the earlier members of a tight cluster (gap < 1e-11 |T|_1;
+//   1e-9 |T|_1 when kernel 0 runs), whose leader walks the cluster in order.  Wider
+//   near-degeneracies leave overlaps of order eps|T|/gap, which the caller removes with
+//   Newton-Schulz steps Z <- Z (3I - Z^T Z)/2 (each squares them): one step for gaps
+//   >= 1e-9 |T|_1 (overlaps <= ~1e-7), a second one for the problems flagged in ns2[] because
+//   a gap lies in [1e-11, 1e-9) |T|_1 (overlaps <= ~1e-5).
 //   A tight cluster of more than BIG members (the near-null spectrum of an ill-conditioned
 //   overlap matrix can chain hundreds) is handed to kernel 3: one block per cluster, the
 //   same iteration with the reorthogonalisation done by the whole block (classical
 //   Gram-Schmidt applied twice) while one thread runs the tridiagonal solves.  A chain can
 //   span far more than the tight band; a member is re-orthogonalised only against the
 //   finished members within the band of its own eigenvalue (the others overlap it by at
-//   most eps|T|/(1e-11 |T|_1), which the Newton-Schulz steps remove).
+//   most eps|T| over the band, which the Newton-Schulz steps remove).
 // * Output: eigenvalues ascending (across blocks), eigenvectors in matching columns,
 //   unit 2-norm, largest component positive.  All loops are bounded.
 #include <cfloat>
@@ -52,7 +52,9 @@ constexpr int EXTRA_ISOLATED = 1; // the same for an eigenvalue outside any tigh
                                   // their rounding floor eps |T| / gap < 2.2e-5 within one solve past
                                   // the growth test; the Newton-Schulz steps remove that floor
 constexpr double TIGHT = 1e-9;      // gaps below it need more than one Newton-Schulz step...
-constexpr double TIGHT_GS = 1e-11;  // ...and below this, Gram-Schmidt
+constexpr double TIGHT_GS = 1e-11;  // ...and below this, Gram-Schmidt (without MRRR vectors; with
+                                    // them, Gram-Schmidt starts at TIGHT: the big clusters that the
+                                    // wider band chains go to MRRR, which needs no serial walk)
 constexpr int NARR = 6;           // scratch arrays per eigenvalue: L, U0inv, U1, U2, PIV, X
 constexpr int BIG = 32;           // tight clusters with more members go to stein_cluster_kernel
 constexpr int NEWTON_MAX = 6;     // Newton steps on an isolated eigenvalue before it is queued
@@ -431,7 +433,7 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
                  double* __restrict__ Zbase, int ldz, long long strideZ, double* __restrict__ scratch,
                  int32_t* __restrict__ status, int* __restrict__ biglist, int bigcap,
                  const int32_t* __restrict__ nvec, int nvec_max, int maxits, const int* __restrict__ mdone,
-                 int* __restrict__ ns2) {
+                 int* __restrict__ ns2, double tgs) {
   extern __shared__ double smd[];
   double* d = smd;
   double* e = smd + n;
@@ -455,7 +457,7 @@ stein_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restri
   double* Z = Zbase + (size_t)p * strideZ;
   double* scr = scratch + (size_t)p * NARR * n * n;
   const double eps = DBL_EPSILON * 0.5;
-  const double tight = TIGHT_GS * T.onenrm, tight1 = TIGHT * T.onenrm;
+  const double tight = tgs * T.onenrm, tight1 = TIGHT * T.onenrm;
   const double pivtol = eps * T.tnorm;
   const size_t nn = (size_t)n * n;
   if (j < m && ns2 && j > bst[j]) {  // a gap that one Newton-Schulz step does not cover
@@ -684,7 +686,8 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
                      const double* __restrict__ ebase, long long strideV, const double* __restrict__ wslot,
                      double* __restrict__ Zbase, int ldz, long long strideZ, double* __restrict__ scratch,
                      int32_t* __restrict__ status, const int* __restrict__ biglist, int bigcap,
-                     const int32_t* __restrict__ nvec, int nvec_max, int maxits, const int* __restrict__ mdone) {
+                     const int32_t* __restrict__ nvec, int nvec_max, int maxits, const int* __restrict__ mdone,
+                     double tgs) {
   extern __shared__ double smc[];
   double* d = smc;
   double* e = smc + n;
@@ -740,7 +743,7 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
       }
       if (tid == 0) {  // finished members within the tight band of w[q]: the earlier ones and
                        // the later MRRR vectors
-        const double tband = TIGHT_GS * T.onenrm, wq = w[q];
+        const double tband = tgs * T.onenrm, wq = w[q];
         int c = 0;
         for (int t = 0; t < jend - j; ++t)
           if ((t < q - j || (t > q - j && dn && dn[j + t])) && fabs(w[j + t] - wq) < tband) fin[c++] = t;
@@ -902,9 +905,9 @@ stein_cluster_kernel(int n, const int32_t* __restrict__ size, const double* __re
 // representation tree): for every unreduced block of a positive semidefinite tridiagonal (the
 // overlap's), shift to just below its smallest eigenvalue, T - sigma I = L D L^T with D > 0.
 // A definite L D L^T determines its eigenvalues to high relative accuracy, so the near-null
-// spectrum of an ill-conditioned overlap, hundreds of eigenvalues within 1e-11 |T| of each
+// spectrum of an ill-conditioned overlap, hundreds of eigenvalues within 1e-9 |T| of each
 // other but relatively far apart, becomes well separated.
-//   A member of a big tight cluster (gaps < 1e-11 |T|_1, more than BIG members: the ones
+//   A member of a big tight cluster (gaps < 1e-9 |T|_1, more than BIG members: the ones
 // inverse iteration would re-orthogonalise at O(k^2 n)) whose shifted eigenvalue
 // mu = lambda - sigma has a relative gap of at least MR_MINRGP to both neighbours is refined
 // by bisection on negative-pivot counts of L D L^T - x I (the stationary qd transform) to
@@ -940,7 +943,7 @@ __global__ void __launch_bounds__(MR_THREADS)
 mrrr_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restrict__ dbase,
                 const double* __restrict__ ebase, long long strideV, const double* __restrict__ wslot,
                 double* __restrict__ Zbase, int ldz, long long strideZ, double* __restrict__ scratch,
-                int* __restrict__ mdone, const int32_t* __restrict__ nvec, int nvec_max, int all) {
+                int* __restrict__ mdone, const int32_t* __restrict__ nvec, int nvec_max, int all, double tgs) {
   extern __shared__ double smr[];
   double* w = smr;           // [n] eigenvalues (slot order)
   double* D = smr + n;       // [n] root representation of each unreduced block
@@ -969,7 +972,7 @@ mrrr_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restric
     __syncthreads();
     atomicMax((unsigned long long*)&s_am, (unsigned long long)__double_as_longlong(am));  // am >= 0
     __syncthreads();
-    const double tb = TIGHT_GS * 3.0 * s_am;
+    const double tb = tgs * 3.0 * s_am;
     for (int i = threadIdx.x; i < m; i += blockDim.x) w[i] = ws[i];
     __syncthreads();
     // only the members of big tight clusters (more than BIG members, the ones kernel 3 would
@@ -1057,8 +1060,8 @@ mrrr_vec_kernel(int n, const int32_t* __restrict__ size, const double* __restric
   // only members of big tight clusters (as above, now within the split block), unless all
   if (!all) {
     int c = 1;
-    for (int t = j; t > b0 && c <= BIG && w[t] - w[t - 1] < TIGHT_GS * tn; --t) ++c;
-    for (int t = j; t < b1 - 1 && c <= BIG && w[t + 1] - w[t] < TIGHT_GS * tn; ++t) ++c;
+    for (int t = j; t > b0 && c <= BIG && w[t] - w[t - 1] < tgs * tn; --t) ++c;
+    for (int t = j; t < b1 - 1 && c <= BIG && w[t + 1] - w[t] < tgs * tn; ++t) ++c;
     if (c <= BIG) return;
   }
   if (!(fmin(gl, gr) >= MR_MINRGP * mu0)) return;  // a relative cluster: kernel 2
@@ -1201,6 +1204,11 @@ cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d,
   if (err != cudaSuccess) return err;
   // kernel 0 (MRRR vectors where the representation separates the eigenvalues), when asked
   int* mdone = nullptr;
+  // Gram-Schmidt band: TIGHT where MRRR takes the members of big clusters (a wide band costs
+  // nothing there; a narrow one splits the near-null spectrum of an ill-conditioned overlap
+  // into small clusters that one thread walks serially), TIGHT_GS and a second Newton-Schulz
+  // step for the band in between where inverse iteration works alone
+  const double tgs = mrrr ? TIGHT : TIGHT_GS;
   if (mrrr) {
     mdone = biglist + 1 + 3 * (size_t)bigcap + 1;  // n ints per problem after the cluster list
     const size_t smem0 = sizeof(double) * 4 * (size_t)n + sizeof(int) * 2 * (size_t)n;
@@ -1208,7 +1216,7 @@ cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d,
     if (err != cudaSuccess) return err;
     dim3 grid0((n + MR_THREADS - 1) / MR_THREADS, nprob);
     mrrr_vec_kernel<<<grid0, MR_THREADS, smem0, st>>>(n, size, d, e, strideV, wslot, Z, ld, strideZ, scratch, mdone,
-                                                       nvec, nvec_max, mrrr == 2);
+                                                       nvec, nvec_max, mrrr == 2, tgs);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
@@ -1220,7 +1228,7 @@ cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d,
     if (err != cudaSuccess) return err;
   }
   stein_vec_kernel<<<grid, ST_THREADS, smem2, st>>>(n, size, d, e, strideV, wslot, w, Z, ld, strideZ, scratch, status,
-                                                    biglist, bigcap, nvec, nvec_max, maxits, mdone, ns2);
+                                                    biglist, bigcap, nvec, nvec_max, maxits, mdone, ns2, tgs);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   // kernel 3: a grid that stays resident; blocks without a listed cluster exit at once
@@ -1231,6 +1239,6 @@ cudaError_t launch_stein(int n, int nprob, const int32_t* size, const double* d,
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   stein_cluster_kernel<<<sms, SC_THREADS, smem3, st>>>(n, size, d, e, strideV, wslot, Z, ld, strideZ, scratch, status,
-                                                       biglist, bigcap, nvec, nvec_max, maxits, mdone);
+                                                       biglist, bigcap, nvec, nvec_max, maxits, mdone, tgs);
   return cudaGetLastError();
 }
