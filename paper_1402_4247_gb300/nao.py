@@ -159,6 +159,107 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _check_tensor(name, t, dtype, shape, device):
+    """Raise ValueError unless ``t`` is a contiguous tensor of ``dtype`` whose shape matches
+    ``shape`` (None: any extent) on ``device``: the kernels read every extent the call
+    passes, so a smaller or differently typed buffer would be read past its end."""
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a torch tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, not {t.dtype}")
+    if t.dim() != len(shape) or any(s is not None and int(e) != int(s) for e, s in zip(t.shape, shape)):
+        want = "[" + ", ".join("*" if s is None else str(s) for s in shape) + "]"
+        raise ValueError(f"{name} must have shape {want}, not {list(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.device != device:
+        raise ValueError(f"{name} must be on {device}, not {t.device}")
+
+
+def check_bloch_sum_args(MR, R, kpts, out, device):
+    """Arguments of ``nao_bloch_sum``: MR float64 [nmat][nR][n][n], R int32 [nR][3], kpts
+    float64 [nk][3], out complex128 [nmat][nk][n][n] (or None)."""
+    _check_tensor("MR", MR, torch.float64, (None, None, None, None), device)
+    nmat, nR, n, n2 = MR.shape
+    if n != n2:
+        raise ValueError(f"MR must hold square matrices, not {n} x {n2}")
+    _check_tensor("R", R, torch.int32, (nR, 3), device)
+    _check_tensor("kpts", kpts, torch.float64, (None, 3), device)
+    if out is not None:
+        _check_tensor("out", out, torch.complex128, (nmat, kpts.shape[0], n, n), device)
+
+
+def check_gen_eig_args(H, S, s_of_prob, nb, out, s_size, device):
+    """Arguments of ``nao_gen_eig``: H complex128 [nprob][n][n], S complex128 [nS][n][n], s_of_prob
+    int32 [nprob] (or None: nS == nprob), 1 <= nb <= n, out = (eps float64 [nprob][n], C
+    complex128 [nprob][n][nb] or None, m_kept int32 [nprob], status int32 [nprob]) or None,
+    s_size int32 [nS] or None."""
+    _check_tensor("H", H, torch.complex128, (None, None, None), device)
+    nprob, n, n2 = H.shape
+    if n != n2:
+        raise ValueError(f"H must hold square matrices, not {n} x {n2}")
+    _check_tensor("S", S, torch.complex128, (None, n, n), device)
+    nS = S.shape[0]
+    if s_of_prob is None:
+        if nS != nprob:
+            raise ValueError("S must have one matrix per problem unless s_of_prob is given")
+    else:
+        _check_tensor("s_of_prob", s_of_prob, torch.int32, (nprob,), device)
+    if not 1 <= nb <= n:
+        raise ValueError(f"nb must lie in [1, {n}], not {nb}")
+    if s_size is not None:
+        _check_tensor("s_size", s_size, torch.int32, (nS,), device)
+    if out is not None:
+        eps, C, m, st = out
+        _check_tensor("eps", eps, torch.float64, (nprob, n), device)
+        if C is not None:
+            _check_tensor("C", C, torch.complex128, (nprob, n, nb), device)
+        _check_tensor("m_kept", m, torch.int32, (nprob,), device)
+        _check_tensor("status", st, torch.int32, (nprob,), device)
+
+
+def check_density_matrix_args(wk, kpts, eps, C, m_kept, R, nspin, out, edm, device):
+    """Arguments of ``nao_density_matrix``: C complex128 [nprob][n][nb] with nprob = nspin nk,
+    wk float64 [nk], kpts float64 [nk][3], eps float64 [nprob][n], m_kept int32 [nprob], R int32
+    [nR][3], out = (mu [1], eband [1], f [nprob][n] or None, rho [nspin][nR][n][n], all float64,
+    status int32 [1]) or None, edm float64 [nspin][nR][n][n] or None."""
+    _check_tensor("C", C, torch.complex128, (None, None, None), device)
+    nprob, n, nb = C.shape
+    _check_tensor("wk", wk, torch.float64, (None,), device)
+    nk = wk.shape[0]
+    if nprob != int(nspin) * nk:
+        raise ValueError(f"C has {nprob} problems, expected nspin * nk = {int(nspin) * nk}")
+    _check_tensor("kpts", kpts, torch.float64, (nk, 3), device)
+    _check_tensor("eps", eps, torch.float64, (nprob, n), device)
+    _check_tensor("m_kept", m_kept, torch.int32, (nprob,), device)
+    _check_tensor("R", R, torch.int32, (None, 3), device)
+    nR = R.shape[0]
+    if out is not None:
+        mu, eb, f, rho, st = out
+        _check_tensor("mu", mu, torch.float64, (1,), device)
+        _check_tensor("eband", eb, torch.float64, (1,), device)
+        if f is not None:
+            _check_tensor("f", f, torch.float64, (nprob, n), device)
+        _check_tensor("rho", rho, torch.float64, (int(nspin), nR, n, n), device)
+        _check_tensor("status", st, torch.int32, (1,), device)
+    if edm is not None:
+        _check_tensor("edm", edm, torch.float64, (int(nspin), nR, n, n), device)
+
+
+def check_zgemm_args(A, B, C, transA, transB, device):
+    """Arguments of ``nao_zgemm``: A, B, C complex128 [nprob][..][..] with op(A) M x K, op(B)
+    K x N and C [nprob][M][N] (or None)."""
+    _check_tensor("A", A, torch.complex128, (None, None, None), device)
+    nprob = A.shape[0]
+    _check_tensor("B", B, torch.complex128, (nprob, None, None), device)
+    M, K = (A.shape[2], A.shape[1]) if transA else (A.shape[1], A.shape[2])
+    KB, N = (B.shape[2], B.shape[1]) if transB else (B.shape[1], B.shape[2])
+    if K != KB:
+        raise ValueError(f"op(A) has {K} columns but op(B) has {KB} rows")
+    if C is not None:
+        _check_tensor("C", C, torch.complex128, (nprob, M, N), device)
+
+
 def _stream(stream):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
@@ -191,6 +292,7 @@ class Context:
         if rc != NAO_OK:
             raise NaoError(f"nao_init failed ({rc}): {self.lib.nao_last_error(None).decode()}")
         self.device = device
+        self._dev = torch.device("cuda", int(device))
 
     def nao_get_config(self) -> dict:
         c = NaoConfig()
@@ -235,6 +337,7 @@ class Context:
 
     def nao_zgemm(self, A, B, C=None, alpha=1.0, beta=0.0, transA=0, transB=0, method=NAO_GEMM_TC, stream=None):
         """Batched C[p] = alpha op(A[p]) op(B[p]) + beta C[p] (complex128, row-major, 3-d tensors)."""
+        check_zgemm_args(A, B, C, transA, transB, self._dev)
         nprob = A.shape[0]
         M = A.shape[2] if transA else A.shape[1]
         K = A.shape[1] if transA else A.shape[2]
@@ -269,6 +372,7 @@ class Context:
     # ------------------------------------------------------------------ Part 1
     def nao_bloch_sum(self, MR, R, kpts, out=None, stream=None):
         """MR float64 [nmat][nR][n][n], R int32 [nR][3], kpts float64 [nk][3] -> complex128 [nmat][nk][n][n]."""
+        check_bloch_sum_args(MR, R, kpts, out, self._dev)
         nmat, nR, n, _ = MR.shape
         nk = kpts.shape[0]
         if out is None:
@@ -284,9 +388,10 @@ class Context:
         """H complex128 [nprob][n][n], S complex128 [nS][n][n] -> (eps, C, m_kept, status).
         s_size (int32 [nS] on the device, optional): each S matrix's order when the matrices
         are padded to n (nao_gen_eig_sized)."""
+        nb = H.shape[1] if nb is None else int(nb)
+        check_gen_eig_args(H, S, s_of_prob, nb, out, s_size, self._dev)
         nprob, n, _ = H.shape
         nS = S.shape[0]
-        nb = n if nb is None else int(nb)
         dev = H.device
         if out is None:
             eps = torch.empty((nprob, n), dtype=torch.float64, device=dev)
@@ -295,11 +400,6 @@ class Context:
             st = torch.empty(nprob, dtype=torch.int32, device=dev)
         else:
             eps, C, m, st = out
-        if s_of_prob is None and nS != nprob:
-            raise ValueError("S must have one matrix per problem unless s_of_prob is given")
-        if s_size is not None:
-            if s_size.dtype != torch.int32 or tuple(s_size.shape) != (nS,) or s_size.device != dev:
-                raise ValueError(f"s_size must be int32 [{nS}] on {dev}")
         rc = self.lib.nao_gen_eig_sized(self.handle, n, nprob, _ptr(H), _ptr(S), _ptr(s_of_prob), nS, _ptr(s_size),
                                         float(s_cut), int(precision), nb, _ptr(eps), _ptr(C), _ptr(m), _ptr(st),
                                         _stream(stream))
@@ -380,6 +480,7 @@ class Context:
         """-> (mu [1], eband [1], f [nprob][n] or None, rho [nspin][nR][n][n], status [1]).
         ``edm``: a float64 [nspin][nR][n][n] device tensor that receives the energy density
         matrix (Part 6's second output), or None."""
+        check_density_matrix_args(wk, kpts, eps, C, m_kept, R, nspin, out, edm, self._dev)
         nprob, n, nb = C.shape
         nk = wk.shape[0]
         nR = R.shape[0]
