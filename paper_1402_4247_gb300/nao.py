@@ -246,6 +246,20 @@ def check_density_matrix_args(wk, kpts, eps, C, m_kept, R, nspin, out, edm, devi
         _check_tensor("edm", edm, torch.float64, (int(nspin), nR, n, n), device)
 
 
+def check_serve_request_args(HR, SR, R, kpts, wk, device):
+    """Arguments of ``nao_serve_submit``: HR float64 [nspin][nR][n][n], SR float64 [nR][n][n], R
+    int32 [nR][3], kpts float64 [nk][3], wk float64 [nk], all on the host or all on ``device``."""
+    where = HR.device if isinstance(HR, torch.Tensor) and HR.device.type == "cpu" else device
+    _check_tensor("HR", HR, torch.float64, (None, None, None, None), where)
+    nspin, nR, n, n2 = HR.shape
+    if n != n2:
+        raise ValueError(f"HR must hold square matrices, not {n} x {n2}")
+    _check_tensor("SR", SR, torch.float64, (nR, n, n), where)
+    _check_tensor("R", R, torch.int32, (nR, 3), where)
+    _check_tensor("kpts", kpts, torch.float64, (None, 3), where)
+    _check_tensor("wk", wk, torch.float64, (kpts.shape[0],), where)
+
+
 def check_zgemm_args(A, B, C, transA, transB, device):
     """Arguments of ``nao_zgemm``: A, B, C complex128 [nprob][..][..] with op(A) M x K, op(B)
     K x N and C [nprob][M][N] (or None)."""
@@ -425,9 +439,7 @@ class Context:
         """Queue one band step.  HR float64 [nspin][nR][n][n], SR [nR][n][n], R int32 [nR][3],
         kpts [nk][3], wk [nk]: contiguous torch tensors on the host or the device (copied
         before the call returns).  Returns the ticket."""
-        for t in (HR, SR, R, kpts, wk):
-            if not t.is_contiguous():
-                raise ValueError("expected contiguous tensors")
+        check_serve_request_args(HR, SR, R, kpts, wk, self._dev)
         nspin, nR, n, _ = HR.shape
         q = NaoRequest(n=n, nspin=nspin, nk=kpts.shape[0], nR=nR, HR=HR.data_ptr(), SR=SR.data_ptr(),
                        R=R.data_ptr(), kpts=kpts.data_ptr(), wk=wk.data_ptr(), n_electrons=float(n_electrons),

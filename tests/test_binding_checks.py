@@ -8,7 +8,7 @@ torch = pytest.importorskip("torch")
 
 from paper_1402_4247_gb300 import synth  # noqa: E402
 from paper_1402_4247_gb300.nao import (check_bloch_sum_args, check_density_matrix_args,  # noqa: E402
-                                       check_gen_eig_args, check_zgemm_args)
+                                       check_gen_eig_args, check_serve_request_args, check_zgemm_args)
 
 CPU = torch.device("cpu")
 C128, F64, I32 = torch.complex128, torch.float64, torch.int32
@@ -135,3 +135,23 @@ def test_zgemm_shapes(tA, tB):
         check_zgemm_args(A, B, torch.zeros((2, N, M), dtype=C128), tA, tB, CPU)
     with pytest.raises(ValueError):   # batch sizes differ
         check_zgemm_args(A, B[:1].contiguous(), None, tA, tB, CPU)
+
+
+def test_serve_request_shapes():
+    inp, t = _step_tensors()
+    SR = t["SR"][0]
+    META = torch.device("meta")
+    # host tensors are accepted whatever the context's device
+    check_serve_request_args(t["HR"], SR, t["R"], t["k"], t["w"], META)
+    check_serve_request_args(t["HR"][:1].contiguous(), SR, t["R"], t["k"], t["w"], META)
+    # device tensors must all be on the context's device
+    on = {k: v.to("meta") for k, v in dict(HR=t["HR"], SR=SR, R=t["R"], k=t["k"], w=t["w"]).items()}
+    check_serve_request_args(on["HR"], on["SR"], on["R"], on["k"], on["w"], META)
+    for args in ((t["HR"], t["SR"], t["R"], t["k"], t["w"]),                    # S(R) with a spin axis
+                 (t["HR"][0], SR, t["R"], t["k"], t["w"]),                      # H(R) without one
+                 (t["HR"], SR, t["R"].long(), t["k"], t["w"]),
+                 (t["HR"], SR, t["R"], t["k"], t["w"][:-1].contiguous()),       # one weight short
+                 (t["HR"], SR.float(), t["R"], t["k"], t["w"]),
+                 (t["HR"], on["SR"], t["R"], t["k"], t["w"])):                   # host and device mixed
+        with pytest.raises(ValueError):
+            check_serve_request_args(*args, META)
