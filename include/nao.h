@@ -179,7 +179,10 @@ int nao_bloch_sum(nao_ctx* ctx, int n, int nR, const int32_t* R, int nmat, const
  *   H         complex128 [nprob][n][n] Hermitian (lower triangle read)
  *   S         complex128 [nS][n][n] Hermitian positive semi-definite (lower triangle read)
  *   s_of_prob int32 [nprob]: index of the S matrix of each problem, or NULL for the
- *             identity map (then nS = nprob).  Each distinct S is reduced once.
+ *             identity map (then nS = nprob).  Each distinct S is reduced once.  The
+ *             entries must lie in [0, nS): they live on the device and are not checked
+ *             (that would cost a device-to-host read per call); an entry outside the range
+ *             makes the kernels read outside S and the workspace.
  *   nS        number of S matrices (ignored when s_of_prob is NULL)
  *   s_cut     absolute cutoff on the eigenvalues of S (e.g. 1e-10)
  *   precision NAO_FP64: every product FP64-accurate (ten-digit tensor-core products, or

@@ -400,6 +400,8 @@ class Context:
     def nao_gen_eig(self, H, S, s_of_prob=None, s_cut=1e-10, nb=None, precision=NAO_FP64, want_vectors=True,
                     out=None, stream=None, s_size=None):
         """H complex128 [nprob][n][n], S complex128 [nS][n][n] -> (eps, C, m_kept, status).
+        s_of_prob (int32 [nprob] on the device, optional): the S matrix of each problem; its
+        entries must lie in [0, nS) (not checked: they are device data).
         s_size (int32 [nS] on the device, optional): each S matrix's order when the matrices
         are padded to n (nao_gen_eig_sized)."""
         nb = H.shape[1] if nb is None else int(nb)
